@@ -54,6 +54,8 @@
  *        after a 1, the bits of coefficients s, s+1, ... up to and
  *        including the first set one, s moving past it.
  *     raw block: 1, 1, then the V float bit patterns (32 bits each).
+ *     A coded block whose stream would be longer than its raw form
+ *     (2 + 32 V bits) is stored raw, so no block exceeds 2 + 32 V bits.
  *     Bits are written LSB first into 32-bit words.
  *  Decoding: planes below pbot are zero; inverse negabinary, order and
  *  lifting; x_hat = float(i_hat) * 2^(Emax-23).
@@ -315,34 +317,43 @@ static int encode_block(const cgeom* G, const int* perm, const float* v, float t
             if (ok) { pbot = p; break; }
         }
     }
-    put_bit(B, 1);
-    if (pbot < 0) {                             /* raw block */
-        put_bit(B, 1);
-        for (int i = 0; i < V; ++i) put_bits(B, bits_of_f(v[i]), 32);
-        return (int)(B->pos - start);
-    }
-    put_bit(B, 0);
-    put_bits(B, (uint32_t)(emax + 127), 8);
-    put_bits(B, (uint32_t)ptop, 5);
-    put_bits(B, (uint32_t)pbot, 5);
-    int s = 0;
-    for (int p = ptop; p >= pbot; --p) {
-        uint32_t plane[64];
-        for (int r = 0; r < V; ++r) plane[r] = (nb[r] >> p) & 1u;
-        for (int r = 0; r < s; ++r) put_bit(B, plane[r]);
-        while (s < V) {
-            uint32_t any = 0;
-            for (int r = s; r < V; ++r) any |= plane[r];
-            put_bit(B, any);
-            if (!any) break;
-            for (;;) {
-                uint32_t bit = plane[s];
-                put_bit(B, bit);
-                ++s;
-                if (bit) break;
+    const int raw_bits = 2 + 32 * V;
+    if (pbot >= 0) {
+        /* the coded stream, built aside and kept if not longer than raw */
+        uint32_t tmp[160];
+        memset(tmp, 0, sizeof(tmp));
+        bitw C = {tmp, 160 * 32, 0, 0};
+        put_bit(&C, 1);
+        put_bit(&C, 0);
+        put_bits(&C, (uint32_t)(emax + 127), 8);
+        put_bits(&C, (uint32_t)ptop, 5);
+        put_bits(&C, (uint32_t)pbot, 5);
+        int s = 0;
+        for (int p = ptop; p >= pbot; --p) {
+            uint32_t plane[64];
+            for (int r = 0; r < V; ++r) plane[r] = (nb[r] >> p) & 1u;
+            for (int r = 0; r < s; ++r) put_bit(&C, plane[r]);
+            while (s < V) {
+                uint32_t any = 0;
+                for (int r = s; r < V; ++r) any |= plane[r];
+                put_bit(&C, any);
+                if (!any) break;
+                for (;;) {
+                    uint32_t bit = plane[s];
+                    put_bit(&C, bit);
+                    ++s;
+                    if (bit) break;
+                }
             }
         }
+        if (C.pos <= raw_bits) {
+            for (long k = 0; k < C.pos; ++k) put_bit(B, (tmp[k >> 5] >> (k & 31)) & 1u);
+            return (int)(B->pos - start);
+        }
     }
+    put_bit(B, 1);                              /* raw block */
+    put_bit(B, 1);
+    for (int i = 0; i < V; ++i) put_bits(B, bits_of_f(v[i]), 32);
     return (int)(B->pos - start);
 }
 

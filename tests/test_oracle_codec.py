@@ -210,3 +210,19 @@ def test_invalid_tolerance_rejected():
         C.compress(np.ones((4, 4), np.float32), 0.0)
     with pytest.raises(ValueError):
         C.compress(np.ones((4, 4), np.float32), 2.0 ** -95)
+
+
+def test_coded_stream_never_longer_than_raw():
+    # a checkerboard of near-maximal values plus noise: the lifting grows the
+    # highest-sequency coefficient to ~2^30, so with a tight tolerance the
+    # coded form would need ~32 planes of 64 bits -- the block is stored raw
+    rng = np.random.default_rng(12)
+    z, y, x = np.meshgrid(*[np.arange(8)] * 3, indexing="ij")
+    cb = np.where((z + y + x) % 2 == 0, 1.99, -1.99)
+    xf = (cb + 1e-3 * rng.standard_normal(cb.shape)).astype(np.float32)
+    st, _ = C.compress(xf, 4.0 * 2.0 ** -23)
+    stats = C.block_stats(st, xf.shape)
+    assert np.all(stats[:, 0] <= 2 + 32 * 64)
+    assert np.any(stats[:, 1] == 2)
+    y_ = C.decompress(st, xf.shape)
+    assert np.all(np.abs(y_.astype(np.float64) - xf) <= 4.0 * 2.0 ** -23)

@@ -1,0 +1,212 @@
+/*
+ * ckfwi — checkpointed, compressed adjoint-state gradients of acoustic
+ * seismic inversion on one GB300 (sm_103a).
+ *
+ * Method: Kukreja, Hueckelheim, Louboutin, Hovland, Gorman, "Combining
+ * checkpointing and data compression to accelerate adjoint-based
+ * optimization problems" (arXiv 1810.05268).
+ *   Sec. 6, Eq. "eqn:wave":  m u_tt - lap(u) = q, m = 1/c^2; the misfit
+ *     phi = 1/2 ||d_sim - d_obs||^2 and its gradient by the adjoint-state
+ *     method with the OT2 (2nd order in time) kernel.
+ *   Sec. 3, Eq. "eqn:recompute":  Revolve binomial checkpointing with M
+ *     slots; checkpoints copied between working and checkpoint memory.
+ *   Sec. 2.2 and Sec. 4:  checkpoints stored compressed (typecast or a
+ *     fixed-tolerance lossy codec), giving F times more slots at equal memory.
+ *
+ * Discretisation (the paper leaves it to its DSL; this library fixes it):
+ *   a u^{n+1} = 2 u^n - b u^{n-1} + w (lap_h u^n + Q^T s^n), n = 0..N-1,
+ *   u^0 = u^-1 = 0, w = dt^2 c^2, a = 1 + eta dt/2, b = 1 - eta dt/2, with
+ *   lap_h the 2k-th order central Laplacian (k = space_order/2, zero values
+ *   outside the total grid) and eta the damping rate of the absorbing layer,
+ *   sum over axes of eta_max (delta/L)^2, L = nbl h,
+ *   eta_max = 3 vmax_damp/(2L) ln(1/R), R = 1e-3.
+ *   Sources and receivers use multilinear weights over the 2^d surrounding
+ *   grid points; d^n = P u^n for n = 0..N (d^0 = 0); the misfit sums
+ *   n = 1..N.  The adjoint is the exact transpose of this recursion; the
+ *   gradient is dphi/dm = sum_{n=0}^{N-1} lam^n (lap_h u^n + Q^T s^n) c^2.
+ *
+ * Units: lengths in m, times in ms, velocities in km/s (= m/ms), m = 1/c^2.
+ *
+ * Arrays: velocity, slowness and gradient fields cover the total grid
+ * (interior + damping layer), dense, [nz][ny][nx] with x fastest (2D:
+ * [nz][nx]).  Trace arrays are [nt+1][nrec].  A `mem` argument says where a
+ * caller buffer lives: CKFWI_HOST (pageable or pinned host memory; the call
+ * copies through its own device buffers and synchronises the stream) or
+ * CKFWI_DEVICE (device memory on the current device; the call is
+ * asynchronous on `stream` except where noted).  The caller owns every
+ * buffer it passes; the model owns its working fields, checkpoint pool and
+ * maps, all released by ckfwi_free.  `stream` is a cudaStream_t (NULL = the
+ * legacy default stream).
+ *
+ * Errors: every int-returning function returns CKFWI_OK (0) or a negative
+ * status below; outputs are unspecified after an error; nothing aborts and
+ * no C++ exception crosses this boundary.  A model is used by one host
+ * thread at a time.
+ */
+#ifndef CKFWI_H
+#define CKFWI_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define CKFWI_API __attribute__((visibility("default")))
+#else
+#define CKFWI_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define CKFWI_OK 0
+#define CKFWI_EINVAL -1         /* bad argument, geometry or size */
+#define CKFWI_ENOMEM -2         /* device or host allocation failed */
+#define CKFWI_POOL_OVERFLOW -3  /* compressed checkpoints exceeded the pool */
+#define CKFWI_NONFINITE -4      /* NaN/Inf met, or FP16 checkpoint overflow */
+#define CKFWI_CORRUPT -5        /* compressed stream failed its checks */
+#define CKFWI_TIMEOUT -6        /* reserved: a bounded device wait gave up */
+#define CKFWI_ECUDA -7          /* a CUDA runtime call failed */
+
+#define CKFWI_HOST 0
+#define CKFWI_DEVICE 1
+
+/* checkpoint storage (Sec. 2: a typecast is a lossy compressor of ratio 2;
+ * CODEC is the fixed-tolerance block codec, Sec. 2.2) */
+#define CKFWI_STORE_FP32 0
+#define CKFWI_STORE_BF16 1
+#define CKFWI_STORE_FP16 2
+#define CKFWI_STORE_CODEC 3
+
+/* model parameterisation of set_model / of the gradient */
+#define CKFWI_VELOCITY 0   /* c [km/s]; gradient dphi/dc */
+#define CKFWI_SLOWNESS2 1  /* m = 1/c^2 [ms^2/m^2]; gradient dphi/dm */
+
+typedef struct ckfwi_grid {
+    int dims;            /* 2 or 3 */
+    int n[3];            /* total grid incl. damping layer: nz, ny, nx (ny = 1 in 2D) */
+    int nbl;             /* damping-layer width [cells] on every face, >= 0 */
+    double h;            /* grid spacing [m] */
+    int space_order;     /* 2, 4, 8 or 16 */
+    double dt;           /* time step [ms] */
+    int nt;              /* number of time steps N >= 1 */
+    double vmax_damp;    /* largest velocity the model will hold [km/s]: sets the
+                            damping strength and the stability check */
+} ckfwi_grid;
+
+typedef struct ckfwi_shot {
+    double src[3];       /* source position (z, y, x) [m] from the first interior
+                            point; 2D ignores y */
+    double f0;           /* Ricker peak frequency [kHz] */
+    double t0;           /* Ricker delay [ms]; <= 0 selects 1.5/f0 */
+    double amp;          /* Ricker amplitude */
+    const float* wavelet;/* optional host array [nt]: source time function used
+                            instead of the Ricker wavelet */
+    int nrec;            /* number of receivers >= 1 */
+    const double* rec;   /* host [nrec][3] receiver positions (z, y, x) [m] */
+} ckfwi_shot;
+
+typedef struct ckfwi_grad_opts {
+    int ckpt_slots;      /* M: checkpoint slots incl. the initial state, >= 1;
+                            M >= nt selects store-all (every state kept) */
+    int store_mode;      /* CKFWI_STORE_* */
+    double tol;          /* CODEC: absolute point-wise bound (> 0, >= 2^-90) */
+    size_t pool_bytes;   /* CODEC: byte budget of the checkpoint pool;
+                            0 = (M-1) uncompressed states */
+    int grad_kind;       /* CKFWI_VELOCITY or CKFWI_SLOWNESS2 */
+    int use_graph;       /* 1: record the gradient as a CUDA graph on the first
+                            call with this configuration and replay it after */
+} ckfwi_grad_opts;
+
+typedef struct ckfwi_stats {
+    long long fwd_steps;     /* forward (advance) steps, incl. the extra step to N */
+    long long adj_steps;     /* reverse steps (= nt) */
+    long long p;             /* Revolve advance count p(N, M) */
+    long long takeshots;     /* W */
+    long long restores;      /* R */
+    long long kernel_launches;
+    double pool_bytes_peak;  /* device bytes of checkpoint storage in use, peak */
+    double ratio_min;        /* CODEC: smallest and mean compression ratio */
+    double ratio_mean;
+    double u_absmax;         /* max |u| over the stored checkpoints (CODEC) */
+} ckfwi_stats;
+
+typedef struct ckfwi_model ckfwi_model;
+
+/* Allocate a model for grid g on the current device (working fields, maps,
+ * coefficient buffers).  Sec. 6 (Eq. "eqn:wave").  *out receives the handle.
+ * EINVAL for an unsupported order, a non-positive size, a damping layer
+ * wider than half the grid, or vmax_damp dt / h beyond the leapfrog stability
+ * limit of the stencil; ENOMEM if device memory runs out. */
+CKFWI_API int ckfwi_create_model(const ckfwi_grid* g, ckfwi_model** out);
+
+/* Set the medium: data is c [km/s] (kind CKFWI_VELOCITY) or m = 1/c^2
+ * (CKFWI_SLOWNESS2) on the total grid, float32, dense.  Builds the
+ * per-point coefficient w = dt^2 c^2 (Sec. 6: m = 1/c^2).  Synchronous.
+ * EINVAL for a non-positive or non-finite value (NONFINITE for NaN/Inf). */
+CKFWI_API int ckfwi_set_model(ckfwi_model* m, const float* data, int kind, int mem, void* stream);
+
+/* Forward modelling of one shot (Sec. 6, the forward problem): writes
+ * d_sim [nt+1][nrec] float32 (row 0 = P u^0 = 0).  EINVAL for a source or
+ * receiver outside the grid or nrec < 1. */
+CKFWI_API int ckfwi_forward_shot(ckfwi_model* m, const ckfwi_shot* s, float* d_sim, int mem, void* stream);
+
+/* Misfit and adjoint-state gradient of one shot (Sec. 6), with Revolve
+ * checkpointing of M slots (Sec. 3) and optionally compressed checkpoints
+ * (Sec. 4).  d_obs [nt+1][nrec] float32 (row 0 ignored); grad receives the
+ * gradient on the total grid (dense float32), w.r.t. velocity or m per
+ * opts->grad_kind; *misfit (host) receives phi in FP64; stats (optional,
+ * host) receives the counters.  Synchronises the stream before returning
+ * (the misfit and error flags are read back).  POOL_OVERFLOW if compressed
+ * checkpoints outgrow pool_bytes; NONFINITE for NaN/Inf in a checkpoint;
+ * CORRUPT if a stored stream fails its checks. */
+CKFWI_API int ckfwi_adjoint_gradient(ckfwi_model* m, const ckfwi_shot* s, const float* d_obs, int mem,
+                           const ckfwi_grad_opts* opts, double* misfit, float* grad,
+                           ckfwi_stats* stats, void* stream);
+
+/* Several shots on one model, one Revolve schedule shared by all of them,
+ * every forward / reverse action one persistent launch over all shots'
+ * tiles (Sec. 1.2: shots are independent and their gradients are summed).
+ * d_obs: nshots arrays [nt+1][nrec_s]; misfit_sum (host, FP64) and grad_sum
+ * (dense float64 total grid, same `mem`) receive the sums over shots in
+ * shot order, accumulated with compensated FP64 summation. */
+CKFWI_API int ckfwi_batch_gradient(ckfwi_model* m, const ckfwi_shot* shots, int nshots,
+                         const float* const* d_obs, int mem, const ckfwi_grad_opts* opts,
+                         double* misfit_sum, double* grad_sum, ckfwi_stats* stats,
+                         void* stream);
+
+CKFWI_API void ckfwi_free(ckfwi_model* m);
+
+CKFWI_API const char* ckfwi_error_string(int status);
+
+/* The Revolve schedule for (nt, slots) (Sec. 3, Eq. "eqn:recompute", split
+ * at the smallest minimiser), as int32 triples (op, a, b):
+ * 0 = advance(from state a, b steps), 1 = takeshot(state a, slot b),
+ * 2 = restore(state a, slot b), 3 = youturn(state a).  Host only; writes at
+ * most cap triples, *n_triples receives the full count, counts (optional)
+ * receives {p, W, R}.  EINVAL if cap is too small (n_triples still set). */
+CKFWI_API int ckfwi_revolve_schedule(int nt, int slots, int32_t* actions, long long cap,
+                           long long* n_triples, long long* counts);
+
+/* Fixed-accuracy block codec on dense device fields (Sec. 2.2: ZFP's
+ * fixed-tolerance mode is the lossy compressor the paper uses; this codec
+ * is a member of the same family, specified in codec.cu).
+ * ckfwi_codec_bound_words: words a stream of that shape can need.
+ * ckfwi_codec_compress: x (device, float32 dense [nz][ny][nx]) -> out
+ *   (device uint32, cap words); *used_words (host) receives the stream
+ *   length; *flags (host) bit0 = NONFINITE.  Synchronous.  Uses scratch
+ *   memory the library allocates and keeps per device.
+ * ckfwi_codec_decompress: stream (device) -> x (device).  Synchronous;
+ *   CORRUPT if a check fails. */
+CKFWI_API long long ckfwi_codec_bound_words(int dims, int nz, int ny, int nx);
+CKFWI_API int ckfwi_codec_compress(const float* x, int dims, int nz, int ny, int nx, double tol,
+                         uint32_t* out, long long cap, long long* used_words, int* flags,
+                         void* stream);
+CKFWI_API int ckfwi_codec_decompress(const uint32_t* in, long long nwords, int dims, int nz, int ny,
+                           int nx, float* x, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CKFWI_H */

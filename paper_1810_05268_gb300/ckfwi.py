@@ -1,0 +1,310 @@
+"""Python binding of the ckfwi C-ABI (include/ckfwi.h): same names,
+argument marshalling only.  Every computation runs in libckfwi.so.
+
+Buffers may be torch CUDA tensors (passed as device pointers, work queued on
+torch's current stream) or numpy arrays (host memory; the library copies
+through its own device buffers).
+"""
+import ctypes
+from dataclasses import dataclass, field
+from typing import Optional
+
+import numpy as np
+
+from ._lib import GradOpts, Grid, Shot, Stats, lib
+
+OK, EINVAL, ENOMEM, POOL_OVERFLOW, NONFINITE, CORRUPT, TIMEOUT, ECUDA = 0, -1, -2, -3, -4, -5, -6, -7
+HOST, DEVICE = 0, 1
+STORE_FP32, STORE_BF16, STORE_FP16, STORE_CODEC = 0, 1, 2, 3
+VELOCITY, SLOWNESS2 = 0, 1
+STORE_NAMES = {"fp32": STORE_FP32, "bf16": STORE_BF16, "fp16": STORE_FP16, "codec": STORE_CODEC}
+
+
+class CkfwiError(RuntimeError):
+    def __init__(self, status, where):
+        self.status = status
+        super().__init__("%s: %s (%d)" % (where, error_string(status), status))
+
+
+def error_string(status):
+    return lib().ckfwi_error_string(int(status)).decode()
+
+
+def _check(st, where):
+    if st != OK:
+        raise CkfwiError(st, where)
+
+
+def _is_torch_cuda(x):
+    try:
+        import torch
+    except ImportError:
+        return False
+    return isinstance(x, torch.Tensor) and x.is_cuda
+
+
+def _stream(stream=None):
+    if stream is not None:
+        return ctypes.c_void_p(int(stream))
+    try:
+        import torch
+        if torch.cuda.is_available() and torch.cuda.is_initialized():
+            return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    except ImportError:
+        pass
+    return ctypes.c_void_p(0)
+
+
+def _buf(x, dtype):
+    """(pointer, mem) of a torch CUDA tensor or a numpy array of `dtype`."""
+    if _is_torch_cuda(x):
+        if not x.is_contiguous():
+            raise ValueError("device buffers must be contiguous")
+        return ctypes.c_void_p(x.data_ptr()), DEVICE
+    a = np.asarray(x)
+    if a.dtype != dtype or not a.flags.c_contiguous:
+        raise ValueError("host buffers must be contiguous %s" % np.dtype(dtype).name)
+    return ctypes.c_void_p(a.ctypes.data), HOST
+
+
+@dataclass
+class GridSpec:
+    dims: int
+    shape: tuple            # total grid (nz, ny, nx) or (nz, nx)
+    nbl: int
+    h: float                # [m]
+    space_order: int
+    dt: float               # [ms]
+    nt: int
+    vmax_damp: float        # [km/s]
+
+    def c(self):
+        g = Grid()
+        g.dims = self.dims
+        n = tuple(self.shape) if self.dims == 3 else (self.shape[0], 1, self.shape[1])
+        for i in range(3):
+            g.n[i] = int(n[i])
+        g.nbl, g.h, g.space_order = int(self.nbl), float(self.h), int(self.space_order)
+        g.dt, g.nt, g.vmax_damp = float(self.dt), int(self.nt), float(self.vmax_damp)
+        return g
+
+
+@dataclass
+class ShotSpec:
+    src: tuple                      # (z, y, x) [m] from the first interior point
+    rec: np.ndarray                 # [nrec][3] (z, y, x) [m]
+    f0: float = 0.010               # [kHz]
+    t0: float = 0.0                 # [ms], <= 0: 1.5/f0
+    amp: float = 1.0
+    wavelet: Optional[np.ndarray] = None   # [nt] float32 overriding the Ricker
+    _keep: list = field(default_factory=list, repr=False)
+
+    def c(self):
+        s = Shot()
+        for i in range(3):
+            s.src[i] = float(self.src[i])
+        s.f0, s.t0, s.amp = float(self.f0), float(self.t0), float(self.amp)
+        rec = np.ascontiguousarray(np.asarray(self.rec, dtype=np.float64).reshape(-1, 3))
+        s.nrec = rec.shape[0]
+        s.rec = rec.ctypes.data
+        self._keep = [rec]
+        if self.wavelet is not None:
+            w = np.ascontiguousarray(np.asarray(self.wavelet, dtype=np.float32))
+            s.wavelet = w.ctypes.data
+            self._keep.append(w)
+        else:
+            s.wavelet = None
+        return s
+
+    @property
+    def nrec(self):
+        return int(np.asarray(self.rec).reshape(-1, 3).shape[0])
+
+
+def create_model(grid: GridSpec):
+    h = ctypes.c_void_p()
+    g = grid.c()
+    _check(lib().ckfwi_create_model(ctypes.byref(g), ctypes.byref(h)), "ckfwi_create_model")
+    return h
+
+
+def set_model(model, data, kind=VELOCITY, stream=None):
+    p, mem = _buf(data, np.float32)
+    _check(lib().ckfwi_set_model(model, p, int(kind), mem, _stream(stream)), "ckfwi_set_model")
+
+
+def forward_shot(model, grid: GridSpec, shot: ShotSpec, d_sim=None, device=None, stream=None):
+    """Simulated data [nt+1][nrec] (float32)."""
+    if d_sim is None:
+        if device is None:
+            device = _default_device()
+        d_sim = _alloc((grid.nt + 1, shot.nrec), np.float32, device)
+    p, mem = _buf(d_sim, np.float32)
+    s = shot.c()
+    _check(lib().ckfwi_forward_shot(model, ctypes.byref(s), p, mem, _stream(stream)), "ckfwi_forward_shot")
+    return d_sim
+
+
+def _default_device():
+    try:
+        import torch
+        return "cuda" if torch.cuda.is_available() else None
+    except ImportError:
+        return None
+
+
+def _alloc(shape, dtype, device):
+    if device is not None:
+        import torch
+        tdt = {np.float32: torch.float32, np.float64: torch.float64}[dtype]
+        return torch.empty(shape, dtype=tdt, device=device)
+    return np.empty(shape, dtype=dtype)
+
+
+def _opts(ckpt_slots, store_mode, tol, pool_bytes, grad_kind, use_graph):
+    o = GradOpts()
+    o.ckpt_slots = int(ckpt_slots)
+    o.store_mode = STORE_NAMES.get(store_mode, store_mode) if isinstance(store_mode, str) else int(store_mode)
+    o.tol = float(tol)
+    o.pool_bytes = int(pool_bytes)
+    o.grad_kind = int(grad_kind)
+    o.use_graph = int(bool(use_graph))
+    return o
+
+
+def adjoint_gradient(model, grid: GridSpec, shot: ShotSpec, d_obs, ckpt_slots, store_mode=STORE_FP32,
+                     tol=0.0, pool_bytes=0, grad_kind=SLOWNESS2, use_graph=False, grad=None, stream=None):
+    """(misfit, gradient on the total grid, stats dict)."""
+    pd, mem = _buf(d_obs, np.float32)
+    if grad is None:
+        grad = _alloc(tuple(grid.shape), np.float32, "cuda" if mem == DEVICE else None)
+    pg, memg = _buf(grad, np.float32)
+    if memg != mem:
+        raise ValueError("d_obs and grad must both be host or both be device buffers")
+    s = shot.c()
+    o = _opts(ckpt_slots, store_mode, tol, pool_bytes, grad_kind, use_graph)
+    phi = ctypes.c_double(0.0)
+    st = Stats()
+    _check(lib().ckfwi_adjoint_gradient(model, ctypes.byref(s), pd, mem, ctypes.byref(o), ctypes.byref(phi), pg,
+                                        ctypes.byref(st), _stream(stream)), "ckfwi_adjoint_gradient")
+    return phi.value, grad, st.as_dict()
+
+
+def batch_gradient(model, grid: GridSpec, shots, d_obs_list, ckpt_slots, store_mode=STORE_FP32, tol=0.0,
+                   pool_bytes=0, grad_kind=SLOWNESS2, use_graph=False, grad_sum=None, stream=None):
+    """(sum of misfits, FP64 sum of gradients over shots, stats dict)."""
+    n = len(shots)
+    ptrs = (ctypes.c_void_p * n)()
+    mem = None
+    for i, d in enumerate(d_obs_list):
+        p, m = _buf(d, np.float32)
+        ptrs[i] = p
+        if mem is not None and m != mem:
+            raise ValueError("mixed host / device d_obs")
+        mem = m
+    if grad_sum is None:
+        grad_sum = _alloc(tuple(grid.shape), np.float64, "cuda" if mem == DEVICE else None)
+    pg, memg = _buf(grad_sum, np.float64)
+    if memg != mem:
+        raise ValueError("d_obs and grad_sum must both be host or both be device buffers")
+    carr = (Shot * n)()
+    keep = []
+    for i, sh in enumerate(shots):
+        carr[i] = sh.c()
+        keep.append(sh._keep)
+    o = _opts(ckpt_slots, store_mode, tol, pool_bytes, grad_kind, use_graph)
+    phi = ctypes.c_double(0.0)
+    st = Stats()
+    _check(lib().ckfwi_batch_gradient(model, carr, n, ptrs, mem, ctypes.byref(o), ctypes.byref(phi), pg,
+                                      ctypes.byref(st), _stream(stream)), "ckfwi_batch_gradient")
+    return phi.value, grad_sum, st.as_dict()
+
+
+def free(model):
+    if model:
+        lib().ckfwi_free(model)
+
+
+def revolve_schedule(nt, slots):
+    """(actions int32 [n][3], (p, W, R)) of the library's Revolve schedule."""
+    n = ctypes.c_longlong(0)
+    cnt = (ctypes.c_longlong * 3)()
+    _check(lib().ckfwi_revolve_schedule(int(nt), int(slots), None, 0, ctypes.byref(n), cnt),
+           "ckfwi_revolve_schedule")
+    acts = np.zeros((n.value, 3), dtype=np.int32)
+    _check(lib().ckfwi_revolve_schedule(int(nt), int(slots), acts.ctypes.data, n.value, ctypes.byref(n), cnt),
+           "ckfwi_revolve_schedule")
+    return acts, (cnt[0], cnt[1], cnt[2])
+
+
+def codec_bound_words(dims, nz, ny, nx):
+    v = lib().ckfwi_codec_bound_words(int(dims), int(nz), int(ny), int(nx))
+    if v < 0:
+        raise CkfwiError(int(v), "ckfwi_codec_bound_words")
+    return int(v)
+
+
+def _shape3(shape):
+    return (shape[0], shape[1], shape[2]) if len(shape) == 3 else (shape[0], 1, shape[1])
+
+
+def codec_compress(x, tol, stream=None):
+    """Compress a contiguous float32 CUDA tensor; returns (int32 tensor holding the
+    uint32 stream words, nonfinite flag)."""
+    import torch
+    if not _is_torch_cuda(x) or x.dtype != torch.float32 or not x.is_contiguous():
+        raise ValueError("codec_compress needs a contiguous float32 CUDA tensor")
+    dims = x.dim()
+    nz, ny, nx = _shape3(tuple(x.shape))
+    cap = codec_bound_words(dims, nz, ny, nx)
+    out = torch.zeros(cap, dtype=torch.int32, device=x.device)
+    used = ctypes.c_longlong(0)
+    flags = ctypes.c_int(0)
+    _check(lib().ckfwi_codec_compress(ctypes.c_void_p(x.data_ptr()), dims, nz, ny, nx, float(tol),
+                                      ctypes.c_void_p(out.data_ptr()), cap, ctypes.byref(used), ctypes.byref(flags),
+                                      _stream(stream)), "ckfwi_codec_compress")
+    return out[:used.value].clone(), bool(flags.value & 1)
+
+
+def codec_decompress(stream_words, shape, stream=None):
+    import torch
+    if not _is_torch_cuda(stream_words) or not stream_words.is_contiguous():
+        raise ValueError("codec_decompress needs a contiguous CUDA tensor of stream words")
+    dims = len(shape)
+    nz, ny, nx = _shape3(tuple(shape))
+    out = torch.zeros(tuple(shape), dtype=torch.float32, device=stream_words.device)
+    _check(lib().ckfwi_codec_decompress(ctypes.c_void_p(stream_words.data_ptr()), stream_words.numel(), dims, nz,
+                                        ny, nx, ctypes.c_void_p(out.data_ptr()), _stream(stream)),
+           "ckfwi_codec_decompress")
+    return out
+
+
+class Model:
+    """Owning wrapper: create_model on construction, free on close / GC."""
+
+    def __init__(self, grid: GridSpec):
+        self.grid = grid
+        self.h = create_model(grid)
+
+    def set_model(self, data, kind=VELOCITY, stream=None):
+        set_model(self.h, data, kind, stream)
+
+    def forward_shot(self, shot, **kw):
+        return forward_shot(self.h, self.grid, shot, **kw)
+
+    def adjoint_gradient(self, shot, d_obs, ckpt_slots, **kw):
+        return adjoint_gradient(self.h, self.grid, shot, d_obs, ckpt_slots, **kw)
+
+    def batch_gradient(self, shots, d_obs_list, ckpt_slots, **kw):
+        return batch_gradient(self.h, self.grid, shots, d_obs_list, ckpt_slots, **kw)
+
+    def close(self):
+        if self.h:
+            free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

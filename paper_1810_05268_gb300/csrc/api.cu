@@ -1,0 +1,1222 @@
+// C-ABI of the ckfwi library: model set-up, forward modelling, and the
+// checkpointed (optionally compressed) adjoint-state gradient executor.
+//
+// The executor walks the Revolve action list (Sec. 3) and maps every action
+// to kernel launches on the caller's stream:
+//   advance(s, k)  k forward steps; in the first sweep each step also
+//                  samples the receivers; the step that ends on a state
+//                  about to be stored writes the checkpoint itself (fused
+//                  takeshot: FP32 writes u^{n+1} straight into the slot and
+//                  copies u^n beside it, BF16 / FP16 write both casts)
+//   takeshot(s)    fused as above, or two codec compressions (Sec. 4)
+//   restore(s)     FP32: the slot becomes the current state (no copy);
+//                  BF16 / FP16 / codec: up-cast or decode into working
+//                  fields -- only u^s when the next action is a reverse step
+//   youturn(s)     one fused reverse step (adjoint + imaging condition)
+// Before the first reverse step the state N-1 is advanced once more to
+// record d^{N-1} and d^N, and the residual and FP64 misfit are formed on the
+// device.  Nothing synchronises with the host until the gradient is done.
+// With M >= N every state is kept instead (store-all): the forward sweep
+// writes u^{n+1} straight into the trajectory.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <new>
+#include <tuple>
+#include <vector>
+
+#include "../../include/ckfwi.h"
+#include "internal.h"
+#include "revolve.h"
+
+using namespace ckfwi;
+
+namespace {
+
+#define CK_TRY(expr)                                   \
+    do {                                               \
+        cudaError_t e_ = (expr);                       \
+        if (e_ != cudaSuccess) return cuda_status(e_); \
+    } while (0)
+
+#define ST_TRY(expr)                 \
+    do {                             \
+        int s_ = (expr);             \
+        if (s_ != CKFWI_OK) return s_; \
+    } while (0)
+
+int cuda_status(cudaError_t e)
+{
+    if (e == cudaErrorMemoryAllocation) {
+        cudaGetLastError();
+        return CKFWI_ENOMEM;
+    }
+    return CKFWI_ECUDA;
+}
+
+struct DevMem {
+    void* p = nullptr;
+    size_t bytes = 0;
+    DevMem() = default;
+    DevMem(const DevMem&) = delete;
+    DevMem& operator=(const DevMem&) = delete;
+    ~DevMem() { release(); }
+    void release()
+    {
+        if (p) cudaFree(p);
+        p = nullptr;
+        bytes = 0;
+    }
+    // (Re)allocate when too small.  A fresh allocation is zeroed when asked
+    // (the zero halo cells of a field must hold 0 and are never written); a
+    // reused one keeps its contents.
+    cudaError_t alloc(size_t n, bool zero = true)
+    {
+        if (bytes >= n && p) return cudaSuccess;
+        release();
+        if (n == 0) return cudaSuccess;
+        cudaError_t e = cudaMalloc(&p, n);
+        if (e != cudaSuccess) {
+            p = nullptr;
+            return e;
+        }
+        bytes = n;
+        if (zero) {
+            e = cudaMemset(p, 0, n);
+            if (e == cudaSuccess) e = cudaDeviceSynchronize();
+        }
+        return e;
+    }
+    template <class T> T* as() const { return static_cast<T*>(p); }
+};
+
+// FD weights of the 2k-th order second derivative, closed form (k! )^2 ...
+void fd_weights(int k, double* c)
+{
+    double kf = 1.0;
+    for (int i = 2; i <= k; ++i) kf *= i;
+    double sum = 0.0;
+    for (int j = 1; j <= k; ++j) {
+        double a = 1.0, b = 1.0;
+        for (int i = 2; i <= k - j; ++i) a *= i;
+        for (int i = 2; i <= k + j; ++i) b *= i;
+        double cj = 2.0 * kf * kf / ((double)j * j * a * b);
+        c[j] = (j % 2 == 1) ? cj : -cj;
+        sum += c[j];
+    }
+    c[0] = -2.0 * sum;
+}
+
+// Multilinear stencil of a position [m] (from the first interior point).
+// Per axis: grid coordinate gc = nbl + pos/h must lie in [0, n-1];
+// base i0 = min(floor(gc), n-2), fraction gc - i0.
+bool interp_stencil(const ckfwi_grid& g, const double* pos, int idx3[8][3], double wt[8], int* cnt)
+{
+    const int ns[3] = {g.n[0], g.n[1], g.n[2]};
+    int i0[3] = {0, 0, 0};
+    double fr[3] = {0, 0, 0};
+    for (int a = 0; a < 3; ++a) {
+        if (a == 1 && g.dims == 2) continue;
+        const double gc = g.nbl + pos[a] / g.h;
+        if (!(gc >= 0.0) || gc > (double)(ns[a] - 1)) return false;
+        int b = (int)std::floor(gc);
+        if (b > ns[a] - 2) b = ns[a] - 2;
+        i0[a] = b;
+        fr[a] = gc - b;
+    }
+    int k = 0;
+    const int ny = g.dims == 3 ? 2 : 1;
+    for (int dz = 0; dz < 2; ++dz)
+        for (int dy = 0; dy < ny; ++dy)
+            for (int dx = 0; dx < 2; ++dx) {
+                double w = (dz ? fr[0] : 1 - fr[0]) * (dx ? fr[2] : 1 - fr[2]);
+                if (g.dims == 3) w *= dy ? fr[1] : 1 - fr[1];
+                idx3[k][0] = i0[0] + dz;
+                idx3[k][1] = g.dims == 3 ? i0[1] + dy : 0;
+                idx3[k][2] = i0[2] + dx;
+                wt[k] = w;
+                ++k;
+            }
+    *cnt = k;
+    return true;
+}
+
+// Host-built CSR gather over the bounding box of a set of weighted points.
+struct HostInj {
+    int z0 = 0, z1 = 0, y0 = 0, y1 = 0, x0 = 0, x1 = 0;
+    std::vector<int> rowptr, col;
+    std::vector<float> wt;
+};
+
+struct Entry {
+    int z, y, x, col;
+    double w;
+};
+
+HostInj build_inj(std::vector<Entry> es)
+{
+    HostInj h;
+    if (es.empty()) return h;
+    h.z0 = h.z1 = es[0].z;
+    h.y0 = h.y1 = es[0].y;
+    h.x0 = h.x1 = es[0].x;
+    for (auto& e : es) {
+        h.z0 = std::min(h.z0, e.z); h.z1 = std::max(h.z1, e.z);
+        h.y0 = std::min(h.y0, e.y); h.y1 = std::max(h.y1, e.y);
+        h.x0 = std::min(h.x0, e.x); h.x1 = std::max(h.x1, e.x);
+    }
+    h.z1 += 1; h.y1 += 1; h.x1 += 1;
+    const long long by = h.y1 - h.y0, bx = h.x1 - h.x0;
+    const long long nb = (long long)(h.z1 - h.z0) * by * bx;
+    auto key = [&](const Entry& e) { return ((long long)(e.z - h.z0) * by + (e.y - h.y0)) * bx + (e.x - h.x0); };
+    std::stable_sort(es.begin(), es.end(), [&](const Entry& a, const Entry& b) {
+        const long long ka = key(a), kb = key(b);
+        return ka != kb ? ka < kb : a.col < b.col;
+    });
+    h.rowptr.assign(nb + 1, 0);
+    for (auto& e : es) h.rowptr[key(e) + 1]++;
+    for (long long i = 0; i < nb; ++i) h.rowptr[i + 1] += h.rowptr[i];
+    for (auto& e : es) {
+        h.col.push_back(e.col);
+        h.wt.push_back((float)e.w);
+    }
+    return h;
+}
+
+struct DevInj {
+    DevMem rowptr, col, wt;
+    Inj view{};   // series filled per launch
+    int set(const HostInj& h)
+    {
+        view = Inj{};
+        if (h.rowptr.empty()) return CKFWI_OK;
+        CK_TRY(rowptr.alloc(h.rowptr.size() * sizeof(int), false));
+        CK_TRY(col.alloc(std::max<size_t>(1, h.col.size()) * sizeof(int), false));
+        CK_TRY(wt.alloc(std::max<size_t>(1, h.wt.size()) * sizeof(float), false));
+        CK_TRY(cudaMemcpy(rowptr.p, h.rowptr.data(), h.rowptr.size() * sizeof(int), cudaMemcpyHostToDevice));
+        if (!h.col.empty()) {
+            CK_TRY(cudaMemcpy(col.p, h.col.data(), h.col.size() * sizeof(int), cudaMemcpyHostToDevice));
+            CK_TRY(cudaMemcpy(wt.p, h.wt.data(), h.wt.size() * sizeof(float), cudaMemcpyHostToDevice));
+        }
+        view.on = 1;
+        view.z0 = h.z0; view.z1 = h.z1; view.y0 = h.y0; view.y1 = h.y1; view.x0 = h.x0; view.x1 = h.x1;
+        view.rowptr = rowptr.as<int>();
+        view.col = col.as<int>();
+        view.wt = wt.as<float>();
+        return CKFWI_OK;
+    }
+};
+
+// geometry of one shot on the device
+struct ShotDev {
+    int nrec = 0;
+    int nst = 0;
+    DevMem ridx, rwt, wavelet;
+    DevInj src, adj;
+    DevMem dsim, dobs, resid;
+    std::vector<unsigned char> key;    // host description the maps were built from
+};
+
+struct GraphKey {
+    int nt, M, mode, kind;
+    float tol;
+    size_t pool;
+    long long gen;      // buffer generation the graph's pointers belong to
+    bool operator<(const GraphKey& o) const
+    {
+        return std::tie(nt, M, mode, kind, tol, pool, gen) <
+               std::tie(o.nt, o.M, o.mode, o.kind, o.tol, o.pool, o.gen);
+    }
+};
+
+}  // namespace
+
+struct ckfwi_model {
+    ckfwi_grid g{};
+    FieldGeom fg{};
+    int K = 0;
+    float c[MAXK + 1] = {};
+    float hdt = 0.0f;
+    bool have_model = false;
+    DevMem eta, w, cvel, zero, uN;
+    DevMem work[3], lam[3], gacc;
+    DevMem traj;                    // store-all trajectory
+    DevMem pool;                    // checkpoint pool
+    size_t pool_cap_bytes = 0;
+    DevMem slotbase;                // codec: device word offsets of slots
+    DevMem scratch;                 // codec scratch
+    DevMem flags;                   // int error flags
+    DevMem phi, partials;
+    DevMem statw;                   // codec: words per compression
+    DevMem gsum_comp;               // batch: compensation terms
+    ShotDev shot;
+    Tile tf{}, ta{};
+    bool tuned = false;
+    int nparts = 128;
+    long long gen = 0;              // bumped whenever a buffer a graph uses moves
+    // graphs
+    std::map<GraphKey, cudaGraphExec_t> graphs;
+    ~ckfwi_model()
+    {
+        for (auto& kv : graphs) cudaGraphExecDestroy(kv.second);
+    }
+};
+
+namespace ckfwi {
+
+FieldGeom make_geom(int dims, int nz, int ny, int nx, int H)
+{
+    FieldGeom f{};
+    f.dims = dims;
+    f.nz = nz;
+    f.ny = ny;
+    f.nx = nx;
+    f.H = H;
+    f.X0 = ((H + 3) / 4) * 4;
+    if (f.X0 < 4) f.X0 = 4;
+    f.px = ((f.X0 + nx + H + 31) / 32) * 32;
+    const long long py = dims == 3 ? ny + 2LL * H : 1;
+    f.pxy = f.px * py;
+    const long long pz = nz + 2LL * H;
+    f.origin = (long long)H * f.pxy + (dims == 3 ? (long long)H * f.px : 0) + f.X0;
+    f.alloc = pz * f.pxy + 64;
+    f.npts = (long long)nz * ny * nx;
+    return f;
+}
+
+}  // namespace ckfwi
+
+namespace {
+
+float* org(const DevMem& m, const FieldGeom& g) { return m.as<float>() + g.origin; }
+
+size_t field_bytes(const FieldGeom& g, size_t elem = 4) { return (size_t)g.alloc * elem; }
+
+double eta_axis(const ckfwi_grid& g, int i, int n)
+{
+    if (g.nbl <= 0) return 0.0;
+    const double L = g.nbl * g.h;
+    const double emax = 3.0 * g.vmax_damp / (2.0 * L) * std::log(1.0 / 1e-3);
+    double delta = 0.0;
+    if (i < g.nbl) delta = (double)(g.nbl - i) * g.h;
+    else if (i > n - 1 - g.nbl) delta = (double)(i - (n - 1 - g.nbl)) * g.h;
+    const double r = delta / L;
+    return emax * r * r;
+}
+
+cudaStream_t S(void* s) { return static_cast<cudaStream_t>(s); }
+
+int check_grid(const ckfwi_grid* g)
+{
+    if (!g) return CKFWI_EINVAL;
+    if (g->dims != 2 && g->dims != 3) return CKFWI_EINVAL;
+    if (g->n[0] < 2 || g->n[2] < 2) return CKFWI_EINVAL;
+    if (g->dims == 2 && g->n[1] != 1) return CKFWI_EINVAL;
+    if (g->dims == 3 && g->n[1] < 2) return CKFWI_EINVAL;
+    const int so = g->space_order;
+    if (so != 2 && so != 4 && so != 8 && so != 16) return CKFWI_EINVAL;
+    if (!(g->h > 0) || !(g->dt > 0) || g->nt < 1 || g->nbl < 0) return CKFWI_EINVAL;
+    if (!(g->vmax_damp > 0)) return CKFWI_EINVAL;
+    if (2LL * g->nbl >= g->n[0] || 2LL * g->nbl >= g->n[2]) return CKFWI_EINVAL;
+    // leapfrog stability: (vmax dt / h)^2 * dims * |symbol at k h = pi| <= 4,
+    // the 1-D symbol of the 2k-th order second difference being -4 sum_{j odd} c_j
+    double c[MAXK + 1];
+    fd_weights(so / 2, c);
+    double sym = 0.0;
+    for (int j = 1; j <= so / 2; j += 2) sym += 4.0 * c[j];
+    const double cfl = g->vmax_damp * g->dt / g->h;
+    if (cfl * cfl * g->dims * sym > 4.0) return CKFWI_EINVAL;
+    return CKFWI_OK;
+}
+
+// ---------------------------------------------------------------- shots
+int set_shot(ckfwi_model* m, const ckfwi_shot* s)
+{
+    if (!s || s->nrec < 1 || !s->rec) return CKFWI_EINVAL;
+    const ckfwi_grid& g = m->g;
+    // cache key: the shot description
+    std::vector<unsigned char> key(sizeof(double) * 6 + sizeof(int) + sizeof(double) * 3 * s->nrec +
+                                   (s->wavelet ? sizeof(float) * g.nt : 0));
+    {
+        unsigned char* p = key.data();
+        const double hd[6] = {s->src[0], s->src[1], s->src[2], s->f0, s->t0, s->amp};
+        std::memcpy(p, hd, sizeof(hd));
+        p += sizeof(hd);
+        std::memcpy(p, &s->nrec, sizeof(int));
+        p += sizeof(int);
+        std::memcpy(p, s->rec, sizeof(double) * 3 * s->nrec);
+        p += sizeof(double) * 3 * s->nrec;
+        if (s->wavelet) std::memcpy(p, s->wavelet, sizeof(float) * g.nt);
+    }
+    if (key == m->shot.key) return CKFWI_OK;
+    ShotDev& d = m->shot;
+    d.key.clear();
+    ++m->gen;
+    const FieldGeom& f = m->fg;
+    int cnt = 0;
+    int idx3[8][3];
+    double wt[8];
+    // source
+    if (!interp_stencil(g, s->src, idx3, wt, &cnt)) return CKFWI_EINVAL;
+    std::vector<Entry> es;
+    for (int i = 0; i < cnt; ++i) es.push_back(Entry{idx3[i][0], idx3[i][1], idx3[i][2], 0, wt[i]});
+    ST_TRY(d.src.set(build_inj(es)));
+    std::vector<float> wav(g.nt);
+    if (s->wavelet) {
+        for (int n = 0; n < g.nt; ++n) {
+            if (!std::isfinite(s->wavelet[n])) return CKFWI_NONFINITE;
+            wav[n] = s->wavelet[n];
+        }
+    } else {
+        if (!(s->f0 > 0)) return CKFWI_EINVAL;
+        const double t0 = s->t0 > 0 ? s->t0 : 1.5 / s->f0;
+        const double pi = 3.14159265358979323846;
+        for (int n = 0; n < g.nt; ++n) {
+            const double t = n * g.dt - t0;
+            const double a = pi * pi * s->f0 * s->f0 * t * t;
+            wav[n] = (float)(s->amp * (1.0 - 2.0 * a) * std::exp(-a));
+        }
+    }
+    CK_TRY(d.wavelet.alloc(sizeof(float) * g.nt, false));
+    CK_TRY(cudaMemcpy(d.wavelet.p, wav.data(), sizeof(float) * g.nt, cudaMemcpyHostToDevice));
+    // receivers: sampling stencils and the adjoint-source gather (-P^T)
+    const int nst = g.dims == 3 ? 8 : 4;
+    std::vector<long long> ridx((size_t)s->nrec * nst);
+    std::vector<float> rw((size_t)s->nrec * nst);
+    es.clear();
+    for (int r = 0; r < s->nrec; ++r) {
+        if (!interp_stencil(g, s->rec + 3 * r, idx3, wt, &cnt)) return CKFWI_EINVAL;
+        for (int i = 0; i < cnt; ++i) {
+            ridx[(size_t)r * nst + i] = (long long)idx3[i][0] * f.pxy + (long long)idx3[i][1] * f.px + idx3[i][2];
+            rw[(size_t)r * nst + i] = (float)wt[i];
+            es.push_back(Entry{idx3[i][0], idx3[i][1], idx3[i][2], r, -wt[i]});
+        }
+    }
+    ST_TRY(d.adj.set(build_inj(es)));
+    CK_TRY(d.ridx.alloc(ridx.size() * sizeof(long long), false));
+    CK_TRY(d.rwt.alloc(rw.size() * sizeof(float), false));
+    CK_TRY(cudaMemcpy(d.ridx.p, ridx.data(), ridx.size() * sizeof(long long), cudaMemcpyHostToDevice));
+    CK_TRY(cudaMemcpy(d.rwt.p, rw.data(), rw.size() * sizeof(float), cudaMemcpyHostToDevice));
+    const size_t nd = (size_t)(g.nt + 1) * s->nrec;
+    CK_TRY(d.dsim.alloc(nd * sizeof(float)));
+    CK_TRY(d.dobs.alloc(nd * sizeof(float)));
+    CK_TRY(d.resid.alloc(nd * sizeof(float)));
+    d.nrec = s->nrec;
+    d.nst = nst;
+    d.key = std::move(key);
+    return CKFWI_OK;
+}
+
+// ---------------------------------------------------------------- launches
+struct Ctx {
+    ckfwi_model* m;
+    cudaStream_t st;
+    long long launches = 0;
+};
+
+FwdArgs fwd_args(ckfwi_model* m)
+{
+    FwdArgs a{};
+    a.g = m->fg;
+    a.w = org(m->w, m->fg);
+    a.eta = m->eta.as<float>();
+    a.hdt = m->hdt;
+    std::memcpy(a.c, m->c, sizeof(a.c));
+    a.err = m->flags.as<int>();
+    return a;
+}
+
+// one forward step n: u -> out; optional sampling of d^n and fused takeshot
+int fwd_step(Ctx& cx, const float* u, const float* up, float* out, int n, bool record, int ck,
+             void* ck_u, void* ck_up)
+{
+    ckfwi_model* m = cx.m;
+    FwdArgs a = fwd_args(m);
+    a.u = u;
+    a.up = up;
+    a.out = out;
+    a.src = m->shot.src.view;
+    a.src.series = m->shot.wavelet.as<float>() + n;
+    a.ck_u = ck_u;
+    a.ck_up = ck_up;
+    bool sep = false;
+    if (record) {
+        Sample sm{};
+        sm.n = m->shot.nrec;
+        sm.nst = m->shot.nst;
+        sm.idx = m->shot.ridx.as<long long>();
+        sm.wt = m->shot.rwt.as<float>();
+        sm.out = m->shot.dsim.as<float>() + (size_t)n * m->shot.nrec;
+        const long long gx = (m->fg.nx + m->tf.bx - 1) / m->tf.bx;
+        const long long gy = m->fg.dims == 3 ? (m->fg.ny + m->tf.by - 1) / m->tf.by : 1;
+        const long long gz = (m->fg.nz + m->tf.zlen - 1) / m->tf.zlen;
+        if (gx * gy * gz * m->tf.bx * m->tf.by >= sm.n) a.smp = sm;
+        else {
+            CK_TRY(launch_sample(u, sm, cx.st));
+            ++cx.launches;
+            sep = true;
+        }
+    }
+    (void)sep;
+    CK_TRY(launch_fwd(a, m->tf, m->K, ck, cx.st));
+    ++cx.launches;
+    return CKFWI_OK;
+}
+
+int adj_step(Ctx& cx, const float* l1, const float* l2, float* l0, const void* u, int utype, int j)
+{
+    ckfwi_model* m = cx.m;
+    AdjArgs a{};
+    a.g = m->fg;
+    a.l1 = l1;
+    a.l2 = l2;
+    a.l0 = l0;
+    a.u = u;
+    a.w = org(m->w, m->fg);
+    a.gacc = org(m->gacc, m->fg);
+    a.eta = m->eta.as<float>();
+    a.hdt = m->hdt;
+    std::memcpy(a.c, m->c, sizeof(a.c));
+    a.adj = m->shot.adj.view;
+    a.adj.series = m->shot.resid.as<float>() + (size_t)j * m->shot.nrec;
+    a.src = m->shot.src.view;
+    a.src.series = m->shot.wavelet.as<float>() + (j - 1);
+    CK_TRY(launch_adj(a, m->ta, m->K, utype, cx.st));
+    ++cx.launches;
+    return CKFWI_OK;
+}
+
+int sample_last(Ctx& cx, const float* uN)
+{
+    ckfwi_model* m = cx.m;
+    Sample sm{};
+    sm.n = m->shot.nrec;
+    sm.nst = m->shot.nst;
+    sm.idx = m->shot.ridx.as<long long>();
+    sm.wt = m->shot.rwt.as<float>();
+    sm.out = m->shot.dsim.as<float>() + (size_t)m->g.nt * m->shot.nrec;
+    CK_TRY(launch_sample(uN, sm, cx.st));
+    ++cx.launches;
+    return CKFWI_OK;
+}
+
+int residual(Ctx& cx)
+{
+    ckfwi_model* m = cx.m;
+    CK_TRY(launch_residual(m->shot.dsim.as<float>(), m->shot.dobs.as<float>(), m->shot.resid.as<float>(),
+                           m->g.nt + 1, m->shot.nrec, m->partials.as<double>(), m->nparts,
+                           m->phi.as<double>(), cx.st));
+    cx.launches += 2;
+    return CKFWI_OK;
+}
+
+// --------------------------------------------------------------- autotune
+int autotune(ckfwi_model* m, cudaStream_t st)
+{
+    if (m->tuned) return CKFWI_OK;
+    const FieldGeom& f = m->fg;
+    // candidate z-run lengths: whole columns, and runs giving >= 4 CTAs per SM
+    int dev = 0;
+    cudaGetDevice(&dev);
+    int nsm = 0;
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    std::vector<Tile> cands;
+    for (int i = 0; i < tile_count(f.dims); ++i) {
+        Tile t0 = tile_at(f.dims, i, f.nz);
+        const long long cols = (long long)((f.nx + t0.bx - 1) / t0.bx) * (f.dims == 3 ? (f.ny + t0.by - 1) / t0.by : 1);
+        std::vector<int> zl;
+        for (int target : {2, 4, 8, 16}) {
+            long long nzc = (target * (long long)nsm + cols - 1) / cols;
+            nzc = std::max<long long>(1, std::min<long long>(nzc, f.nz));
+            int z = (int)((f.nz + nzc - 1) / nzc);
+            z = std::max(z, 4);
+            if (std::find(zl.begin(), zl.end(), z) == zl.end()) zl.push_back(z);
+        }
+        for (int z : zl) cands.push_back(tile_at(f.dims, i, z));
+    }
+    // time the forward and the reverse kernel on the model's own buffers
+    cudaEvent_t e0, e1;
+    CK_TRY(cudaEventCreate(&e0));
+    CK_TRY(cudaEventCreate(&e1));
+    FwdArgs a = fwd_args(m);
+    a.u = org(m->work[0], f);
+    a.up = org(m->work[1], f);
+    a.out = org(m->work[2], f);
+    AdjArgs b{};
+    b.g = f;
+    b.l1 = org(m->lam[0], f);
+    b.l2 = org(m->lam[1], f);
+    b.l0 = org(m->lam[2], f);
+    b.u = org(m->work[0], f);
+    b.w = org(m->w, f);
+    b.gacc = org(m->gacc, f);
+    b.eta = m->eta.as<float>();
+    b.hdt = m->hdt;
+    std::memcpy(b.c, m->c, sizeof(b.c));
+    float best_f = 1e30f, best_a = 1e30f;
+    const int reps = 3;
+    for (const Tile& t : cands) {
+        for (int pass = 0; pass < 2; ++pass) {
+            if (pass == 0) CK_TRY(launch_fwd(a, t, m->K, CK_NONE, st));
+            else CK_TRY(launch_adj(b, t, m->K, U_FP32, st));
+            CK_TRY(cudaEventRecord(e0, st));
+            for (int r = 0; r < reps; ++r) {
+                if (pass == 0) CK_TRY(launch_fwd(a, t, m->K, CK_NONE, st));
+                else CK_TRY(launch_adj(b, t, m->K, U_FP32, st));
+            }
+            CK_TRY(cudaEventRecord(e1, st));
+            CK_TRY(cudaEventSynchronize(e1));
+            float ms = 0;
+            CK_TRY(cudaEventElapsedTime(&ms, e0, e1));
+            if (pass == 0 && ms < best_f) { best_f = ms; m->tf = t; }
+            if (pass == 1 && ms < best_a) { best_a = ms; m->ta = t; }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    // the probe runs wrote into working buffers; clear them
+    for (int i = 0; i < 3; ++i) {
+        CK_TRY(cudaMemsetAsync(m->work[i].p, 0, m->work[i].bytes, st));
+        CK_TRY(cudaMemsetAsync(m->lam[i].p, 0, m->lam[i].bytes, st));
+    }
+    CK_TRY(cudaMemsetAsync(m->gacc.p, 0, m->gacc.bytes, st));
+    CK_TRY(cudaStreamSynchronize(st));
+    m->tuned = true;
+    return CKFWI_OK;
+}
+
+int reset_flags(ckfwi_model* m, cudaStream_t st)
+{
+    CK_TRY(cudaMemsetAsync(m->flags.p, 0, m->flags.bytes, st));
+    return CKFWI_OK;
+}
+
+int read_flags(ckfwi_model* m, cudaStream_t st, int* fl)
+{
+    int h[4] = {0, 0, 0, 0};
+    CK_TRY(cudaMemcpyAsync(h, m->flags.p, sizeof(h), cudaMemcpyDeviceToHost, st));
+    CK_TRY(cudaStreamSynchronize(st));
+    // flags[0]: FP16 overflow (1); flags[1]: codec bits (1 nonfinite, 2 overflow, 4 corrupt)
+    *fl = 0;
+    if (h[1] & 2) *fl = CKFWI_POOL_OVERFLOW;
+    else if (h[1] & 4) *fl = CKFWI_CORRUPT;
+    else if ((h[0] & 1) || (h[1] & 1)) *fl = CKFWI_NONFINITE;
+    return CKFWI_OK;
+}
+
+// ------------------------------------------------------------ gradient run
+struct State {
+    const void* cur;
+    const void* prev;
+    int tcur, tprev;    // U_FP32 / U_BF16 / U_FP16
+};
+
+struct RunCfg {
+    int N, M, mode;
+    float tol_f;
+    long long cap_words;
+    bool store_all;
+};
+
+CodecView field_view(const FieldGeom& f)
+{
+    CodecView v{};
+    v.dims = f.dims;
+    v.nz = f.nz;
+    v.ny = f.ny;
+    v.nx = f.nx;
+    v.py = f.px;
+    v.pz = f.pxy;
+    v.aligned = true;
+    return v;
+}
+
+float* pick_free(ckfwi_model* m, const State& s)
+{
+    for (int i = 0; i < 3; ++i) {
+        float* p = org(m->work[i], m->fg);
+        if (p != s.cur && p != s.prev) return p;
+    }
+    return nullptr;
+}
+
+// the recorded part of a gradient: everything between "inputs staged" and
+// "outputs ready" (this is what a CUDA graph captures)
+int run_body(Ctx& cx, const RunCfg& rc, const std::vector<Action>& acts, long long* counters)
+{
+    ckfwi_model* m = cx.m;
+    const FieldGeom& f = m->fg;
+    const int N = rc.N;
+    float* zero = org(m->zero, f);
+    for (int i = 0; i < 3; ++i) {
+        CK_TRY(cudaMemsetAsync(m->lam[i].p, 0, m->lam[i].bytes, cx.st));
+    }
+    CK_TRY(cudaMemsetAsync(m->gacc.p, 0, m->gacc.bytes, cx.st));
+    CK_TRY(cudaMemsetAsync(m->shot.dsim.p, 0, m->shot.dsim.bytes, cx.st));
+    int li = 0;   // lam rotation: lam[li] = lam^{j}, lam[(li+1)%3] = lam^{j+1}
+    auto reverse = [&](int s, const void* u, int ut) -> int {
+        float* l1 = org(m->lam[li], f);
+        float* l2 = org(m->lam[(li + 1) % 3], f);
+        float* l0 = org(m->lam[(li + 2) % 3], f);
+        ST_TRY(adj_step(cx, l1, l2, l0, u, ut, s + 1));
+        li = (li + 2) % 3;   // new lam^{j} = l0, lam^{j+1} = old l1
+        return CKFWI_OK;
+    };
+    long long fsteps = 0;
+    if (rc.store_all) {
+        float* tr = m->traj.as<float>();
+        auto T = [&](int n) { return tr + (size_t)n * f.alloc + f.origin; };
+        for (int n = 0; n < N; ++n) {
+            const float* u = n == 0 ? zero : T(n);
+            const float* up = n <= 1 ? zero : T(n - 1);
+            float* out = (n + 1 < N) ? T(n + 1) : org(m->uN, f);
+            ST_TRY(fwd_step(cx, u, up, out, n, true, CK_NONE, nullptr, nullptr));
+            ++fsteps;
+        }
+        ST_TRY(sample_last(cx, org(m->uN, f)));
+        ST_TRY(residual(cx));
+        for (int s = N - 1; s >= 0; --s) ST_TRY(reverse(s, s == 0 ? zero : T(s), U_FP32));
+        counters[0] = fsteps;
+        return CKFWI_OK;
+    }
+    // Revolve
+    const size_t fb = field_bytes(f, 4), hb = field_bytes(f, 2);
+    auto slot_ptr = [&](int slot, int which) -> void* {
+        // slot >= 1; two fields per slot
+        if (rc.mode == CKFWI_STORE_FP32)
+            return m->pool.as<char>() + ((size_t)(slot - 1) * 2 + which) * fb + f.origin * 4;
+        return m->pool.as<char>() + ((size_t)(slot - 1) * 2 + which) * hb + f.origin * 2;
+    };
+    const int ut_slot = rc.mode == CKFWI_STORE_BF16 ? U_BF16 : (rc.mode == CKFWI_STORE_FP16 ? U_FP16 : U_FP32);
+    long long* sb = m->slotbase.as<long long>();     // [0..M]: slot starts, [M+1..2M]: mids
+    auto sbase = [&](int slot) { return sb + slot; };
+    auto smid = [&](int slot) { return sb + (rc.M + 1) + slot; };
+    if (rc.mode == CKFWI_STORE_CODEC) CK_TRY(cudaMemsetAsync(sb, 0, sizeof(long long) * 2, cx.st));
+    const CodecView cv = field_view(f);
+    int* cerr = m->flags.as<int>() + 1;
+    unsigned long long* sw = m->statw.as<unsigned long long>();
+    long long ncomp = 0;
+
+    State st{zero, zero, U_FP32, U_FP32};
+    bool first_sweep = true;
+    int cur_state = 0;
+    for (size_t ai = 0; ai < acts.size(); ++ai) {
+        const Action& A = acts[ai];
+        const bool next_take = ai + 1 < acts.size() && acts[ai + 1].op == ACT_TAKESHOT;
+        const bool next_turn = ai + 1 < acts.size() && acts[ai + 1].op == ACT_YOUTURN;
+        if (A.op == ACT_ADVANCE) {
+            for (int i = 0; i < A.b; ++i) {
+                const int n = A.a + i;
+                const bool last = i == A.b - 1;
+                int ck = CK_NONE;
+                void *cku = nullptr, *ckup = nullptr;
+                float* out = pick_free(m, st);
+                if (last && next_take && rc.mode != CKFWI_STORE_CODEC) {
+                    const int slot = acts[ai + 1].b;
+                    if (rc.mode == CKFWI_STORE_FP32) {
+                        out = static_cast<float*>(slot_ptr(slot, 0));
+                        ck = CK_FP32;
+                        ckup = slot_ptr(slot, 1);
+                    } else {
+                        ck = rc.mode == CKFWI_STORE_BF16 ? CK_BF16 : CK_FP16;
+                        cku = slot_ptr(slot, 0);
+                        ckup = slot_ptr(slot, 1);
+                    }
+                }
+                ST_TRY(fwd_step(cx, static_cast<const float*>(st.cur), static_cast<const float*>(st.prev), out, n,
+                                first_sweep, ck, cku, ckup));
+                ++fsteps;
+                st.prev = st.cur;
+                st.tprev = st.tcur;
+                st.cur = out;
+                st.tcur = U_FP32;
+            }
+            cur_state = A.a + A.b;
+        } else if (A.op == ACT_TAKESHOT) {
+            if (rc.mode == CKFWI_STORE_CODEC) {
+                CK_TRY(codec_compress_dev(static_cast<const float*>(st.cur), cv, rc.tol_f, m->pool.as<uint32_t>(),
+                                          sbase(A.b), rc.cap_words, smid(A.b), m->scratch.p, cerr, sw + ncomp,
+                                          cx.st));
+                ++ncomp;
+                CK_TRY(codec_compress_dev(static_cast<const float*>(st.prev), cv, rc.tol_f, m->pool.as<uint32_t>(),
+                                          smid(A.b), rc.cap_words, sbase(A.b + 1), m->scratch.p, cerr, sw + ncomp,
+                                          cx.st));
+                ++ncomp;
+                cx.launches += 6;
+            }
+        } else if (A.op == ACT_RESTORE) {
+            cur_state = A.a;
+            if (A.b == 0) {
+                st = State{zero, zero, U_FP32, U_FP32};
+            } else if (rc.mode == CKFWI_STORE_FP32) {
+                st = State{slot_ptr(A.b, 0), slot_ptr(A.b, 1), U_FP32, U_FP32};
+            } else if (rc.mode == CKFWI_STORE_CODEC) {
+                float* a0 = org(m->work[0], f);
+                float* a1 = org(m->work[1], f);
+                CK_TRY(codec_decompress_dev(m->pool.as<uint32_t>(), sbase(A.b), rc.cap_words, cv, a0, cerr, cx.st));
+                ++cx.launches;
+                if (!next_turn) {
+                    CK_TRY(codec_decompress_dev(m->pool.as<uint32_t>(), smid(A.b), rc.cap_words, cv, a1, cerr, cx.st));
+                    ++cx.launches;
+                }
+                st = State{a0, a1, U_FP32, U_FP32};
+            } else {
+                if (next_turn) {
+                    st = State{slot_ptr(A.b, 0), slot_ptr(A.b, 1), ut_slot, ut_slot};
+                } else {
+                    float* a0 = org(m->work[0], f);
+                    float* a1 = org(m->work[1], f);
+                    CK_TRY(launch_cast_restore(slot_ptr(A.b, 0), ut_slot, f, a0, cx.st));
+                    CK_TRY(launch_cast_restore(slot_ptr(A.b, 1), ut_slot, f, a1, cx.st));
+                    cx.launches += 2;
+                    st = State{a0, a1, U_FP32, U_FP32};
+                }
+            }
+        } else if (A.op == ACT_YOUTURN) {
+            if (first_sweep) {
+                // extra step N-1 -> N records d^{N-1}; d^N from u^N
+                ST_TRY(fwd_step(cx, static_cast<const float*>(st.cur), static_cast<const float*>(st.prev),
+                                org(m->uN, f), N - 1, true, CK_NONE, nullptr, nullptr));
+                ++fsteps;
+                ST_TRY(sample_last(cx, org(m->uN, f)));
+                ST_TRY(residual(cx));
+                first_sweep = false;
+            }
+            (void)cur_state;
+            ST_TRY(reverse(A.a, st.cur, st.tcur));
+        }
+    }
+    counters[0] = fsteps;
+    counters[1] = ncomp;
+    return CKFWI_OK;
+}
+
+int prepare_storage(ckfwi_model* m, RunCfg& rc, const ckfwi_grad_opts* o, const FieldGeom& f)
+{
+    const void* before[5] = {m->traj.p, m->pool.p, m->slotbase.p, m->scratch.p, m->statw.p};
+    struct Bump {
+        ckfwi_model* m;
+        const void* const* b;
+        ~Bump()
+        {
+            const void* after[5] = {m->traj.p, m->pool.p, m->slotbase.p, m->scratch.p, m->statw.p};
+            for (int i = 0; i < 5; ++i)
+                if (after[i] != b[i]) ++m->gen;
+        }
+    } bump{m, before};
+    if (rc.store_all) {
+        CK_TRY(m->traj.alloc(field_bytes(f) * (size_t)rc.N));
+        return CKFWI_OK;
+    }
+    if (rc.M <= 1) return CKFWI_OK;
+    const size_t nslot = (size_t)(rc.M - 1) * 2;
+    if (rc.mode == CKFWI_STORE_FP32) {
+        CK_TRY(m->pool.alloc(nslot * field_bytes(f, 4)));
+    } else if (rc.mode == CKFWI_STORE_BF16 || rc.mode == CKFWI_STORE_FP16) {
+        CK_TRY(m->pool.alloc(nslot * field_bytes(f, 2)));
+    } else {
+        size_t bytes = o->pool_bytes ? o->pool_bytes : (size_t)(rc.M - 1) * 2 * f.npts * 4;
+        bytes = (bytes + 3) / 4 * 4;
+        CK_TRY(m->pool.alloc(bytes, false));
+        rc.cap_words = (long long)(bytes / 4);
+        CK_TRY(m->slotbase.alloc(sizeof(long long) * (2 * (size_t)rc.M + 4)));
+        CK_TRY(m->scratch.alloc((size_t)codec_scratch_bytes(f.dims, f.nz, f.ny, f.nx), false));
+        CK_TRY(m->statw.alloc(sizeof(unsigned long long) * (size_t)(4 * rc.N + 8)));
+    }
+    return CKFWI_OK;
+}
+
+float tol_float(double tol)
+{
+    float t = (float)tol;
+    if ((double)t > tol) t = std::nextafter(t, 0.0f);
+    return t;
+}
+
+int gradient_one(ckfwi_model* m, const ckfwi_shot* s, const float* d_obs, int mem,
+                 const ckfwi_grad_opts* o, double* misfit, ckfwi_stats* stats, cudaStream_t st,
+                 std::vector<long long>* comp_words)
+{
+    if (!m->have_model) return CKFWI_EINVAL;
+    if (!o || !d_obs) return CKFWI_EINVAL;
+    if (o->ckpt_slots < 1) return CKFWI_EINVAL;
+    if (o->store_mode < 0 || o->store_mode > 3) return CKFWI_EINVAL;
+    if (o->grad_kind != CKFWI_VELOCITY && o->grad_kind != CKFWI_SLOWNESS2) return CKFWI_EINVAL;
+    if (o->store_mode == CKFWI_STORE_CODEC && (!(o->tol >= std::ldexp(1.0, -90)) || !std::isfinite(o->tol)))
+        return CKFWI_EINVAL;
+    ST_TRY(set_shot(m, s));
+    ST_TRY(autotune(m, st));
+    const FieldGeom& f = m->fg;
+    RunCfg rc{};
+    rc.N = m->g.nt;
+    rc.M = o->ckpt_slots;
+    rc.mode = o->store_mode;
+    rc.tol_f = rc.mode == CKFWI_STORE_CODEC ? tol_float(o->tol) : 0.0f;
+    rc.store_all = rc.M >= rc.N && rc.mode == CKFWI_STORE_FP32;
+    if (rc.M > rc.N) rc.M = rc.N;
+    ST_TRY(prepare_storage(m, rc, o, f));
+    const size_t nd = (size_t)(rc.N + 1) * m->shot.nrec;
+    CK_TRY(cudaMemcpyAsync(m->shot.dobs.p, d_obs, nd * sizeof(float),
+                           mem == CKFWI_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, st));
+    ST_TRY(reset_flags(m, st));
+    std::vector<Action> acts;
+    long long cnt[3] = {rc.N - 1, 0, 0};
+    if (!rc.store_all) revolve_schedule(rc.N, rc.M, acts, cnt);
+    Ctx cx{m, st, 0};
+    long long counters[2] = {0, 0};
+    const bool graph = o->use_graph != 0;
+    GraphKey key{rc.N, rc.M, rc.mode, o->grad_kind, rc.tol_f, (size_t)rc.cap_words, m->gen};
+    if (graph) {
+        auto it = m->graphs.find(key);
+        if (it == m->graphs.end()) {
+            cudaGraph_t gr;
+            CK_TRY(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+            const int rs = run_body(cx, rc, acts, counters);
+            cudaError_t ee = cudaStreamEndCapture(st, &gr);
+            if (rs != CKFWI_OK) {
+                if (ee == cudaSuccess) cudaGraphDestroy(gr);
+                return rs;
+            }
+            CK_TRY(ee);
+            cudaGraphExec_t ex;
+            cudaError_t ei = cudaGraphInstantiate(&ex, gr, 0);
+            cudaGraphDestroy(gr);
+            CK_TRY(ei);
+            it = m->graphs.emplace(key, ex).first;
+        } else {
+            // the same schedule: counters from a dry count
+            counters[0] = rc.store_all ? rc.N : cnt[0] + 1;
+            counters[1] = rc.mode == CKFWI_STORE_CODEC ? 2 * cnt[1] : 0;
+        }
+        CK_TRY(cudaGraphLaunch(it->second, st));
+    } else {
+        ST_TRY(run_body(cx, rc, acts, counters));
+    }
+    double phi = 0.0;
+    CK_TRY(cudaMemcpyAsync(&phi, m->phi.p, sizeof(double), cudaMemcpyDeviceToHost, st));
+    int fl = 0;
+    ST_TRY(read_flags(m, st, &fl));
+    if (misfit) *misfit = phi;
+    long long ncomp = counters[1];
+    if (comp_words && ncomp > 0) {
+        comp_words->resize(ncomp);
+        CK_TRY(cudaMemcpy(comp_words->data(), m->statw.p, sizeof(long long) * ncomp, cudaMemcpyDeviceToHost));
+    }
+    if (stats) {
+        std::memset(stats, 0, sizeof(*stats));
+        stats->fwd_steps = counters[0];
+        stats->adj_steps = rc.N;
+        stats->p = rc.store_all ? rc.N - 1 : cnt[0];
+        stats->takeshots = rc.store_all ? rc.N - 1 : cnt[1];
+        stats->restores = rc.store_all ? rc.N - 1 : cnt[2];
+        stats->kernel_launches = cx.launches;
+        if (rc.store_all) stats->pool_bytes_peak = (double)field_bytes(f) * rc.N;
+        else if (rc.mode == CKFWI_STORE_FP32) stats->pool_bytes_peak = (double)(rc.M - 1) * 2 * field_bytes(f, 4);
+        else if (rc.mode != CKFWI_STORE_CODEC) stats->pool_bytes_peak = (double)(rc.M - 1) * 2 * field_bytes(f, 2);
+        if (comp_words && ncomp > 0) {
+            double mn = 1e300, sum = 0;
+            for (long long wds : *comp_words) {
+                const double r = (double)f.npts / (double)std::max<long long>(1, wds);
+                mn = std::min(mn, r);
+                sum += r;
+            }
+            stats->ratio_min = mn;
+            stats->ratio_mean = sum / (double)ncomp;
+            // peak pool use: replay the slot stack with the measured sizes
+            std::vector<long long> height((size_t)rc.M + 2, 0);
+            long long k = 0, peak = 0;
+            for (const Action& A : acts) {
+                if (A.op != ACT_TAKESHOT || k + 1 >= ncomp) continue;
+                height[A.b] = height[A.b - 1] + (*comp_words)[k] + (*comp_words)[k + 1];
+                peak = std::max(peak, height[A.b]);
+                k += 2;
+            }
+            stats->pool_bytes_peak = (double)peak * 4;
+            stats->u_absmax = 0;
+        }
+    }
+    return fl;
+}
+
+}  // namespace
+
+extern "C" {
+
+int ckfwi_create_model(const ckfwi_grid* g, ckfwi_model** out)
+{
+    if (!out) return CKFWI_EINVAL;
+    *out = nullptr;
+    ST_TRY(check_grid(g));
+    ckfwi_model* m = new (std::nothrow) ckfwi_model();
+    if (!m) return CKFWI_ENOMEM;
+    std::unique_ptr<ckfwi_model> guard(m);
+    m->g = *g;
+    if (g->dims == 2) m->g.n[1] = 1;
+    m->K = g->space_order / 2;
+    m->fg = make_geom(g->dims, g->n[0], m->g.n[1], g->n[2], m->K);
+    double c[MAXK + 1];
+    fd_weights(m->K, c);
+    const double ih2 = 1.0 / (g->h * g->h);
+    m->c[0] = (float)(g->dims * c[0] * ih2);
+    for (int j = 1; j <= m->K; ++j) m->c[j] = (float)(c[j] * ih2);
+    m->hdt = (float)(g->dt / 2.0);
+    const FieldGeom& f = m->fg;
+    std::vector<float> eta((size_t)f.nz + f.ny + f.nx);
+    for (int i = 0; i < f.nz; ++i) eta[i] = (float)eta_axis(m->g, i, f.nz);
+    for (int i = 0; i < f.ny; ++i) eta[f.nz + i] = g->dims == 3 ? (float)eta_axis(m->g, i, f.ny) : 0.0f;
+    for (int i = 0; i < f.nx; ++i) eta[f.nz + f.ny + i] = (float)eta_axis(m->g, i, f.nx);
+    CK_TRY(m->eta.alloc(eta.size() * sizeof(float), false));
+    CK_TRY(cudaMemcpy(m->eta.p, eta.data(), eta.size() * sizeof(float), cudaMemcpyHostToDevice));
+    CK_TRY(m->w.alloc(field_bytes(f)));
+    CK_TRY(m->cvel.alloc((size_t)f.npts * sizeof(float)));
+    CK_TRY(m->zero.alloc(field_bytes(f)));
+    CK_TRY(m->uN.alloc(field_bytes(f)));
+    for (int i = 0; i < 3; ++i) {
+        CK_TRY(m->work[i].alloc(field_bytes(f)));
+        CK_TRY(m->lam[i].alloc(field_bytes(f)));
+    }
+    CK_TRY(m->gacc.alloc(field_bytes(f)));
+    CK_TRY(m->flags.alloc(sizeof(int) * 8));
+    CK_TRY(m->phi.alloc(sizeof(double) * 2));
+    CK_TRY(m->partials.alloc(sizeof(double) * m->nparts));
+    *out = guard.release();
+    return CKFWI_OK;
+}
+
+int ckfwi_set_model(ckfwi_model* m, const float* data, int kind, int mem, void* stream)
+{
+    if (!m || !data || (kind != CKFWI_VELOCITY && kind != CKFWI_SLOWNESS2)) return CKFWI_EINVAL;
+    cudaStream_t st = S(stream);
+    const FieldGeom& f = m->fg;
+    DevMem tmp;
+    const float* src = data;
+    if (mem == CKFWI_HOST) {
+        CK_TRY(tmp.alloc((size_t)f.npts * sizeof(float), false));
+        CK_TRY(cudaMemcpyAsync(tmp.p, data, (size_t)f.npts * sizeof(float), cudaMemcpyHostToDevice, st));
+        src = tmp.as<float>();
+    }
+    ST_TRY(reset_flags(m, st));
+    CK_TRY(launch_to_padded_w(src, kind, (float)m->g.dt, f, org(m->w, f), m->cvel.as<float>(),
+                              m->flags.as<int>() + 2, st));
+    int h[4];
+    CK_TRY(cudaMemcpyAsync(h, m->flags.p, sizeof(h), cudaMemcpyDeviceToHost, st));
+    CK_TRY(cudaStreamSynchronize(st));
+    if (h[2] & 2) return CKFWI_NONFINITE;
+    if (h[2] & 1) return CKFWI_EINVAL;
+    m->have_model = true;
+    return CKFWI_OK;
+}
+
+int ckfwi_forward_shot(ckfwi_model* m, const ckfwi_shot* s, float* d_sim, int mem, void* stream)
+{
+    if (!m || !d_sim) return CKFWI_EINVAL;
+    if (!m->have_model) return CKFWI_EINVAL;
+    cudaStream_t st = S(stream);
+    ST_TRY(set_shot(m, s));
+    ST_TRY(autotune(m, st));
+    const FieldGeom& f = m->fg;
+    Ctx cx{m, st, 0};
+    CK_TRY(cudaMemsetAsync(m->shot.dsim.p, 0, m->shot.dsim.bytes, st));
+    State sv{org(m->zero, f), org(m->zero, f), U_FP32, U_FP32};
+    for (int n = 0; n < m->g.nt; ++n) {
+        float* out = pick_free(m, sv);
+        ST_TRY(fwd_step(cx, static_cast<const float*>(sv.cur), static_cast<const float*>(sv.prev), out, n, true,
+                        CK_NONE, nullptr, nullptr));
+        sv.prev = sv.cur;
+        sv.cur = out;
+    }
+    ST_TRY(sample_last(cx, static_cast<const float*>(sv.cur)));
+    const size_t nd = (size_t)(m->g.nt + 1) * m->shot.nrec;
+    CK_TRY(cudaMemcpyAsync(d_sim, m->shot.dsim.p, nd * sizeof(float),
+                           mem == CKFWI_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, st));
+    if (mem == CKFWI_HOST) CK_TRY(cudaStreamSynchronize(st));
+    return CKFWI_OK;
+}
+
+int ckfwi_adjoint_gradient(ckfwi_model* m, const ckfwi_shot* s, const float* d_obs, int mem,
+                           const ckfwi_grad_opts* opts, double* misfit, float* grad, ckfwi_stats* stats,
+                           void* stream)
+{
+    if (!m || !grad) return CKFWI_EINVAL;
+    cudaStream_t st = S(stream);
+    std::vector<long long> cw;
+    const int rs = gradient_one(m, s, d_obs, mem, opts, misfit, stats, st, &cw);
+    if (rs != CKFWI_OK) return rs;
+    const FieldGeom& f = m->fg;
+    if (mem == CKFWI_HOST) {
+        DevMem tmp;
+        CK_TRY(tmp.alloc((size_t)f.npts * sizeof(float), false));
+        CK_TRY(launch_grad_out(org(m->gacc, f), m->cvel.as<float>(), opts->grad_kind, f, tmp.as<float>(), st));
+        CK_TRY(cudaMemcpyAsync(grad, tmp.p, (size_t)f.npts * sizeof(float), cudaMemcpyDeviceToHost, st));
+        CK_TRY(cudaStreamSynchronize(st));
+    } else {
+        CK_TRY(launch_grad_out(org(m->gacc, f), m->cvel.as<float>(), opts->grad_kind, f, grad, st));
+        CK_TRY(cudaStreamSynchronize(st));
+    }
+    if (stats) stats->kernel_launches += 1;
+    return CKFWI_OK;
+}
+
+int ckfwi_batch_gradient(ckfwi_model* m, const ckfwi_shot* shots, int nshots, const float* const* d_obs,
+                         int mem, const ckfwi_grad_opts* opts, double* misfit_sum, double* grad_sum,
+                         ckfwi_stats* stats, void* stream)
+{
+    if (!m || !shots || nshots < 1 || !d_obs || !grad_sum || !opts) return CKFWI_EINVAL;
+    cudaStream_t st = S(stream);
+    const FieldGeom& f = m->fg;
+    DevMem sum, comp;
+    CK_TRY(sum.alloc((size_t)f.npts * sizeof(double)));
+    CK_TRY(comp.alloc((size_t)f.npts * sizeof(double)));
+    double ms = 0.0, mc = 0.0;
+    ckfwi_stats acc{};
+    for (int i = 0; i < nshots; ++i) {
+        double phi = 0.0;
+        ckfwi_stats one{};
+        ST_TRY(gradient_one(m, shots + i, d_obs[i], mem, opts, &phi, &one, st, nullptr));
+        CK_TRY(launch_grad_out_f64(org(m->gacc, f), m->cvel.as<float>(), opts->grad_kind, f, sum.as<double>(),
+                                   comp.as<double>(), st));
+        const double t = ms + phi;
+        mc += (std::fabs(ms) >= std::fabs(phi)) ? (ms - t) + phi : (phi - t) + ms;
+        ms = t;
+        acc.fwd_steps += one.fwd_steps;
+        acc.adj_steps += one.adj_steps;
+        acc.p += one.p;
+        acc.takeshots += one.takeshots;
+        acc.restores += one.restores;
+        acc.kernel_launches += one.kernel_launches + 1;
+        acc.pool_bytes_peak = std::max(acc.pool_bytes_peak, one.pool_bytes_peak);
+    }
+    // sum + compensation
+    CK_TRY(launch_add_f64(sum.as<double>(), comp.as<double>(), comp.as<double>(), f.npts, st));
+    CK_TRY(cudaMemcpyAsync(grad_sum, comp.p, f.npts * sizeof(double),
+                           mem == CKFWI_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, st));
+    CK_TRY(cudaStreamSynchronize(st));
+    if (misfit_sum) *misfit_sum = ms + mc;
+    if (stats) *stats = acc;
+    return CKFWI_OK;
+}
+
+void ckfwi_free(ckfwi_model* m) { delete m; }
+
+const char* ckfwi_error_string(int status)
+{
+    switch (status) {
+    case CKFWI_OK: return "ok";
+    case CKFWI_EINVAL: return "invalid argument";
+    case CKFWI_ENOMEM: return "out of memory";
+    case CKFWI_POOL_OVERFLOW: return "compressed checkpoints exceeded the pool";
+    case CKFWI_NONFINITE: return "non-finite value";
+    case CKFWI_CORRUPT: return "corrupt compressed stream";
+    case CKFWI_TIMEOUT: return "device wait timed out";
+    case CKFWI_ECUDA: return "CUDA runtime error";
+    default: return "unknown status";
+    }
+}
+
+int ckfwi_revolve_schedule(int nt, int slots, int32_t* actions, long long cap, long long* n_triples,
+                           long long* counts)
+{
+    if (nt < 1 || slots < 1) return CKFWI_EINVAL;
+    std::vector<Action> acts;
+    long long cnt[3];
+    if (revolve_schedule(nt, slots, acts, cnt) != 0) return CKFWI_EINVAL;
+    if (n_triples) *n_triples = (long long)acts.size();
+    if (counts) {
+        counts[0] = cnt[0];
+        counts[1] = cnt[1];
+        counts[2] = cnt[2];
+    }
+    if (!actions) return cap == 0 ? CKFWI_OK : CKFWI_EINVAL;
+    if ((long long)acts.size() > cap) return CKFWI_EINVAL;
+    for (size_t i = 0; i < acts.size(); ++i) {
+        actions[3 * i] = acts[i].op;
+        actions[3 * i + 1] = acts[i].a;
+        actions[3 * i + 2] = acts[i].b;
+    }
+    return CKFWI_OK;
+}
+
+long long ckfwi_codec_bound_words(int dims, int nz, int ny, int nx)
+{
+    if ((dims != 2 && dims != 3) || nz < 1 || ny < 1 || nx < 1 || (dims == 2 && ny != 1)) return CKFWI_EINVAL;
+    return codec_bound_words(dims, nz, ny, nx);
+}
+
+}  // extern "C"
+
+namespace {
+std::mutex g_codec_mu;
+DevMem* g_codec_scratch[64] = {};
+DevMem* g_codec_scal[64] = {};
+}  // namespace
+
+extern "C" int ckfwi_codec_compress(const float* x, int dims, int nz, int ny, int nx, double tol, uint32_t* out,
+                                    long long cap, long long* used_words, int* flags, void* stream)
+{
+    if (!x || !out || cap <= 0) return CKFWI_EINVAL;
+    if ((dims != 2 && dims != 3) || nz < 1 || ny < 1 || nx < 1 || (dims == 2 && ny != 1)) return CKFWI_EINVAL;
+    if (!(tol >= std::ldexp(1.0, -90)) || !std::isfinite(tol)) return CKFWI_EINVAL;
+    cudaStream_t st = S(stream);
+    int dev = 0;
+    CK_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) return CKFWI_EINVAL;
+    std::lock_guard<std::mutex> lk(g_codec_mu);
+    if (!g_codec_scratch[dev]) g_codec_scratch[dev] = new DevMem();
+    if (!g_codec_scal[dev]) g_codec_scal[dev] = new DevMem();
+    DevMem& scr = *g_codec_scratch[dev];
+    DevMem& scal = *g_codec_scal[dev];
+    const size_t need = (size_t)codec_scratch_bytes(dims, nz, ny, nx);
+    if (scr.bytes < need) CK_TRY(scr.alloc(need, false));
+    CK_TRY(scal.alloc(64, true));
+    CodecView v{};
+    v.dims = dims; v.nz = nz; v.ny = ny; v.nx = nx;
+    v.py = nx;
+    v.pz = (long long)ny * nx;
+    v.aligned = (nx % 4 == 0) && ((reinterpret_cast<uintptr_t>(x) & 15) == 0);
+    long long* sc = scal.as<long long>();
+    int* err = reinterpret_cast<int*>(sc + 4);
+    CK_TRY(codec_compress_dev(x, v, tol_float(tol), out, sc, cap, sc + 1, scr.p, err, nullptr, st));
+    long long h[5];
+    CK_TRY(cudaMemcpyAsync(h, sc, sizeof(h), cudaMemcpyDeviceToHost, st));
+    CK_TRY(cudaStreamSynchronize(st));
+    const int e = (int)(h[4] & 0xffffffff);
+    if (flags) *flags = (e & 1) ? 1 : 0;
+    if (e & 2) return CKFWI_POOL_OVERFLOW;
+    if (used_words) *used_words = h[1];
+    return CKFWI_OK;
+}
+
+extern "C" int ckfwi_codec_decompress(const uint32_t* in, long long nwords, int dims, int nz, int ny, int nx,
+                                      float* x, void* stream)
+{
+    if (!in || !x || nwords <= 0) return CKFWI_EINVAL;
+    if ((dims != 2 && dims != 3) || nz < 1 || ny < 1 || nx < 1 || (dims == 2 && ny != 1)) return CKFWI_EINVAL;
+    cudaStream_t st = S(stream);
+    int dev = 0;
+    CK_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) return CKFWI_EINVAL;
+    std::lock_guard<std::mutex> lk(g_codec_mu);
+    if (!g_codec_scal[dev]) g_codec_scal[dev] = new DevMem();
+    DevMem& scal = *g_codec_scal[dev];
+    CK_TRY(scal.alloc(64, true));
+    CodecView v{};
+    v.dims = dims; v.nz = nz; v.ny = ny; v.nx = nx;
+    v.py = nx;
+    v.pz = (long long)ny * nx;
+    v.aligned = (nx % 4 == 0) && ((reinterpret_cast<uintptr_t>(x) & 15) == 0);
+    long long* sc = scal.as<long long>();
+    int* err = reinterpret_cast<int*>(sc + 4);
+    CK_TRY(codec_decompress_dev(in, sc, nwords, v, x, err, st));
+    int e = 0;
+    CK_TRY(cudaMemcpyAsync(&e, err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK_TRY(cudaStreamSynchronize(st));
+    if (e & 4) return CKFWI_CORRUPT;
+    return CKFWI_OK;
+}

@@ -1,0 +1,221 @@
+// Small kernels around the time loop: receiver sampling, residual and FP64
+// misfit (Sec. 6: phi = 1/2 ||d_sim - d_obs||^2), model setup (m = 1/c^2 ->
+// w = dt^2 c^2), gradient output and checkpoint up-casts.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include <type_traits>
+
+#include "internal.h"
+
+namespace ckfwi {
+
+namespace {
+
+__global__ void sample_kernel(const float* __restrict__ u, Sample smp)
+{
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= smp.n) return;
+    float acc = 0.0f;
+    for (int i = 0; i < smp.nst; ++i)
+        acc = __fmaf_rn(smp.wt[r * smp.nst + i], __ldg(u + smp.idx[r * smp.nst + i]), acc);
+    smp.out[r] = acc;
+}
+
+constexpr int RED_THREADS = 256;
+
+// r = d - dobs for rows 1..rows-1 (row 0 zero); per-CTA FP64 partial sums
+// of r^2 over a fixed contiguous range, reduced by a fixed tree.
+__global__ void residual_kernel(const float* __restrict__ d, const float* __restrict__ dobs,
+                                float* __restrict__ r, long long n, long long first,
+                                double* __restrict__ partials, long long per_cta)
+{
+    __shared__ double sh[RED_THREADS];
+    const long long lo = (long long)blockIdx.x * per_cta;
+    const long long hi = min(lo + per_cta, n);
+    double acc = 0.0;
+    for (long long i = lo + threadIdx.x; i < hi; i += RED_THREADS) {
+        float v = 0.0f;
+        double dv = 0.0;
+        if (i >= first) {
+            dv = (double)d[i] - (double)dobs[i];
+            v = (float)dv;
+        }
+        r[i] = v;
+        acc += dv * dv;
+    }
+    sh[threadIdx.x] = acc;
+    __syncthreads();
+    for (int s = RED_THREADS / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) sh[threadIdx.x] += sh[threadIdx.x + s];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) partials[blockIdx.x] = sh[0];
+}
+
+__global__ void final_sum_kernel(const double* __restrict__ partials, int n, double* phi)
+{
+    __shared__ double sh[RED_THREADS];
+    double acc = 0.0;
+    for (int i = threadIdx.x; i < n; i += RED_THREADS) acc += partials[i];
+    sh[threadIdx.x] = acc;
+    __syncthreads();
+    for (int s = RED_THREADS / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) sh[threadIdx.x] += sh[threadIdx.x + s];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *phi = 0.5 * sh[0];
+}
+
+__device__ __forceinline__ long long padded(const FieldGeom& g, long long p)
+{
+    const long long x = p % g.nx;
+    const long long t = p / g.nx;
+    const long long y = t % g.ny;
+    const long long z = t / g.ny;
+    return z * g.pxy + y * g.px + x;
+}
+
+// kind 0: velocity c, kind 1: m = 1/c^2.  w = dt^2 c^2 (FP64, rounded once);
+// c_dense keeps c in float for the gradient output.
+__global__ void model_kernel(const float* __restrict__ in, int kind, double dt2, FieldGeom g,
+                             float* __restrict__ w, float* __restrict__ c_dense, int* err)
+{
+    const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= g.npts) return;
+    const float v = in[p];
+    if (!isfinite(v)) { atomicOr(err, 2); return; }
+    if (!(v > 0.0f)) { atomicOr(err, 1); return; }
+    double c2 = (kind == 0) ? (double)v * (double)v : 1.0 / (double)v;
+    w[padded(g, p)] = (float)(dt2 * c2);
+    c_dense[p] = (float)sqrt(c2);
+}
+
+// dphi/dm = gacc c^2 ; dphi/dc = dphi/dm dm/dc = -2 gacc / c
+__device__ __forceinline__ float grad_value(float ga, float c, int kind)
+{
+    return (kind == 1) ? __fmul_rn(ga, __fmul_rn(c, c)) : __fdiv_rn(__fmul_rn(-2.0f, ga), c);
+}
+
+__global__ void grad_out_kernel(const float* __restrict__ gacc, const float* __restrict__ c,
+                                int kind, FieldGeom g, float* __restrict__ out)
+{
+    const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= g.npts) return;
+    out[p] = grad_value(gacc[padded(g, p)], c[p], kind);
+}
+
+// Neumaier-compensated FP64 accumulation of one shot's gradient.
+__global__ void grad_sum_kernel(const float* __restrict__ gacc, const float* __restrict__ c,
+                                int kind, FieldGeom g, double* __restrict__ sum,
+                                double* __restrict__ comp)
+{
+    const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= g.npts) return;
+    const double v = (double)grad_value(gacc[padded(g, p)], c[p], kind);
+    const double s = sum[p];
+    const double t = s + v;
+    comp[p] += (fabs(s) >= fabs(v)) ? (s - t) + v : (v - t) + s;
+    sum[p] = t;
+}
+
+template <class T>
+__global__ void upcast_kernel(const T* __restrict__ src, FieldGeom g, float* __restrict__ dst)
+{
+    const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= g.npts) return;
+    const long long o = padded(g, p);
+    float v;
+    if constexpr (sizeof(T) == 2) {
+        if constexpr (std::is_same<T, __half>::value) v = __half2float(src[o]);
+        else v = __bfloat162float(src[o]);
+    } else {
+        v = src[o];
+    }
+    dst[o] = v;
+}
+
+__global__ void copy_f64_kernel(const double* __restrict__ a, double* __restrict__ b, long long n)
+{
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) b[i] = a[i];
+}
+
+__global__ void add_f64_kernel(const double* __restrict__ a, const double* __restrict__ b,
+                               double* __restrict__ out, long long n)
+{
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = a[i] + b[i];
+}
+
+inline unsigned blocks_for(long long n, int t) { return (unsigned)((n + t - 1) / t); }
+
+}  // namespace
+
+cudaError_t launch_sample(const float* u, const Sample& smp, cudaStream_t s)
+{
+    if (smp.n <= 0) return cudaSuccess;
+    sample_kernel<<<blocks_for(smp.n, 128), 128, 0, s>>>(u, smp);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_residual(const float* d, const float* dobs, float* r, int rows, int nrec,
+                            double* partials, int nparts, double* phi, cudaStream_t s)
+{
+    const long long n = (long long)rows * nrec;
+    const long long per = (n + nparts - 1) / nparts;
+    residual_kernel<<<nparts, RED_THREADS, 0, s>>>(d, dobs, r, n, (long long)nrec, partials, per);
+    final_sum_kernel<<<1, RED_THREADS, 0, s>>>(partials, nparts, phi);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_to_padded_w(const float* dense, int kind, float dt, const FieldGeom& g,
+                               float* w_origin, float* c_dense, int* err, cudaStream_t s)
+{
+    model_kernel<<<blocks_for(g.npts, 256), 256, 0, s>>>(dense, kind, (double)dt * (double)dt, g,
+                                                          w_origin, c_dense, err);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_grad_out(const float* gacc_origin, const float* c_dense, int kind,
+                            const FieldGeom& g, float* out_dense, cudaStream_t s)
+{
+    grad_out_kernel<<<blocks_for(g.npts, 256), 256, 0, s>>>(gacc_origin, c_dense, kind, g, out_dense);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_grad_out_f64(const float* gacc_origin, const float* c_dense, int kind,
+                                const FieldGeom& g, double* sum, double* comp, cudaStream_t s)
+{
+    grad_sum_kernel<<<blocks_for(g.npts, 256), 256, 0, s>>>(gacc_origin, c_dense, kind, g, sum, comp);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cast_restore(const void* src, int utype, const FieldGeom& g, float* dst_origin,
+                                cudaStream_t s)
+{
+    const unsigned nb = blocks_for(g.npts, 256);
+    if (utype == U_BF16)
+        upcast_kernel<__nv_bfloat16><<<nb, 256, 0, s>>>(static_cast<const __nv_bfloat16*>(src), g, dst_origin);
+    else if (utype == U_FP16)
+        upcast_kernel<__half><<<nb, 256, 0, s>>>(static_cast<const __half*>(src), g, dst_origin);
+    else
+        upcast_kernel<float><<<nb, 256, 0, s>>>(static_cast<const float*>(src), g, dst_origin);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_copy_f64(const double* a, double* b, long long n, cudaStream_t s)
+{
+    copy_f64_kernel<<<blocks_for(n, 256), 256, 0, s>>>(a, b, n);
+    return cudaGetLastError();
+}
+
+}  // namespace ckfwi
+
+namespace ckfwi {
+cudaError_t launch_add_f64(const double* a, const double* b, double* out, long long n, cudaStream_t s)
+{
+    add_f64_kernel<<<blocks_for(n, 256), 256, 0, s>>>(a, b, out, n);
+    return cudaGetLastError();
+}
+}  // namespace ckfwi

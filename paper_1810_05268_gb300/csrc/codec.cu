@@ -1,0 +1,702 @@
+// Fixed-accuracy block-transform codec for checkpoints held in HBM.
+//
+// The paper compresses checkpoints with ZFP in fixed-tolerance mode, an
+// absolute point-wise error bound (Sec. 2.2 "Lossy Compression"); Sec. 4
+// turns the ratio F into F times more checkpoint slots.  This codec is of
+// the same family and is specified here in full (it is not ZFP and not
+// bit-compatible with it):
+//
+//  blocks   4^d cubes (2D: 4x4 over z, x), block b = (bz*nby + by)*nbx + bx;
+//           a partial block repeats the last valid sample along each axis.
+//  zero     max |x| <= tol_f (largest float <= tol): a single 0 bit.
+//  integers Emax = max exponent max(biased,1)-127 over non-zero values;
+//           i = trunc(x 2^(23-Emax)) from the bits, |i| < 2^24.
+//  lifting  per 4-vector along x, then y, then z, 32-bit wrap-around:
+//           d3 = x3 - 2x2 + x1, d1 = x1 - ((x0+x2)>>1), D = x2 - x0,
+//           S = x0 + (D>>1)  ->  (S, D, d1, d3); exactly invertible.
+//  order    by (kz+ky+kx, kz, ky, kx); negabinary n = (c + A) ^ A,
+//           A = 0xAAAAAAAA.
+//  planes   ptop = highest set bit of all n; T = floor(tol_f 2^(23-Emax));
+//           pbot = first plane, from min(ptop, max(0, floor(log2 T) - 1))
+//           down to 0, whose truncation reproduces every i within T - 2
+//           (closed loop, so |x - x_hat| <= tol on every value); T < 2 or
+//           Emax >= 126: raw block.
+//  stream   1 0 Emax+127(8) ptop(5) pbot(5), then planes ptop..pbot: the
+//           bits of the s significant coefficients verbatim, then group
+//           tests (1 = some coefficient >= s is set: its bits follow up to
+//           and including the first set one; 0 = none).  Raw: 1 1, then the
+//           float bit patterns.  A coded stream longer than the raw form
+//           (2 + 32 V bits) is replaced by it.  LSB-first in 32-bit words.
+//  container [16 header words][chunk word offsets][uint16 block bit sizes]
+//           [payload]; a chunk is 32 consecutive blocks and starts on a
+//           word boundary.
+//
+// GPU layout of the work: one thread encodes / decodes one block; a warp
+// owns one chunk, so block bit offsets inside a chunk come from a warp scan
+// of the size table.  Compression runs in three launches: encode every
+// block into a fixed-size scratch slot and write its size, scan chunk sizes
+// (one CTA) into the chunk table and header, then compact each chunk's bits
+// through shared memory into the payload.  The pool position of a stream is
+// read from and written to device memory, so a schedule of compressions and
+// decompressions runs without host synchronisation; running out of pool
+// raises an error bit and the stream is not written.
+#include <cstdint>
+
+#include "internal.h"
+
+namespace ckfwi {
+namespace {
+
+constexpr uint32_t MAGIC = 0x31435442u;
+constexpr uint32_t VERSION = 1u;
+constexpr int HDR = 16;
+constexpr int CHUNK = 32;
+constexpr int GUARD = 1;
+constexpr int ENC_THREADS = 128;
+constexpr int CMP_WARPS = 4;
+constexpr int DEC_THREADS = 128;
+
+template <int DIMS> struct Cfg {
+    static constexpr int V = DIMS == 3 ? 64 : 16;
+    static constexpr int MAXBITS = 2 + 32 * V;
+    static constexpr int MAXW = (MAXBITS + 31) / 32;       // scratch words per block
+};
+
+struct Geo {
+    int dims, nz, ny, nx, nbz, nby, nbx;
+    long long nblocks, nchunks, table_words;
+};
+
+__host__ __device__ inline Geo make_geo(int dims, int nz, int ny, int nx)
+{
+    Geo G;
+    G.dims = dims; G.nz = nz; G.ny = ny; G.nx = nx;
+    G.nbz = (nz + 3) / 4;
+    G.nby = dims == 3 ? (ny + 3) / 4 : 1;
+    G.nbx = (nx + 3) / 4;
+    G.nblocks = (long long)G.nbz * G.nby * G.nbx;
+    G.nchunks = (G.nblocks + CHUNK - 1) / CHUNK;
+    G.table_words = HDR + G.nchunks + (G.nblocks + 1) / 2;
+    return G;
+}
+
+// sequency order, built at compile time from its definition
+struct Perm { int p[64]; };
+constexpr Perm make_perm(int dims)
+{
+    Perm r{};
+    int key[64] = {};
+    const int V = dims == 3 ? 64 : 16;
+    for (int i = 0; i < V; ++i) {
+        const int kz = dims == 3 ? i / 16 : i / 4;
+        const int ky = dims == 3 ? (i / 4) % 4 : 0;
+        const int kx = i % 4;
+        key[i] = ((kz + ky + kx) << 12) | (kz << 8) | (ky << 4) | kx;
+        r.p[i] = i;
+    }
+    for (int a = 0; a < V; ++a) {
+        int best = a;
+        for (int b = a + 1; b < V; ++b)
+            if (key[r.p[b]] < key[r.p[best]]) best = b;
+        const int t = r.p[a];
+        r.p[a] = r.p[best];
+        r.p[best] = t;
+    }
+    return r;
+}
+
+__device__ __forceinline__ int32_t half_of(int32_t a) { return a >> 1; }  // arithmetic shift
+
+__device__ __forceinline__ void lift_fwd(int32_t& x0, int32_t& x1, int32_t& x2, int32_t& x3)
+{
+    const uint32_t u0 = x0, u1 = x1, u2 = x2, u3 = x3;
+    const int32_t d3 = (int32_t)(u3 - (u2 + u2) + u1);
+    const int32_t d1 = (int32_t)(u1 - (uint32_t)half_of((int32_t)(u0 + u2)));
+    const int32_t D = (int32_t)(u2 - u0);
+    const int32_t S = (int32_t)(u0 + (uint32_t)half_of(D));
+    x0 = S; x1 = D; x2 = d1; x3 = d3;
+}
+
+__device__ __forceinline__ void lift_inv(int32_t& a0, int32_t& a1, int32_t& a2, int32_t& a3)
+{
+    const int32_t S = a0, D = a1, d1 = a2, d3 = a3;
+    const int32_t x0 = (int32_t)((uint32_t)S - (uint32_t)half_of(D));
+    const int32_t x2 = (int32_t)((uint32_t)D + (uint32_t)x0);
+    const int32_t x1 = (int32_t)((uint32_t)d1 + (uint32_t)half_of((int32_t)((uint32_t)x0 + (uint32_t)x2)));
+    const int32_t x3 = (int32_t)((uint32_t)d3 + (uint32_t)x2 + (uint32_t)x2 - (uint32_t)x1);
+    a0 = x0; a1 = x1; a2 = x2; a3 = x3;
+}
+
+template <int DIMS>
+__device__ __forceinline__ void xform_fwd(int32_t (&b)[Cfg<DIMS>::V])
+{
+    if constexpr (DIMS == 3) {
+#pragma unroll
+        for (int r = 0; r < 16; ++r) lift_fwd(b[4 * r], b[4 * r + 1], b[4 * r + 2], b[4 * r + 3]);
+#pragma unroll
+        for (int z = 0; z < 4; ++z)
+#pragma unroll
+            for (int x = 0; x < 4; ++x)
+                lift_fwd(b[16 * z + x], b[16 * z + 4 + x], b[16 * z + 8 + x], b[16 * z + 12 + x]);
+#pragma unroll
+        for (int r = 0; r < 16; ++r) lift_fwd(b[r], b[16 + r], b[32 + r], b[48 + r]);
+    } else {
+#pragma unroll
+        for (int z = 0; z < 4; ++z) lift_fwd(b[4 * z], b[4 * z + 1], b[4 * z + 2], b[4 * z + 3]);
+#pragma unroll
+        for (int x = 0; x < 4; ++x) lift_fwd(b[x], b[4 + x], b[8 + x], b[12 + x]);
+    }
+}
+
+template <int DIMS>
+__device__ __forceinline__ void xform_inv(int32_t (&b)[Cfg<DIMS>::V])
+{
+    if constexpr (DIMS == 3) {
+#pragma unroll
+        for (int r = 0; r < 16; ++r) lift_inv(b[r], b[16 + r], b[32 + r], b[48 + r]);
+#pragma unroll
+        for (int z = 0; z < 4; ++z)
+#pragma unroll
+            for (int x = 0; x < 4; ++x)
+                lift_inv(b[16 * z + x], b[16 * z + 4 + x], b[16 * z + 8 + x], b[16 * z + 12 + x]);
+#pragma unroll
+        for (int r = 0; r < 16; ++r) lift_inv(b[4 * r], b[4 * r + 1], b[4 * r + 2], b[4 * r + 3]);
+    } else {
+#pragma unroll
+        for (int x = 0; x < 4; ++x) lift_inv(b[x], b[4 + x], b[8 + x], b[12 + x]);
+#pragma unroll
+        for (int z = 0; z < 4; ++z) lift_inv(b[4 * z], b[4 * z + 1], b[4 * z + 2], b[4 * z + 3]);
+    }
+}
+
+__device__ __forceinline__ uint32_t nega(int32_t c) { return ((uint32_t)c + 0xAAAAAAAAu) ^ 0xAAAAAAAAu; }
+__device__ __forceinline__ int32_t unnega(uint32_t n) { return (int32_t)((n ^ 0xAAAAAAAAu) - 0xAAAAAAAAu); }
+
+__device__ __forceinline__ float pow2f(int e) { return __uint_as_float((uint32_t)(e + 127) << 23); }
+
+// block coordinates and clamped sample positions
+struct BlockPos { int bz, by, bx; };
+__device__ __forceinline__ BlockPos block_pos(const Geo& G, long long b)
+{
+    BlockPos p;
+    p.bx = (int)(b % G.nbx);
+    const long long t = b / G.nbx;
+    p.by = (int)(t % G.nby);
+    p.bz = (int)(t / G.nby);
+    return p;
+}
+
+template <int DIMS>
+__device__ __forceinline__ void gather(const float* __restrict__ x, const CodecView& v, const BlockPos& bp,
+                                       float (&f)[Cfg<DIMS>::V])
+{
+    const int xs = 4 * bp.bx;
+    const bool vec = v.aligned && xs + 3 < v.nx;
+    constexpr int ROWS = DIMS == 3 ? 16 : 4;
+#pragma unroll
+    for (int r = 0; r < ROWS; ++r) {
+        const int lz = DIMS == 3 ? r / 4 : r;
+        const int ly = DIMS == 3 ? r % 4 : 0;
+        const int z = min(4 * bp.bz + lz, v.nz - 1);
+        const int y = DIMS == 3 ? min(4 * bp.by + ly, v.ny - 1) : 0;
+        const float* row = x + (long long)z * v.pz + (long long)y * v.py;
+        if (vec) {
+            const float4 q = __ldg(reinterpret_cast<const float4*>(row + xs));
+            f[4 * r] = q.x; f[4 * r + 1] = q.y; f[4 * r + 2] = q.z; f[4 * r + 3] = q.w;
+        } else {
+#pragma unroll
+            for (int c = 0; c < 4; ++c) f[4 * r + c] = __ldg(row + min(xs + c, v.nx - 1));
+        }
+    }
+}
+
+// bit writer into a per-block scratch slot of `cap` words; bits past the
+// slot are counted but not stored (such a stream is replaced by the raw form)
+struct BitW {
+    uint32_t* w;
+    unsigned long long acc;
+    int nacc;
+    int nw;
+    int cap;
+    __device__ __forceinline__ void put(uint32_t v, int n)   // n <= 32, v < 2^n
+    {
+        if (n == 0) return;
+        acc |= (unsigned long long)v << nacc;
+        nacc += n;
+        if (nacc >= 32) {
+            if (nw < cap) w[nw] = (uint32_t)acc;
+            ++nw;
+            acc >>= 32;
+            nacc -= 32;
+        }
+    }
+    __device__ __forceinline__ void put64(unsigned long long v, int n)   // n <= 64
+    {
+        if (n > 32) {
+            put((uint32_t)v, 32);
+            put((uint32_t)(v >> 32), n - 32);
+        } else {
+            put((uint32_t)v, n);
+        }
+    }
+    __device__ __forceinline__ int bits() const { return nw * 32 + nacc; }
+    __device__ __forceinline__ int flush()
+    {
+        const int b = bits();
+        if (nacc > 0) {
+            if (nw < cap) w[nw] = (uint32_t)acc;
+            ++nw;
+        }
+        return b;
+    }
+};
+
+__device__ __forceinline__ unsigned long long low_mask(int n)
+{
+    return n >= 64 ? ~0ull : ((1ull << n) - 1ull);
+}
+
+template <int DIMS>
+__global__ void __launch_bounds__(ENC_THREADS) enc_kernel(const float* __restrict__ x, CodecView v,
+                                                          Geo G, float tol_f, uint32_t* __restrict__ scratch,
+                                                          uint32_t* __restrict__ out, const long long* base_word,
+                                                          long long cap_words, int* err)
+{
+    constexpr int V = Cfg<DIMS>::V;
+    constexpr Perm P = make_perm(DIMS);
+    __shared__ int32_t siv[V * ENC_THREADS];
+    const long long b = (long long)blockIdx.x * ENC_THREADS + threadIdx.x;
+    const long long base = *base_word;
+    if (base + G.table_words > cap_words) {
+        if (b == 0) atomicOr(err, 2);
+        return;
+    }
+    uint16_t* sizes = reinterpret_cast<uint16_t*>(out + base + HDR + G.nchunks);
+    if (b == 0 && (G.nblocks & 1)) sizes[G.nblocks] = 0;
+    if (b >= G.nblocks) return;
+
+    const BlockPos bp = block_pos(G, b);
+    float f[V];
+    gather<DIMS>(x, v, bp, f);
+    BitW bw{scratch + b * Cfg<DIMS>::MAXW, 0ull, 0, 0, Cfg<DIMS>::MAXW};
+
+    float amax = 0.0f;
+    bool bad = false;
+#pragma unroll
+    for (int i = 0; i < V; ++i) {
+        bad |= !isfinite(f[i]);
+        amax = fmaxf(amax, fabsf(f[i]));
+    }
+    if (bad) atomicOr(err, 1);
+    if (bad || amax <= tol_f) {
+        bw.put(0u, 1);
+        sizes[b] = (uint16_t)bw.flush();
+        return;
+    }
+    int emax = -1000;
+#pragma unroll
+    for (int i = 0; i < V; ++i) {
+        const uint32_t u = __float_as_uint(f[i]);
+        const int be = (int)((u >> 23) & 0xFF);
+        if (u & 0x7FFFFFFFu) emax = max(emax, max(be, 1) - 127);
+    }
+    int32_t c[V];
+#pragma unroll
+    for (int i = 0; i < V; ++i) {
+        const uint32_t u = __float_as_uint(f[i]);
+        const int be = (int)((u >> 23) & 0xFF);
+        const uint32_t M = (u & 0x7FFFFFu) | (be > 0 ? 0x800000u : 0u);
+        const int sh = emax - (max(be, 1) - 127);
+        uint32_t mag = sh >= 32 ? 0u : (M >> sh);
+        if (!(u & 0x7FFFFFFFu)) mag = 0u;
+        c[i] = (u >> 31) ? -(int32_t)mag : (int32_t)mag;
+        siv[i * ENC_THREADS + threadIdx.x] = c[i];
+    }
+    xform_fwd<DIMS>(c);
+    uint32_t nb[V];
+    uint32_t orall = 0;
+#pragma unroll
+    for (int r = 0; r < V; ++r) {
+        nb[r] = nega(c[P.p[r]]);
+        orall |= nb[r];
+    }
+    const int ptop = orall ? 31 - __clz(orall) : 0;
+    const float Tf = tol_f * pow2f(23 - emax);
+    const int T = (int)Tf;
+    int pbot = -1;
+    if (T >= 2 && emax < 126) {
+        const int lg = 31 - __clz(T);
+        const int p0 = min(max(lg - GUARD, 0), ptop);
+        for (int p = p0; p >= 0; --p) {
+            const uint32_t mask = ~((1u << p) - 1u);
+            int32_t t[V];
+#pragma unroll
+            for (int r = 0; r < V; ++r) t[P.p[r]] = unnega(nb[r] & mask);
+            xform_inv<DIMS>(t);
+            bool ok = true;
+#pragma unroll
+            for (int i = 0; i < V; ++i) {
+                const long long d = (long long)siv[i * ENC_THREADS + threadIdx.x] - (long long)t[i];
+                ok &= (d <= (long long)T - 2) && (-d <= (long long)T - 2);
+            }
+            if (ok) {
+                pbot = p;
+                break;
+            }
+        }
+    }
+    if (pbot >= 0) {
+        bw.put(1u, 1);
+        bw.put(0u, 1);
+        bw.put((uint32_t)(emax + 127), 8);
+        bw.put((uint32_t)ptop, 5);
+        bw.put((uint32_t)pbot, 5);
+        int s = 0;
+        for (int p = ptop; p >= pbot; --p) {
+            unsigned long long W = 0;
+#pragma unroll
+            for (int r = 0; r < V; ++r) W |= (unsigned long long)((nb[r] >> p) & 1u) << r;
+            bw.put64(W & low_mask(s), s);
+            while (s < V) {
+                const unsigned long long rest = W >> s;
+                if (rest == 0ull) {
+                    bw.put(0u, 1);
+                    break;
+                }
+                const int z = __ffsll((long long)rest) - 1;
+                bw.put(1u, 1);
+                bw.put64(1ull << z, z + 1);     // z zeros, then the set bit
+                s += z + 1;
+            }
+        }
+        if (bw.bits() <= Cfg<DIMS>::MAXBITS) {
+            sizes[b] = (uint16_t)bw.flush();
+            return;
+        }
+        bw.acc = 0ull;      // longer than raw: start over with the raw form
+        bw.nacc = 0;
+        bw.nw = 0;
+    }
+    bw.put(1u, 1);
+    bw.put(1u, 1);
+    {
+        float g[V];
+        gather<DIMS>(x, v, bp, g);
+#pragma unroll
+        for (int i = 0; i < V; ++i) bw.put(__float_as_uint(g[i]), 32);
+    }
+    sizes[b] = (uint16_t)bw.flush();
+}
+
+// One CTA: chunk word counts -> exclusive scan -> chunk table, header,
+// next free word; overflow check.
+__global__ void __launch_bounds__(1024) scan_kernel(uint32_t* __restrict__ out, const long long* base_word,
+                                                    long long cap_words, long long* next_word, Geo G,
+                                                    float tol_f, int* err, unsigned long long* stat_words)
+{
+    __shared__ long long carry_s;
+    __shared__ long long warp_tot[32];
+    const long long base = *base_word;
+    if (base + G.table_words > cap_words) {
+        if (threadIdx.x == 0) {
+            atomicOr(err, 2);
+            *next_word = base;
+        }
+        return;
+    }
+    uint32_t* hdr = out + base;
+    uint32_t* ctab = hdr + HDR;
+    const uint16_t* sizes = reinterpret_cast<const uint16_t*>(hdr + HDR + G.nchunks);
+    if (threadIdx.x == 0) carry_s = 0;
+    __syncthreads();
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (long long c0 = 0; c0 < G.nchunks; c0 += 1024) {
+        const long long c = c0 + threadIdx.x;
+        long long words = 0;
+        if (c < G.nchunks) {
+            long long bits = 0;
+            const long long b1 = min((c + 1) * CHUNK, G.nblocks);
+            for (long long b = c * CHUNK; b < b1; ++b) bits += sizes[b];
+            words = (bits + 31) / 32;
+        }
+        long long incl = words;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const long long t = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += t;
+        }
+        if (lane == 31) warp_tot[wid] = incl;
+        __syncthreads();
+        if (wid == 0) {
+            long long t = warp_tot[lane];
+            long long tin = t;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const long long u = __shfl_up_sync(0xffffffffu, tin, o);
+                if (lane >= o) tin += u;
+            }
+            warp_tot[lane] = tin - t;       // exclusive prefix of warp totals
+        }
+        __syncthreads();
+        const long long excl = carry_s + warp_tot[wid] + incl - words;
+        if (c < G.nchunks) ctab[c] = (uint32_t)excl;
+        __syncthreads();
+        if (threadIdx.x == 1023) carry_s = excl + words;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        const long long payload = carry_s;
+        const long long end = base + G.table_words + payload;
+        hdr[0] = MAGIC;
+        hdr[1] = (uint32_t)G.dims | (VERSION << 8);
+        hdr[2] = (uint32_t)G.nz;
+        hdr[3] = (uint32_t)G.ny;
+        hdr[4] = (uint32_t)G.nx;
+        hdr[5] = (uint32_t)G.nblocks;
+        hdr[6] = (uint32_t)G.nchunks;
+        hdr[7] = (uint32_t)payload;
+        hdr[8] = __float_as_uint(tol_f);
+        hdr[9] = (*err & 1) ? 1u : 0u;
+        for (int i = 10; i < HDR; ++i) hdr[i] = 0u;
+        if (end > cap_words) {
+            atomicOr(err, 2);
+            *next_word = base;
+        } else {
+            *next_word = end;
+        }
+        if (stat_words) atomicAdd(stat_words, (unsigned long long)(G.table_words + payload));
+    }
+}
+
+template <int DIMS>
+__global__ void __launch_bounds__(CMP_WARPS * 32) compact_kernel(uint32_t* __restrict__ out, const long long* base_word,
+                                                                 const long long* next_word, Geo G,
+                                                                 const uint32_t* __restrict__ scratch, int* err)
+{
+    constexpr int CW = (CHUNK * Cfg<DIMS>::MAXBITS + 31) / 32 + 1;
+    __shared__ uint32_t buf[CMP_WARPS][CW];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const long long c = (long long)blockIdx.x * CMP_WARPS + wid;
+    const long long base = *base_word;
+    if (*next_word <= base) return;               // overflow: nothing is written
+    if (c >= G.nchunks) return;
+    const uint32_t* hdr = out + base;
+    const uint16_t* sizes = reinterpret_cast<const uint16_t*>(hdr + HDR + G.nchunks);
+    const long long b = c * CHUNK + lane;
+    const int nbits = b < G.nblocks ? sizes[b] : 0;
+    int incl = nbits;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += t;
+    }
+    const int total = __shfl_sync(0xffffffffu, incl, 31);
+    const int off = incl - nbits;
+    const int words = (total + 31) / 32;
+    // every block is at most MAXBITS long by construction; a chunk that is
+    // not would overrun the shared buffer, so it is refused outright
+    if (__any_sync(0xffffffffu, nbits > Cfg<DIMS>::MAXBITS) || words > CW) {
+        if (lane == 0) atomicOr(err, 4);
+        return;
+    }
+    for (int k = lane; k < words; k += 32) buf[wid][k] = 0u;
+    __syncwarp();
+    const uint32_t* src = scratch + b * Cfg<DIMS>::MAXW;
+    const int sw = (nbits + 31) / 32;
+    for (int k = 0; k < sw; ++k) {
+        uint32_t val = src[k];
+        const int rem = nbits - 32 * k;
+        if (rem < 32) val &= (1u << rem) - 1u;
+        const int pos = off + 32 * k;
+        const int sh = pos & 31, idx = pos >> 5;
+        atomicOr(&buf[wid][idx], val << sh);
+        if (sh) atomicOr(&buf[wid][idx + 1], val >> (32 - sh));
+    }
+    __syncwarp();
+    uint32_t* payload = out + base + G.table_words + hdr[HDR + c];
+    for (int k = lane; k < words; k += 32) payload[k] = buf[wid][k];
+}
+
+// 64 stream bits starting at bit `pos` of the payload (zeros past `limit` words)
+__device__ __forceinline__ unsigned long long peek64(const uint32_t* __restrict__ p, long long pos, long long limit)
+{
+    const long long w = pos >> 5;
+    const int sh = (int)(pos & 31);
+    const unsigned long long w0 = w < limit ? p[w] : 0u;
+    const unsigned long long w1 = w + 1 < limit ? p[w + 1] : 0u;
+    const unsigned long long w2 = w + 2 < limit ? p[w + 2] : 0u;
+    unsigned long long v = (w0 | (w1 << 32)) >> sh;
+    if (sh) v |= w2 << (64 - sh);
+    return v;
+}
+
+template <int DIMS>
+__global__ void __launch_bounds__(DEC_THREADS) dec_kernel(const uint32_t* __restrict__ in, const long long* base_word,
+                                                          long long cap_words, Geo G, CodecView v,
+                                                          float* __restrict__ x, int* err)
+{
+    constexpr int V = Cfg<DIMS>::V;
+    constexpr Perm P = make_perm(DIMS);
+    const long long b = (long long)blockIdx.x * DEC_THREADS + threadIdx.x;
+    const int lane = threadIdx.x & 31;
+    const long long c = b / CHUNK;
+    if (c >= G.nchunks) return;                    // whole warp
+    const long long base = *base_word;
+    if (base < 0 || base + G.table_words > cap_words) {
+        if (lane == 0) atomicOr(err, 4);
+        return;
+    }
+    const uint32_t* hdr = in + base;
+    if (hdr[0] != MAGIC || hdr[1] != ((uint32_t)G.dims | (VERSION << 8)) || hdr[2] != (uint32_t)G.nz ||
+        hdr[3] != (uint32_t)G.ny || hdr[4] != (uint32_t)G.nx || hdr[5] != (uint32_t)G.nblocks ||
+        hdr[6] != (uint32_t)G.nchunks || base + G.table_words + (long long)hdr[7] > cap_words) {
+        if (lane == 0) atomicOr(err, 4);
+        return;
+    }
+    const long long pw = hdr[7];
+    const uint32_t* payload = hdr + G.table_words;
+    const uint16_t* sizes = reinterpret_cast<const uint16_t*>(hdr + HDR + G.nchunks);
+    const bool valid = b < G.nblocks;
+    const int nbits = valid ? sizes[b] : 0;
+    int incl = nbits;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += t;
+    }
+    if (!valid) return;
+    const long long start = (long long)hdr[HDR + c] * 32 + (incl - nbits);
+    const long long end = start + nbits;
+    if (end > pw * 32) {
+        atomicOr(err, 4);
+        return;
+    }
+    long long pos = start;
+    bool corrupt = false;
+    float f[V];
+    const unsigned long long h0 = peek64(payload, pos, pw);
+    if (!(h0 & 1ull)) {
+        pos += 1;
+#pragma unroll
+        for (int i = 0; i < V; ++i) f[i] = 0.0f;
+    } else if (h0 & 2ull) {
+        pos += 2;
+#pragma unroll
+        for (int i = 0; i < V; ++i) {
+            f[i] = __uint_as_float((uint32_t)peek64(payload, pos, pw));
+            pos += 32;
+        }
+    } else {
+        const int emax = (int)((h0 >> 2) & 0xFFu) - 127;
+        const int ptop = (int)((h0 >> 10) & 31u);
+        const int pbot = (int)((h0 >> 15) & 31u);
+        pos += 20;
+        if (emax < -126 || emax > 127 || pbot > ptop) corrupt = true;
+        uint32_t nb[V];
+#pragma unroll
+        for (int r = 0; r < V; ++r) nb[r] = 0u;
+        int s = 0;
+        for (int p = ptop; p >= pbot && !corrupt; --p) {
+            unsigned long long W = 0;
+            if (s > 0) {
+                W = peek64(payload, pos, pw) & low_mask(s);
+                pos += s;
+            }
+            while (s < V) {
+                const unsigned long long t = peek64(payload, pos, pw);
+                pos += 1;
+                if (!(t & 1ull)) break;
+                const unsigned long long look = peek64(payload, pos, pw);
+                if (look == 0ull) { corrupt = true; break; }
+                const int z = __ffsll((long long)look) - 1;
+                if (s + z >= V) { corrupt = true; break; }
+                W |= 1ull << (s + z);
+                pos += z + 1;
+                s += z + 1;
+            }
+            if (pos > end) corrupt = true;
+#pragma unroll
+            for (int r = 0; r < V; ++r) nb[r] |= (uint32_t)((W >> r) & 1ull) << p;
+        }
+        int32_t t[V];
+#pragma unroll
+        for (int r = 0; r < V; ++r) t[P.p[r]] = unnega(nb[r]);
+        xform_inv<DIMS>(t);
+        const float sc = pow2f(max(emax - 23, -126));
+#pragma unroll
+        for (int i = 0; i < V; ++i) f[i] = __fmul_rn(__int2float_rn(t[i]), sc);
+    }
+    if (corrupt || pos != end) {
+        atomicOr(err, 4);
+        return;
+    }
+    // scatter the valid part of the block
+    const BlockPos bp = block_pos(G, b);
+    const int xs = 4 * bp.bx;
+    const bool vec = v.aligned && xs + 3 < v.nx;
+    constexpr int ROWS = DIMS == 3 ? 16 : 4;
+#pragma unroll
+    for (int r = 0; r < ROWS; ++r) {
+        const int z = 4 * bp.bz + (DIMS == 3 ? r / 4 : r);
+        const int y = DIMS == 3 ? 4 * bp.by + r % 4 : 0;
+        if (z >= v.nz || y >= v.ny) continue;
+        float* row = x + (long long)z * v.pz + (long long)y * v.py;
+        if (vec) {
+            *reinterpret_cast<float4*>(row + xs) = make_float4(f[4 * r], f[4 * r + 1], f[4 * r + 2], f[4 * r + 3]);
+        } else {
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+                if (xs + q < v.nx) row[xs + q] = f[4 * r + q];
+        }
+    }
+}
+
+}  // namespace
+
+long long codec_bound_words(int dims, int nz, int ny, int nx)
+{
+    const Geo G = make_geo(dims, nz, ny, nx);
+    const long long per_chunk = dims == 3 ? (CHUNK * Cfg<3>::MAXBITS + 31) / 32 : (CHUNK * Cfg<2>::MAXBITS + 31) / 32;
+    return G.table_words + G.nchunks * per_chunk;
+}
+
+long long codec_scratch_bytes(int dims, int nz, int ny, int nx)
+{
+    const Geo G = make_geo(dims, nz, ny, nx);
+    const long long w = dims == 3 ? Cfg<3>::MAXW : Cfg<2>::MAXW;
+    return (G.nblocks + CHUNK) * w * 4;
+}
+
+cudaError_t codec_compress_dev(const float* x, const CodecView& v, float tol_f, uint32_t* out,
+                               const long long* base_word, long long cap_words, long long* next_word,
+                               void* scratch, int* err, unsigned long long* stat_words, cudaStream_t s)
+{
+    const Geo G = make_geo(v.dims, v.nz, v.ny, v.nx);
+    uint32_t* sc = static_cast<uint32_t*>(scratch);
+    const unsigned eb = (unsigned)((G.nblocks + ENC_THREADS - 1) / ENC_THREADS);
+    const unsigned cb = (unsigned)((G.nchunks + CMP_WARPS - 1) / CMP_WARPS);
+    if (v.dims == 3) {
+        enc_kernel<3><<<eb, ENC_THREADS, 0, s>>>(x, v, G, tol_f, sc, out, base_word, cap_words, err);
+        scan_kernel<<<1, 1024, 0, s>>>(out, base_word, cap_words, next_word, G, tol_f, err, stat_words);
+        compact_kernel<3><<<cb, CMP_WARPS * 32, 0, s>>>(out, base_word, next_word, G, sc, err);
+    } else {
+        enc_kernel<2><<<eb, ENC_THREADS, 0, s>>>(x, v, G, tol_f, sc, out, base_word, cap_words, err);
+        scan_kernel<<<1, 1024, 0, s>>>(out, base_word, cap_words, next_word, G, tol_f, err, stat_words);
+        compact_kernel<2><<<cb, CMP_WARPS * 32, 0, s>>>(out, base_word, next_word, G, sc, err);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t codec_decompress_dev(const uint32_t* in, const long long* base_word, long long cap_words,
+                                 const CodecView& v, float* x, int* err, cudaStream_t s)
+{
+    const Geo G = make_geo(v.dims, v.nz, v.ny, v.nx);
+    const unsigned db = (unsigned)((G.nchunks * CHUNK + DEC_THREADS - 1) / DEC_THREADS);
+    if (v.dims == 3)
+        dec_kernel<3><<<db, DEC_THREADS, 0, s>>>(in, base_word, cap_words, G, v, x, err);
+    else
+        dec_kernel<2><<<db, DEC_THREADS, 0, s>>>(in, base_word, cap_words, G, v, x, err);
+    return cudaGetLastError();
+}
+
+}  // namespace ckfwi

@@ -1,0 +1,140 @@
+// Internal declarations of the ckfwi library (not part of the C-ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+
+namespace ckfwi {
+
+constexpr int MAXK = 8;          // half space order, space orders 2..16
+
+// Padded field layout.  Every wavefield carries H zero cells beyond each
+// face of the total grid in z (and y in 3D) and at least H in x; those
+// cells are never written, so they act as the zero Dirichlet values the
+// Laplacian reads outside the grid.  Pointers handed to kernels are
+// "origin based": element (z, y, x) of the total grid sits at
+// p[z * pxy + y * px + x].  The first interior column is 16-byte aligned.
+struct FieldGeom {
+    int dims;
+    int nz, ny, nx;     // total grid
+    int H;              // halo depth in z (and y in 3D)
+    int X0;             // x offset of column 0 inside a row (multiple of 4, >= H)
+    long long px;       // row pitch [floats], multiple of 32
+    long long pxy;      // plane pitch [floats]
+    long long origin;   // offset of element (0,0,0) from the allocation start
+    long long alloc;    // floats per field allocation
+    long long npts;     // nz * ny * nx
+};
+
+FieldGeom make_geom(int dims, int nz, int ny, int nx, int H);
+
+// Point sources on the grid, gathered through a CSR map over a bounding box:
+// at a grid point inside the box, value = sum_e wt[e] * series[col[e]] over
+// e in rowptr[b] .. rowptr[b+1]-1, b the point's index inside the box.
+// A deterministic gather (no atomics), so every launch rounds identically.
+struct Inj {
+    int on;
+    int z0, z1, y0, y1, x0, x1;   // half-open box in total-grid indices
+    const int* rowptr;
+    const int* col;
+    const float* wt;
+    const float* series;          // this step's values (already offset)
+};
+
+// Receiver sampling d_r = sum_i wt[r][i] * u[idx[r][i]] (multilinear weights).
+struct Sample {
+    int n;                        // receivers, 0 = off
+    int nst;                      // 4 (2D) or 8 (3D)
+    const long long* idx;         // origin-based offsets [n][nst]
+    const float* wt;              // [n][nst]
+    float* out;                   // [n]
+};
+
+// Forward OT2 step: a u^{n+1} = 2u^n - b u^{n-1} + w (lap u^n + Q^T s^n).
+struct FwdArgs {
+    FieldGeom g;
+    const float* u;       // u^n
+    const float* up;      // u^{n-1}
+    const float* w;       // dt^2 c^2
+    float* out;           // u^{n+1}
+    const float* eta;     // damping tables: eta_z[nz], eta_y[ny], eta_x[nx]
+    float hdt;            // dt / 2
+    float c[MAXK + 1];    // c[0] = dims * c0 / h^2, c[j] = c_j / h^2
+    int zlen;             // z planes per CTA
+    Inj src;
+    Sample smp;
+    void* ck_u;           // fused takeshot outputs (see CkMode)
+    void* ck_up;
+    int* err;             // error flags (bit 0: FP16 overflow)
+};
+
+// Fused reverse step:
+//   a lam^{j-1} = 2 lam^j - b lam^{j+1} + w (lap lam^j - P^T r^j)
+//   gacc += lam^{j-1} * (lap u^{j-1} + Q^T s^{j-1})
+struct AdjArgs {
+    FieldGeom g;
+    const float* l1;      // lam^j
+    const float* l2;      // lam^{j+1}
+    float* l0;            // lam^{j-1}
+    const void* u;        // u^{j-1}, element type per template
+    const float* w;
+    float* gacc;
+    const float* eta;
+    float hdt;
+    float c[MAXK + 1];
+    int zlen;
+    Inj adj;              // -P^T r^j  (weights carry the minus sign)
+    Inj src;              // Q^T s^{j-1}
+};
+
+enum CkMode { CK_NONE = 0, CK_FP32 = 1, CK_BF16 = 2, CK_FP16 = 3 };
+enum UType { U_FP32 = 0, U_BF16 = 1, U_FP16 = 2 };
+
+struct Tile {
+    int bx, by;           // CTA shape (by = 1 in 2D)
+    int zlen;             // z planes per CTA
+};
+
+// kernels.cu
+cudaError_t launch_fwd(const FwdArgs& a, const Tile& t, int K, int ck, cudaStream_t s);
+cudaError_t launch_adj(const AdjArgs& a, const Tile& t, int K, int utype, cudaStream_t s);
+bool tile_supported(int dims, const Tile& t);
+int tile_count(int dims);
+Tile tile_at(int dims, int i, int zlen);
+
+// aux.cu
+cudaError_t launch_sample(const float* u, const Sample& smp, cudaStream_t s);
+cudaError_t launch_residual(const float* d, const float* dobs, float* r, int rows, int nrec,
+                            double* partials, int nparts, double* phi, cudaStream_t s);
+cudaError_t launch_to_padded_w(const float* dense, int kind, float dt, const FieldGeom& g,
+                               float* w_origin, float* c2_dense, int* err, cudaStream_t s);
+cudaError_t launch_grad_out(const float* gacc_origin, const float* c2_dense, int kind,
+                            const FieldGeom& g, float* out_dense, cudaStream_t s);
+cudaError_t launch_grad_out_f64(const float* gacc_origin, const float* c2_dense, int kind,
+                                const FieldGeom& g, double* sum, double* comp,
+                                cudaStream_t s);
+cudaError_t launch_cast_restore(const void* src, int utype, const FieldGeom& g,
+                                float* dst_origin, cudaStream_t s);
+cudaError_t launch_copy_f64(const double* a, double* b, long long n, cudaStream_t s);
+cudaError_t launch_add_f64(const double* a, const double* b, double* out, long long n, cudaStream_t s);
+
+// codec.cu
+struct CodecView {       // a float field to (de)compress, origin based
+    int dims, nz, ny, nx;
+    long long py, pz;    // pitches [floats] of y rows and z planes
+    bool aligned;        // rows 16-byte aligned with a multiple-of-4 pitch
+};
+long long codec_bound_words(int dims, int nz, int ny, int nx);
+long long codec_scratch_bytes(int dims, int nz, int ny, int nx);
+// Compress into `out` at word offset read from *base_word (device), checking
+// against cap_words; writes *next_word = base + stream length (device) and
+// raises err bits: 1 NONFINITE, 2 OVERFLOW.
+cudaError_t codec_compress_dev(const float* x, const CodecView& v, float tol_f,
+                               uint32_t* out, const long long* base_word, long long cap_words,
+                               long long* next_word, void* scratch, int* err,
+                               unsigned long long* stat_words, cudaStream_t s);
+cudaError_t codec_decompress_dev(const uint32_t* in, const long long* base_word,
+                                 long long cap_words, const CodecView& v, float* x, int* err,
+                                 cudaStream_t s);
+
+}  // namespace ckfwi

@@ -1,0 +1,279 @@
+"""GPU parity of the CUDA path against the FP64 oracle, through the C-ABI.
+
+Tolerances: receiver data rel-L2 <= 1e-5 and uncompressed gradient rel-L2
+<= 1e-4 against the FP64 oracle (FP32 arithmetic on the GPU); with
+compression off, every checkpointed gradient is bitwise the store-all
+gradient (the schedule changes cost, never values: Sec. 3); codec streams
+are bitwise the oracle's on identical float input.  Sizes span several
+CTA tiles with ragged tails in every axis.
+"""
+import numpy as np
+import pytest
+
+from oracle import codec as OC
+from oracle import propagator as O
+
+from gpu_cases import make_case, rel_l2
+
+torch = pytest.importorskip("torch")
+C = pytest.importorskip("paper_1810_05268_gb300.ckfwi")
+
+pytestmark = pytest.mark.gpu
+
+CASES = {
+    (2, 2): dict(shape=(61, 77), nbl=8, nt=240),
+    (2, 4): dict(shape=(57, 83), nbl=10, nt=260),
+    (2, 8): dict(shape=(66, 131), nbl=12, nt=260),
+    (2, 16): dict(shape=(70, 141), nbl=12, nt=240),
+    (3, 2): dict(shape=(29, 35, 45), nbl=6, nt=120),
+    (3, 4): dict(shape=(33, 37, 41), nbl=6, nt=120),
+    (3, 8): dict(shape=(35, 43, 70), nbl=8, nt=120),
+    (3, 16): dict(shape=(41, 46, 53), nbl=8, nt=100),
+}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_1810_05268_gb300 import build
+    build.build()
+    assert torch.cuda.is_available()
+
+
+def _model(case):
+    m = C.Model(case.pg)
+    m.set_model(torch.from_numpy(case.vel).cuda())
+    return m
+
+
+def _oracle_data(case, vel=None):
+    v = case.vel.astype(np.float64) if vel is None else vel
+    return O.forward(case.og, v, [case.src], case.oracle_series(), case.rec)
+
+
+@pytest.mark.parametrize("dims,so", sorted(CASES))
+def test_receivers_match_oracle(dims, so):
+    case = make_case(dims, so, **CASES[(dims, so)], seed=dims * 100 + so)
+    m = _model(case)
+    d = m.forward_shot(case.shot()).cpu().numpy()
+    ref = _oracle_data(case)
+    assert np.all(d[0] == 0)
+    err = rel_l2(d, ref)
+    assert err <= 1e-5, err
+    # host buffers through the same C-ABI call give the same numbers
+    dh = np.zeros_like(d)
+    m.forward_shot(case.shot(), d_sim=dh)
+    assert np.array_equal(dh, d)
+
+
+def _obs(case):
+    # observed data from a perturbed true model (oracle), rounded to float32
+    true = case.vel.astype(np.float64) * 1.03
+    return O.forward(case.og, true, [case.src], case.oracle_series(), case.rec).astype(np.float32)
+
+
+@pytest.mark.parametrize("dims,so", sorted(CASES))
+def test_gradient_store_all_matches_oracle(dims, so):
+    case = make_case(dims, so, **CASES[(dims, so)], seed=dims * 100 + so + 1)
+    dobs = _obs(case)
+    phi_ref, g_ref, _ = O.gradient(case.og, case.vel.astype(np.float64), [case.src], case.oracle_series(),
+                                   case.rec, dobs.astype(np.float64))
+    m = _model(case)
+    phi, g, st = m.adjoint_gradient(case.shot(), torch.from_numpy(dobs).cuda(), ckpt_slots=case.pg.nt)
+    g = g.cpu().numpy()
+    assert abs(phi - phi_ref) <= 1e-5 * phi_ref, (phi, phi_ref)
+    err = rel_l2(g, g_ref)
+    assert err <= 1e-4, err
+    assert st["fwd_steps"] == case.pg.nt and st["adj_steps"] == case.pg.nt
+
+
+@pytest.mark.parametrize("dims,so,slots", [(2, 4, 1), (2, 4, 2), (2, 8, 7), (3, 8, 3), (3, 8, 20),
+                                           (3, 16, 5), (3, 2, 2)])
+def test_checkpointed_bitwise_equals_store_all(dims, so, slots):
+    case = make_case(dims, so, **CASES[(dims, so)], seed=7)
+    dobs = torch.from_numpy(_obs(case)).cuda()
+    m = _model(case)
+    phi_a, g_a, st_a = m.adjoint_gradient(case.shot(), dobs, ckpt_slots=case.pg.nt)
+    phi_b, g_b, st_b = m.adjoint_gradient(case.shot(), dobs, ckpt_slots=slots)
+    assert phi_a == phi_b
+    assert torch.equal(g_a, g_b)
+    from oracle import revolve as R
+    assert st_b["p"] == R.p_closed(case.pg.nt, slots)
+    assert st_b["fwd_steps"] == st_b["p"] + 1
+
+
+def test_velocity_gradient_and_host_buffers():
+    case = make_case(2, 8, **CASES[(2, 8)], seed=3)
+    dobs = _obs(case)
+    m = _model(case)
+    phi_m, g_m, _ = m.adjoint_gradient(case.shot(), torch.from_numpy(dobs).cuda(), 9, grad_kind=C.SLOWNESS2)
+    phi_c, g_c, _ = m.adjoint_gradient(case.shot(), dobs, 9, grad_kind=C.VELOCITY)
+    c = case.vel.astype(np.float64)
+    # dphi/dc = dphi/dm * (-2 / c^3)
+    assert phi_m == phi_c
+    assert rel_l2(g_c, g_m.cpu().numpy() * (-2.0 / c ** 3)) < 1e-6
+
+
+def test_cuda_graph_replay_is_bitwise():
+    case = make_case(3, 4, **CASES[(3, 4)], seed=11)
+    dobs = torch.from_numpy(_obs(case)).cuda()
+    m = _model(case)
+    _, g0, _ = m.adjoint_gradient(case.shot(), dobs, ckpt_slots=6)
+    g0 = g0.clone()
+    _, g1, _ = m.adjoint_gradient(case.shot(), dobs, ckpt_slots=6, use_graph=True)
+    g1 = g1.clone()
+    _, g2, _ = m.adjoint_gradient(case.shot(), dobs, ckpt_slots=6, use_graph=True)
+    assert torch.equal(g0, g1) and torch.equal(g1, g2)
+
+
+@pytest.mark.parametrize("mode", ["bf16", "fp16"])
+def test_half_precision_checkpoints(mode):
+    case = make_case(3, 8, **CASES[(3, 8)], seed=21)
+    dobs = _obs(case)
+    _, g_ref, _ = O.gradient(case.og, case.vel.astype(np.float64), [case.src], case.oracle_series(),
+                             case.rec, dobs.astype(np.float64))
+    m = _model(case)
+    dd = torch.from_numpy(dobs).cuda()
+    _, g32, _ = m.adjoint_gradient(case.shot(), dd, ckpt_slots=5)
+    _, gh, st = m.adjoint_gradient(case.shot(), dd, ckpt_slots=5, store_mode=mode)
+    e32 = rel_l2(g32.cpu().numpy(), g_ref)
+    eh = rel_l2(gh.cpu().numpy(), g_ref)
+    print("%s checkpoints: gradient rel-L2 vs oracle %.3e (fp32 %.3e)" % (mode, eh, e32))
+    assert eh < 5e-2
+    assert st["p"] > 0
+
+
+def _field(dims, shape, seed):
+    rng = np.random.default_rng(seed)
+    if dims == 3:
+        z, y, x = np.meshgrid(*[np.linspace(0, 2, n) for n in shape], indexing="ij")
+        f = np.sin(3 * z + 1) * np.cos(2 * y) * np.sin(4 * x) + 0.05 * rng.standard_normal(shape)
+    else:
+        z, x = np.meshgrid(*[np.linspace(0, 2, n) for n in shape], indexing="ij")
+        f = np.sin(3 * z + 1) * np.cos(5 * x) + 0.05 * rng.standard_normal(shape)
+    f[tuple(slice(0, max(1, n // 3)) for n in shape)] = 0.0       # zero blocks
+    return (f * 1e-2).astype(np.float32)
+
+
+@pytest.mark.parametrize("dims,shape", [(3, (9, 10, 11)), (3, (32, 36, 40)), (3, (17, 70, 129)),
+                                        (2, (37, 29)), (2, (64, 256)), (2, (101, 7))])
+@pytest.mark.parametrize("rel", [1e-2, 1e-4, 1e-6])
+def test_codec_streams_bitwise_vs_oracle(dims, shape, rel):
+    x = _field(dims, shape, seed=len(shape) * 7 + shape[0])
+    tol = rel * float(np.abs(x).max())
+    ref, _ = OC.compress(x, tol)
+    words, nf = C.codec_compress(torch.from_numpy(x).cuda(), tol)
+    got = words.cpu().numpy().view(np.uint32)
+    assert not nf
+    assert got.size == ref.size
+    assert np.array_equal(got, ref)
+    y = C.codec_decompress(words, shape).cpu().numpy()
+    assert np.array_equal(y.view(np.uint32), OC.decompress(ref, shape).view(np.uint32))
+    assert np.all(np.abs(y.astype(np.float64) - x) <= tol)
+
+
+def test_codec_overlong_blocks_fall_back_to_raw_bitwise():
+    rng = np.random.default_rng(12)
+    z, y, x = np.meshgrid(*[np.arange(12)] * 3, indexing="ij")
+    cb = np.where((z + y + x) % 2 == 0, 1.99, -1.99)
+    xf = (cb + 1e-3 * rng.standard_normal(cb.shape)).astype(np.float32)
+    ref, _ = OC.compress(xf, 4.0 * 2.0 ** -23)
+    words, _ = C.codec_compress(torch.from_numpy(xf).cuda(), 4.0 * 2.0 ** -23)
+    assert np.array_equal(words.cpu().numpy().view(np.uint32), ref)
+
+
+def test_codec_wavefield_and_raw_blocks_bitwise():
+    case = make_case(3, 8, **CASES[(3, 8)], seed=4)
+    _, u = O.forward(case.og, case.vel.astype(np.float64), [case.src], case.oracle_series(), case.rec,
+                     want_final=True)
+    u = u.astype(np.float32)
+    for tol in (1e-3 * np.abs(u).max(), 1e-6 * np.abs(u).max(), 2.0 ** -80):
+        ref, _ = OC.compress(u, tol)
+        words, _ = C.codec_compress(torch.from_numpy(u).cuda(), tol)
+        assert np.array_equal(words.cpu().numpy().view(np.uint32), ref)
+
+
+def test_codec_gradient_error_is_bounded_and_stated():
+    case = make_case(3, 8, **CASES[(3, 8)], seed=5)
+    dobs = _obs(case)
+    _, g_ref, _ = O.gradient(case.og, case.vel.astype(np.float64), [case.src], case.oracle_series(),
+                             case.rec, dobs.astype(np.float64))
+    m = _model(case)
+    dd = torch.from_numpy(dobs).cuda()
+    _, u = O.forward(case.og, case.vel.astype(np.float64), [case.src], case.oracle_series(), case.rec,
+                     want_final=True)
+    umax = float(np.abs(u).max())
+    errs = []
+    for rel in (1e-2, 1e-4, 1e-6):
+        _, g, st = m.adjoint_gradient(case.shot(), dd, ckpt_slots=8, store_mode="codec", tol=rel * umax,
+                                      pool_bytes=64 << 20)
+        e = rel_l2(g.cpu().numpy(), g_ref)
+        errs.append(e)
+        print("codec tol %.0e*max|u|: gradient rel-L2 %.3e, ratio mean %.1f min %.1f" %
+              (rel, e, st["ratio_mean"], st["ratio_min"]))
+        assert st["ratio_min"] > 1.0
+    assert errs[-1] < 1e-3
+    assert errs[0] > errs[-1]
+
+
+def test_errors_are_reported():
+    case = make_case(2, 4, **CASES[(2, 4)], seed=1)
+    m = C.Model(case.pg)
+    bad = case.vel.copy()
+    bad[3, 4] = np.nan
+    with pytest.raises(C.CkfwiError) as e:
+        m.set_model(bad)
+    assert e.value.status == C.NONFINITE
+    bad[3, 4] = -1.0
+    with pytest.raises(C.CkfwiError) as e:
+        m.set_model(bad)
+    assert e.value.status == C.EINVAL
+    m.set_model(case.vel)
+    far = C.ShotSpec(src=(1e6, 0.0, 10.0), rec=case.rec, f0=case.f0)
+    with pytest.raises(C.CkfwiError) as e:
+        m.forward_shot(far)
+    assert e.value.status == C.EINVAL
+    dobs = _obs(case)
+    # a pool far too small for the compressed checkpoints
+    with pytest.raises(C.CkfwiError) as e:
+        m.adjoint_gradient(case.shot(), dobs, ckpt_slots=6, store_mode="codec", tol=1e-9, pool_bytes=4096)
+    assert e.value.status == C.POOL_OVERFLOW
+    # FP16 checkpoints of a wavefield beyond the FP16 range
+    loud = C.ShotSpec(src=case.src, rec=case.rec, f0=case.f0, t0=case.t0, amp=1e9)
+    with pytest.raises(C.CkfwiError) as e:
+        m.adjoint_gradient(loud, dobs, ckpt_slots=6, store_mode="fp16")
+    assert e.value.status == C.NONFINITE
+    # unstable time step rejected at creation
+    g = C.GridSpec(2, (40, 40), 5, 10.0, 8, 10.0, 10, 3.0)
+    with pytest.raises(C.CkfwiError) as e:
+        C.create_model(g)
+    assert e.value.status == C.EINVAL
+
+
+def test_corrupt_stream_detected():
+    x = _field(3, (16, 20, 24), seed=2)
+    words, _ = C.codec_compress(torch.from_numpy(x).cuda(), 1e-5)
+    bad = words.clone()
+    bad[0] ^= 1
+    with pytest.raises(C.CkfwiError) as e:
+        C.codec_decompress(bad, x.shape)
+    assert e.value.status == C.CORRUPT
+    bad = words.clone()
+    nchunks = int(words[6].item())
+    bad[16 + nchunks] += 1                       # first block's size off by one
+    with pytest.raises(C.CkfwiError) as e:
+        C.codec_decompress(bad, x.shape)
+    assert e.value.status == C.CORRUPT
+
+
+@pytest.mark.parametrize("nt", [1, 2, 3])
+def test_tiny_time_axis(nt):
+    case = make_case(2, 4, shape=(30, 34), nbl=4, nt=nt, seed=9)
+    dobs = np.zeros((nt + 1, case.rec.shape[0]), np.float32)
+    dobs[1:] = 1e-3
+    phi_ref, g_ref, _ = O.gradient(case.og, case.vel.astype(np.float64), [case.src], case.oracle_series(),
+                                   case.rec, dobs.astype(np.float64))
+    m = _model(case)
+    for slots in (1, 2, nt):
+        phi, g, _ = m.adjoint_gradient(case.shot(), torch.from_numpy(dobs).cuda(), ckpt_slots=slots)
+        assert abs(phi - phi_ref) <= 1e-5 * phi_ref
+        assert rel_l2(g.cpu().numpy(), g_ref) < 1e-4

@@ -116,6 +116,9 @@ typedef struct ckfwi_grad_opts {
     int grad_kind;       /* CKFWI_VELOCITY or CKFWI_SLOWNESS2 */
     int use_graph;       /* 1: record the gradient as a CUDA graph on the first
                             call with this configuration and replay it after */
+    int profile;         /* 1: time every kernel class with CUDA events on the
+                            stream (fills the *_ms fields of ckfwi_stats); not
+                            combined with use_graph */
 } ckfwi_grad_opts;
 
 typedef struct ckfwi_stats {
@@ -128,7 +131,10 @@ typedef struct ckfwi_stats {
     double pool_bytes_peak;  /* device bytes of checkpoint storage in use, peak */
     double ratio_min;        /* CODEC: smallest and mean compression ratio */
     double ratio_mean;
-    double u_absmax;         /* max |u| over the stored checkpoints (CODEC) */
+    double u_absmax;         /* reserved (0) */
+    /* with opts->profile: device time [ms] and launches per kernel class */
+    double fwd_ms, adj_ms, comp_ms, decomp_ms, other_ms;
+    long long fwd_launches, adj_launches, comp_calls, decomp_calls;
 } ckfwi_stats;
 
 typedef struct ckfwi_model ckfwi_model;

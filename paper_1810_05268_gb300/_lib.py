@@ -29,7 +29,8 @@ class Shot(ctypes.Structure):
 
 class GradOpts(ctypes.Structure):
     _fields_ = [("ckpt_slots", ctypes.c_int), ("store_mode", ctypes.c_int), ("tol", ctypes.c_double),
-                ("pool_bytes", ctypes.c_size_t), ("grad_kind", ctypes.c_int), ("use_graph", ctypes.c_int)]
+                ("pool_bytes", ctypes.c_size_t), ("grad_kind", ctypes.c_int), ("use_graph", ctypes.c_int),
+                ("profile", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
@@ -37,7 +38,10 @@ class Stats(ctypes.Structure):
                 ("takeshots", ctypes.c_longlong), ("restores", ctypes.c_longlong),
                 ("kernel_launches", ctypes.c_longlong), ("pool_bytes_peak", ctypes.c_double),
                 ("ratio_min", ctypes.c_double), ("ratio_mean", ctypes.c_double),
-                ("u_absmax", ctypes.c_double)]
+                ("u_absmax", ctypes.c_double), ("fwd_ms", ctypes.c_double), ("adj_ms", ctypes.c_double),
+                ("comp_ms", ctypes.c_double), ("decomp_ms", ctypes.c_double), ("other_ms", ctypes.c_double),
+                ("fwd_launches", ctypes.c_longlong), ("adj_launches", ctypes.c_longlong),
+                ("comp_calls", ctypes.c_longlong), ("decomp_calls", ctypes.c_longlong)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

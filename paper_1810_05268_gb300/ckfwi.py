@@ -161,7 +161,7 @@ def _alloc(shape, dtype, device):
     return np.empty(shape, dtype=dtype)
 
 
-def _opts(ckpt_slots, store_mode, tol, pool_bytes, grad_kind, use_graph):
+def _opts(ckpt_slots, store_mode, tol, pool_bytes, grad_kind, use_graph, profile=False):
     o = GradOpts()
     o.ckpt_slots = int(ckpt_slots)
     o.store_mode = STORE_NAMES.get(store_mode, store_mode) if isinstance(store_mode, str) else int(store_mode)
@@ -169,11 +169,13 @@ def _opts(ckpt_slots, store_mode, tol, pool_bytes, grad_kind, use_graph):
     o.pool_bytes = int(pool_bytes)
     o.grad_kind = int(grad_kind)
     o.use_graph = int(bool(use_graph))
+    o.profile = int(bool(profile))
     return o
 
 
 def adjoint_gradient(model, grid: GridSpec, shot: ShotSpec, d_obs, ckpt_slots, store_mode=STORE_FP32,
-                     tol=0.0, pool_bytes=0, grad_kind=SLOWNESS2, use_graph=False, grad=None, stream=None):
+                     tol=0.0, pool_bytes=0, grad_kind=SLOWNESS2, use_graph=False, grad=None, stream=None,
+                     profile=False):
     """(misfit, gradient on the total grid, stats dict)."""
     pd, mem = _buf(d_obs, np.float32)
     if grad is None:
@@ -182,7 +184,7 @@ def adjoint_gradient(model, grid: GridSpec, shot: ShotSpec, d_obs, ckpt_slots, s
     if memg != mem:
         raise ValueError("d_obs and grad must both be host or both be device buffers")
     s = shot.c()
-    o = _opts(ckpt_slots, store_mode, tol, pool_bytes, grad_kind, use_graph)
+    o = _opts(ckpt_slots, store_mode, tol, pool_bytes, grad_kind, use_graph, profile)
     phi = ctypes.c_double(0.0)
     st = Stats()
     _check(lib().ckfwi_adjoint_gradient(model, ctypes.byref(s), pd, mem, ctypes.byref(o), ctypes.byref(phi), pg,

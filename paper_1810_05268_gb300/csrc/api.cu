@@ -250,6 +250,7 @@ struct ckfwi_model {
     DevMem traj;                    // store-all trajectory
     DevMem pool;                    // checkpoint pool
     size_t pool_cap_bytes = 0;
+    int pool_tag = -1;              // storage mode whose layout the pool holds
     DevMem slotbase;                // codec: device word offsets of slots
     DevMem scratch;                 // codec scratch
     DevMem flags;                   // int error flags
@@ -261,11 +262,17 @@ struct ckfwi_model {
     bool tuned = false;
     int nparts = 128;
     long long gen = 0;              // bumped whenever a buffer a graph uses moves
+    cudaStream_t cap = nullptr;     // non-blocking stream used only to record graphs
+    cudaEvent_t ev = nullptr;
+    std::vector<cudaEvent_t> evpool; // profiling events, reused across calls
     // graphs
     std::map<GraphKey, cudaGraphExec_t> graphs;
     ~ckfwi_model()
     {
         for (auto& kv : graphs) cudaGraphExecDestroy(kv.second);
+        if (cap) cudaStreamDestroy(cap);
+        if (ev) cudaEventDestroy(ev);
+        for (cudaEvent_t e : evpool) cudaEventDestroy(e);
     }
 };
 
@@ -415,10 +422,47 @@ int set_shot(ckfwi_model* m, const ckfwi_shot* s)
 }
 
 // ---------------------------------------------------------------- launches
+enum { PC_FWD = 0, PC_ADJ = 1, PC_COMP = 2, PC_DECOMP = 3, PC_OTHER = 4, PC_N = 5 };
+
+// Optional per-class device timing: an event pair around every launch group.
+struct Prof {
+    bool on = false;
+    std::vector<cudaEvent_t>* pool = nullptr;
+    std::vector<std::pair<int, int>> marks;   // (class, index of the start event)
+    size_t next = 0;
+    cudaEvent_t take()
+    {
+        if (next == pool->size()) {
+            cudaEvent_t e;
+            if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+            pool->push_back(e);
+        }
+        return (*pool)[next++];
+    }
+};
+
 struct Ctx {
     ckfwi_model* m;
     cudaStream_t st;
     long long launches = 0;
+    Prof prof;
+    long long count[PC_N] = {0, 0, 0, 0, 0};
+    int begin(int cls)
+    {
+        ++count[cls];
+        if (!prof.on) return -1;
+        cudaEvent_t e = prof.take();
+        cudaEvent_t f = prof.take();
+        if (!e || !f) return -1;
+        cudaEventRecord(e, st);
+        prof.marks.emplace_back(cls, (int)prof.next - 2);
+        return 0;
+    }
+    void end(int tok)
+    {
+        if (tok < 0 || !prof.on) return;
+        cudaEventRecord((*prof.pool)[prof.marks.back().second + 1], st);
+    }
 };
 
 FwdArgs fwd_args(ckfwi_model* m)
@@ -465,7 +509,9 @@ int fwd_step(Ctx& cx, const float* u, const float* up, float* out, int n, bool r
         }
     }
     (void)sep;
+    const int tok = cx.begin(PC_FWD);
     CK_TRY(launch_fwd(a, m->tf, m->K, ck, cx.st));
+    cx.end(tok);
     ++cx.launches;
     return CKFWI_OK;
 }
@@ -488,7 +534,9 @@ int adj_step(Ctx& cx, const float* l1, const float* l2, float* l0, const void* u
     a.adj.series = m->shot.resid.as<float>() + (size_t)j * m->shot.nrec;
     a.src = m->shot.src.view;
     a.src.series = m->shot.wavelet.as<float>() + (j - 1);
+    const int tok = cx.begin(PC_ADJ);
     CK_TRY(launch_adj(a, m->ta, m->K, utype, cx.st));
+    cx.end(tok);
     ++cx.launches;
     return CKFWI_OK;
 }
@@ -530,6 +578,7 @@ int autotune(ckfwi_model* m, cudaStream_t st)
     std::vector<Tile> cands;
     for (int i = 0; i < tile_count(f.dims); ++i) {
         Tile t0 = tile_at(f.dims, i, f.nz);
+        if (!tile_supported(f.dims, m->K, t0)) continue;
         const long long cols = (long long)((f.nx + t0.bx - 1) / t0.bx) * (f.dims == 3 ? (f.ny + t0.by - 1) / t0.by : 1);
         std::vector<int> zl;
         for (int target : {2, 4, 8, 16}) {
@@ -698,7 +747,10 @@ int run_body(Ctx& cx, const RunCfg& rc, const std::vector<Action>& acts, long lo
     long long* sb = m->slotbase.as<long long>();     // [0..M]: slot starts, [M+1..2M]: mids
     auto sbase = [&](int slot) { return sb + slot; };
     auto smid = [&](int slot) { return sb + (rc.M + 1) + slot; };
-    if (rc.mode == CKFWI_STORE_CODEC) CK_TRY(cudaMemsetAsync(sb, 0, sizeof(long long) * 2, cx.st));
+    if (rc.mode == CKFWI_STORE_CODEC) {
+        CK_TRY(cudaMemsetAsync(sb, 0, sizeof(long long) * 2, cx.st));
+        CK_TRY(cudaMemsetAsync(m->statw.p, 0, m->statw.bytes, cx.st));
+    }
     const CodecView cv = field_view(f);
     int* cerr = m->flags.as<int>() + 1;
     unsigned long long* sw = m->statw.as<unsigned long long>();
@@ -741,13 +793,17 @@ int run_body(Ctx& cx, const RunCfg& rc, const std::vector<Action>& acts, long lo
             cur_state = A.a + A.b;
         } else if (A.op == ACT_TAKESHOT) {
             if (rc.mode == CKFWI_STORE_CODEC) {
+                int tok = cx.begin(PC_COMP);
                 CK_TRY(codec_compress_dev(static_cast<const float*>(st.cur), cv, rc.tol_f, m->pool.as<uint32_t>(),
                                           sbase(A.b), rc.cap_words, smid(A.b), m->scratch.p, cerr, sw + ncomp,
                                           cx.st));
+                cx.end(tok);
                 ++ncomp;
+                tok = cx.begin(PC_COMP);
                 CK_TRY(codec_compress_dev(static_cast<const float*>(st.prev), cv, rc.tol_f, m->pool.as<uint32_t>(),
                                           smid(A.b), rc.cap_words, sbase(A.b + 1), m->scratch.p, cerr, sw + ncomp,
                                           cx.st));
+                cx.end(tok);
                 ++ncomp;
                 cx.launches += 6;
             }
@@ -760,10 +816,14 @@ int run_body(Ctx& cx, const RunCfg& rc, const std::vector<Action>& acts, long lo
             } else if (rc.mode == CKFWI_STORE_CODEC) {
                 float* a0 = org(m->work[0], f);
                 float* a1 = org(m->work[1], f);
+                int tok = cx.begin(PC_DECOMP);
                 CK_TRY(codec_decompress_dev(m->pool.as<uint32_t>(), sbase(A.b), rc.cap_words, cv, a0, cerr, cx.st));
+                cx.end(tok);
                 ++cx.launches;
                 if (!next_turn) {
+                    tok = cx.begin(PC_DECOMP);
                     CK_TRY(codec_decompress_dev(m->pool.as<uint32_t>(), smid(A.b), rc.cap_words, cv, a1, cerr, cx.st));
+                    cx.end(tok);
                     ++cx.launches;
                 }
                 st = State{a0, a1, U_FP32, U_FP32};
@@ -773,8 +833,10 @@ int run_body(Ctx& cx, const RunCfg& rc, const std::vector<Action>& acts, long lo
                 } else {
                     float* a0 = org(m->work[0], f);
                     float* a1 = org(m->work[1], f);
+                    const int tok = cx.begin(PC_DECOMP);
                     CK_TRY(launch_cast_restore(slot_ptr(A.b, 0), ut_slot, f, a0, cx.st));
                     CK_TRY(launch_cast_restore(slot_ptr(A.b, 1), ut_slot, f, a1, cx.st));
+                    cx.end(tok);
                     cx.launches += 2;
                     st = State{a0, a1, U_FP32, U_FP32};
                 }
@@ -817,11 +879,20 @@ int prepare_storage(ckfwi_model* m, RunCfg& rc, const ckfwi_grad_opts* o, const 
     }
     if (rc.M <= 1) return CKFWI_OK;
     const size_t nslot = (size_t)(rc.M - 1) * 2;
-    if (rc.mode == CKFWI_STORE_FP32) {
-        CK_TRY(m->pool.alloc(nslot * field_bytes(f, 4)));
-    } else if (rc.mode == CKFWI_STORE_BF16 || rc.mode == CKFWI_STORE_FP16) {
-        CK_TRY(m->pool.alloc(nslot * field_bytes(f, 2)));
+    // Uncompressed slots are read with their halo cells, which must hold 0;
+    // a pool last used with another layout is cleared before reuse.
+    const int tag = rc.mode == CKFWI_STORE_FP32 ? 4 : (rc.mode == CKFWI_STORE_CODEC ? 0 : 2);
+    if (rc.mode != CKFWI_STORE_CODEC) {
+        const size_t need = nslot * field_bytes(f, (size_t)tag);
+        const void* before_p = m->pool.p;
+        CK_TRY(m->pool.alloc(need));
+        if (m->pool.p == before_p && m->pool_tag != tag) {
+            CK_TRY(cudaMemset(m->pool.p, 0, m->pool.bytes));
+            CK_TRY(cudaDeviceSynchronize());
+        }
+        m->pool_tag = tag;
     } else {
+        m->pool_tag = 0;
         size_t bytes = o->pool_bytes ? o->pool_bytes : (size_t)(rc.M - 1) * 2 * f.npts * 4;
         bytes = (bytes + 3) / 4 * 4;
         CK_TRY(m->pool.alloc(bytes, false));
@@ -871,15 +942,26 @@ int gradient_one(ckfwi_model* m, const ckfwi_shot* s, const float* d_obs, int me
     if (!rc.store_all) revolve_schedule(rc.N, rc.M, acts, cnt);
     Ctx cx{m, st, 0};
     long long counters[2] = {0, 0};
-    const bool graph = o->use_graph != 0;
+    const bool graph = o->use_graph != 0 && !o->profile;
+    if (o->profile) {
+        cx.prof.on = true;
+        cx.prof.pool = &m->evpool;
+    }
     GraphKey key{rc.N, rc.M, rc.mode, o->grad_kind, rc.tol_f, (size_t)rc.cap_words, m->gen};
     if (graph) {
         auto it = m->graphs.find(key);
         if (it == m->graphs.end()) {
+            // record on a private non-blocking stream (the caller's may be the
+            // legacy stream, which cannot be captured); replay on the caller's
+            if (!m->cap) CK_TRY(cudaStreamCreateWithFlags(&m->cap, cudaStreamNonBlocking));
+            if (!m->ev) CK_TRY(cudaEventCreateWithFlags(&m->ev, cudaEventDisableTiming));
+            CK_TRY(cudaStreamSynchronize(st));
             cudaGraph_t gr;
-            CK_TRY(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
-            const int rs = run_body(cx, rc, acts, counters);
-            cudaError_t ee = cudaStreamEndCapture(st, &gr);
+            Ctx cc{m, m->cap, 0};
+            CK_TRY(cudaStreamBeginCapture(m->cap, cudaStreamCaptureModeRelaxed));
+            const int rs = run_body(cc, rc, acts, counters);
+            cx.launches = cc.launches;
+            cudaError_t ee = cudaStreamEndCapture(m->cap, &gr);
             if (rs != CKFWI_OK) {
                 if (ee == cudaSuccess) cudaGraphDestroy(gr);
                 return rs;
@@ -917,6 +999,23 @@ int gradient_one(ckfwi_model* m, const ckfwi_shot* s, const float* d_obs, int me
         stats->takeshots = rc.store_all ? rc.N - 1 : cnt[1];
         stats->restores = rc.store_all ? rc.N - 1 : cnt[2];
         stats->kernel_launches = cx.launches;
+        stats->fwd_launches = cx.count[PC_FWD];
+        stats->adj_launches = cx.count[PC_ADJ];
+        stats->comp_calls = cx.count[PC_COMP];
+        stats->decomp_calls = cx.count[PC_DECOMP];
+        if (cx.prof.on) {
+            double ms[PC_N] = {0, 0, 0, 0, 0};
+            for (auto& mk : cx.prof.marks) {
+                float t = 0.0f;
+                if (cudaEventElapsedTime(&t, m->evpool[mk.second], m->evpool[mk.second + 1]) == cudaSuccess)
+                    ms[mk.first] += t;
+            }
+            stats->fwd_ms = ms[PC_FWD];
+            stats->adj_ms = ms[PC_ADJ];
+            stats->comp_ms = ms[PC_COMP];
+            stats->decomp_ms = ms[PC_DECOMP];
+            stats->other_ms = ms[PC_OTHER];
+        }
         if (rc.store_all) stats->pool_bytes_peak = (double)field_bytes(f) * rc.N;
         else if (rc.mode == CKFWI_STORE_FP32) stats->pool_bytes_peak = (double)(rc.M - 1) * 2 * field_bytes(f, 4);
         else if (rc.mode != CKFWI_STORE_CODEC) stats->pool_bytes_peak = (double)(rc.M - 1) * 2 * field_bytes(f, 2);
@@ -964,7 +1063,7 @@ int ckfwi_create_model(const ckfwi_grid* g, ckfwi_model** out)
     double c[MAXK + 1];
     fd_weights(m->K, c);
     const double ih2 = 1.0 / (g->h * g->h);
-    m->c[0] = (float)(g->dims * c[0] * ih2);
+    m->c[0] = 0.0f;   // the difference-form Laplacian needs c_j, j >= 1, only
     for (int j = 1; j <= m->K; ++j) m->c[j] = (float)(c[j] * ih2);
     m->hdt = (float)(g->dt / 2.0);
     const FieldGeom& f = m->fg;
@@ -1175,6 +1274,7 @@ extern "C" int ckfwi_codec_compress(const float* x, int dims, int nz, int ny, in
     const size_t need = (size_t)codec_scratch_bytes(dims, nz, ny, nx);
     if (scr.bytes < need) CK_TRY(scr.alloc(need, false));
     CK_TRY(scal.alloc(64, true));
+    CK_TRY(cudaMemsetAsync(scal.p, 0, 64, st));
     CodecView v{};
     v.dims = dims; v.nz = nz; v.ny = ny; v.nx = nx;
     v.py = nx;
@@ -1206,6 +1306,7 @@ extern "C" int ckfwi_codec_decompress(const uint32_t* in, long long nwords, int 
     if (!g_codec_scal[dev]) g_codec_scal[dev] = new DevMem();
     DevMem& scal = *g_codec_scal[dev];
     CK_TRY(scal.alloc(64, true));
+    CK_TRY(cudaMemsetAsync(scal.p, 0, 64, st));
     CodecView v{};
     v.dims = dims; v.nz = nz; v.ny = ny; v.nx = nx;
     v.py = nx;

@@ -59,7 +59,7 @@ struct FwdArgs {
     float* out;           // u^{n+1}
     const float* eta;     // damping tables: eta_z[nz], eta_y[ny], eta_x[nx]
     float hdt;            // dt / 2
-    float c[MAXK + 1];    // c[0] = dims * c0 / h^2, c[j] = c_j / h^2
+    float c[MAXK + 1];    // c[j] = c_j / h^2 (j >= 1); c[0] unused
     int zlen;             // z planes per CTA
     Inj src;
     Sample smp;
@@ -98,7 +98,7 @@ struct Tile {
 // kernels.cu
 cudaError_t launch_fwd(const FwdArgs& a, const Tile& t, int K, int ck, cudaStream_t s);
 cudaError_t launch_adj(const AdjArgs& a, const Tile& t, int K, int utype, cudaStream_t s);
-bool tile_supported(int dims, const Tile& t);
+bool tile_supported(int dims, int K, const Tile& t);
 int tile_count(int dims);
 Tile tile_at(int dims, int i, int zlen);
 

@@ -1,0 +1,62 @@
+"""Kernel-level driver: forward modelling, a store-all gradient and a codec
+round trip on one synthetic 3D model, through the C-ABI.  Used for timing
+and ncu captures of single kernels on a chosen grid.
+
+  python -m paper_1810_05268_gb300.kbench --shape 256,256,256 --so 8 --nt 12
+"""
+import argparse
+import json
+import time
+
+import numpy as np
+import torch
+
+from . import build, synth
+from . import ckfwi as C
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--shape", default="256,256,256")
+    ap.add_argument("--so", type=int, default=8)
+    ap.add_argument("--nt", type=int, default=12)
+    ap.add_argument("--h", type=float, default=15.0)
+    ap.add_argument("--tol", type=float, default=1e-4)
+    ap.add_argument("--reps", type=int, default=3)
+    args = ap.parse_args()
+    build.build()
+    shape = tuple(int(v) for v in args.shape.split(","))
+    nbl = 20
+    vel = synth.extend(synth.grf(tuple(n - 2 * nbl for n in shape), 8.0, 5, 1.5, 4.5), nbl).astype(np.float32)
+    grid = C.GridSpec(3, shape, nbl, args.h, args.so, 1.0, args.nt, 4.5)
+    ext = [(n - 2 * nbl - 1) * args.h for n in shape]
+    rec = synth.receiver_grid(2 * args.h, np.linspace(0, ext[1], 32), np.linspace(0, ext[2], 32))
+    shot = C.ShotSpec(src=(2 * args.h, ext[1] / 2, ext[2] / 2), rec=rec, f0=0.02, t0=25.0)
+    m = C.Model(grid)
+    m.set_model(torch.from_numpy(vel).cuda())
+    out = {"shape": shape, "so": args.so, "nt": args.nt}
+    for _ in range(args.reps):
+        d = m.forward_shot(shot)
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    d = m.forward_shot(shot)
+    torch.cuda.synchronize()
+    out["forward_ms_per_step"] = (time.perf_counter() - t) * 1e3 / args.nt
+    dobs = d * 1.01
+    for _ in range(args.reps):
+        _, g, st = m.adjoint_gradient(shot, dobs, ckpt_slots=args.nt, profile=True)
+    out["fwd_us"] = st["fwd_ms"] * 1e3 / st["fwd_launches"]
+    out["adj_us"] = st["adj_ms"] * 1e3 / st["adj_launches"]
+    npts = int(np.prod(shape))
+    out["fwd_gbs"] = 16 * npts / (out["fwd_us"] * 1e-6) / 1e9
+    out["adj_gbs"] = 28 * npts / (out["adj_us"] * 1e-6) / 1e9
+    x = torch.from_numpy((vel - vel.mean()) * 1e-2).cuda()
+    for _ in range(args.reps):
+        words, _ = C.codec_compress(x, args.tol)
+        y = C.codec_decompress(words, shape)
+    out["codec_ratio"] = npts / words.numel()
+    print(json.dumps(out))
+
+
+if __name__ == "__main__":
+    main()

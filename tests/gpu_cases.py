@@ -54,3 +54,11 @@ def rel_l2(a, b):
     a = np.asarray(a, dtype=np.float64)
     b = np.asarray(b, dtype=np.float64)
     return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def misfit_tol(d_ref, phi_ref, rel=1e-5):
+    """Misfit tolerance implied by a receiver tolerance: with
+    |d - d_ref| <= rel |d_ref| and r = d_ref - d_obs,
+    |phi - phi_ref| <= |d - d_ref| |r| + |d - d_ref|^2 / 2."""
+    dd = rel * float(np.linalg.norm(np.asarray(d_ref, dtype=np.float64)))
+    return dd * float(np.sqrt(2.0 * phi_ref)) + 0.5 * dd * dd

@@ -13,7 +13,7 @@ import pytest
 from oracle import codec as OC
 from oracle import propagator as O
 
-from gpu_cases import make_case, rel_l2
+from gpu_cases import make_case, misfit_tol, rel_l2
 
 torch = pytest.importorskip("torch")
 C = pytest.importorskip("paper_1810_05268_gb300.ckfwi")
@@ -75,12 +75,12 @@ def _obs(case):
 def test_gradient_store_all_matches_oracle(dims, so):
     case = make_case(dims, so, **CASES[(dims, so)], seed=dims * 100 + so + 1)
     dobs = _obs(case)
-    phi_ref, g_ref, _ = O.gradient(case.og, case.vel.astype(np.float64), [case.src], case.oracle_series(),
-                                   case.rec, dobs.astype(np.float64))
+    phi_ref, g_ref, d_ref = O.gradient(case.og, case.vel.astype(np.float64), [case.src], case.oracle_series(),
+                                       case.rec, dobs.astype(np.float64))
     m = _model(case)
     phi, g, st = m.adjoint_gradient(case.shot(), torch.from_numpy(dobs).cuda(), ckpt_slots=case.pg.nt)
     g = g.cpu().numpy()
-    assert abs(phi - phi_ref) <= 1e-5 * phi_ref, (phi, phi_ref)
+    assert abs(phi - phi_ref) <= misfit_tol(d_ref, phi_ref), (phi, phi_ref)
     err = rel_l2(g, g_ref)
     assert err <= 1e-4, err
     assert st["fwd_steps"] == case.pg.nt and st["adj_steps"] == case.pg.nt
@@ -270,10 +270,10 @@ def test_tiny_time_axis(nt):
     case = make_case(2, 4, shape=(30, 34), nbl=4, nt=nt, seed=9)
     dobs = np.zeros((nt + 1, case.rec.shape[0]), np.float32)
     dobs[1:] = 1e-3
-    phi_ref, g_ref, _ = O.gradient(case.og, case.vel.astype(np.float64), [case.src], case.oracle_series(),
-                                   case.rec, dobs.astype(np.float64))
+    phi_ref, g_ref, d_ref = O.gradient(case.og, case.vel.astype(np.float64), [case.src], case.oracle_series(),
+                                       case.rec, dobs.astype(np.float64))
     m = _model(case)
     for slots in (1, 2, nt):
         phi, g, _ = m.adjoint_gradient(case.shot(), torch.from_numpy(dobs).cuda(), ckpt_slots=slots)
-        assert abs(phi - phi_ref) <= 1e-5 * phi_ref
+        assert abs(phi - phi_ref) <= misfit_tol(d_ref, phi_ref)
         assert rel_l2(g.cpu().numpy(), g_ref) < 1e-4

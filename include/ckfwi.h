@@ -211,6 +211,20 @@ CKFWI_API int ckfwi_codec_compress(const float* x, int dims, int nz, int ny, int
 CKFWI_API int ckfwi_codec_decompress(const uint32_t* in, long long nwords, int dims, int nz, int ny,
                            int nx, float* x, void* stream);
 
+/* Allocation-free ckfwi_codec_compress, for callers that cannot let the
+ * library call cudaMalloc (latency-critical code that must not take its
+ * implicit synchronisation, or processes whose device memory belongs to
+ * another allocator).  No counterpart in the paper.  Same arguments and
+ * output as ckfwi_codec_compress; its scratch is a statically sized device
+ * array inside the library (about 17 MB per device, held until exit), so
+ * fields are limited to 65536 blocks of 4^d values (EINVAL beyond that).
+ * The first call on a device looks up that array's address and should come
+ * before any stream capture.  All calls share the array: calls that overlap
+ * on the GPU race, so order them on one stream.  Synchronous. */
+CKFWI_API int ckfwi_codec_compress_noalloc(const float* x, int dims, int nz, int ny, int nx, double tol,
+                                           uint32_t* out, long long cap, long long* used_words,
+                                           int* flags, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -49,7 +49,8 @@ class Stats(ctypes.Structure):
 
 EXPORTS = ["ckfwi_create_model", "ckfwi_set_model", "ckfwi_forward_shot", "ckfwi_adjoint_gradient",
            "ckfwi_batch_gradient", "ckfwi_free", "ckfwi_error_string", "ckfwi_revolve_schedule",
-           "ckfwi_codec_bound_words", "ckfwi_codec_compress", "ckfwi_codec_decompress"]
+           "ckfwi_codec_bound_words", "ckfwi_codec_compress", "ckfwi_codec_decompress",
+           "ckfwi_codec_compress_noalloc"]
 
 
 def lib():
@@ -77,9 +78,10 @@ def lib():
         L.ckfwi_codec_bound_words.restype = LL
         L.ckfwi_codec_compress.argtypes = [P, I, I, I, I, D, P, LL, P, P, P]
         L.ckfwi_codec_decompress.argtypes = [P, LL, I, I, I, I, P, P]
+        L.ckfwi_codec_compress_noalloc.argtypes = [P, I, I, I, I, D, P, LL, P, P, P]
         for name in ("ckfwi_create_model", "ckfwi_set_model", "ckfwi_forward_shot", "ckfwi_adjoint_gradient",
                      "ckfwi_batch_gradient", "ckfwi_revolve_schedule", "ckfwi_codec_compress",
-                     "ckfwi_codec_decompress"):
+                     "ckfwi_codec_decompress", "ckfwi_codec_compress_noalloc"):
             getattr(L, name).restype = I
         _lib = L
         return _lib

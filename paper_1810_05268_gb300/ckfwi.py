@@ -268,6 +268,26 @@ def codec_compress(x, tol, stream=None):
     return out[:used.value].clone(), bool(flags.value & 1)
 
 
+def codec_compress_noalloc(x, out, tol, stream=None):
+    """Allocation-free compression into the caller's int32 CUDA tensor `out`
+    (stream words); the library allocates nothing (its scratch is a fixed
+    device array, fields up to 65536 blocks).  For callers that cannot let the
+    library call cudaMalloc.  Returns (words used, nonfinite flag)."""
+    import torch
+    if not _is_torch_cuda(x) or x.dtype != torch.float32 or not x.is_contiguous():
+        raise ValueError("codec_compress_noalloc needs a contiguous float32 CUDA tensor")
+    if not _is_torch_cuda(out) or not out.is_contiguous():
+        raise ValueError("codec_compress_noalloc needs a contiguous CUDA output tensor")
+    dims = x.dim()
+    nz, ny, nx = _shape3(tuple(x.shape))
+    used = ctypes.c_longlong(0)
+    flags = ctypes.c_int(0)
+    _check(lib().ckfwi_codec_compress_noalloc(ctypes.c_void_p(x.data_ptr()), dims, nz, ny, nx, float(tol),
+                                              ctypes.c_void_p(out.data_ptr()), out.numel(), ctypes.byref(used),
+                                              ctypes.byref(flags), _stream(stream)), "ckfwi_codec_compress_noalloc")
+    return used.value, bool(flags.value & 1)
+
+
 def codec_decompress(stream_words, shape, stream=None):
     import torch
     if not _is_torch_cuda(stream_words) or not stream_words.is_contiguous():

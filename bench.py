@@ -232,17 +232,20 @@ def main():
                 if e.status != C.POOL_OVERFLOW or kw.get("store_mode") != "codec":
                     raise
                 kw["ckpt_slots"] = max(2, int(kw["ckpt_slots"] * 0.8))
+        # profiled warm-up creates the library's timing events, so that the
+        # profiled steps below do not include host-side event creation
+        one(kw, True)
         if ws > 1:
             torch.distributed.barrier()
         torch.cuda.synchronize()
         if name == headline:
             clocks = Clocks(lr)
+        # timed region: K un-profiled gradients, CUDA events on torch's stream
+        # (the library launches on that stream), max over ranks
         ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         ev0.record()
-        sts = []
         for _ in range(args.steps):
-            _, phi, st = one(kw, True)
-            sts.append(st)
+            _, phi, st_plain = one(kw, False)
         ev1.record()
         torch.cuda.synchronize()
         ms = ev0.elapsed_time(ev1) / args.steps
@@ -250,6 +253,11 @@ def main():
             t = torch.tensor([ms], device="cuda")
             torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
             ms = float(t.item())
+        # per-kernel-class device time from profiled gradients (same work)
+        sts = []
+        for _ in range(max(1, min(args.steps, 3))):
+            _, _, st = one(kw, True)
+            sts.append(st)
         clk = clocks.stop() if name == headline else None
         st = sts[-1]
         fwd_ms = float(np.mean([s["fwd_ms"] for s in sts]))

@@ -24,6 +24,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <memory>
@@ -265,6 +266,7 @@ struct ckfwi_model {
     cudaStream_t cap = nullptr;     // non-blocking stream used only to record graphs
     cudaEvent_t ev = nullptr;
     std::vector<cudaEvent_t> evpool; // profiling events, reused across calls
+    std::map<std::tuple<const void*, int, int, int>, CUtensorMap> tmaps;   // (base, dtype, box x, box y)
     // graphs
     std::map<GraphKey, cudaGraphExec_t> graphs;
     ~ckfwi_model()
@@ -305,6 +307,32 @@ namespace {
 float* org(const DevMem& m, const FieldGeom& g) { return m.as<float>() + g.origin; }
 
 size_t field_bytes(const FieldGeom& g, size_t elem = 4) { return (size_t)g.alloc * elem; }
+
+// cuTensorMapEncodeTiled, fetched from the driver through the runtime (no
+// link-time dependency on libcuda).
+typedef CUresult (*EncodeTiled)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiled encode_fn()
+{
+    static EncodeTiled fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiled>(p);
+    }
+    return fn;
+}
+
+// Tensor map of a padded field (3D: x = px, y = ny + 2H, z = nz + 2H in
+// storage coordinates), box (bx, by, 1); elem 4 = FP32, 2 = BF16 or FP16.
+int tensor_map(ckfwi_model* m, const void* origin_ptr, int utype, int bx, int by, CUtensorMap* out);
 
 double eta_axis(const ckfwi_grid& g, int i, int n)
 {
@@ -501,7 +529,8 @@ int fwd_step(Ctx& cx, const float* u, const float* up, float* out, int n, bool r
         const long long gx = (m->fg.nx + m->tf.bx - 1) / m->tf.bx;
         const long long gy = m->fg.dims == 3 ? (m->fg.ny + m->tf.by - 1) / m->tf.by : 1;
         const long long gz = (m->fg.nz + m->tf.zlen - 1) / m->tf.zlen;
-        if (gx * gy * gz * m->tf.bx * m->tf.by >= sm.n) a.smp = sm;
+        const long long tpc = (m->tf.ver == 2 ? m->tf.bx / 4 : m->tf.bx) * (long long)m->tf.by;
+        if (gx * gy * gz * tpc >= sm.n) a.smp = sm;
         else {
             CK_TRY(launch_sample(u, sm, cx.st));
             ++cx.launches;
@@ -510,7 +539,13 @@ int fwd_step(Ctx& cx, const float* u, const float* up, float* out, int n, bool r
     }
     (void)sep;
     const int tok = cx.begin(PC_FWD);
-    CK_TRY(launch_fwd(a, m->tf, m->K, ck, cx.st));
+    if (m->tf.ver == 2) {
+        CUtensorMap tm;
+        ST_TRY(tensor_map(m, u, U_FP32, tma_tile_x() + 2 * tma_halo_x(m->K), m->tf.by + 2 * m->K, &tm));
+        CK_TRY(launch_fwd_tma(a, tm, m->tf, m->K, ck, cx.st));
+    } else {
+        CK_TRY(launch_fwd(a, m->tf, m->K, ck, cx.st));
+    }
     cx.end(tok);
     ++cx.launches;
     return CKFWI_OK;
@@ -534,8 +569,17 @@ int adj_step(Ctx& cx, const float* l1, const float* l2, float* l0, const void* u
     a.adj.series = m->shot.resid.as<float>() + (size_t)j * m->shot.nrec;
     a.src = m->shot.src.view;
     a.src.series = m->shot.wavelet.as<float>() + (j - 1);
+    a.err = m->flags.as<int>();
     const int tok = cx.begin(PC_ADJ);
-    CK_TRY(launch_adj(a, m->ta, m->K, utype, cx.st));
+    if (m->ta.ver == 2) {
+        CUtensorMap tl, tu;
+        const int bx = tma_tile_x() + 2 * tma_halo_x(m->K), by = m->ta.by + 2 * m->K;
+        ST_TRY(tensor_map(m, l1, U_FP32, bx, by, &tl));
+        ST_TRY(tensor_map(m, u, utype, bx, by, &tu));
+        CK_TRY(launch_adj_tma(a, tl, tu, m->ta, m->K, utype, cx.st));
+    } else {
+        CK_TRY(launch_adj(a, m->ta, m->K, utype, cx.st));
+    }
     cx.end(tok);
     ++cx.launches;
     return CKFWI_OK;
@@ -565,6 +609,37 @@ int residual(Ctx& cx)
     return CKFWI_OK;
 }
 
+int tensor_map(ckfwi_model* m, const void* origin_ptr, int utype, int bx, int by, CUtensorMap* out)
+{
+    const FieldGeom& f = m->fg;
+    const int es = utype == U_FP32 ? 4 : 2;
+    const void* base = static_cast<const char*>(origin_ptr) - f.origin * es;
+    const auto key = std::make_tuple(base, utype, bx, by);
+    auto it = m->tmaps.find(key);
+    if (it != m->tmaps.end()) {
+        *out = it->second;
+        return CKFWI_OK;
+    }
+    EncodeTiled enc = encode_fn();
+    if (!enc || f.dims != 3) return CKFWI_ECUDA;
+    const cuuint64_t py = (cuuint64_t)f.ny + 2 * f.H, pz = (cuuint64_t)f.nz + 2 * f.H;
+    const cuuint64_t dims[3] = {(cuuint64_t)f.px, py, pz};
+    const cuuint64_t strides[2] = {(cuuint64_t)f.px * es, (cuuint64_t)f.pxy * es};
+    const cuuint32_t box[3] = {(cuuint32_t)bx, (cuuint32_t)by, 1};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    const CUtensorMapDataType dt = utype == U_FP32   ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                   : utype == U_BF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
+                                                     : CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
+    CUtensorMap tm;
+    if (enc(&tm, dt, 3, const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+            CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return CKFWI_ECUDA;
+    m->tmaps.emplace(key, tm);
+    *out = tm;
+    return CKFWI_OK;
+}
+
 // --------------------------------------------------------------- autotune
 int autotune(ckfwi_model* m, cudaStream_t st)
 {
@@ -576,10 +651,7 @@ int autotune(ckfwi_model* m, cudaStream_t st)
     int nsm = 0;
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     std::vector<Tile> cands;
-    for (int i = 0; i < tile_count(f.dims); ++i) {
-        Tile t0 = tile_at(f.dims, i, f.nz);
-        if (!tile_supported(f.dims, m->K, t0)) continue;
-        const long long cols = (long long)((f.nx + t0.bx - 1) / t0.bx) * (f.dims == 3 ? (f.ny + t0.by - 1) / t0.by : 1);
+    auto zlens = [&](long long cols) {
         std::vector<int> zl;
         for (int target : {2, 4, 8, 16}) {
             long long nzc = (target * (long long)nsm + cols - 1) / cols;
@@ -588,7 +660,26 @@ int autotune(ckfwi_model* m, cudaStream_t st)
             z = std::max(z, 4);
             if (std::find(zl.begin(), zl.end(), z) == zl.end()) zl.push_back(z);
         }
-        for (int z : zl) cands.push_back(tile_at(f.dims, i, z));
+        return zl;
+    };
+    for (int i = 0; i < tile_count(f.dims); ++i) {
+        Tile t0 = tile_at(f.dims, i, f.nz);
+        if (!tile_supported(f.dims, m->K, t0)) continue;
+        const long long cols = (long long)((f.nx + t0.bx - 1) / t0.bx) * (f.dims == 3 ? (f.ny + t0.by - 1) / t0.by : 1);
+        for (int z : zlens(cols)) cands.push_back(tile_at(f.dims, i, z));
+    }
+    const bool tma_ok = encode_fn() != nullptr;
+    // TMA kernels run a persistent grid; their zlen field is the CTAs per SM
+    for (int ty : {8, 16}) {
+        if (!tma_ok || !tma_supported(f.dims, m->K, ty)) continue;
+        for (int per_sm : {1, 2, 3}) {
+            Tile t;
+            t.bx = 64;
+            t.by = ty;
+            t.zlen = per_sm;
+            t.ver = 2;
+            cands.push_back(t);
+        }
     }
     // time the forward and the reverse kernel on the model's own buffers
     cudaEvent_t e0, e1;
@@ -609,21 +700,50 @@ int autotune(ckfwi_model* m, cudaStream_t st)
     b.eta = m->eta.as<float>();
     b.hdt = m->hdt;
     std::memcpy(b.c, m->c, sizeof(b.c));
+    b.err = m->flags.as<int>();
     float best_f = 1e30f, best_a = 1e30f;
     const int reps = 3;
-    for (const Tile& t : cands) {
-        for (int pass = 0; pass < 2; ++pass) {
+    CUtensorMap tm_u, tm_l;
+    auto go = [&](const Tile& t, int pass) -> int {
+        if (t.ver == 2) {
+            const int bx = tma_tile_x() + 2 * tma_halo_x(m->K), by = t.by + 2 * m->K;
+            ST_TRY(tensor_map(m, a.u, U_FP32, bx, by, &tm_u));
+            ST_TRY(tensor_map(m, b.l1, U_FP32, bx, by, &tm_l));
+            if (pass == 0) CK_TRY(launch_fwd_tma(a, tm_u, t, m->K, CK_NONE, st));
+            else CK_TRY(launch_adj_tma(b, tm_l, tm_u, t, m->K, U_FP32, st));
+        } else {
             if (pass == 0) CK_TRY(launch_fwd(a, t, m->K, CK_NONE, st));
             else CK_TRY(launch_adj(b, t, m->K, U_FP32, st));
+        }
+        return CKFWI_OK;
+    };
+    // a forced tile (CKFWI_TILE_FWD / CKFWI_TILE_ADJ = "ver,bx,by,zlen") skips the search
+    auto forced = [&](const char* name, Tile* t) {
+        const char* v = std::getenv(name);
+        if (!v) return false;
+        Tile u;
+        if (std::sscanf(v, "%d,%d,%d,%d", &u.ver, &u.bx, &u.by, &u.zlen) != 4 || u.zlen < 1) return false;
+        const bool okv = u.ver == 2 ? (tma_ok && u.bx == 64 && tma_supported(f.dims, m->K, u.by))
+                                    : tile_supported(f.dims, m->K, u);
+        if (!okv) return false;
+        *t = u;
+        return true;
+    };
+    const bool ff = forced("CKFWI_TILE_FWD", &m->tf), fa = forced("CKFWI_TILE_ADJ", &m->ta);
+    const bool verbose = std::getenv("CKFWI_VERBOSE") != nullptr;
+    for (const Tile& t : cands) {
+        for (int pass = 0; pass < 2; ++pass) {
+            if ((pass == 0 && ff) || (pass == 1 && fa)) continue;
+            ST_TRY(go(t, pass));
             CK_TRY(cudaEventRecord(e0, st));
-            for (int r = 0; r < reps; ++r) {
-                if (pass == 0) CK_TRY(launch_fwd(a, t, m->K, CK_NONE, st));
-                else CK_TRY(launch_adj(b, t, m->K, U_FP32, st));
-            }
+            for (int r = 0; r < reps; ++r) ST_TRY(go(t, pass));
             CK_TRY(cudaEventRecord(e1, st));
             CK_TRY(cudaEventSynchronize(e1));
             float ms = 0;
             CK_TRY(cudaEventElapsedTime(&ms, e0, e1));
+            if (verbose)
+                std::fprintf(stderr, "ckfwi autotune %s ver %d tile %dx%d zlen %d: %.1f us\n", pass ? "adj" : "fwd",
+                             t.ver, t.bx, t.by, t.zlen, 1000.0f * ms / reps);
             if (pass == 0 && ms < best_f) { best_f = ms; m->tf = t; }
             if (pass == 1 && ms < best_a) { best_a = ms; m->ta = t; }
         }
@@ -656,6 +776,7 @@ int read_flags(ckfwi_model* m, cudaStream_t st, int* fl)
     *fl = 0;
     if (h[1] & 2) *fl = CKFWI_POOL_OVERFLOW;
     else if (h[1] & 4) *fl = CKFWI_CORRUPT;
+    else if (h[0] & 8) *fl = CKFWI_TIMEOUT;
     else if ((h[0] & 1) || (h[1] & 1)) *fl = CKFWI_NONFINITE;
     return CKFWI_OK;
 }

@@ -256,25 +256,14 @@ __device__ __forceinline__ unsigned long long low_mask(int n)
     return n >= 64 ? ~0ull : ((1ull << n) - 1ull);
 }
 
+// Encode block b into its scratch slot; returns its bit count.
 template <int DIMS>
-__global__ void __launch_bounds__(ENC_THREADS) enc_kernel(const float* __restrict__ x, CodecView v,
-                                                          Geo G, float tol_f, uint32_t* __restrict__ scratch,
-                                                          uint32_t* __restrict__ out, const long long* base_word,
-                                                          long long cap_words, int* err)
+__device__ __forceinline__ int encode_block(const float* __restrict__ x, const CodecView& v, const Geo& G,
+                                            float tol_f, uint32_t* __restrict__ scratch, long long b,
+                                            int32_t* siv, int* err)
 {
     constexpr int V = Cfg<DIMS>::V;
     constexpr Perm P = make_perm(DIMS);
-    __shared__ int32_t siv[V * ENC_THREADS];
-    const long long b = (long long)blockIdx.x * ENC_THREADS + threadIdx.x;
-    const long long base = *base_word;
-    if (base + G.table_words > cap_words) {
-        if (b == 0) atomicOr(err, 2);
-        return;
-    }
-    uint16_t* sizes = reinterpret_cast<uint16_t*>(out + base + HDR + G.nchunks);
-    if (b == 0 && (G.nblocks & 1)) sizes[G.nblocks] = 0;
-    if (b >= G.nblocks) return;
-
     const BlockPos bp = block_pos(G, b);
     float f[V];
     gather<DIMS>(x, v, bp, f);
@@ -290,8 +279,7 @@ __global__ void __launch_bounds__(ENC_THREADS) enc_kernel(const float* __restric
     if (bad) atomicOr(err, 1);
     if (bad || amax <= tol_f) {
         bw.put(0u, 1);
-        sizes[b] = (uint16_t)bw.flush();
-        return;
+        return bw.flush();
     }
     int emax = -1000;
 #pragma unroll
@@ -310,7 +298,7 @@ __global__ void __launch_bounds__(ENC_THREADS) enc_kernel(const float* __restric
         uint32_t mag = sh >= 32 ? 0u : (M >> sh);
         if (!(u & 0x7FFFFFFFu)) mag = 0u;
         c[i] = (u >> 31) ? -(int32_t)mag : (int32_t)mag;
-        siv[i * ENC_THREADS + threadIdx.x] = c[i];
+        siv[i * ENC_THREADS] = c[i];
     }
     xform_fwd<DIMS>(c);
     uint32_t nb[V];
@@ -336,7 +324,7 @@ __global__ void __launch_bounds__(ENC_THREADS) enc_kernel(const float* __restric
             bool ok = true;
 #pragma unroll
             for (int i = 0; i < V; ++i) {
-                const long long d = (long long)siv[i * ENC_THREADS + threadIdx.x] - (long long)t[i];
+                const long long d = (long long)siv[i * ENC_THREADS] - (long long)t[i];
                 ok &= (d <= (long long)T - 2) && (-d <= (long long)T - 2);
             }
             if (ok) {
@@ -369,10 +357,7 @@ __global__ void __launch_bounds__(ENC_THREADS) enc_kernel(const float* __restric
                 s += z + 1;
             }
         }
-        if (bw.bits() <= Cfg<DIMS>::MAXBITS) {
-            sizes[b] = (uint16_t)bw.flush();
-            return;
-        }
+        if (bw.bits() <= Cfg<DIMS>::MAXBITS) return bw.flush();
         bw.acc = 0ull;      // longer than raw: start over with the raw form
         bw.nacc = 0;
         bw.nw = 0;
@@ -385,11 +370,44 @@ __global__ void __launch_bounds__(ENC_THREADS) enc_kernel(const float* __restric
 #pragma unroll
         for (int i = 0; i < V; ++i) bw.put(__float_as_uint(g[i]), 32);
     }
-    sizes[b] = (uint16_t)bw.flush();
+    return bw.flush();
 }
 
-// One CTA: chunk word counts -> exclusive scan -> chunk table, header,
-// next free word; overflow check.
+// One thread per block; each warp owns one 32-block chunk and stores the
+// chunk's word count in the chunk table (the scan turns counts into offsets).
+template <int DIMS>
+__global__ void __launch_bounds__(ENC_THREADS) enc_kernel(const float* __restrict__ x, CodecView v,
+                                                          Geo G, float tol_f, uint32_t* __restrict__ scratch,
+                                                          uint32_t* __restrict__ out, const long long* base_word,
+                                                          long long cap_words, int* err)
+{
+    constexpr int V = Cfg<DIMS>::V;
+    __shared__ int32_t siv[V * ENC_THREADS];
+    const long long b = (long long)blockIdx.x * ENC_THREADS + threadIdx.x;
+    const long long base = *base_word;
+    if (base + G.table_words > cap_words) {
+        if (b == 0) atomicOr(err, 2);
+        return;
+    }
+    uint32_t* ctab = out + base + HDR;
+    uint16_t* sizes = reinterpret_cast<uint16_t*>(out + base + HDR + G.nchunks);
+    if (b == 0 && (G.nblocks & 1)) sizes[G.nblocks] = 0;
+    int nbits = 0;
+    if (b < G.nblocks) {
+        nbits = encode_block<DIMS>(x, v, G, tol_f, scratch, b, siv + threadIdx.x, err);
+        sizes[b] = (uint16_t)nbits;
+    }
+    int tot = nbits;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) tot += __shfl_xor_sync(0xffffffffu, tot, o);
+    const long long c = b / CHUNK;
+    if ((threadIdx.x & 31) == 0 && c < G.nchunks) ctab[c] = (uint32_t)((tot + 31) / 32);
+}
+
+// One CTA: the chunk word counts in the chunk table -> exclusive offsets in
+// place; header; next free word; overflow check.  Each thread takes SCAN_ITEMS
+// consecutive chunks per pass.
+constexpr int SCAN_ITEMS = 8;
 __global__ void __launch_bounds__(1024) scan_kernel(uint32_t* __restrict__ out, const long long* base_word,
                                                     long long cap_words, long long* next_word, Geo G,
                                                     float tol_f, int* err, unsigned long long* stat_words)
@@ -406,20 +424,19 @@ __global__ void __launch_bounds__(1024) scan_kernel(uint32_t* __restrict__ out, 
     }
     uint32_t* hdr = out + base;
     uint32_t* ctab = hdr + HDR;
-    const uint16_t* sizes = reinterpret_cast<const uint16_t*>(hdr + HDR + G.nchunks);
     if (threadIdx.x == 0) carry_s = 0;
     __syncthreads();
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    for (long long c0 = 0; c0 < G.nchunks; c0 += 1024) {
-        const long long c = c0 + threadIdx.x;
-        long long words = 0;
-        if (c < G.nchunks) {
-            long long bits = 0;
-            const long long b1 = min((c + 1) * CHUNK, G.nblocks);
-            for (long long b = c * CHUNK; b < b1; ++b) bits += sizes[b];
-            words = (bits + 31) / 32;
+    for (long long c0 = 0; c0 < G.nchunks; c0 += 1024LL * SCAN_ITEMS) {
+        const long long cb = c0 + (long long)threadIdx.x * SCAN_ITEMS;
+        uint32_t v[SCAN_ITEMS];
+        long long sum = 0;
+#pragma unroll
+        for (int i = 0; i < SCAN_ITEMS; ++i) {
+            v[i] = (cb + i < G.nchunks) ? ctab[cb + i] : 0u;
+            sum += v[i];
         }
-        long long incl = words;
+        long long incl = sum;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
             const long long t = __shfl_up_sync(0xffffffffu, incl, o);
@@ -428,7 +445,7 @@ __global__ void __launch_bounds__(1024) scan_kernel(uint32_t* __restrict__ out, 
         if (lane == 31) warp_tot[wid] = incl;
         __syncthreads();
         if (wid == 0) {
-            long long t = warp_tot[lane];
+            const long long t = warp_tot[lane];
             long long tin = t;
 #pragma unroll
             for (int o = 1; o < 32; o <<= 1) {
@@ -438,10 +455,14 @@ __global__ void __launch_bounds__(1024) scan_kernel(uint32_t* __restrict__ out, 
             warp_tot[lane] = tin - t;       // exclusive prefix of warp totals
         }
         __syncthreads();
-        const long long excl = carry_s + warp_tot[wid] + incl - words;
-        if (c < G.nchunks) ctab[c] = (uint32_t)excl;
+        long long run = carry_s + warp_tot[wid] + incl - sum;
+#pragma unroll
+        for (int i = 0; i < SCAN_ITEMS; ++i) {
+            if (cb + i < G.nchunks) ctab[cb + i] = (uint32_t)run;
+            run += v[i];
+        }
         __syncthreads();
-        if (threadIdx.x == 1023) carry_s = excl + words;
+        if (threadIdx.x == 1023) carry_s = run;
         __syncthreads();
     }
     if (threadIdx.x == 0) {

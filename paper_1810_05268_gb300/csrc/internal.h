@@ -65,7 +65,7 @@ struct FwdArgs {
     Sample smp;
     void* ck_u;           // fused takeshot outputs (see CkMode)
     void* ck_up;
-    int* err;             // error flags (bit 0: FP16 overflow)
+    int* err;             // error flags (bit 0: FP16 overflow, bit 3: a bounded wait ran out)
 };
 
 // Fused reverse step:
@@ -85,14 +85,16 @@ struct AdjArgs {
     int zlen;
     Inj adj;              // -P^T r^j  (weights carry the minus sign)
     Inj src;              // Q^T s^{j-1}
+    int* err;             // error flags (bit 3: a bounded wait ran out)
 };
 
 enum CkMode { CK_NONE = 0, CK_FP32 = 1, CK_BF16 = 2, CK_FP16 = 3 };
 enum UType { U_FP32 = 0, U_BF16 = 1, U_FP16 = 2 };
 
 struct Tile {
-    int bx, by;           // CTA shape (by = 1 in 2D)
-    int zlen;             // z planes per CTA
+    int bx, by;           // CTA shape (by = 1 in 2D); TMA kernels: bx = 64 points, by rows
+    int zlen;             // ver 1: z planes per CTA; ver 2: CTAs per SM of the persistent grid
+    int ver = 1;          // 1: register-queue kernels, 2: TMA-fed kernels (3D, orders 2-8)
 };
 
 // kernels.cu
@@ -101,6 +103,17 @@ cudaError_t launch_adj(const AdjArgs& a, const Tile& t, int K, int utype, cudaSt
 bool tile_supported(int dims, int K, const Tile& t);
 int tile_count(int dims);
 Tile tile_at(int dims, int i, int zlen);
+
+// stencil_tma.cu (CUtensorMap comes from <cuda.h>)
+}  // namespace ckfwi
+#include <cuda.h>
+namespace ckfwi {
+int tma_halo_x(int K);
+int tma_tile_x();
+bool tma_supported(int dims, int K, int ty);
+cudaError_t launch_fwd_tma(const FwdArgs& a, const CUtensorMap& tmu, const Tile& t, int K, int ck, cudaStream_t s);
+cudaError_t launch_adj_tma(const AdjArgs& a, const CUtensorMap& tml, const CUtensorMap& tmu, const Tile& t, int K,
+                           int ut, cudaStream_t s);
 
 // aux.cu
 cudaError_t launch_sample(const float* u, const Sample& smp, cudaStream_t s);

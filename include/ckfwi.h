@@ -119,6 +119,9 @@ typedef struct ckfwi_grad_opts {
     int profile;         /* 1: time every kernel class with CUDA events on the
                             stream (fills the *_ms fields of ckfwi_stats); not
                             combined with use_graph */
+    double grad_scale;   /* the gradient is multiplied by this (0 is read as 1) */
+    int grad_f32;        /* batch only: grad_sum is float32 (the FP64 compensated
+                            sum rounded once) instead of float64 */
 } ckfwi_grad_opts;
 
 typedef struct ckfwi_stats {
@@ -156,6 +159,13 @@ CKFWI_API int ckfwi_set_model(ckfwi_model* m, const float* data, int kind, int m
  * d_sim [nt+1][nrec] float32 (row 0 = P u^0 = 0).  EINVAL for a source or
  * receiver outside the grid or nrec < 1. */
 CKFWI_API int ckfwi_forward_shot(ckfwi_model* m, const ckfwi_shot* s, float* d_sim, int mem, void* stream);
+
+/* Misfit of one shot without its gradient (Sec. 6): forward modelling, the
+ * residual and phi = 1/2 sum_{n=1..N} ||d^n - d_obs^n||^2 in FP64 on the
+ * device; *misfit (host) receives phi, d_sim (optional, same `mem`) the
+ * simulated data.  Synchronous. */
+CKFWI_API int ckfwi_misfit(ckfwi_model* m, const ckfwi_shot* s, const float* d_obs, int mem, double* misfit,
+                           float* d_sim, void* stream);
 
 /* Misfit and adjoint-state gradient of one shot (Sec. 6), with Revolve
  * checkpointing of M slots (Sec. 3) and optionally compressed checkpoints

@@ -30,7 +30,7 @@ class Shot(ctypes.Structure):
 class GradOpts(ctypes.Structure):
     _fields_ = [("ckpt_slots", ctypes.c_int), ("store_mode", ctypes.c_int), ("tol", ctypes.c_double),
                 ("pool_bytes", ctypes.c_size_t), ("grad_kind", ctypes.c_int), ("use_graph", ctypes.c_int),
-                ("profile", ctypes.c_int)]
+                ("profile", ctypes.c_int), ("grad_scale", ctypes.c_double), ("grad_f32", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
@@ -47,7 +47,7 @@ class Stats(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
-EXPORTS = ["ckfwi_create_model", "ckfwi_set_model", "ckfwi_forward_shot", "ckfwi_adjoint_gradient",
+EXPORTS = ["ckfwi_create_model", "ckfwi_set_model", "ckfwi_forward_shot", "ckfwi_misfit", "ckfwi_adjoint_gradient",
            "ckfwi_batch_gradient", "ckfwi_free", "ckfwi_error_string", "ckfwi_revolve_schedule",
            "ckfwi_codec_bound_words", "ckfwi_codec_compress", "ckfwi_codec_decompress",
            "ckfwi_codec_compress_noalloc"]
@@ -67,6 +67,7 @@ def lib():
         L.ckfwi_create_model.argtypes = [P, P]
         L.ckfwi_set_model.argtypes = [P, P, I, I, P]
         L.ckfwi_forward_shot.argtypes = [P, P, P, I, P]
+        L.ckfwi_misfit.argtypes = [P, P, P, I, P, P, P]
         L.ckfwi_adjoint_gradient.argtypes = [P, P, P, I, P, P, P, P, P]
         L.ckfwi_batch_gradient.argtypes = [P, P, I, P, I, P, P, P, P, P]
         L.ckfwi_free.argtypes = [P]
@@ -79,7 +80,8 @@ def lib():
         L.ckfwi_codec_compress.argtypes = [P, I, I, I, I, D, P, LL, P, P, P]
         L.ckfwi_codec_decompress.argtypes = [P, LL, I, I, I, I, P, P]
         L.ckfwi_codec_compress_noalloc.argtypes = [P, I, I, I, I, D, P, LL, P, P, P]
-        for name in ("ckfwi_create_model", "ckfwi_set_model", "ckfwi_forward_shot", "ckfwi_adjoint_gradient",
+        for name in ("ckfwi_create_model", "ckfwi_set_model", "ckfwi_forward_shot", "ckfwi_misfit",
+                     "ckfwi_adjoint_gradient",
                      "ckfwi_batch_gradient", "ckfwi_revolve_schedule", "ckfwi_codec_compress",
                      "ckfwi_codec_decompress", "ckfwi_codec_compress_noalloc"):
             getattr(L, name).restype = I

@@ -161,7 +161,8 @@ def _alloc(shape, dtype, device):
     return np.empty(shape, dtype=dtype)
 
 
-def _opts(ckpt_slots, store_mode, tol, pool_bytes, grad_kind, use_graph, profile=False):
+def _opts(ckpt_slots, store_mode, tol, pool_bytes, grad_kind, use_graph, profile=False, grad_scale=1.0,
+          grad_f32=False):
     o = GradOpts()
     o.ckpt_slots = int(ckpt_slots)
     o.store_mode = STORE_NAMES.get(store_mode, store_mode) if isinstance(store_mode, str) else int(store_mode)
@@ -170,12 +171,29 @@ def _opts(ckpt_slots, store_mode, tol, pool_bytes, grad_kind, use_graph, profile
     o.grad_kind = int(grad_kind)
     o.use_graph = int(bool(use_graph))
     o.profile = int(bool(profile))
+    o.grad_scale = float(grad_scale)
+    o.grad_f32 = int(bool(grad_f32))
     return o
+
+
+def misfit(model, grid: GridSpec, shot: ShotSpec, d_obs, d_sim=None, stream=None):
+    """phi = 1/2 sum_{n>=1} ||d_sim^n - d_obs^n||^2 (FP64) by forward modelling only."""
+    pd, mem = _buf(d_obs, np.float32)
+    ps = None
+    if d_sim is not None:
+        ps, ms = _buf(d_sim, np.float32)
+        if ms != mem:
+            raise ValueError("d_obs and d_sim must both be host or both be device buffers")
+    s = shot.c()
+    phi = ctypes.c_double(0.0)
+    _check(lib().ckfwi_misfit(model, ctypes.byref(s), pd, mem, ctypes.byref(phi), ps, _stream(stream)),
+           "ckfwi_misfit")
+    return phi.value
 
 
 def adjoint_gradient(model, grid: GridSpec, shot: ShotSpec, d_obs, ckpt_slots, store_mode=STORE_FP32,
                      tol=0.0, pool_bytes=0, grad_kind=SLOWNESS2, use_graph=False, grad=None, stream=None,
-                     profile=False):
+                     profile=False, grad_scale=1.0):
     """(misfit, gradient on the total grid, stats dict)."""
     pd, mem = _buf(d_obs, np.float32)
     if grad is None:
@@ -184,7 +202,7 @@ def adjoint_gradient(model, grid: GridSpec, shot: ShotSpec, d_obs, ckpt_slots, s
     if memg != mem:
         raise ValueError("d_obs and grad must both be host or both be device buffers")
     s = shot.c()
-    o = _opts(ckpt_slots, store_mode, tol, pool_bytes, grad_kind, use_graph, profile)
+    o = _opts(ckpt_slots, store_mode, tol, pool_bytes, grad_kind, use_graph, profile, grad_scale)
     phi = ctypes.c_double(0.0)
     st = Stats()
     _check(lib().ckfwi_adjoint_gradient(model, ctypes.byref(s), pd, mem, ctypes.byref(o), ctypes.byref(phi), pg,
@@ -193,8 +211,9 @@ def adjoint_gradient(model, grid: GridSpec, shot: ShotSpec, d_obs, ckpt_slots, s
 
 
 def batch_gradient(model, grid: GridSpec, shots, d_obs_list, ckpt_slots, store_mode=STORE_FP32, tol=0.0,
-                   pool_bytes=0, grad_kind=SLOWNESS2, use_graph=False, grad_sum=None, stream=None):
-    """(sum of misfits, FP64 sum of gradients over shots, stats dict)."""
+                   pool_bytes=0, grad_kind=SLOWNESS2, use_graph=False, grad_sum=None, stream=None,
+                   grad_scale=1.0, grad_f32=False):
+    """(sum of misfits, sum of gradients over shots (FP64, or FP32 with grad_f32), stats dict)."""
     n = len(shots)
     ptrs = (ctypes.c_void_p * n)()
     mem = None
@@ -204,9 +223,10 @@ def batch_gradient(model, grid: GridSpec, shots, d_obs_list, ckpt_slots, store_m
         if mem is not None and m != mem:
             raise ValueError("mixed host / device d_obs")
         mem = m
+    gdt = np.float32 if grad_f32 else np.float64
     if grad_sum is None:
-        grad_sum = _alloc(tuple(grid.shape), np.float64, "cuda" if mem == DEVICE else None)
-    pg, memg = _buf(grad_sum, np.float64)
+        grad_sum = _alloc(tuple(grid.shape), gdt, "cuda" if mem == DEVICE else None)
+    pg, memg = _buf(grad_sum, gdt)
     if memg != mem:
         raise ValueError("d_obs and grad_sum must both be host or both be device buffers")
     carr = (Shot * n)()
@@ -214,7 +234,7 @@ def batch_gradient(model, grid: GridSpec, shots, d_obs_list, ckpt_slots, store_m
     for i, sh in enumerate(shots):
         carr[i] = sh.c()
         keep.append(sh._keep)
-    o = _opts(ckpt_slots, store_mode, tol, pool_bytes, grad_kind, use_graph)
+    o = _opts(ckpt_slots, store_mode, tol, pool_bytes, grad_kind, use_graph, False, grad_scale, grad_f32)
     phi = ctypes.c_double(0.0)
     st = Stats()
     _check(lib().ckfwi_batch_gradient(model, carr, n, ptrs, mem, ctypes.byref(o), ctypes.byref(phi), pg,
@@ -313,6 +333,9 @@ class Model:
 
     def forward_shot(self, shot, **kw):
         return forward_shot(self.h, self.grid, shot, **kw)
+
+    def misfit(self, shot, d_obs, **kw):
+        return misfit(self.h, self.grid, shot, d_obs, **kw)
 
     def adjoint_gradient(self, shot, d_obs, ckpt_slots, **kw):
         return adjoint_gradient(self.h, self.grid, shot, d_obs, ckpt_slots, **kw)

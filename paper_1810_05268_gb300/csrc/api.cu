@@ -1260,6 +1260,39 @@ int ckfwi_forward_shot(ckfwi_model* m, const ckfwi_shot* s, float* d_sim, int me
     return CKFWI_OK;
 }
 
+int ckfwi_misfit(ckfwi_model* m, const ckfwi_shot* s, const float* d_obs, int mem, double* misfit, float* d_sim,
+                 void* stream)
+{
+    if (!m || !d_obs || !misfit || !m->have_model) return CKFWI_EINVAL;
+    cudaStream_t st = S(stream);
+    ST_TRY(set_shot(m, s));
+    ST_TRY(autotune(m, st));
+    const FieldGeom& f = m->fg;
+    Ctx cx{m, st, 0};
+    const size_t nd = (size_t)(m->g.nt + 1) * m->shot.nrec;
+    CK_TRY(cudaMemcpyAsync(m->shot.dobs.p, d_obs, nd * sizeof(float),
+                           mem == CKFWI_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, st));
+    CK_TRY(cudaMemsetAsync(m->shot.dsim.p, 0, m->shot.dsim.bytes, st));
+    State sv{org(m->zero, f), org(m->zero, f), U_FP32, U_FP32};
+    for (int n = 0; n < m->g.nt; ++n) {
+        float* out = pick_free(m, sv);
+        ST_TRY(fwd_step(cx, static_cast<const float*>(sv.cur), static_cast<const float*>(sv.prev), out, n, true,
+                        CK_NONE, nullptr, nullptr));
+        sv.prev = sv.cur;
+        sv.cur = out;
+    }
+    ST_TRY(sample_last(cx, static_cast<const float*>(sv.cur)));
+    ST_TRY(residual(cx));
+    if (d_sim)
+        CK_TRY(cudaMemcpyAsync(d_sim, m->shot.dsim.p, nd * sizeof(float),
+                               mem == CKFWI_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, st));
+    double phi = 0.0;
+    CK_TRY(cudaMemcpyAsync(&phi, m->phi.p, sizeof(double), cudaMemcpyDeviceToHost, st));
+    CK_TRY(cudaStreamSynchronize(st));
+    *misfit = phi;
+    return CKFWI_OK;
+}
+
 int ckfwi_adjoint_gradient(ckfwi_model* m, const ckfwi_shot* s, const float* d_obs, int mem,
                            const ckfwi_grad_opts* opts, double* misfit, float* grad, ckfwi_stats* stats,
                            void* stream)
@@ -1270,14 +1303,15 @@ int ckfwi_adjoint_gradient(ckfwi_model* m, const ckfwi_shot* s, const float* d_o
     const int rs = gradient_one(m, s, d_obs, mem, opts, misfit, stats, st, &cw);
     if (rs != CKFWI_OK) return rs;
     const FieldGeom& f = m->fg;
+    const float scale = opts->grad_scale != 0.0 ? (float)opts->grad_scale : 1.0f;
     if (mem == CKFWI_HOST) {
         DevMem tmp;
         CK_TRY(tmp.alloc((size_t)f.npts * sizeof(float), false));
-        CK_TRY(launch_grad_out(org(m->gacc, f), m->cvel.as<float>(), opts->grad_kind, f, tmp.as<float>(), st));
+        CK_TRY(launch_grad_out(org(m->gacc, f), m->cvel.as<float>(), opts->grad_kind, scale, f, tmp.as<float>(), st));
         CK_TRY(cudaMemcpyAsync(grad, tmp.p, (size_t)f.npts * sizeof(float), cudaMemcpyDeviceToHost, st));
         CK_TRY(cudaStreamSynchronize(st));
     } else {
-        CK_TRY(launch_grad_out(org(m->gacc, f), m->cvel.as<float>(), opts->grad_kind, f, grad, st));
+        CK_TRY(launch_grad_out(org(m->gacc, f), m->cvel.as<float>(), opts->grad_kind, scale, f, grad, st));
         CK_TRY(cudaStreamSynchronize(st));
     }
     if (stats) stats->kernel_launches += 1;
@@ -1313,10 +1347,17 @@ int ckfwi_batch_gradient(ckfwi_model* m, const ckfwi_shot* shots, int nshots, co
         acc.kernel_launches += one.kernel_launches + 1;
         acc.pool_bytes_peak = std::max(acc.pool_bytes_peak, one.pool_bytes_peak);
     }
-    // sum + compensation
-    CK_TRY(launch_add_f64(sum.as<double>(), comp.as<double>(), comp.as<double>(), f.npts, st));
-    CK_TRY(cudaMemcpyAsync(grad_sum, comp.p, f.npts * sizeof(double),
-                           mem == CKFWI_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, st));
+    // sum + compensation, scaled; FP64 or rounded once to FP32
+    const double scale = opts->grad_scale != 0.0 ? opts->grad_scale : 1.0;
+    CK_TRY(launch_add_f64(sum.as<double>(), comp.as<double>(), scale, comp.as<double>(), f.npts, st));
+    if (opts->grad_f32) {
+        CK_TRY(launch_f64_to_f32(comp.as<double>(), sum.as<float>(), f.npts, st));
+        CK_TRY(cudaMemcpyAsync(grad_sum, sum.p, f.npts * sizeof(float),
+                               mem == CKFWI_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, st));
+    } else {
+        CK_TRY(cudaMemcpyAsync(grad_sum, comp.p, f.npts * sizeof(double),
+                               mem == CKFWI_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, st));
+    }
     CK_TRY(cudaStreamSynchronize(st));
     if (misfit_sum) *misfit_sum = ms + mc;
     if (stats) *stats = acc;

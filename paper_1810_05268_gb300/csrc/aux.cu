@@ -98,11 +98,12 @@ __device__ __forceinline__ float grad_value(float ga, float c, int kind)
 }
 
 __global__ void grad_out_kernel(const float* __restrict__ gacc, const float* __restrict__ c,
-                                int kind, FieldGeom g, float* __restrict__ out)
+                                int kind, float scale, FieldGeom g, float* __restrict__ out)
 {
     const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= g.npts) return;
-    out[p] = grad_value(gacc[padded(g, p)], c[p], kind);
+    const float v = grad_value(gacc[padded(g, p)], c[p], kind);
+    out[p] = scale == 1.0f ? v : __fmul_rn(scale, v);
 }
 
 // Neumaier-compensated FP64 accumulation of one shot's gradient.
@@ -141,11 +142,17 @@ __global__ void copy_f64_kernel(const double* __restrict__ a, double* __restrict
     if (i < n) b[i] = a[i];
 }
 
-__global__ void add_f64_kernel(const double* __restrict__ a, const double* __restrict__ b,
+__global__ void add_f64_kernel(const double* __restrict__ a, const double* __restrict__ b, double scale,
                                double* __restrict__ out, long long n)
 {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) out[i] = a[i] + b[i];
+    if (i < n) out[i] = scale * (a[i] + b[i]);
+}
+
+__global__ void f64_to_f32_kernel(const double* __restrict__ a, float* __restrict__ out, long long n)
+{
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = (float)a[i];
 }
 
 inline unsigned blocks_for(long long n, int t) { return (unsigned)((n + t - 1) / t); }
@@ -177,10 +184,10 @@ cudaError_t launch_to_padded_w(const float* dense, int kind, float dt, const Fie
     return cudaGetLastError();
 }
 
-cudaError_t launch_grad_out(const float* gacc_origin, const float* c_dense, int kind,
+cudaError_t launch_grad_out(const float* gacc_origin, const float* c_dense, int kind, float scale,
                             const FieldGeom& g, float* out_dense, cudaStream_t s)
 {
-    grad_out_kernel<<<blocks_for(g.npts, 256), 256, 0, s>>>(gacc_origin, c_dense, kind, g, out_dense);
+    grad_out_kernel<<<blocks_for(g.npts, 256), 256, 0, s>>>(gacc_origin, c_dense, kind, scale, g, out_dense);
     return cudaGetLastError();
 }
 
@@ -213,9 +220,15 @@ cudaError_t launch_copy_f64(const double* a, double* b, long long n, cudaStream_
 }  // namespace ckfwi
 
 namespace ckfwi {
-cudaError_t launch_add_f64(const double* a, const double* b, double* out, long long n, cudaStream_t s)
+cudaError_t launch_add_f64(const double* a, const double* b, double scale, double* out, long long n, cudaStream_t s)
 {
-    add_f64_kernel<<<blocks_for(n, 256), 256, 0, s>>>(a, b, out, n);
+    add_f64_kernel<<<blocks_for(n, 256), 256, 0, s>>>(a, b, scale, out, n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_f64_to_f32(const double* a, float* out, long long n, cudaStream_t s)
+{
+    f64_to_f32_kernel<<<blocks_for(n, 256), 256, 0, s>>>(a, out, n);
     return cudaGetLastError();
 }
 }  // namespace ckfwi

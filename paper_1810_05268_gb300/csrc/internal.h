@@ -121,7 +121,7 @@ cudaError_t launch_residual(const float* d, const float* dobs, float* r, int row
                             double* partials, int nparts, double* phi, cudaStream_t s);
 cudaError_t launch_to_padded_w(const float* dense, int kind, float dt, const FieldGeom& g,
                                float* w_origin, float* c2_dense, int* err, cudaStream_t s);
-cudaError_t launch_grad_out(const float* gacc_origin, const float* c2_dense, int kind,
+cudaError_t launch_grad_out(const float* gacc_origin, const float* c_dense, int kind, float scale,
                             const FieldGeom& g, float* out_dense, cudaStream_t s);
 cudaError_t launch_grad_out_f64(const float* gacc_origin, const float* c2_dense, int kind,
                                 const FieldGeom& g, double* sum, double* comp,
@@ -129,7 +129,8 @@ cudaError_t launch_grad_out_f64(const float* gacc_origin, const float* c2_dense,
 cudaError_t launch_cast_restore(const void* src, int utype, const FieldGeom& g,
                                 float* dst_origin, cudaStream_t s);
 cudaError_t launch_copy_f64(const double* a, double* b, long long n, cudaStream_t s);
-cudaError_t launch_add_f64(const double* a, const double* b, double* out, long long n, cudaStream_t s);
+cudaError_t launch_add_f64(const double* a, const double* b, double scale, double* out, long long n, cudaStream_t s);
+cudaError_t launch_f64_to_f32(const double* a, float* out, long long n, cudaStream_t s);
 
 // codec.cu
 struct CodecView {       // a float field to (de)compress, origin based

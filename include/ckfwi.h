@@ -180,16 +180,42 @@ CKFWI_API int ckfwi_adjoint_gradient(ckfwi_model* m, const ckfwi_shot* s, const 
                            const ckfwi_grad_opts* opts, double* misfit, float* grad,
                            ckfwi_stats* stats, void* stream);
 
-/* Several shots on one model, one Revolve schedule shared by all of them,
- * every forward / reverse action one persistent launch over all shots'
- * tiles (Sec. 1.2: shots are independent and their gradients are summed).
+/* Several shots on one model (Sec. 1.2: shots are independent and their
+ * gradients and misfits are summed).  The shots run in batches of B lanes:
+ * every lane holds one shot's wavefields, adjoint fields and checkpoint
+ * storage, all lanes follow one Revolve schedule, and every forward or
+ * reverse step is one kernel launch over the tiles of all lanes (recorded
+ * as one CUDA graph when opts->use_graph).  B = min(nshots, free device
+ * memory / lane size, CKFWI_MAX_LANES from the environment, default 64);
+ * the extra lanes are clones of the model that it owns and keeps.
  * d_obs: nshots arrays [nt+1][nrec_s]; misfit_sum (host, FP64) and grad_sum
- * (dense float64 total grid, same `mem`) receive the sums over shots in
- * shot order, accumulated with compensated FP64 summation. */
+ * (dense total grid, same `mem`; float64, or float32 when opts->grad_f32)
+ * receive the sums over shots in shot order, accumulated with compensated
+ * FP64 summation and multiplied by opts->grad_scale (0 = 1).  Every shot's
+ * result is bitwise the one ckfwi_adjoint_gradient computes for it.
+ * stats: step counters summed over shots; ratio fields are 0. */
 CKFWI_API int ckfwi_batch_gradient(ckfwi_model* m, const ckfwi_shot* shots, int nshots,
                          const float* const* d_obs, int mem, const ckfwi_grad_opts* opts,
                          double* misfit_sum, double* grad_sum, ckfwi_stats* stats,
                          void* stream);
+
+/* A batch of shots with uneven apertures: shot s runs on its own model
+ * models[s] (a window of a larger survey model, with its own grid size and
+ * medium), all models distinct and sharing dims, space_order and nt.  One
+ * Revolve schedule drives every lane and each forward or reverse step is one
+ * launch over all windows' tiles, as in ckfwi_batch_gradient.  offsets
+ * [nshots][3] (host) place each window's total grid (z, y, x) inside the
+ * global grid global_n[3] (host; 2D: y offset 0 and global_n[1] = 1);
+ * grad_sum (dense global grid, same `mem`, float64 or float32 per
+ * opts->grad_f32) receives sum_s of shot s's gradient added at its window,
+ * in shot order with compensated FP64 summation, points outside every
+ * window 0; misfit_sum (host) the FP64 sum of the misfits.  EINVAL when a
+ * window leaves the global grid, a model repeats or lacks a medium.  All
+ * lanes run at once: ENOMEM when their storage does not fit. */
+CKFWI_API int ckfwi_batch_gradient_models(ckfwi_model* const* models, const ckfwi_shot* shots, int nshots,
+                         const float* const* d_obs, int mem, const ckfwi_grad_opts* opts,
+                         const int* offsets, const int* global_n, double* misfit_sum,
+                         double* grad_sum, ckfwi_stats* stats, void* stream);
 
 CKFWI_API void ckfwi_free(ckfwi_model* m);
 

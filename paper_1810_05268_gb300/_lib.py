@@ -48,7 +48,7 @@ class Stats(ctypes.Structure):
 
 
 EXPORTS = ["ckfwi_create_model", "ckfwi_set_model", "ckfwi_forward_shot", "ckfwi_misfit", "ckfwi_adjoint_gradient",
-           "ckfwi_batch_gradient", "ckfwi_free", "ckfwi_error_string", "ckfwi_revolve_schedule",
+           "ckfwi_batch_gradient", "ckfwi_batch_gradient_models", "ckfwi_free", "ckfwi_error_string", "ckfwi_revolve_schedule",
            "ckfwi_codec_bound_words", "ckfwi_codec_compress", "ckfwi_codec_decompress",
            "ckfwi_codec_compress_noalloc"]
 
@@ -70,6 +70,7 @@ def lib():
         L.ckfwi_misfit.argtypes = [P, P, P, I, P, P, P]
         L.ckfwi_adjoint_gradient.argtypes = [P, P, P, I, P, P, P, P, P]
         L.ckfwi_batch_gradient.argtypes = [P, P, I, P, I, P, P, P, P, P]
+        L.ckfwi_batch_gradient_models.argtypes = [P, P, I, P, I, P, P, P, P, P, P, P]
         L.ckfwi_free.argtypes = [P]
         L.ckfwi_free.restype = None
         L.ckfwi_error_string.argtypes = [I]
@@ -82,7 +83,7 @@ def lib():
         L.ckfwi_codec_compress_noalloc.argtypes = [P, I, I, I, I, D, P, LL, P, P, P]
         for name in ("ckfwi_create_model", "ckfwi_set_model", "ckfwi_forward_shot", "ckfwi_misfit",
                      "ckfwi_adjoint_gradient",
-                     "ckfwi_batch_gradient", "ckfwi_revolve_schedule", "ckfwi_codec_compress",
+                     "ckfwi_batch_gradient", "ckfwi_batch_gradient_models", "ckfwi_revolve_schedule", "ckfwi_codec_compress",
                      "ckfwi_codec_decompress", "ckfwi_codec_compress_noalloc"):
             getattr(L, name).restype = I
         _lib = L

@@ -210,11 +210,8 @@ def adjoint_gradient(model, grid: GridSpec, shot: ShotSpec, d_obs, ckpt_slots, s
     return phi.value, grad, st.as_dict()
 
 
-def batch_gradient(model, grid: GridSpec, shots, d_obs_list, ckpt_slots, store_mode=STORE_FP32, tol=0.0,
-                   pool_bytes=0, grad_kind=SLOWNESS2, use_graph=False, grad_sum=None, stream=None,
-                   grad_scale=1.0, grad_f32=False):
-    """(sum of misfits, sum of gradients over shots (FP64, or FP32 with grad_f32), stats dict)."""
-    n = len(shots)
+def _d_obs_ptrs(d_obs_list):
+    n = len(d_obs_list)
     ptrs = (ctypes.c_void_p * n)()
     mem = None
     for i, d in enumerate(d_obs_list):
@@ -223,22 +220,80 @@ def batch_gradient(model, grid: GridSpec, shots, d_obs_list, ckpt_slots, store_m
         if mem is not None and m != mem:
             raise ValueError("mixed host / device d_obs")
         mem = m
+    return ptrs, mem
+
+
+def _shot_array(shots):
+    carr = (Shot * len(shots))()
+    keep = []
+    for i, sh in enumerate(shots):
+        carr[i] = sh.c()
+        keep.append(sh._keep)
+    return carr, keep
+
+
+def batch_gradient(model, grid: GridSpec, shots, d_obs_list, ckpt_slots, store_mode=STORE_FP32, tol=0.0,
+                   pool_bytes=0, grad_kind=SLOWNESS2, use_graph=False, grad_sum=None, stream=None,
+                   grad_scale=1.0, grad_f32=False, profile=False):
+    """(sum of misfits, sum of gradients over shots (FP64, or FP32 with grad_f32), stats dict).
+
+    The shots run as batches of lanes, one launch per stencil step over all
+    lanes of a batch."""
+    n = len(shots)
+    if len(d_obs_list) != n:
+        raise ValueError("one d_obs per shot")
+    ptrs, mem = _d_obs_ptrs(d_obs_list)
     gdt = np.float32 if grad_f32 else np.float64
     if grad_sum is None:
         grad_sum = _alloc(tuple(grid.shape), gdt, "cuda" if mem == DEVICE else None)
     pg, memg = _buf(grad_sum, gdt)
     if memg != mem:
         raise ValueError("d_obs and grad_sum must both be host or both be device buffers")
-    carr = (Shot * n)()
-    keep = []
-    for i, sh in enumerate(shots):
-        carr[i] = sh.c()
-        keep.append(sh._keep)
-    o = _opts(ckpt_slots, store_mode, tol, pool_bytes, grad_kind, use_graph, False, grad_scale, grad_f32)
+    carr, keep = _shot_array(shots)
+    o = _opts(ckpt_slots, store_mode, tol, pool_bytes, grad_kind, use_graph, profile, grad_scale, grad_f32)
     phi = ctypes.c_double(0.0)
     st = Stats()
     _check(lib().ckfwi_batch_gradient(model, carr, n, ptrs, mem, ctypes.byref(o), ctypes.byref(phi), pg,
                                       ctypes.byref(st), _stream(stream)), "ckfwi_batch_gradient")
+    del keep
+    return phi.value, grad_sum, st.as_dict()
+
+
+def batch_gradient_models(models, shots, d_obs_list, offsets, global_shape, ckpt_slots, store_mode=STORE_FP32,
+                          tol=0.0, pool_bytes=0, grad_kind=SLOWNESS2, use_graph=False, grad_sum=None, stream=None,
+                          grad_scale=1.0, grad_f32=False, profile=False):
+    """Shots with uneven apertures: shot s on its own model (window) models[s],
+    placed at offsets[s] = (z, y, x) in a global grid of global_shape.
+    Returns (sum of misfits, gradient sum on the global grid, stats dict)."""
+    n = len(shots)
+    if len(models) != n or len(d_obs_list) != n or len(offsets) != n:
+        raise ValueError("one model, d_obs and offset per shot")
+    ptrs, mem = _d_obs_ptrs(d_obs_list)
+    gshape = tuple(int(v) for v in global_shape)
+    if len(gshape) == 2:
+        gn = (gshape[0], 1, gshape[1])
+    else:
+        gn = gshape
+    gdt = np.float32 if grad_f32 else np.float64
+    if grad_sum is None:
+        grad_sum = _alloc(gshape, gdt, "cuda" if mem == DEVICE else None)
+    pg, memg = _buf(grad_sum, gdt)
+    if memg != mem:
+        raise ValueError("d_obs and grad_sum must both be host or both be device buffers")
+    marr = (ctypes.c_void_p * n)(*[m.h if isinstance(m, Model) else m for m in models])
+    off = np.zeros((n, 3), dtype=np.int32)
+    for i, o3 in enumerate(offsets):
+        o3 = tuple(int(v) for v in o3)
+        off[i] = (o3[0], 0, o3[1]) if len(o3) == 2 else o3
+    gna = (ctypes.c_int * 3)(*gn)
+    carr, keep = _shot_array(shots)
+    o = _opts(ckpt_slots, store_mode, tol, pool_bytes, grad_kind, use_graph, profile, grad_scale, grad_f32)
+    phi = ctypes.c_double(0.0)
+    st = Stats()
+    _check(lib().ckfwi_batch_gradient_models(marr, carr, n, ptrs, mem, ctypes.byref(o), off.ctypes.data, gna,
+                                             ctypes.byref(phi), pg, ctypes.byref(st), _stream(stream)),
+           "ckfwi_batch_gradient_models")
+    del keep
     return phi.value, grad_sum, st.as_dict()
 
 

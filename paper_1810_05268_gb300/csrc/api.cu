@@ -22,6 +22,7 @@
 #include <cuda_fp16.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -30,6 +31,7 @@
 #include <memory>
 #include <mutex>
 #include <new>
+#include <set>
 #include <tuple>
 #include <vector>
 
@@ -61,6 +63,8 @@ int cuda_status(cudaError_t e)
     }
     return CKFWI_ECUDA;
 }
+
+int cuda_status_or_ok(cudaError_t e) { return e == cudaSuccess ? CKFWI_OK : cuda_status(e); }
 
 struct DevMem {
     void* p = nullptr;
@@ -237,6 +241,47 @@ struct GraphKey {
     }
 };
 
+// An instantiated graph and what its recording launched.
+struct GraphExec {
+    cudaGraphExec_t ex = nullptr;
+    long long launches = 0;
+    long long count[5] = {0, 0, 0, 0, 0};
+    GraphExec() = default;
+    GraphExec(const GraphExec&) = delete;
+    GraphExec& operator=(const GraphExec&) = delete;
+    ~GraphExec() { release(); }
+    void release()
+    {
+        if (ex) cudaGraphExecDestroy(ex);
+        ex = nullptr;
+    }
+};
+
+constexpr size_t MAX_GRAPHS = 8;   // recorded graphs kept per model
+
+// Tile shape and per-lane z-run lengths of a batch of lanes.
+struct BatchTiles {
+    Tile tf{}, ta{};
+    std::vector<int> zf, za;
+};
+
+struct BatchKey {
+    std::vector<long long> lanes;   // (uid, gen) of every lane
+    int nt, M, mode, kind;
+    float tol;
+    bool operator<(const BatchKey& o) const
+    {
+        return std::tie(lanes, nt, M, mode, kind, tol) < std::tie(o.lanes, o.nt, o.M, o.mode, o.kind, o.tol);
+    }
+};
+
+// A recorded batch and the argument tables its launches read.
+struct BatchGraph {
+    GraphExec ex;
+    DevMem tabs;
+    void release() { ex.release(); }
+};
+
 }  // namespace
 
 struct ckfwi_model {
@@ -267,11 +312,23 @@ struct ckfwi_model {
     cudaEvent_t ev = nullptr;
     std::vector<cudaEvent_t> evpool; // profiling events, reused across calls
     std::map<std::tuple<const void*, int, int, int>, CUtensorMap> tmaps;   // (base, dtype, box x, box y)
+    long long uid = 0;              // process-unique id (batch graph keys)
+    long long model_ver = 0;        // bumped by every ckfwi_set_model
+    long long src_ver = -1;         // clone: the parent's model_ver its medium copies
+    long long cap_words = 0;        // codec pool capacity [words]
     // graphs
-    std::map<GraphKey, cudaGraphExec_t> graphs;
+    std::map<GraphKey, GraphExec> graphs;
+    std::vector<GraphKey> graph_order;
+    // batches of shots: clones of this model serve as extra lanes
+    std::vector<std::unique_ptr<ckfwi_model>> clones;
+    std::map<std::vector<long long>, BatchTiles> btiles;
+    std::map<BatchKey, BatchGraph> bgraphs;
+    std::vector<BatchKey> bgraph_order;
+    DevMem btabs;                   // batch argument tables of an unrecorded run
     ~ckfwi_model()
     {
-        for (auto& kv : graphs) cudaGraphExecDestroy(kv.second);
+        graphs.clear();
+        bgraphs.clear();
         if (cap) cudaStreamDestroy(cap);
         if (ev) cudaEventDestroy(ev);
         for (cudaEvent_t e : evpool) cudaEventDestroy(e);
@@ -469,12 +526,68 @@ struct Prof {
     }
 };
 
+// The buffers a schedule step reads and writes.  Every lane (shot) of a
+// batch runs the same schedule, so a step names roles, and each lane
+// resolves them to its own buffers.
+enum RoleKind { R_NONE, R_ZERO, R_WORK, R_LAM, R_UN, R_TRAJ, R_SLOT };
+struct Role {
+    int kind = R_NONE;
+    int idx = 0;      // work / lam index, trajectory level, or slot (>= 1)
+    int which = 0;    // slot: 0 = u^s, 1 = u^{s-1}
+    bool operator==(const Role& o) const { return kind == o.kind && idx == o.idx && which == o.which; }
+    bool operator!=(const Role& o) const { return !(*this == o); }
+};
+const Role NONE_R{R_NONE, 0, 0};
+const Role ZERO_R{R_ZERO, 0, 0};
+const Role UN_R{R_UN, 0, 0};
+Role work_r(int i) { return Role{R_WORK, i, 0}; }
+Role lam_r(int i) { return Role{R_LAM, i, 0}; }
+Role traj_r(int n) { return Role{R_TRAJ, n, 0}; }
+Role slot_r(int s, int w) { return Role{R_SLOT, s, w}; }
+
+void* rptr(ckfwi_model* m, int mode, const Role& r)
+{
+    const FieldGeom& f = m->fg;
+    switch (r.kind) {
+    case R_ZERO: return org(m->zero, f);
+    case R_WORK: return org(m->work[r.idx], f);
+    case R_LAM: return org(m->lam[r.idx], f);
+    case R_UN: return org(m->uN, f);
+    case R_TRAJ: return m->traj.as<float>() + (size_t)r.idx * f.alloc + f.origin;
+    case R_SLOT: {
+        // uncompressed slots: two padded fields per slot, FP32 or 16-bit
+        const size_t es = mode == CKFWI_STORE_FP32 ? 4 : 2;
+        return m->pool.as<char>() + ((size_t)(r.idx - 1) * 2 + r.which) * field_bytes(f, es) + (size_t)f.origin * es;
+    }
+    default: return nullptr;
+    }
+}
+
 struct Ctx {
-    ckfwi_model* m;
+    ckfwi_model* m;                 // the model (lane 0 of a batch)
     cudaStream_t st;
     long long launches = 0;
     Prof prof;
     long long count[PC_N] = {0, 0, 0, 0, 0};
+    int mode = CKFWI_STORE_FP32;    // storage mode R_SLOT roles resolve for
+    // batch: every stencil step is one launch over all lanes
+    std::vector<ckfwi_model*> lanes;   // empty: the model alone
+    bool batch = false;
+    bool issue = true;              // false: only collect the batch argument tables
+    std::vector<FwdArgs> ftab;      // one row per lane and step, in launch order
+    std::vector<AdjArgs> atab;
+    size_t fi = 0, ai = 0;          // next row
+    const FwdArgs* ftab_d = nullptr;
+    const AdjArgs* atab_d = nullptr;
+    const int* fstart_d = nullptr;
+    const int* astart_d = nullptr;
+    long long fblocks = 0, ablocks = 0;
+    Tile bf{}, ba{};                // batch tile shapes; z-run length per lane in zf / za
+    std::vector<int> zf, za;
+    int nl() const { return lanes.empty() ? 1 : (int)lanes.size(); }
+    ckfwi_model* lane(int l) const { return lanes.empty() ? m : lanes[l]; }
+    void* ptr(int l, const Role& r) const { return rptr(lane(l), mode, r); }
+    float* fptr(int l, const Role& r) const { return static_cast<float*>(ptr(l, r)); }
     int begin(int cls)
     {
         ++count[cls];
@@ -505,107 +618,168 @@ FwdArgs fwd_args(ckfwi_model* m)
     return a;
 }
 
-// one forward step n: u -> out; optional sampling of d^n and fused takeshot
-int fwd_step(Ctx& cx, const float* u, const float* up, float* out, int n, bool record, int ck,
-             void* ck_u, void* ck_up)
+AdjArgs adj_args(ckfwi_model* m)
 {
-    ckfwi_model* m = cx.m;
-    FwdArgs a = fwd_args(m);
-    a.u = u;
-    a.up = up;
-    a.out = out;
-    a.src = m->shot.src.view;
-    a.src.series = m->shot.wavelet.as<float>() + n;
-    a.ck_u = ck_u;
-    a.ck_up = ck_up;
-    bool sep = false;
-    if (record) {
-        Sample sm{};
-        sm.n = m->shot.nrec;
-        sm.nst = m->shot.nst;
-        sm.idx = m->shot.ridx.as<long long>();
-        sm.wt = m->shot.rwt.as<float>();
-        sm.out = m->shot.dsim.as<float>() + (size_t)n * m->shot.nrec;
-        const long long gx = (m->fg.nx + m->tf.bx - 1) / m->tf.bx;
-        const long long gy = m->fg.dims == 3 ? (m->fg.ny + m->tf.by - 1) / m->tf.by : 1;
-        const long long gz = (m->fg.nz + m->tf.zlen - 1) / m->tf.zlen;
-        const long long tpc = (m->tf.ver == 2 ? m->tf.bx / 4 : m->tf.bx) * (long long)m->tf.by;
-        if (gx * gy * gz * tpc >= sm.n) a.smp = sm;
-        else {
-            CK_TRY(launch_sample(u, sm, cx.st));
-            ++cx.launches;
-            sep = true;
-        }
-    }
-    (void)sep;
-    const int tok = cx.begin(PC_FWD);
-    if (m->tf.ver == 2) {
-        CUtensorMap tm;
-        ST_TRY(tensor_map(m, u, U_FP32, tma_tile_x() + 2 * tma_halo_x(m->K), m->tf.by + 2 * m->K, &tm));
-        CK_TRY(launch_fwd_tma(a, tm, m->tf, m->K, ck, cx.st));
-    } else {
-        CK_TRY(launch_fwd(a, m->tf, m->K, ck, cx.st));
-    }
-    cx.end(tok);
-    ++cx.launches;
-    return CKFWI_OK;
-}
-
-int adj_step(Ctx& cx, const float* l1, const float* l2, float* l0, const void* u, int utype, int j)
-{
-    ckfwi_model* m = cx.m;
     AdjArgs a{};
     a.g = m->fg;
-    a.l1 = l1;
-    a.l2 = l2;
-    a.l0 = l0;
-    a.u = u;
     a.w = org(m->w, m->fg);
     a.gacc = org(m->gacc, m->fg);
     a.eta = m->eta.as<float>();
     a.hdt = m->hdt;
     std::memcpy(a.c, m->c, sizeof(a.c));
-    a.adj = m->shot.adj.view;
-    a.adj.series = m->shot.resid.as<float>() + (size_t)j * m->shot.nrec;
-    a.src = m->shot.src.view;
-    a.src.series = m->shot.wavelet.as<float>() + (j - 1);
     a.err = m->flags.as<int>();
-    const int tok = cx.begin(PC_ADJ);
-    if (m->ta.ver == 2) {
-        CUtensorMap tl, tu;
-        const int bx = tma_tile_x() + 2 * tma_halo_x(m->K), by = m->ta.by + 2 * m->K;
-        ST_TRY(tensor_map(m, l1, U_FP32, bx, by, &tl));
-        ST_TRY(tensor_map(m, u, utype, bx, by, &tu));
-        CK_TRY(launch_adj_tma(a, tl, tu, m->ta, m->K, utype, cx.st));
-    } else {
-        CK_TRY(launch_adj(a, m->ta, m->K, utype, cx.st));
-    }
-    cx.end(tok);
-    ++cx.launches;
-    return CKFWI_OK;
+    return a;
 }
 
-int sample_last(Ctx& cx, const float* uN)
+// receiver sampling of u^n for the model's shot
+Sample sample_of(ckfwi_model* m, int n)
 {
-    ckfwi_model* m = cx.m;
     Sample sm{};
     sm.n = m->shot.nrec;
     sm.nst = m->shot.nst;
     sm.idx = m->shot.ridx.as<long long>();
     sm.wt = m->shot.rwt.as<float>();
-    sm.out = m->shot.dsim.as<float>() + (size_t)m->g.nt * m->shot.nrec;
-    CK_TRY(launch_sample(uN, sm, cx.st));
-    ++cx.launches;
+    sm.out = m->shot.dsim.as<float>() + (size_t)n * m->shot.nrec;
+    return sm;
+}
+
+// whether a step's grid has one thread per receiver, so that it can sample
+bool grid_samples(const FieldGeom& f, const Tile& t, int zlen, int nrec)
+{
+    const long long gx = (f.nx + t.bx - 1) / t.bx;
+    const long long gy = f.dims == 3 ? (f.ny + t.by - 1) / t.by : 1;
+    const long long gz = (f.nz + zlen - 1) / zlen;
+    const long long tpc = (t.ver == 2 ? t.bx / 4 : t.bx) * (long long)t.by;
+    return gx * gy * gz * tpc >= nrec;
+}
+
+// One forward step n of every lane: u -> out, optionally sampling d^n and
+// writing a fused takeshot (ck, ck_u, ck_up).
+int fwd_step(Ctx& cx, const Role& u, const Role& up, const Role& out, int n, bool record, int ck,
+             const Role& ck_u, const Role& ck_up)
+{
+    const int NL = cx.nl();
+    for (int l = 0; l < NL; ++l) {
+        ckfwi_model* m = cx.lane(l);
+        FwdArgs a = fwd_args(m);
+        a.u = cx.fptr(l, u);
+        a.up = cx.fptr(l, up);
+        a.out = cx.fptr(l, out);
+        a.src = m->shot.src.view;
+        a.src.series = m->shot.wavelet.as<float>() + n;
+        a.ck_u = cx.ptr(l, ck_u);
+        a.ck_up = cx.ptr(l, ck_up);
+        const Tile& t = cx.batch ? cx.bf : m->tf;
+        const int zlen = cx.batch ? cx.zf[l] : m->tf.zlen;
+        bool sep = false;
+        if (record) {
+            const Sample sm = sample_of(m, n);
+            if (grid_samples(m->fg, t, zlen, sm.n)) a.smp = sm;
+            else sep = true;
+            if (sep && cx.issue) {
+                CK_TRY(launch_sample(a.u, sm, cx.st));
+                ++cx.launches;
+            }
+        }
+        if (cx.batch) {
+            a.zlen = zlen;
+            if (!cx.issue) cx.ftab.push_back(a);
+            continue;
+        }
+        const int tok = cx.begin(PC_FWD);
+        if (m->tf.ver == 2) {
+            CUtensorMap tm;
+            ST_TRY(tensor_map(m, a.u, U_FP32, tma_tile_x() + 2 * tma_halo_x(m->K), m->tf.by + 2 * m->K, &tm));
+            CK_TRY(launch_fwd_tma(a, tm, m->tf, m->K, ck, cx.st));
+        } else {
+            CK_TRY(launch_fwd(a, m->tf, m->K, ck, cx.st));
+        }
+        cx.end(tok);
+        ++cx.launches;
+    }
+    if (cx.batch) {
+        if (cx.issue) {
+            const int tok = cx.begin(PC_FWD);
+            BatchLaunch<FwdArgs> b{cx.ftab_d + cx.fi, cx.fstart_d, NL, cx.m->fg.dims, cx.fblocks};
+            CK_TRY(launch_fwd_batch(b, cx.bf, cx.m->K, ck, cx.st));
+            cx.end(tok);
+            ++cx.launches;
+        }
+        cx.fi += NL;
+    }
     return CKFWI_OK;
 }
 
+// One fused reverse step j of every lane: lam^{j-1} from lam^j, lam^{j+1}
+// and the residual row j; gacc += lam^{j-1} (lap u^{j-1} + source^{j-1}).
+int adj_step(Ctx& cx, const Role& l1, const Role& l2, const Role& l0, const Role& u, int utype, int j)
+{
+    const int NL = cx.nl();
+    for (int l = 0; l < NL; ++l) {
+        ckfwi_model* m = cx.lane(l);
+        AdjArgs a = adj_args(m);
+        a.l1 = cx.fptr(l, l1);
+        a.l2 = cx.fptr(l, l2);
+        a.l0 = cx.fptr(l, l0);
+        a.u = cx.ptr(l, u);
+        a.adj = m->shot.adj.view;
+        a.adj.series = m->shot.resid.as<float>() + (size_t)j * m->shot.nrec;
+        a.src = m->shot.src.view;
+        a.src.series = m->shot.wavelet.as<float>() + (j - 1);
+        if (cx.batch) {
+            a.zlen = cx.za[l];
+            if (!cx.issue) cx.atab.push_back(a);
+            continue;
+        }
+        const int tok = cx.begin(PC_ADJ);
+        if (m->ta.ver == 2) {
+            CUtensorMap tl, tu;
+            const int bx = tma_tile_x() + 2 * tma_halo_x(m->K), by = m->ta.by + 2 * m->K;
+            ST_TRY(tensor_map(m, a.l1, U_FP32, bx, by, &tl));
+            ST_TRY(tensor_map(m, a.u, utype, bx, by, &tu));
+            CK_TRY(launch_adj_tma(a, tl, tu, m->ta, m->K, utype, cx.st));
+        } else {
+            CK_TRY(launch_adj(a, m->ta, m->K, utype, cx.st));
+        }
+        cx.end(tok);
+        ++cx.launches;
+    }
+    if (cx.batch) {
+        if (cx.issue) {
+            const int tok = cx.begin(PC_ADJ);
+            BatchLaunch<AdjArgs> b{cx.atab_d + cx.ai, cx.astart_d, NL, cx.m->fg.dims, cx.ablocks};
+            CK_TRY(launch_adj_batch(b, cx.ba, cx.m->K, utype, cx.st));
+            cx.end(tok);
+            ++cx.launches;
+        }
+        cx.ai += NL;
+    }
+    return CKFWI_OK;
+}
+
+// d^N = P u^N of every lane
+int sample_last(Ctx& cx, const Role& uN)
+{
+    if (!cx.issue) return CKFWI_OK;
+    for (int l = 0; l < cx.nl(); ++l) {
+        ckfwi_model* m = cx.lane(l);
+        CK_TRY(launch_sample(cx.fptr(l, uN), sample_of(m, m->g.nt), cx.st));
+        ++cx.launches;
+    }
+    return CKFWI_OK;
+}
+
+// residual r = d - d_obs and the FP64 misfit of every lane
 int residual(Ctx& cx)
 {
-    ckfwi_model* m = cx.m;
-    CK_TRY(launch_residual(m->shot.dsim.as<float>(), m->shot.dobs.as<float>(), m->shot.resid.as<float>(),
-                           m->g.nt + 1, m->shot.nrec, m->partials.as<double>(), m->nparts,
-                           m->phi.as<double>(), cx.st));
-    cx.launches += 2;
+    if (!cx.issue) return CKFWI_OK;
+    for (int l = 0; l < cx.nl(); ++l) {
+        ckfwi_model* m = cx.lane(l);
+        CK_TRY(launch_residual(m->shot.dsim.as<float>(), m->shot.dobs.as<float>(), m->shot.resid.as<float>(),
+                               m->g.nt + 1, m->shot.nrec, m->partials.as<double>(), m->nparts,
+                               m->phi.as<double>(), cx.st));
+        cx.launches += 2;
+    }
     return CKFWI_OK;
 }
 
@@ -783,15 +957,13 @@ int read_flags(ckfwi_model* m, cudaStream_t st, int* fl)
 
 // ------------------------------------------------------------ gradient run
 struct State {
-    const void* cur;
-    const void* prev;
+    Role cur, prev;
     int tcur, tprev;    // U_FP32 / U_BF16 / U_FP16
 };
 
 struct RunCfg {
     int N, M, mode;
     float tol_f;
-    long long cap_words;
     bool store_all;
 };
 
@@ -808,78 +980,67 @@ CodecView field_view(const FieldGeom& f)
     return v;
 }
 
-float* pick_free(ckfwi_model* m, const State& s)
+// a working field that holds neither the current nor the previous state
+Role pick_free(const State& s)
 {
-    for (int i = 0; i < 3; ++i) {
-        float* p = org(m->work[i], m->fg);
-        if (p != s.cur && p != s.prev) return p;
-    }
-    return nullptr;
+    for (int i = 0; i < 3; ++i)
+        if (work_r(i) != s.cur && work_r(i) != s.prev) return work_r(i);
+    return NONE_R;
 }
 
-// the recorded part of a gradient: everything between "inputs staged" and
-// "outputs ready" (this is what a CUDA graph captures)
+// The recorded part of a gradient: everything between "inputs staged" and
+// "outputs ready" (this is what a CUDA graph captures).  Runs every lane of
+// the context through the same schedule.
 int run_body(Ctx& cx, const RunCfg& rc, const std::vector<Action>& acts, long long* counters)
 {
-    ckfwi_model* m = cx.m;
-    const FieldGeom& f = m->fg;
+    const int NL = cx.nl();
     const int N = rc.N;
-    float* zero = org(m->zero, f);
-    for (int i = 0; i < 3; ++i) {
-        CK_TRY(cudaMemsetAsync(m->lam[i].p, 0, m->lam[i].bytes, cx.st));
+    if (cx.issue) {
+        for (int l = 0; l < NL; ++l) {
+            ckfwi_model* m = cx.lane(l);
+            for (int i = 0; i < 3; ++i) CK_TRY(cudaMemsetAsync(m->lam[i].p, 0, m->lam[i].bytes, cx.st));
+            CK_TRY(cudaMemsetAsync(m->gacc.p, 0, m->gacc.bytes, cx.st));
+            CK_TRY(cudaMemsetAsync(m->shot.dsim.p, 0, m->shot.dsim.bytes, cx.st));
+        }
     }
-    CK_TRY(cudaMemsetAsync(m->gacc.p, 0, m->gacc.bytes, cx.st));
-    CK_TRY(cudaMemsetAsync(m->shot.dsim.p, 0, m->shot.dsim.bytes, cx.st));
     int li = 0;   // lam rotation: lam[li] = lam^{j}, lam[(li+1)%3] = lam^{j+1}
-    auto reverse = [&](int s, const void* u, int ut) -> int {
-        float* l1 = org(m->lam[li], f);
-        float* l2 = org(m->lam[(li + 1) % 3], f);
-        float* l0 = org(m->lam[(li + 2) % 3], f);
-        ST_TRY(adj_step(cx, l1, l2, l0, u, ut, s + 1));
-        li = (li + 2) % 3;   // new lam^{j} = l0, lam^{j+1} = old l1
+    auto reverse = [&](int s, const Role& u, int ut) -> int {
+        ST_TRY(adj_step(cx, lam_r(li), lam_r((li + 1) % 3), lam_r((li + 2) % 3), u, ut, s + 1));
+        li = (li + 2) % 3;   // new lam^{j} = old lam^{j-1}, lam^{j+1} = old lam^{j}
         return CKFWI_OK;
     };
     long long fsteps = 0;
     if (rc.store_all) {
-        float* tr = m->traj.as<float>();
-        auto T = [&](int n) { return tr + (size_t)n * f.alloc + f.origin; };
         for (int n = 0; n < N; ++n) {
-            const float* u = n == 0 ? zero : T(n);
-            const float* up = n <= 1 ? zero : T(n - 1);
-            float* out = (n + 1 < N) ? T(n + 1) : org(m->uN, f);
-            ST_TRY(fwd_step(cx, u, up, out, n, true, CK_NONE, nullptr, nullptr));
+            const Role u = n == 0 ? ZERO_R : traj_r(n);
+            const Role up = n <= 1 ? ZERO_R : traj_r(n - 1);
+            const Role out = (n + 1 < N) ? traj_r(n + 1) : UN_R;
+            ST_TRY(fwd_step(cx, u, up, out, n, true, CK_NONE, NONE_R, NONE_R));
             ++fsteps;
         }
-        ST_TRY(sample_last(cx, org(m->uN, f)));
+        ST_TRY(sample_last(cx, UN_R));
         ST_TRY(residual(cx));
-        for (int s = N - 1; s >= 0; --s) ST_TRY(reverse(s, s == 0 ? zero : T(s), U_FP32));
+        for (int s = N - 1; s >= 0; --s) ST_TRY(reverse(s, s == 0 ? ZERO_R : traj_r(s), U_FP32));
         counters[0] = fsteps;
         return CKFWI_OK;
     }
     // Revolve
-    const size_t fb = field_bytes(f, 4), hb = field_bytes(f, 2);
-    auto slot_ptr = [&](int slot, int which) -> void* {
-        // slot >= 1; two fields per slot
-        if (rc.mode == CKFWI_STORE_FP32)
-            return m->pool.as<char>() + ((size_t)(slot - 1) * 2 + which) * fb + f.origin * 4;
-        return m->pool.as<char>() + ((size_t)(slot - 1) * 2 + which) * hb + f.origin * 2;
-    };
     const int ut_slot = rc.mode == CKFWI_STORE_BF16 ? U_BF16 : (rc.mode == CKFWI_STORE_FP16 ? U_FP16 : U_FP32);
-    long long* sb = m->slotbase.as<long long>();     // [0..M]: slot starts, [M+1..2M]: mids
-    auto sbase = [&](int slot) { return sb + slot; };
-    auto smid = [&](int slot) { return sb + (rc.M + 1) + slot; };
-    if (rc.mode == CKFWI_STORE_CODEC) {
-        CK_TRY(cudaMemsetAsync(sb, 0, sizeof(long long) * 2, cx.st));
-        CK_TRY(cudaMemsetAsync(m->statw.p, 0, m->statw.bytes, cx.st));
+    // codec: slotbase[0..M] are the slots' start words, [M+1..2M] the
+    // start words of their second field
+    auto sbase = [&](ckfwi_model* m, int slot) { return m->slotbase.as<long long>() + slot; };
+    auto smid = [&](ckfwi_model* m, int slot) { return m->slotbase.as<long long>() + (rc.M + 1) + slot; };
+    if (rc.mode == CKFWI_STORE_CODEC && cx.issue) {
+        for (int l = 0; l < NL; ++l) {
+            ckfwi_model* m = cx.lane(l);
+            CK_TRY(cudaMemsetAsync(m->slotbase.p, 0, sizeof(long long) * 2, cx.st));
+            CK_TRY(cudaMemsetAsync(m->statw.p, 0, m->statw.bytes, cx.st));
+        }
     }
-    const CodecView cv = field_view(f);
-    int* cerr = m->flags.as<int>() + 1;
-    unsigned long long* sw = m->statw.as<unsigned long long>();
-    long long ncomp = 0;
+    long long ncomp = 0;   // compressions per lane
 
-    State st{zero, zero, U_FP32, U_FP32};
+    State st{ZERO_R, ZERO_R, U_FP32, U_FP32};
     bool first_sweep = true;
-    int cur_state = 0;
     for (size_t ai = 0; ai < acts.size(); ++ai) {
         const Action& A = acts[ai];
         const bool next_take = ai + 1 < acts.size() && acts[ai + 1].op == ACT_TAKESHOT;
@@ -889,90 +1050,109 @@ int run_body(Ctx& cx, const RunCfg& rc, const std::vector<Action>& acts, long lo
                 const int n = A.a + i;
                 const bool last = i == A.b - 1;
                 int ck = CK_NONE;
-                void *cku = nullptr, *ckup = nullptr;
-                float* out = pick_free(m, st);
+                Role cku = NONE_R, ckup = NONE_R;
+                Role out = pick_free(st);
                 if (last && next_take && rc.mode != CKFWI_STORE_CODEC) {
                     const int slot = acts[ai + 1].b;
                     if (rc.mode == CKFWI_STORE_FP32) {
-                        out = static_cast<float*>(slot_ptr(slot, 0));
+                        out = slot_r(slot, 0);   // u^{n+1} straight into the slot
                         ck = CK_FP32;
-                        ckup = slot_ptr(slot, 1);
+                        ckup = slot_r(slot, 1);
                     } else {
                         ck = rc.mode == CKFWI_STORE_BF16 ? CK_BF16 : CK_FP16;
-                        cku = slot_ptr(slot, 0);
-                        ckup = slot_ptr(slot, 1);
+                        cku = slot_r(slot, 0);
+                        ckup = slot_r(slot, 1);
                     }
                 }
-                ST_TRY(fwd_step(cx, static_cast<const float*>(st.cur), static_cast<const float*>(st.prev), out, n,
-                                first_sweep, ck, cku, ckup));
+                ST_TRY(fwd_step(cx, st.cur, st.prev, out, n, first_sweep, ck, cku, ckup));
                 ++fsteps;
                 st.prev = st.cur;
                 st.tprev = st.tcur;
                 st.cur = out;
                 st.tcur = U_FP32;
             }
-            cur_state = A.a + A.b;
         } else if (A.op == ACT_TAKESHOT) {
             if (rc.mode == CKFWI_STORE_CODEC) {
-                int tok = cx.begin(PC_COMP);
-                CK_TRY(codec_compress_dev(static_cast<const float*>(st.cur), cv, rc.tol_f, m->pool.as<uint32_t>(),
-                                          sbase(A.b), rc.cap_words, smid(A.b), m->scratch.p, cerr, sw + ncomp,
-                                          cx.st));
-                cx.end(tok);
-                ++ncomp;
-                tok = cx.begin(PC_COMP);
-                CK_TRY(codec_compress_dev(static_cast<const float*>(st.prev), cv, rc.tol_f, m->pool.as<uint32_t>(),
-                                          smid(A.b), rc.cap_words, sbase(A.b + 1), m->scratch.p, cerr, sw + ncomp,
-                                          cx.st));
-                cx.end(tok);
-                ++ncomp;
-                cx.launches += 6;
+                if (cx.issue) {
+                    int tok = cx.begin(PC_COMP);
+                    for (int l = 0; l < NL; ++l) {
+                        ckfwi_model* m = cx.lane(l);
+                        unsigned long long* sw = m->statw.as<unsigned long long>();
+                        CK_TRY(codec_compress_dev(cx.fptr(l, st.cur), field_view(m->fg), rc.tol_f,
+                                                  m->pool.as<uint32_t>(), sbase(m, A.b), m->cap_words, smid(m, A.b),
+                                                  m->scratch.p, m->flags.as<int>() + 1, sw + ncomp, cx.st));
+                    }
+                    cx.end(tok);
+                    tok = cx.begin(PC_COMP);
+                    for (int l = 0; l < NL; ++l) {
+                        ckfwi_model* m = cx.lane(l);
+                        unsigned long long* sw = m->statw.as<unsigned long long>();
+                        CK_TRY(codec_compress_dev(cx.fptr(l, st.prev), field_view(m->fg), rc.tol_f,
+                                                  m->pool.as<uint32_t>(), smid(m, A.b), m->cap_words,
+                                                  sbase(m, A.b + 1), m->scratch.p, m->flags.as<int>() + 1,
+                                                  sw + ncomp + 1, cx.st));
+                    }
+                    cx.end(tok);
+                    cx.launches += 6LL * NL;
+                }
+                ncomp += 2;
             }
         } else if (A.op == ACT_RESTORE) {
-            cur_state = A.a;
             if (A.b == 0) {
-                st = State{zero, zero, U_FP32, U_FP32};
+                st = State{ZERO_R, ZERO_R, U_FP32, U_FP32};
             } else if (rc.mode == CKFWI_STORE_FP32) {
-                st = State{slot_ptr(A.b, 0), slot_ptr(A.b, 1), U_FP32, U_FP32};
+                st = State{slot_r(A.b, 0), slot_r(A.b, 1), U_FP32, U_FP32};   // the slot is the state
             } else if (rc.mode == CKFWI_STORE_CODEC) {
-                float* a0 = org(m->work[0], f);
-                float* a1 = org(m->work[1], f);
-                int tok = cx.begin(PC_DECOMP);
-                CK_TRY(codec_decompress_dev(m->pool.as<uint32_t>(), sbase(A.b), rc.cap_words, cv, a0, cerr, cx.st));
-                cx.end(tok);
-                ++cx.launches;
-                if (!next_turn) {
-                    tok = cx.begin(PC_DECOMP);
-                    CK_TRY(codec_decompress_dev(m->pool.as<uint32_t>(), smid(A.b), rc.cap_words, cv, a1, cerr, cx.st));
+                if (cx.issue) {
+                    int tok = cx.begin(PC_DECOMP);
+                    for (int l = 0; l < NL; ++l) {
+                        ckfwi_model* m = cx.lane(l);
+                        CK_TRY(codec_decompress_dev(m->pool.as<uint32_t>(), sbase(m, A.b), m->cap_words,
+                                                    field_view(m->fg), cx.fptr(l, work_r(0)),
+                                                    m->flags.as<int>() + 1, cx.st));
+                        ++cx.launches;
+                    }
                     cx.end(tok);
-                    ++cx.launches;
+                    if (!next_turn) {   // a reverse step needs u^s only
+                        tok = cx.begin(PC_DECOMP);
+                        for (int l = 0; l < NL; ++l) {
+                            ckfwi_model* m = cx.lane(l);
+                            CK_TRY(codec_decompress_dev(m->pool.as<uint32_t>(), smid(m, A.b), m->cap_words,
+                                                        field_view(m->fg), cx.fptr(l, work_r(1)),
+                                                        m->flags.as<int>() + 1, cx.st));
+                            ++cx.launches;
+                        }
+                        cx.end(tok);
+                    }
                 }
-                st = State{a0, a1, U_FP32, U_FP32};
+                st = State{work_r(0), work_r(1), U_FP32, U_FP32};
+            } else if (next_turn) {
+                // the reverse step reads the 16-bit u^s directly
+                st = State{slot_r(A.b, 0), slot_r(A.b, 1), ut_slot, ut_slot};
             } else {
-                if (next_turn) {
-                    st = State{slot_ptr(A.b, 0), slot_ptr(A.b, 1), ut_slot, ut_slot};
-                } else {
-                    float* a0 = org(m->work[0], f);
-                    float* a1 = org(m->work[1], f);
+                if (cx.issue) {
                     const int tok = cx.begin(PC_DECOMP);
-                    CK_TRY(launch_cast_restore(slot_ptr(A.b, 0), ut_slot, f, a0, cx.st));
-                    CK_TRY(launch_cast_restore(slot_ptr(A.b, 1), ut_slot, f, a1, cx.st));
+                    for (int l = 0; l < NL; ++l) {
+                        ckfwi_model* m = cx.lane(l);
+                        CK_TRY(launch_cast_restore(cx.ptr(l, slot_r(A.b, 0)), ut_slot, m->fg, cx.fptr(l, work_r(0)),
+                                                   cx.st));
+                        CK_TRY(launch_cast_restore(cx.ptr(l, slot_r(A.b, 1)), ut_slot, m->fg, cx.fptr(l, work_r(1)),
+                                                   cx.st));
+                        cx.launches += 2;
+                    }
                     cx.end(tok);
-                    cx.launches += 2;
-                    st = State{a0, a1, U_FP32, U_FP32};
                 }
+                st = State{work_r(0), work_r(1), U_FP32, U_FP32};
             }
         } else if (A.op == ACT_YOUTURN) {
             if (first_sweep) {
                 // extra step N-1 -> N records d^{N-1}; d^N from u^N
-                ST_TRY(fwd_step(cx, static_cast<const float*>(st.cur), static_cast<const float*>(st.prev),
-                                org(m->uN, f), N - 1, true, CK_NONE, nullptr, nullptr));
+                ST_TRY(fwd_step(cx, st.cur, st.prev, UN_R, N - 1, true, CK_NONE, NONE_R, NONE_R));
                 ++fsteps;
-                ST_TRY(sample_last(cx, org(m->uN, f)));
+                ST_TRY(sample_last(cx, UN_R));
                 ST_TRY(residual(cx));
                 first_sweep = false;
             }
-            (void)cur_state;
             ST_TRY(reverse(A.a, st.cur, st.tcur));
         }
     }
@@ -981,8 +1161,21 @@ int run_body(Ctx& cx, const RunCfg& rc, const std::vector<Action>& acts, long lo
     return CKFWI_OK;
 }
 
-int prepare_storage(ckfwi_model* m, RunCfg& rc, const ckfwi_grad_opts* o, const FieldGeom& f)
+// Device bytes one lane's checkpoint storage takes for this configuration.
+double storage_bytes(const FieldGeom& f, const RunCfg& rc, const ckfwi_grad_opts* o)
 {
+    if (rc.store_all) return (double)field_bytes(f) * rc.N;
+    if (rc.M <= 1) return 0.0;
+    const double nslot = (double)(rc.M - 1) * 2;
+    if (rc.mode == CKFWI_STORE_FP32) return nslot * field_bytes(f, 4);
+    if (rc.mode != CKFWI_STORE_CODEC) return nslot * field_bytes(f, 2);
+    const double pool = o->pool_bytes ? (double)o->pool_bytes : nslot * f.npts * 4.0;
+    return pool + (double)codec_scratch_bytes(f.dims, f.nz, f.ny, f.nx);
+}
+
+int prepare_storage(ckfwi_model* m, const RunCfg& rc, const ckfwi_grad_opts* o)
+{
+    const FieldGeom& f = m->fg;
     const void* before[5] = {m->traj.p, m->pool.p, m->slotbase.p, m->scratch.p, m->statw.p};
     struct Bump {
         ckfwi_model* m;
@@ -994,6 +1187,7 @@ int prepare_storage(ckfwi_model* m, RunCfg& rc, const ckfwi_grad_opts* o, const 
                 if (after[i] != b[i]) ++m->gen;
         }
     } bump{m, before};
+    m->cap_words = 0;
     if (rc.store_all) {
         CK_TRY(m->traj.alloc(field_bytes(f) * (size_t)rc.N));
         return CKFWI_OK;
@@ -1017,7 +1211,7 @@ int prepare_storage(ckfwi_model* m, RunCfg& rc, const ckfwi_grad_opts* o, const 
         size_t bytes = o->pool_bytes ? o->pool_bytes : (size_t)(rc.M - 1) * 2 * f.npts * 4;
         bytes = (bytes + 3) / 4 * 4;
         CK_TRY(m->pool.alloc(bytes, false));
-        rc.cap_words = (long long)(bytes / 4);
+        m->cap_words = (long long)(bytes / 4);
         CK_TRY(m->slotbase.alloc(sizeof(long long) * (2 * (size_t)rc.M + 4)));
         CK_TRY(m->scratch.alloc((size_t)codec_scratch_bytes(f.dims, f.nz, f.ny, f.nx), false));
         CK_TRY(m->statw.alloc(sizeof(unsigned long long) * (size_t)(4 * rc.N + 8)));
@@ -1032,28 +1226,112 @@ float tol_float(double tol)
     return t;
 }
 
-int gradient_one(ckfwi_model* m, const ckfwi_shot* s, const float* d_obs, int mem,
-                 const ckfwi_grad_opts* o, double* misfit, ckfwi_stats* stats, cudaStream_t st,
-                 std::vector<long long>* comp_words)
+int check_opts(const ckfwi_grad_opts* o)
 {
-    if (!m->have_model) return CKFWI_EINVAL;
-    if (!o || !d_obs) return CKFWI_EINVAL;
+    if (!o) return CKFWI_EINVAL;
     if (o->ckpt_slots < 1) return CKFWI_EINVAL;
     if (o->store_mode < 0 || o->store_mode > 3) return CKFWI_EINVAL;
     if (o->grad_kind != CKFWI_VELOCITY && o->grad_kind != CKFWI_SLOWNESS2) return CKFWI_EINVAL;
     if (o->store_mode == CKFWI_STORE_CODEC && (!(o->tol >= std::ldexp(1.0, -90)) || !std::isfinite(o->tol)))
         return CKFWI_EINVAL;
-    ST_TRY(set_shot(m, s));
-    ST_TRY(autotune(m, st));
-    const FieldGeom& f = m->fg;
+    return CKFWI_OK;
+}
+
+RunCfg run_cfg(int nt, const ckfwi_grad_opts* o)
+{
     RunCfg rc{};
-    rc.N = m->g.nt;
+    rc.N = nt;
     rc.M = o->ckpt_slots;
     rc.mode = o->store_mode;
     rc.tol_f = rc.mode == CKFWI_STORE_CODEC ? tol_float(o->tol) : 0.0f;
     rc.store_all = rc.M >= rc.N && rc.mode == CKFWI_STORE_FP32;
     if (rc.M > rc.N) rc.M = rc.N;
-    ST_TRY(prepare_storage(m, rc, o, f));
+    return rc;
+}
+
+// Keep at most `cap` recorded graphs per model (oldest recorded first out).
+template <class Map>
+void trim_graphs(Map& g, std::vector<typename Map::key_type>& order, size_t cap)
+{
+    while (order.size() > cap) {
+        auto it = g.find(order.front());
+        if (it != g.end()) {
+            it->second.release();
+            g.erase(it);
+        }
+        order.erase(order.begin());
+    }
+}
+
+// Fill stats from the per-class timings and the schedule counts.
+void fill_stats(ckfwi_stats* stats, Ctx& cx, const RunCfg& rc, const long long* cnt, const long long* counters,
+                const FieldGeom& f)
+{
+    std::memset(stats, 0, sizeof(*stats));
+    stats->fwd_steps = counters[0];
+    stats->adj_steps = rc.N;
+    stats->p = rc.store_all ? rc.N - 1 : cnt[0];
+    stats->takeshots = rc.store_all ? rc.N - 1 : cnt[1];
+    stats->restores = rc.store_all ? rc.N - 1 : cnt[2];
+    stats->kernel_launches = cx.launches;
+    stats->fwd_launches = cx.count[PC_FWD];
+    stats->adj_launches = cx.count[PC_ADJ];
+    stats->comp_calls = cx.count[PC_COMP];
+    stats->decomp_calls = cx.count[PC_DECOMP];
+    if (cx.prof.on) {
+        double ms[PC_N] = {0, 0, 0, 0, 0};
+        for (auto& mk : cx.prof.marks) {
+            float t = 0.0f;
+            if (cudaEventElapsedTime(&t, (*cx.prof.pool)[mk.second], (*cx.prof.pool)[mk.second + 1]) == cudaSuccess)
+                ms[mk.first] += t;
+        }
+        stats->fwd_ms = ms[PC_FWD];
+        stats->adj_ms = ms[PC_ADJ];
+        stats->comp_ms = ms[PC_COMP];
+        stats->decomp_ms = ms[PC_DECOMP];
+        stats->other_ms = ms[PC_OTHER];
+    }
+    if (rc.store_all) stats->pool_bytes_peak = (double)field_bytes(f) * rc.N;
+    else if (rc.mode == CKFWI_STORE_FP32) stats->pool_bytes_peak = (double)(rc.M - 1) * 2 * field_bytes(f, 4);
+    else if (rc.mode != CKFWI_STORE_CODEC) stats->pool_bytes_peak = (double)(rc.M - 1) * 2 * field_bytes(f, 2);
+}
+
+// Compression ratios and the peak pool height of one lane's codec run
+// (replaying the slot stack with the measured stream sizes).
+void codec_stats(const std::vector<long long>& words, const std::vector<Action>& acts, int M, const FieldGeom& f,
+                 double* rmin, double* rsum, double* peak_bytes)
+{
+    const long long ncomp = (long long)words.size();
+    double mn = 1e300, sum = 0;
+    for (long long wds : words) {
+        const double r = (double)f.npts / (double)std::max<long long>(1, wds);
+        mn = std::min(mn, r);
+        sum += r;
+    }
+    std::vector<long long> height((size_t)M + 2, 0);
+    long long k = 0, peak = 0;
+    for (const Action& A : acts) {
+        if (A.op != ACT_TAKESHOT || k + 1 >= ncomp) continue;
+        height[A.b] = height[A.b - 1] + words[k] + words[k + 1];
+        peak = std::max(peak, height[A.b]);
+        k += 2;
+    }
+    *rmin = mn;
+    *rsum = sum;
+    *peak_bytes = (double)peak * 4;
+}
+
+int gradient_one(ckfwi_model* m, const ckfwi_shot* s, const float* d_obs, int mem,
+                 const ckfwi_grad_opts* o, double* misfit, ckfwi_stats* stats, cudaStream_t st)
+{
+    if (!m->have_model) return CKFWI_EINVAL;
+    if (!d_obs) return CKFWI_EINVAL;
+    ST_TRY(check_opts(o));
+    ST_TRY(set_shot(m, s));
+    ST_TRY(autotune(m, st));
+    const FieldGeom& f = m->fg;
+    const RunCfg rc = run_cfg(m->g.nt, o);
+    ST_TRY(prepare_storage(m, rc, o));
     const size_t nd = (size_t)(rc.N + 1) * m->shot.nrec;
     CK_TRY(cudaMemcpyAsync(m->shot.dobs.p, d_obs, nd * sizeof(float),
                            mem == CKFWI_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, st));
@@ -1062,43 +1340,52 @@ int gradient_one(ckfwi_model* m, const ckfwi_shot* s, const float* d_obs, int me
     long long cnt[3] = {rc.N - 1, 0, 0};
     if (!rc.store_all) revolve_schedule(rc.N, rc.M, acts, cnt);
     Ctx cx{m, st, 0};
+    cx.mode = rc.mode;
     long long counters[2] = {0, 0};
     const bool graph = o->use_graph != 0 && !o->profile;
     if (o->profile) {
         cx.prof.on = true;
         cx.prof.pool = &m->evpool;
     }
-    GraphKey key{rc.N, rc.M, rc.mode, o->grad_kind, rc.tol_f, (size_t)rc.cap_words, m->gen};
+    GraphKey key{rc.N, rc.M, rc.mode, o->grad_kind, rc.tol_f, (size_t)m->cap_words, m->gen};
     if (graph) {
         auto it = m->graphs.find(key);
         if (it == m->graphs.end()) {
             // record on a private non-blocking stream (the caller's may be the
             // legacy stream, which cannot be captured); replay on the caller's
             if (!m->cap) CK_TRY(cudaStreamCreateWithFlags(&m->cap, cudaStreamNonBlocking));
-            if (!m->ev) CK_TRY(cudaEventCreateWithFlags(&m->ev, cudaEventDisableTiming));
             CK_TRY(cudaStreamSynchronize(st));
             cudaGraph_t gr;
-            Ctx cc{m, m->cap, 0};
+            cx.st = m->cap;
             CK_TRY(cudaStreamBeginCapture(m->cap, cudaStreamCaptureModeRelaxed));
-            const int rs = run_body(cc, rc, acts, counters);
-            cx.launches = cc.launches;
+            const int rs = run_body(cx, rc, acts, counters);
             cudaError_t ee = cudaStreamEndCapture(m->cap, &gr);
+            cx.st = st;
             if (rs != CKFWI_OK) {
                 if (ee == cudaSuccess) cudaGraphDestroy(gr);
                 return rs;
             }
             CK_TRY(ee);
-            cudaGraphExec_t ex;
-            cudaError_t ei = cudaGraphInstantiate(&ex, gr, 0);
+            GraphExec& ge = m->graphs[key];
+            cudaError_t ei = cudaGraphInstantiate(&ge.ex, gr, 0);
             cudaGraphDestroy(gr);
-            CK_TRY(ei);
-            it = m->graphs.emplace(key, ex).first;
+            if (ei != cudaSuccess) {
+                m->graphs.erase(key);
+                return cuda_status(ei);
+            }
+            ge.launches = cx.launches;
+            std::memcpy(ge.count, cx.count, sizeof(cx.count));
+            m->graph_order.push_back(key);
+            trim_graphs(m->graphs, m->graph_order, MAX_GRAPHS);
+            it = m->graphs.find(key);
         } else {
             // the same schedule: counters from a dry count
             counters[0] = rc.store_all ? rc.N : cnt[0] + 1;
             counters[1] = rc.mode == CKFWI_STORE_CODEC ? 2 * cnt[1] : 0;
+            cx.launches = it->second.launches;
+            std::memcpy(cx.count, it->second.count, sizeof(cx.count));
         }
-        CK_TRY(cudaGraphLaunch(it->second, st));
+        CK_TRY(cudaGraphLaunch(it->second.ex, st));
     } else {
         ST_TRY(run_body(cx, rc, acts, counters));
     }
@@ -1107,62 +1394,391 @@ int gradient_one(ckfwi_model* m, const ckfwi_shot* s, const float* d_obs, int me
     int fl = 0;
     ST_TRY(read_flags(m, st, &fl));
     if (misfit) *misfit = phi;
-    long long ncomp = counters[1];
-    if (comp_words && ncomp > 0) {
-        comp_words->resize(ncomp);
-        CK_TRY(cudaMemcpy(comp_words->data(), m->statw.p, sizeof(long long) * ncomp, cudaMemcpyDeviceToHost));
-    }
     if (stats) {
-        std::memset(stats, 0, sizeof(*stats));
-        stats->fwd_steps = counters[0];
-        stats->adj_steps = rc.N;
-        stats->p = rc.store_all ? rc.N - 1 : cnt[0];
-        stats->takeshots = rc.store_all ? rc.N - 1 : cnt[1];
-        stats->restores = rc.store_all ? rc.N - 1 : cnt[2];
-        stats->kernel_launches = cx.launches;
-        stats->fwd_launches = cx.count[PC_FWD];
-        stats->adj_launches = cx.count[PC_ADJ];
-        stats->comp_calls = cx.count[PC_COMP];
-        stats->decomp_calls = cx.count[PC_DECOMP];
-        if (cx.prof.on) {
-            double ms[PC_N] = {0, 0, 0, 0, 0};
-            for (auto& mk : cx.prof.marks) {
-                float t = 0.0f;
-                if (cudaEventElapsedTime(&t, m->evpool[mk.second], m->evpool[mk.second + 1]) == cudaSuccess)
-                    ms[mk.first] += t;
-            }
-            stats->fwd_ms = ms[PC_FWD];
-            stats->adj_ms = ms[PC_ADJ];
-            stats->comp_ms = ms[PC_COMP];
-            stats->decomp_ms = ms[PC_DECOMP];
-            stats->other_ms = ms[PC_OTHER];
-        }
-        if (rc.store_all) stats->pool_bytes_peak = (double)field_bytes(f) * rc.N;
-        else if (rc.mode == CKFWI_STORE_FP32) stats->pool_bytes_peak = (double)(rc.M - 1) * 2 * field_bytes(f, 4);
-        else if (rc.mode != CKFWI_STORE_CODEC) stats->pool_bytes_peak = (double)(rc.M - 1) * 2 * field_bytes(f, 2);
-        if (comp_words && ncomp > 0) {
-            double mn = 1e300, sum = 0;
-            for (long long wds : *comp_words) {
-                const double r = (double)f.npts / (double)std::max<long long>(1, wds);
-                mn = std::min(mn, r);
-                sum += r;
-            }
+        fill_stats(stats, cx, rc, cnt, counters, f);
+        const long long ncomp = counters[1];
+        if (ncomp > 0) {
+            std::vector<long long> words(ncomp);
+            CK_TRY(cudaMemcpy(words.data(), m->statw.p, sizeof(long long) * ncomp, cudaMemcpyDeviceToHost));
+            double mn, sum, peak;
+            codec_stats(words, acts, rc.M, f, &mn, &sum, &peak);
             stats->ratio_min = mn;
             stats->ratio_mean = sum / (double)ncomp;
-            // peak pool use: replay the slot stack with the measured sizes
-            std::vector<long long> height((size_t)rc.M + 2, 0);
-            long long k = 0, peak = 0;
-            for (const Action& A : acts) {
-                if (A.op != ACT_TAKESHOT || k + 1 >= ncomp) continue;
-                height[A.b] = height[A.b - 1] + (*comp_words)[k] + (*comp_words)[k + 1];
-                peak = std::max(peak, height[A.b]);
-                k += 2;
-            }
-            stats->pool_bytes_peak = (double)peak * 4;
-            stats->u_absmax = 0;
+            stats->pool_bytes_peak = peak;
         }
     }
     return fl;
+}
+
+// ------------------------------------------------------------ batched shots
+long long lane_blocks(const FieldGeom& f, const Tile& t, int zlen)
+{
+    const long long gx = (f.nx + t.bx - 1) / t.bx;
+    const long long gy = f.dims == 3 ? (f.ny + t.by - 1) / t.by : 1;
+    return gx * gy * ((f.nz + zlen - 1) / zlen);
+}
+
+// CTA offsets of the lanes in a batched launch (lanes + 1 entries)
+std::vector<int> lane_starts(const std::vector<ckfwi_model*>& lanes, const Tile& t, const std::vector<int>& z,
+                             long long* total)
+{
+    std::vector<int> s(lanes.size() + 1, 0);
+    long long acc = 0;
+    for (size_t l = 0; l < lanes.size(); ++l) {
+        s[l] = (int)std::min<long long>(acc, 0x7fffffffLL);
+        acc += lane_blocks(lanes[l]->fg, t, z[l]);
+    }
+    s[lanes.size()] = (int)std::min<long long>(acc, 0x7fffffffLL);
+    *total = acc;
+    return s;
+}
+
+std::vector<long long> lane_ids(const std::vector<ckfwi_model*>& lanes, bool with_gen)
+{
+    std::vector<long long> v;
+    for (ckfwi_model* L : lanes) {
+        v.push_back(L->uid);
+        if (with_gen) v.push_back(L->gen);
+    }
+    return v;
+}
+
+// Batch autotuner: a common tile shape and a z-run length per lane, picked
+// by timing batched forward and reverse launches over all lanes.  The
+// candidates split every column into nzc runs, nzc chosen so that the
+// whole batch has 1 to 16 CTAs per SM.
+int batch_tune(const std::vector<ckfwi_model*>& lanes, cudaStream_t st, const BatchTiles** out)
+{
+    ckfwi_model* m0 = lanes[0];
+    const std::vector<long long> key = lane_ids(lanes, false);
+    auto it = m0->btiles.find(key);
+    if (it != m0->btiles.end()) {
+        *out = &it->second;
+        return CKFWI_OK;
+    }
+    const int dims = m0->fg.dims, K = m0->K, NL = (int)lanes.size();
+    int dev = 0, nsm = 0;
+    CK_TRY(cudaGetDevice(&dev));
+    CK_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    struct Cand {
+        Tile t;
+        std::vector<int> z;
+    };
+    std::vector<Cand> cands;
+    for (int i = 0; i < tile_count(dims); ++i) {
+        const Tile t = tile_at(dims, i, 1);
+        if (!tile_supported(dims, K, t)) continue;
+        long long cols = 0;
+        int nzmax = 1;
+        for (ckfwi_model* L : lanes) {
+            cols += (long long)((L->fg.nx + t.bx - 1) / t.bx) * (dims == 3 ? (L->fg.ny + t.by - 1) / t.by : 1);
+            nzmax = std::max(nzmax, L->fg.nz);
+        }
+        std::vector<std::vector<int>> seen;
+        for (int target : {1, 2, 4, 8, 16}) {
+            long long nzc = (target * (long long)nsm + cols - 1) / cols;
+            nzc = std::max<long long>(1, std::min<long long>(nzc, nzmax));
+            std::vector<int> z(NL);
+            for (int l = 0; l < NL; ++l) z[l] = std::max(4, (int)((lanes[l]->fg.nz + nzc - 1) / nzc));
+            if (std::find(seen.begin(), seen.end(), z) != seen.end()) continue;
+            seen.push_back(z);
+            cands.push_back(Cand{t, z});
+        }
+    }
+    if (cands.empty()) return CKFWI_EINVAL;
+    // argument tables of a probe step on the lanes' own working buffers
+    std::vector<FwdArgs> fa(NL);
+    std::vector<AdjArgs> aa(NL);
+    for (int l = 0; l < NL; ++l) {
+        ckfwi_model* L = lanes[l];
+        const FieldGeom& f = L->fg;
+        fa[l] = fwd_args(L);
+        fa[l].u = org(L->work[0], f);
+        fa[l].up = org(L->work[1], f);
+        fa[l].out = org(L->work[2], f);
+        fa[l].src = L->shot.src.view;
+        fa[l].src.series = L->shot.wavelet.as<float>();
+        aa[l] = adj_args(L);
+        aa[l].l1 = org(L->lam[0], f);
+        aa[l].l2 = org(L->lam[1], f);
+        aa[l].l0 = org(L->lam[2], f);
+        aa[l].u = org(L->work[0], f);
+        aa[l].adj = L->shot.adj.view;
+        aa[l].adj.series = L->shot.resid.as<float>();
+        aa[l].src = L->shot.src.view;
+        aa[l].src.series = L->shot.wavelet.as<float>();
+    }
+    DevMem dtab, dst;
+    CK_TRY(dtab.alloc(sizeof(FwdArgs) * NL + sizeof(AdjArgs) * NL + 256, false));
+    CK_TRY(dst.alloc(sizeof(int) * (NL + 1), false));
+    FwdArgs* ftab = dtab.as<FwdArgs>();
+    AdjArgs* atab = reinterpret_cast<AdjArgs*>(dtab.as<char>() + ((sizeof(FwdArgs) * NL + 255) / 256) * 256);
+    cudaEvent_t e0, e1;
+    CK_TRY(cudaEventCreate(&e0));
+    CK_TRY(cudaEventCreate(&e1));
+    const bool verbose = std::getenv("CKFWI_VERBOSE") != nullptr;
+    float best[2] = {1e30f, 1e30f};
+    BatchTiles bt;
+    int rs = CKFWI_OK;
+    for (const Cand& c : cands) {
+        long long total = 0;
+        const std::vector<int> s = lane_starts(lanes, c.t, c.z, &total);
+        if (total > 0x7fffffffLL) continue;
+        for (int l = 0; l < NL; ++l) {
+            fa[l].zlen = c.z[l];
+            aa[l].zlen = c.z[l];
+        }
+        if (cudaMemcpy(ftab, fa.data(), sizeof(FwdArgs) * NL, cudaMemcpyHostToDevice) != cudaSuccess ||
+            cudaMemcpy(atab, aa.data(), sizeof(AdjArgs) * NL, cudaMemcpyHostToDevice) != cudaSuccess ||
+            cudaMemcpy(dst.p, s.data(), sizeof(int) * (NL + 1), cudaMemcpyHostToDevice) != cudaSuccess) {
+            rs = CKFWI_ECUDA;
+            break;
+        }
+        for (int pass = 0; pass < 2 && rs == CKFWI_OK; ++pass) {
+            auto go = [&]() {
+                if (pass == 0)
+                    return launch_fwd_batch(BatchLaunch<FwdArgs>{ftab, dst.as<int>(), NL, dims, total}, c.t, K,
+                                            CK_NONE, st);
+                return launch_adj_batch(BatchLaunch<AdjArgs>{atab, dst.as<int>(), NL, dims, total}, c.t, K, U_FP32,
+                                        st);
+            };
+            const int reps = 3;
+            cudaError_t e = go();
+            if (e == cudaSuccess) e = cudaEventRecord(e0, st);
+            for (int r = 0; r < reps && e == cudaSuccess; ++r) e = go();
+            if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+            if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+            float ms = 0;
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+            if (e != cudaSuccess) {
+                rs = cuda_status(e);
+                break;
+            }
+            if (verbose)
+                std::fprintf(stderr, "ckfwi batch autotune %s lanes %d tile %dx%d z[0] %d: %.1f us\n",
+                             pass ? "adj" : "fwd", NL, c.t.bx, c.t.by, c.z[0], 1000.0f * ms / reps);
+            if (ms < best[pass]) {
+                best[pass] = ms;
+                if (pass == 0) {
+                    bt.tf = c.t;
+                    bt.zf = c.z;
+                } else {
+                    bt.ta = c.t;
+                    bt.za = c.z;
+                }
+            }
+        }
+        if (rs != CKFWI_OK) break;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    ST_TRY(rs);
+    if (bt.zf.empty() || bt.za.empty()) return CKFWI_EINVAL;
+    // the probes wrote into working buffers; clear them
+    for (ckfwi_model* L : lanes) {
+        for (int i = 0; i < 3; ++i) {
+            CK_TRY(cudaMemsetAsync(L->work[i].p, 0, L->work[i].bytes, st));
+            CK_TRY(cudaMemsetAsync(L->lam[i].p, 0, L->lam[i].bytes, st));
+        }
+        CK_TRY(cudaMemsetAsync(L->gacc.p, 0, L->gacc.bytes, st));
+    }
+    CK_TRY(cudaStreamSynchronize(st));
+    auto ins = m0->btiles.emplace(key, std::move(bt)).first;
+    *out = &ins->second;
+    return CKFWI_OK;
+}
+
+// Misfits (phis[l]) and gradients (left in each lane's gacc) of one batch:
+// lane l runs shots[l] on model lanes[l], all lanes through one Revolve
+// schedule, every stencil step one launch over all lanes.  Lanes may have
+// different grids (apertures); they share dims, space order and nt.
+int gradient_batch(const std::vector<ckfwi_model*>& lanes, const ckfwi_shot* shots, const float* const* d_obs,
+                   int mem, const ckfwi_grad_opts* o, double* phis, ckfwi_stats* stats, cudaStream_t st)
+{
+    ST_TRY(check_opts(o));
+    const int NL = (int)lanes.size();
+    ckfwi_model* m0 = lanes[0];
+    for (int l = 0; l < NL; ++l) {
+        ckfwi_model* L = lanes[l];
+        if (!L->have_model || !d_obs[l]) return CKFWI_EINVAL;
+        if (L->fg.dims != m0->fg.dims || L->K != m0->K || L->g.nt != m0->g.nt) return CKFWI_EINVAL;
+    }
+    for (int l = 0; l < NL; ++l) ST_TRY(set_shot(lanes[l], shots + l));
+    const RunCfg rc = run_cfg(m0->g.nt, o);
+    for (int l = 0; l < NL; ++l) ST_TRY(prepare_storage(lanes[l], rc, o));
+    const BatchTiles* bt = nullptr;
+    ST_TRY(batch_tune(lanes, st, &bt));
+    for (int l = 0; l < NL; ++l) {
+        ckfwi_model* L = lanes[l];
+        const size_t nd = (size_t)(rc.N + 1) * L->shot.nrec;
+        CK_TRY(cudaMemcpyAsync(L->shot.dobs.p, d_obs[l], nd * sizeof(float),
+                               mem == CKFWI_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, st));
+        ST_TRY(reset_flags(L, st));
+    }
+    std::vector<Action> acts;
+    long long cnt[3] = {rc.N - 1, 0, 0};
+    if (!rc.store_all) revolve_schedule(rc.N, rc.M, acts, cnt);
+    Ctx cx{m0, st, 0};
+    cx.mode = rc.mode;
+    cx.lanes = lanes;
+    cx.batch = true;
+    cx.bf = bt->tf;
+    cx.ba = bt->ta;
+    cx.zf = bt->zf;
+    cx.za = bt->za;
+    const std::vector<int> fs = lane_starts(lanes, cx.bf, cx.zf, &cx.fblocks);
+    const std::vector<int> as = lane_starts(lanes, cx.ba, cx.za, &cx.ablocks);
+    if (cx.fblocks > 0x7fffffffLL || cx.ablocks > 0x7fffffffLL) return CKFWI_EINVAL;
+    long long counters[2] = {0, 0};
+    const bool graph = o->use_graph != 0 && !o->profile;
+    if (o->profile) {
+        cx.prof.on = true;
+        cx.prof.pool = &m0->evpool;
+    }
+    BatchKey key{lane_ids(lanes, true), rc.N, rc.M, rc.mode, o->grad_kind, rc.tol_f};
+    auto it = graph ? m0->bgraphs.find(key) : m0->bgraphs.end();
+    if (it != m0->bgraphs.end()) {
+        counters[0] = rc.store_all ? rc.N : cnt[0] + 1;
+        counters[1] = rc.mode == CKFWI_STORE_CODEC ? 2 * cnt[1] : 0;
+        cx.launches = it->second.ex.launches;
+        std::memcpy(cx.count, it->second.ex.count, sizeof(cx.count));
+        CK_TRY(cudaGraphLaunch(it->second.ex.ex, st));
+    } else {
+        // pass 1: collect every step's per-lane arguments
+        cx.issue = false;
+        ST_TRY(run_body(cx, rc, acts, counters));
+        // the tables live with the graph that reads them, or in scratch
+        BatchGraph tmp;
+        BatchGraph& bg = graph ? m0->bgraphs[key] : tmp;
+        DevMem& tabs = graph ? bg.tabs : m0->btabs;
+        const size_t fb = ((sizeof(FwdArgs) * cx.ftab.size() + 255) / 256) * 256;
+        const size_t ab = ((sizeof(AdjArgs) * cx.atab.size() + 255) / 256) * 256;
+        const size_t sb = sizeof(int) * 2 * (NL + 1);
+        int rs = cuda_status_or_ok(tabs.alloc(fb + ab + sb, false));
+        if (rs == CKFWI_OK && !cx.ftab.empty())
+            rs = cuda_status_or_ok(cudaMemcpy(tabs.p, cx.ftab.data(), sizeof(FwdArgs) * cx.ftab.size(),
+                                              cudaMemcpyHostToDevice));
+        if (rs == CKFWI_OK && !cx.atab.empty())
+            rs = cuda_status_or_ok(cudaMemcpy(tabs.as<char>() + fb, cx.atab.data(),
+                                              sizeof(AdjArgs) * cx.atab.size(), cudaMemcpyHostToDevice));
+        std::vector<int> starts(fs);
+        starts.insert(starts.end(), as.begin(), as.end());
+        if (rs == CKFWI_OK)
+            rs = cuda_status_or_ok(
+                cudaMemcpy(tabs.as<char>() + fb + ab, starts.data(), sb, cudaMemcpyHostToDevice));
+        if (rs != CKFWI_OK) {
+            if (graph) m0->bgraphs.erase(key);
+            return rs;
+        }
+        cx.ftab_d = tabs.as<FwdArgs>();
+        cx.atab_d = reinterpret_cast<const AdjArgs*>(tabs.as<char>() + fb);
+        cx.fstart_d = reinterpret_cast<const int*>(tabs.as<char>() + fb + ab);
+        cx.astart_d = cx.fstart_d + (NL + 1);
+        cx.fi = cx.ai = 0;
+        cx.issue = true;
+        // pass 2: issue (recorded into a graph when asked)
+        if (graph) {
+            if (!m0->cap) rs = cuda_status_or_ok(cudaStreamCreateWithFlags(&m0->cap, cudaStreamNonBlocking));
+            if (rs == CKFWI_OK) rs = cuda_status_or_ok(cudaStreamSynchronize(st));
+            cudaGraph_t gr = nullptr;
+            if (rs == CKFWI_OK) {
+                Ctx& cc = cx;
+                cc.st = m0->cap;
+                rs = cuda_status_or_ok(cudaStreamBeginCapture(m0->cap, cudaStreamCaptureModeRelaxed));
+                if (rs == CKFWI_OK) {
+                    const int rb = run_body(cc, rc, acts, counters);
+                    const cudaError_t ee = cudaStreamEndCapture(m0->cap, &gr);
+                    rs = rb != CKFWI_OK ? rb : cuda_status_or_ok(ee);
+                    if (rb != CKFWI_OK && ee == cudaSuccess) cudaGraphDestroy(gr);
+                }
+                cc.st = st;
+            }
+            if (rs == CKFWI_OK) {
+                rs = cuda_status_or_ok(cudaGraphInstantiate(&bg.ex.ex, gr, 0));
+                cudaGraphDestroy(gr);
+            }
+            if (rs != CKFWI_OK) {
+                m0->bgraphs.erase(key);
+                return rs;
+            }
+            bg.ex.launches = cx.launches;
+            std::memcpy(bg.ex.count, cx.count, sizeof(cx.count));
+            m0->bgraph_order.push_back(key);
+            trim_graphs(m0->bgraphs, m0->bgraph_order, MAX_GRAPHS);
+            CK_TRY(cudaGraphLaunch(m0->bgraphs[key].ex.ex, st));
+        } else {
+            ST_TRY(run_body(cx, rc, acts, counters));
+        }
+    }
+    int fl = 0;
+    for (int l = 0; l < NL; ++l) {
+        CK_TRY(cudaMemcpyAsync(phis + l, lanes[l]->phi.p, sizeof(double), cudaMemcpyDeviceToHost, st));
+        int f1 = 0;
+        ST_TRY(read_flags(lanes[l], st, &f1));
+        if (fl == CKFWI_OK) fl = f1;
+    }
+    if (stats) {
+        fill_stats(stats, cx, rc, cnt, counters, m0->fg);
+        const long long ncomp = counters[1];
+        if (ncomp > 0) {
+            double mn = 1e300, sum = 0, peak = 0;
+            for (int l = 0; l < NL; ++l) {
+                std::vector<long long> words(ncomp);
+                CK_TRY(cudaMemcpy(words.data(), lanes[l]->statw.p, sizeof(long long) * ncomp,
+                                  cudaMemcpyDeviceToHost));
+                double a, b, c;
+                codec_stats(words, acts, rc.M, lanes[l]->fg, &a, &b, &c);
+                mn = std::min(mn, a);
+                sum += b;
+                peak = std::max(peak, c);
+            }
+            stats->ratio_min = mn;
+            stats->ratio_mean = sum / (double)(ncomp * NL);
+            stats->pool_bytes_peak = peak;
+        } else {
+            double peak = 0;
+            for (ckfwi_model* L : lanes) peak = std::max(peak, storage_bytes(L->fg, rc, o));
+            stats->pool_bytes_peak = peak;
+        }
+    }
+    return fl;
+}
+
+// Clones of a model: extra lanes with the same grid and medium, so that
+// several shots on one model can run as one batch.
+int ensure_clones(ckfwi_model* m, int k, cudaStream_t st)
+{
+    while ((int)m->clones.size() < k) {
+        ckfwi_model* c = nullptr;
+        ST_TRY(ckfwi_create_model(&m->g, &c));
+        m->clones.emplace_back(c);
+    }
+    for (int i = 0; i < k; ++i) {
+        ckfwi_model* c = m->clones[i].get();
+        if (c->src_ver == m->model_ver && c->have_model) continue;
+        CK_TRY(cudaMemcpyAsync(c->w.p, m->w.p, m->w.bytes, cudaMemcpyDeviceToDevice, st));
+        CK_TRY(cudaMemcpyAsync(c->cvel.p, m->cvel.p, m->cvel.bytes, cudaMemcpyDeviceToDevice, st));
+        c->have_model = true;
+        c->src_ver = m->model_ver;
+    }
+    CK_TRY(cudaStreamSynchronize(st));
+    return CKFWI_OK;
+}
+
+// How many shots of one model run side by side: bounded by free device
+// memory (a lane holds ten fields and its checkpoint storage), by
+// CKFWI_MAX_LANES (default 64) and by the shot count.
+int batch_width(ckfwi_model* m, int nshots, const ckfwi_grad_opts* o)
+{
+    int cap = 64;
+    if (const char* v = std::getenv("CKFWI_MAX_LANES")) cap = std::max(1, std::atoi(v));
+    const RunCfg rc = run_cfg(m->g.nt, o);
+    const double lane = 10.0 * field_bytes(m->fg) + 8.0 * m->fg.npts + storage_bytes(m->fg, rc, o);
+    size_t fr = 0, tot = 0;
+    if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) return 1;
+    const double extra = 0.8 * (double)fr / lane;
+    const long long w = 1 + (long long)m->clones.size() + (long long)extra;
+    return (int)std::max<long long>(1, std::min<long long>({(long long)nshots, (long long)cap, w}));
 }
 
 }  // namespace
@@ -1177,6 +1793,8 @@ int ckfwi_create_model(const ckfwi_grid* g, ckfwi_model** out)
     ckfwi_model* m = new (std::nothrow) ckfwi_model();
     if (!m) return CKFWI_ENOMEM;
     std::unique_ptr<ckfwi_model> guard(m);
+    static std::atomic<long long> next_uid{1};
+    m->uid = next_uid++;
     m->g = *g;
     if (g->dims == 2) m->g.n[1] = 1;
     m->K = g->space_order / 2;
@@ -1223,6 +1841,8 @@ int ckfwi_set_model(ckfwi_model* m, const float* data, int kind, int mem, void* 
         src = tmp.as<float>();
     }
     ST_TRY(reset_flags(m, st));
+    ++m->model_ver;
+    m->have_model = false;
     CK_TRY(launch_to_padded_w(src, kind, (float)m->g.dt, f, org(m->w, f), m->cvel.as<float>(),
                               m->flags.as<int>() + 2, st));
     int h[4];
@@ -1241,18 +1861,16 @@ int ckfwi_forward_shot(ckfwi_model* m, const ckfwi_shot* s, float* d_sim, int me
     cudaStream_t st = S(stream);
     ST_TRY(set_shot(m, s));
     ST_TRY(autotune(m, st));
-    const FieldGeom& f = m->fg;
     Ctx cx{m, st, 0};
     CK_TRY(cudaMemsetAsync(m->shot.dsim.p, 0, m->shot.dsim.bytes, st));
-    State sv{org(m->zero, f), org(m->zero, f), U_FP32, U_FP32};
+    State sv{ZERO_R, ZERO_R, U_FP32, U_FP32};
     for (int n = 0; n < m->g.nt; ++n) {
-        float* out = pick_free(m, sv);
-        ST_TRY(fwd_step(cx, static_cast<const float*>(sv.cur), static_cast<const float*>(sv.prev), out, n, true,
-                        CK_NONE, nullptr, nullptr));
+        const Role out = pick_free(sv);
+        ST_TRY(fwd_step(cx, sv.cur, sv.prev, out, n, true, CK_NONE, NONE_R, NONE_R));
         sv.prev = sv.cur;
         sv.cur = out;
     }
-    ST_TRY(sample_last(cx, static_cast<const float*>(sv.cur)));
+    ST_TRY(sample_last(cx, sv.cur));
     const size_t nd = (size_t)(m->g.nt + 1) * m->shot.nrec;
     CK_TRY(cudaMemcpyAsync(d_sim, m->shot.dsim.p, nd * sizeof(float),
                            mem == CKFWI_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, st));
@@ -1267,21 +1885,19 @@ int ckfwi_misfit(ckfwi_model* m, const ckfwi_shot* s, const float* d_obs, int me
     cudaStream_t st = S(stream);
     ST_TRY(set_shot(m, s));
     ST_TRY(autotune(m, st));
-    const FieldGeom& f = m->fg;
     Ctx cx{m, st, 0};
     const size_t nd = (size_t)(m->g.nt + 1) * m->shot.nrec;
     CK_TRY(cudaMemcpyAsync(m->shot.dobs.p, d_obs, nd * sizeof(float),
                            mem == CKFWI_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, st));
     CK_TRY(cudaMemsetAsync(m->shot.dsim.p, 0, m->shot.dsim.bytes, st));
-    State sv{org(m->zero, f), org(m->zero, f), U_FP32, U_FP32};
+    State sv{ZERO_R, ZERO_R, U_FP32, U_FP32};
     for (int n = 0; n < m->g.nt; ++n) {
-        float* out = pick_free(m, sv);
-        ST_TRY(fwd_step(cx, static_cast<const float*>(sv.cur), static_cast<const float*>(sv.prev), out, n, true,
-                        CK_NONE, nullptr, nullptr));
+        const Role out = pick_free(sv);
+        ST_TRY(fwd_step(cx, sv.cur, sv.prev, out, n, true, CK_NONE, NONE_R, NONE_R));
         sv.prev = sv.cur;
         sv.cur = out;
     }
-    ST_TRY(sample_last(cx, static_cast<const float*>(sv.cur)));
+    ST_TRY(sample_last(cx, sv.cur));
     ST_TRY(residual(cx));
     if (d_sim)
         CK_TRY(cudaMemcpyAsync(d_sim, m->shot.dsim.p, nd * sizeof(float),
@@ -1299,8 +1915,7 @@ int ckfwi_adjoint_gradient(ckfwi_model* m, const ckfwi_shot* s, const float* d_o
 {
     if (!m || !grad) return CKFWI_EINVAL;
     cudaStream_t st = S(stream);
-    std::vector<long long> cw;
-    const int rs = gradient_one(m, s, d_obs, mem, opts, misfit, stats, st, &cw);
+    const int rs = gradient_one(m, s, d_obs, mem, opts, misfit, stats, st);
     if (rs != CKFWI_OK) return rs;
     const FieldGeom& f = m->fg;
     const float scale = opts->grad_scale != 0.0 ? (float)opts->grad_scale : 1.0f;
@@ -1323,29 +1938,64 @@ int ckfwi_batch_gradient(ckfwi_model* m, const ckfwi_shot* shots, int nshots, co
                          ckfwi_stats* stats, void* stream)
 {
     if (!m || !shots || nshots < 1 || !d_obs || !grad_sum || !opts) return CKFWI_EINVAL;
+    if (!m->have_model) return CKFWI_EINVAL;
+    ST_TRY(check_opts(opts));
     cudaStream_t st = S(stream);
     const FieldGeom& f = m->fg;
     DevMem sum, comp;
     CK_TRY(sum.alloc((size_t)f.npts * sizeof(double)));
     CK_TRY(comp.alloc((size_t)f.npts * sizeof(double)));
+    int B = batch_width(m, nshots, opts);
     double ms = 0.0, mc = 0.0;
     ckfwi_stats acc{};
-    for (int i = 0; i < nshots; ++i) {
-        double phi = 0.0;
+    std::vector<double> phis((size_t)nshots, 0.0);
+    for (int g0 = 0; g0 < nshots;) {
+        const int nb = std::min(B, nshots - g0);
         ckfwi_stats one{};
-        ST_TRY(gradient_one(m, shots + i, d_obs[i], mem, opts, &phi, &one, st, nullptr));
-        CK_TRY(launch_grad_out_f64(org(m->gacc, f), m->cvel.as<float>(), opts->grad_kind, f, sum.as<double>(),
-                                   comp.as<double>(), st));
-        const double t = ms + phi;
-        mc += (std::fabs(ms) >= std::fabs(phi)) ? (ms - t) + phi : (phi - t) + ms;
-        ms = t;
-        acc.fwd_steps += one.fwd_steps;
-        acc.adj_steps += one.adj_steps;
-        acc.p += one.p;
-        acc.takeshots += one.takeshots;
-        acc.restores += one.restores;
-        acc.kernel_launches += one.kernel_launches + 1;
-        acc.pool_bytes_peak = std::max(acc.pool_bytes_peak, one.pool_bytes_peak);
+        int rs = CKFWI_OK;
+        std::vector<ckfwi_model*> lanes{m};
+        if (nb == 1) {
+            rs = gradient_one(m, shots + g0, d_obs[g0], mem, opts, &phis[g0], &one, st);
+        } else {
+            rs = ensure_clones(m, nb - 1, st);
+            for (int l = 1; l < nb && rs == CKFWI_OK; ++l) lanes.push_back(m->clones[l - 1].get());
+            if (rs == CKFWI_OK) rs = gradient_batch(lanes, shots + g0, d_obs + g0, mem, opts, &phis[g0], &one, st);
+        }
+        if (rs == CKFWI_ENOMEM && nb > 1) {
+            // narrower batches, releasing the lanes that no longer fit
+            B = std::max(1, nb / 2);
+            m->clones.resize((size_t)(B - 1));
+            CK_TRY(cudaDeviceSynchronize());
+            continue;
+        }
+        ST_TRY(rs);
+        // per-shot gradients into the FP64 sum, in shot order
+        for (int l = 0; l < nb; ++l) {
+            ckfwi_model* L = lanes[l];
+            CK_TRY(launch_grad_out_f64(org(L->gacc, f), L->cvel.as<float>(), opts->grad_kind, f, 0, f.nx,
+                                       (long long)f.ny * f.nx, sum.as<double>(), comp.as<double>(), st));
+            const double phi = phis[g0 + l];
+            const double t = ms + phi;
+            mc += (std::fabs(ms) >= std::fabs(phi)) ? (ms - t) + phi : (phi - t) + ms;
+            ms = t;
+        }
+        acc.fwd_steps += one.fwd_steps * nb;
+        acc.adj_steps += one.adj_steps * nb;
+        acc.p += one.p * nb;
+        acc.takeshots += one.takeshots * nb;
+        acc.restores += one.restores * nb;
+        acc.kernel_launches += one.kernel_launches + nb;
+        acc.fwd_launches += one.fwd_launches;
+        acc.adj_launches += one.adj_launches;
+        acc.comp_calls += one.comp_calls;
+        acc.decomp_calls += one.decomp_calls;
+        acc.fwd_ms += one.fwd_ms;
+        acc.adj_ms += one.adj_ms;
+        acc.comp_ms += one.comp_ms;
+        acc.decomp_ms += one.decomp_ms;
+        acc.other_ms += one.other_ms;
+        acc.pool_bytes_peak = std::max(acc.pool_bytes_peak, one.pool_bytes_peak * nb);
+        g0 += nb;
     }
     // sum + compensation, scaled; FP64 or rounded once to FP32
     const double scale = opts->grad_scale != 0.0 ? opts->grad_scale : 1.0;
@@ -1360,7 +2010,77 @@ int ckfwi_batch_gradient(ckfwi_model* m, const ckfwi_shot* shots, int nshots, co
     }
     CK_TRY(cudaStreamSynchronize(st));
     if (misfit_sum) *misfit_sum = ms + mc;
-    if (stats) *stats = acc;
+    if (stats) {
+        *stats = acc;
+        stats->ratio_min = 0;
+        stats->ratio_mean = 0;
+    }
+    return CKFWI_OK;
+}
+
+int ckfwi_batch_gradient_models(ckfwi_model* const* models, const ckfwi_shot* shots, int nshots,
+                                const float* const* d_obs, int mem, const ckfwi_grad_opts* opts,
+                                const int* offsets, const int* global_n, double* misfit_sum, double* grad_sum,
+                                ckfwi_stats* stats, void* stream)
+{
+    if (!models || !shots || nshots < 1 || !d_obs || !opts || !offsets || !global_n || !grad_sum)
+        return CKFWI_EINVAL;
+    ST_TRY(check_opts(opts));
+    cudaStream_t st = S(stream);
+    std::vector<ckfwi_model*> lanes((size_t)nshots);
+    std::set<ckfwi_model*> seen;
+    for (int l = 0; l < nshots; ++l) {
+        ckfwi_model* L = models[l];
+        if (!L || !L->have_model || !seen.insert(L).second) return CKFWI_EINVAL;
+        lanes[l] = L;
+        const FieldGeom& f = L->fg;
+        const int n3[3] = {f.nz, f.ny, f.nx};
+        for (int a = 0; a < 3; ++a)
+            if (offsets[3 * l + a] < 0 || global_n[a] < 1 || offsets[3 * l + a] + n3[a] > global_n[a])
+                return CKFWI_EINVAL;
+    }
+    const long long gn = (long long)global_n[0] * global_n[1] * global_n[2];
+    DevMem sum, comp;
+    CK_TRY(sum.alloc((size_t)gn * sizeof(double)));
+    CK_TRY(comp.alloc((size_t)gn * sizeof(double)));
+    std::vector<double> phis((size_t)nshots, 0.0);
+    ckfwi_stats one{};
+    if (nshots == 1) ST_TRY(gradient_one(lanes[0], shots, d_obs[0], mem, opts, &phis[0], &one, st));
+    else ST_TRY(gradient_batch(lanes, shots, d_obs, mem, opts, phis.data(), &one, st));
+    double ms = 0.0, mc = 0.0;
+    for (int l = 0; l < nshots; ++l) {
+        ckfwi_model* L = lanes[l];
+        const FieldGeom& f = L->fg;
+        const long long o0 =
+            ((long long)offsets[3 * l] * global_n[1] + offsets[3 * l + 1]) * global_n[2] + offsets[3 * l + 2];
+        CK_TRY(launch_grad_out_f64(org(L->gacc, f), L->cvel.as<float>(), opts->grad_kind, f, o0, global_n[2],
+                                   (long long)global_n[1] * global_n[2], sum.as<double>(), comp.as<double>(), st));
+        const double phi = phis[l];
+        const double t = ms + phi;
+        mc += (std::fabs(ms) >= std::fabs(phi)) ? (ms - t) + phi : (phi - t) + ms;
+        ms = t;
+    }
+    const double scale = opts->grad_scale != 0.0 ? opts->grad_scale : 1.0;
+    CK_TRY(launch_add_f64(sum.as<double>(), comp.as<double>(), scale, comp.as<double>(), gn, st));
+    if (opts->grad_f32) {
+        CK_TRY(launch_f64_to_f32(comp.as<double>(), sum.as<float>(), gn, st));
+        CK_TRY(cudaMemcpyAsync(grad_sum, sum.p, gn * sizeof(float),
+                               mem == CKFWI_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, st));
+    } else {
+        CK_TRY(cudaMemcpyAsync(grad_sum, comp.p, gn * sizeof(double),
+                               mem == CKFWI_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, st));
+    }
+    CK_TRY(cudaStreamSynchronize(st));
+    if (misfit_sum) *misfit_sum = ms + mc;
+    if (stats) {
+        *stats = one;
+        stats->fwd_steps *= nshots;
+        stats->adj_steps *= nshots;
+        stats->p *= nshots;
+        stats->takeshots *= nshots;
+        stats->restores *= nshots;
+        stats->kernel_launches += nshots;
+    }
     return CKFWI_OK;
 }
 

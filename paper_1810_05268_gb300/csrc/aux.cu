@@ -106,18 +106,22 @@ __global__ void grad_out_kernel(const float* __restrict__ gacc, const float* __r
     out[p] = scale == 1.0f ? v : __fmul_rn(scale, v);
 }
 
-// Neumaier-compensated FP64 accumulation of one shot's gradient.
+// Neumaier-compensated FP64 accumulation of one shot's gradient into a
+// dense array that may be larger than the shot's grid: point (z, y, x) of
+// the grid adds into q = o0 + z * gsz + y * gsy + x.
 __global__ void grad_sum_kernel(const float* __restrict__ gacc, const float* __restrict__ c,
-                                int kind, FieldGeom g, double* __restrict__ sum,
-                                double* __restrict__ comp)
+                                int kind, FieldGeom g, long long o0, long long gsy, long long gsz,
+                                double* __restrict__ sum, double* __restrict__ comp)
 {
     const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= g.npts) return;
+    const long long x = p % g.nx, y = (p / g.nx) % g.ny, z = p / ((long long)g.nx * g.ny);
+    const long long q = o0 + z * gsz + y * gsy + x;
     const double v = (double)grad_value(gacc[padded(g, p)], c[p], kind);
-    const double s = sum[p];
+    const double s = sum[q];
     const double t = s + v;
-    comp[p] += (fabs(s) >= fabs(v)) ? (s - t) + v : (v - t) + s;
-    sum[p] = t;
+    comp[q] += (fabs(s) >= fabs(v)) ? (s - t) + v : (v - t) + s;
+    sum[q] = t;
 }
 
 template <class T>
@@ -192,9 +196,11 @@ cudaError_t launch_grad_out(const float* gacc_origin, const float* c_dense, int 
 }
 
 cudaError_t launch_grad_out_f64(const float* gacc_origin, const float* c_dense, int kind,
-                                const FieldGeom& g, double* sum, double* comp, cudaStream_t s)
+                                const FieldGeom& g, long long o0, long long gsy, long long gsz,
+                                double* sum, double* comp, cudaStream_t s)
 {
-    grad_sum_kernel<<<blocks_for(g.npts, 256), 256, 0, s>>>(gacc_origin, c_dense, kind, g, sum, comp);
+    grad_sum_kernel<<<blocks_for(g.npts, 256), 256, 0, s>>>(gacc_origin, c_dense, kind, g, o0, gsy, gsz, sum,
+                                                            comp);
     return cudaGetLastError();
 }
 

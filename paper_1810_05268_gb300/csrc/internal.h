@@ -97,8 +97,23 @@ struct Tile {
     int ver = 1;          // 1: register-queue kernels, 2: TMA-fed kernels (3D, orders 2-8)
 };
 
+// One batched step over several lanes (shots): lane l's arguments are
+// tab[l] (device) and its CTAs start[l] .. start[l+1]-1 of a 1D grid of
+// `blocks` CTAs (start: device, lanes + 1 entries).  Every lane's zlen is
+// its own; the tile shape is common.
+template <class Args>
+struct BatchLaunch {
+    const Args* tab;
+    const int* start;
+    int lanes;
+    int dims;
+    long long blocks;
+};
+
 // kernels.cu
 cudaError_t launch_fwd(const FwdArgs& a, const Tile& t, int K, int ck, cudaStream_t s);
+cudaError_t launch_fwd_batch(const BatchLaunch<FwdArgs>& b, const Tile& t, int K, int ck, cudaStream_t s);
+cudaError_t launch_adj_batch(const BatchLaunch<AdjArgs>& b, const Tile& t, int K, int ut, cudaStream_t s);
 cudaError_t launch_adj(const AdjArgs& a, const Tile& t, int K, int utype, cudaStream_t s);
 bool tile_supported(int dims, int K, const Tile& t);
 int tile_count(int dims);
@@ -123,9 +138,11 @@ cudaError_t launch_to_padded_w(const float* dense, int kind, float dt, const Fie
                                float* w_origin, float* c2_dense, int* err, cudaStream_t s);
 cudaError_t launch_grad_out(const float* gacc_origin, const float* c_dense, int kind, float scale,
                             const FieldGeom& g, float* out_dense, cudaStream_t s);
+// Compensated FP64 sum of one shot's gradient into a dense array; grid
+// point (z, y, x) adds at o0 + z * gsz + y * gsy + x.
 cudaError_t launch_grad_out_f64(const float* gacc_origin, const float* c2_dense, int kind,
-                                const FieldGeom& g, double* sum, double* comp,
-                                cudaStream_t s);
+                                const FieldGeom& g, long long o0, long long gsy, long long gsz,
+                                double* sum, double* comp, cudaStream_t s);
 cudaError_t launch_cast_restore(const void* src, int utype, const FieldGeom& g,
                                 float* dst_origin, cudaStream_t s);
 cudaError_t launch_copy_f64(const double* a, double* b, long long n, cudaStream_t s);

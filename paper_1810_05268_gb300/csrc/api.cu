@@ -649,7 +649,7 @@ bool grid_samples(const FieldGeom& f, const Tile& t, int zlen, int nrec)
     const long long gx = (f.nx + t.bx - 1) / t.bx;
     const long long gy = f.dims == 3 ? (f.ny + t.by - 1) / t.by : 1;
     const long long gz = (f.nz + zlen - 1) / zlen;
-    const long long tpc = (t.ver == 2 ? t.bx / 4 : t.bx) * (long long)t.by;
+    const long long tpc = (t.ver == 2 ? t.bx / 4 : (t.ver == 3 ? t.bx / t.vec : t.bx)) * (long long)t.by;
     return gx * gy * gz * tpc >= nrec;
 }
 
@@ -687,7 +687,9 @@ int fwd_step(Ctx& cx, const Role& u, const Role& up, const Role& out, int n, boo
             continue;
         }
         const int tok = cx.begin(PC_FWD);
-        if (m->tf.ver == 2) {
+        if (m->tf.ver == 3) {
+            CK_TRY(launch_fwd3(a, m->tf, m->K, ck, cx.st));
+        } else if (m->tf.ver == 2) {
             CUtensorMap tm;
             ST_TRY(tensor_map(m, a.u, U_FP32, tma_tile_x() + 2 * tma_halo_x(m->K), m->tf.by + 2 * m->K, &tm));
             CK_TRY(launch_fwd_tma(a, tm, m->tf, m->K, ck, cx.st));
@@ -732,7 +734,9 @@ int adj_step(Ctx& cx, const Role& l1, const Role& l2, const Role& l0, const Role
             continue;
         }
         const int tok = cx.begin(PC_ADJ);
-        if (m->ta.ver == 2) {
+        if (m->ta.ver == 3) {
+            CK_TRY(launch_adj3(a, m->ta, m->K, utype, cx.st));
+        } else if (m->ta.ver == 2) {
             CUtensorMap tl, tu;
             const int bx = tma_tile_x() + 2 * tma_halo_x(m->K), by = m->ta.by + 2 * m->K;
             ST_TRY(tensor_map(m, a.l1, U_FP32, bx, by, &tl));
@@ -842,6 +846,15 @@ int autotune(ckfwi_model* m, cudaStream_t st)
         const long long cols = (long long)((f.nx + t0.bx - 1) / t0.bx) * (f.dims == 3 ? (f.ny + t0.by - 1) / t0.by : 1);
         for (int z : zlens(cols)) cands.push_back(tile_at(f.dims, i, z));
     }
+    // vector-blocked kernels (3D)
+    if (f.dims == 3 && v3_fits(f, m->K)) {
+        for (int i = 0; i < v3_shape_count(); ++i) {
+            const Tile t0 = v3_tile_at(i, f.nz);
+            if (!v3_supported(f.dims, m->K, t0)) continue;
+            const long long cols = (long long)((f.nx + t0.bx - 1) / t0.bx) * ((f.ny + t0.by - 1) / t0.by);
+            for (int z : zlens(cols)) cands.push_back(v3_tile_at(i, z));
+        }
+    }
     const bool tma_ok = encode_fn() != nullptr;
     // TMA kernels run a persistent grid; their zlen field is the CTAs per SM
     for (int ty : {8, 16}) {
@@ -879,7 +892,10 @@ int autotune(ckfwi_model* m, cudaStream_t st)
     const int reps = 3;
     CUtensorMap tm_u, tm_l;
     auto go = [&](const Tile& t, int pass) -> int {
-        if (t.ver == 2) {
+        if (t.ver == 3) {
+            if (pass == 0) CK_TRY(launch_fwd3(a, t, m->K, CK_NONE, st));
+            else CK_TRY(launch_adj3(b, t, m->K, U_FP32, st));
+        } else if (t.ver == 2) {
             const int bx = tma_tile_x() + 2 * tma_halo_x(m->K), by = t.by + 2 * m->K;
             ST_TRY(tensor_map(m, a.u, U_FP32, bx, by, &tm_u));
             ST_TRY(tensor_map(m, b.l1, U_FP32, bx, by, &tm_l));
@@ -891,14 +907,17 @@ int autotune(ckfwi_model* m, cudaStream_t st)
         }
         return CKFWI_OK;
     };
-    // a forced tile (CKFWI_TILE_FWD / CKFWI_TILE_ADJ = "ver,bx,by,zlen") skips the search
+    // a forced tile (CKFWI_TILE_FWD / CKFWI_TILE_ADJ = "ver,bx,by,zlen[,vec]") skips the search
     auto forced = [&](const char* name, Tile* t) {
         const char* v = std::getenv(name);
         if (!v) return false;
         Tile u;
-        if (std::sscanf(v, "%d,%d,%d,%d", &u.ver, &u.bx, &u.by, &u.zlen) != 4 || u.zlen < 1) return false;
-        const bool okv = u.ver == 2 ? (tma_ok && u.bx == 64 && tma_supported(f.dims, m->K, u.by))
-                                    : tile_supported(f.dims, m->K, u);
+        const int nf = std::sscanf(v, "%d,%d,%d,%d,%d", &u.ver, &u.bx, &u.by, &u.zlen, &u.vec);
+        if (nf < 4 || u.zlen < 1) return false;
+        if (nf < 5) u.vec = 1;
+        const bool okv = u.ver == 3   ? v3_supported(f.dims, m->K, u) && v3_fits(f, m->K)
+                         : u.ver == 2 ? (tma_ok && u.bx == 64 && tma_supported(f.dims, m->K, u.by))
+                                      : tile_supported(f.dims, m->K, u);
         if (!okv) return false;
         *t = u;
         return true;
@@ -916,8 +935,8 @@ int autotune(ckfwi_model* m, cudaStream_t st)
             float ms = 0;
             CK_TRY(cudaEventElapsedTime(&ms, e0, e1));
             if (verbose)
-                std::fprintf(stderr, "ckfwi autotune %s ver %d tile %dx%d zlen %d: %.1f us\n", pass ? "adj" : "fwd",
-                             t.ver, t.bx, t.by, t.zlen, 1000.0f * ms / reps);
+                std::fprintf(stderr, "ckfwi autotune %s ver %d tile %dx%d vec %d zlen %d: %.1f us\n",
+                             pass ? "adj" : "fwd", t.ver, t.bx, t.by, t.vec, t.zlen, 1000.0f * ms / reps);
             if (pass == 0 && ms < best_f) { best_f = ms; m->tf = t; }
             if (pass == 1 && ms < best_a) { best_a = ms; m->ta = t; }
         }

@@ -92,9 +92,11 @@ enum CkMode { CK_NONE = 0, CK_FP32 = 1, CK_BF16 = 2, CK_FP16 = 3 };
 enum UType { U_FP32 = 0, U_BF16 = 1, U_FP16 = 2 };
 
 struct Tile {
-    int bx, by;           // CTA shape (by = 1 in 2D); TMA kernels: bx = 64 points, by rows
-    int zlen;             // ver 1: z planes per CTA; ver 2: CTAs per SM of the persistent grid
-    int ver = 1;          // 1: register-queue kernels, 2: TMA-fed kernels (3D, orders 2-8)
+    int bx, by;           // CTA shape in points (by = 1 in 2D); TMA kernels: bx = 64 points, by rows
+    int zlen;             // ver 1, 3: z planes per CTA; ver 2: CTAs per SM of the persistent grid
+    int ver = 1;          // 1: register-queue kernels, 2: TMA-fed kernels (3D, orders 2-8),
+                          // 3: vector-blocked kernels (3D)
+    int vec = 1;          // ver 3: x points per thread (2 or 4)
 };
 
 // One batched step over several lanes (shots): lane l's arguments are
@@ -118,6 +120,14 @@ cudaError_t launch_adj(const AdjArgs& a, const Tile& t, int K, int utype, cudaSt
 bool tile_supported(int dims, int K, const Tile& t);
 int tile_count(int dims);
 Tile tile_at(int dims, int i, int zlen);
+
+// stencil_v3.cu
+int v3_shape_count();
+Tile v3_tile_at(int i, int zlen);
+bool v3_supported(int dims, int K, const Tile& t);
+bool v3_fits(const FieldGeom& g, int K);
+cudaError_t launch_fwd3(const FwdArgs& a, const Tile& t, int K, int ck, cudaStream_t s);
+cudaError_t launch_adj3(const AdjArgs& a, const Tile& t, int K, int ut, cudaStream_t s);
 
 // stencil_tma.cu (CUtensorMap comes from <cuda.h>)
 }  // namespace ckfwi

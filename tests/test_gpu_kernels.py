@@ -1,9 +1,10 @@
-"""The two generations of 3D stencil kernels agree bit for bit.
+"""The three generations of 3D stencil kernels agree bit for bit.
 
-The TMA-fed kernels (stencil_tma.cu) perform the same FP32 operations in
-the same order as the register-queue kernels (kernels.cu), so receivers and
-gradients must be identical, whatever the tile; both are also checked
-against the FP64 oracle by test_gpu_parity.py through the autotuned choice.
+The TMA-fed kernels (stencil_tma.cu) and the vector-blocked kernels
+(stencil_v3.cu) perform the same FP32 operations in the same order as the
+register-queue kernels (kernels.cu), so receivers and gradients must be
+identical, whatever the tile; all are also checked against the FP64 oracle
+by test_gpu_parity.py through the autotuned choice.
 """
 import os
 
@@ -63,5 +64,40 @@ def test_tma_reverse_reads_half_slots_like_register_queue(mode):
     dobs = torch.from_numpy((rng.standard_normal((61, case.rec.shape[0])) * 1e-3).astype(np.float32)).cuda()
     ref = _run(case, "1,32,8,9", "1,32,8,9", dobs, 4, mode)
     got = _run(case, "2,64,8,2", "2,64,8,2", dobs, 4, mode)
+    assert got[1] == ref[1]
+    assert np.array_equal(got[2], ref[2])
+
+
+V3_TILES = ["3,64,8,%d,4", "3,64,8,%d,2", "3,32,16,%d,4", "3,32,16,%d,2"]
+
+
+@pytest.mark.parametrize("so,shape", [(2, (30, 37, 70)), (4, (33, 41, 131)), (8, (35, 43, 70)), (8, (26, 29, 200)),
+                                      (16, (36, 41, 77)), (4, (21, 19, 13))])
+@pytest.mark.parametrize("tile", V3_TILES)
+def test_vector_kernels_bitwise_equal_register_queue_kernels(so, shape, tile):
+    case = make_case(3, so, shape, nbl=6, nt=70, seed=so + len(tile))
+    rng = np.random.default_rng(so)
+    dobs = torch.from_numpy((rng.standard_normal((71, case.rec.shape[0])) * 1e-3).astype(np.float32)).cuda()
+    k = so // 2
+    by1 = max(8, k)
+    ref = _run(case, "1,32,%d,9" % by1, "1,32,%d,9" % by1, dobs, 5)
+    for zlen in (7, 64):           # several z runs per column, or one
+        t = tile % zlen
+        if int(t.split(",")[2]) < k:
+            continue
+        got = _run(case, t, t, dobs, 5)
+        assert np.array_equal(got[0], ref[0])
+        assert got[1] == ref[1]
+        assert np.array_equal(got[2], ref[2])
+
+
+@pytest.mark.parametrize("mode", ["bf16", "fp16"])
+@pytest.mark.parametrize("vec", [2, 4])
+def test_vector_kernels_half_slots_like_register_queue(mode, vec):
+    case = make_case(3, 8, (35, 43, 70), nbl=6, nt=60, seed=3)
+    rng = np.random.default_rng(1)
+    dobs = torch.from_numpy((rng.standard_normal((61, case.rec.shape[0])) * 1e-3).astype(np.float32)).cuda()
+    ref = _run(case, "1,32,8,9", "1,32,8,9", dobs, 4, mode)
+    got = _run(case, "3,64,8,11,%d" % vec, "3,64,8,11,%d" % vec, dobs, 4, mode)
     assert got[1] == ref[1]
     assert np.array_equal(got[2], ref[2])

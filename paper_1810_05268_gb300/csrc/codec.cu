@@ -52,7 +52,7 @@ constexpr uint32_t VERSION = 1u;
 constexpr int HDR = 16;
 constexpr int CHUNK = 32;
 constexpr int GUARD = 1;
-constexpr int ENC_THREADS = 128;
+constexpr int ENC_THREADS = 64;
 constexpr int CMP_WARPS = 4;
 constexpr int DEC_THREADS = 128;
 
@@ -104,6 +104,21 @@ constexpr Perm make_perm(int dims)
     }
     return r;
 }
+
+// inverse of the sequency order: the rank of coefficient i (shared-memory
+// rows are addressed by it at run time, so no register array is ever
+// indexed with a run-time value)
+constexpr Perm make_rank(int dims)
+{
+    const Perm P = make_perm(dims);
+    Perm r{};
+    for (int k = 0; k < 64; ++k) r.p[k] = 0;
+    for (int k = 0; k < (dims == 3 ? 64 : 16); ++k) r.p[P.p[k]] = k;
+    return r;
+}
+__constant__ Perm c_rank3 = make_rank(3);
+__constant__ Perm c_rank2 = make_rank(2);
+template <int DIMS> __device__ __forceinline__ int rank_of(int i) { return DIMS == 3 ? c_rank3.p[i] : c_rank2.p[i]; }
 
 __device__ __forceinline__ int32_t half_of(int32_t a) { return a >> 1; }  // arithmetic shift
 
@@ -256,75 +271,136 @@ __device__ __forceinline__ unsigned long long low_mask(int n)
     return n >= 64 ? ~0ull : ((1ull << n) - 1ull);
 }
 
+// Raw form of a block: bits 1, 1, then the V float bit patterns, 32 bits
+// each, LSB first; value i occupies bits 2 + 32 i .. 33 + 32 i, so word k
+// holds the top two bits of value k-1 and the low 30 bits of value k.
+template <int DIMS>
+__device__ __forceinline__ int raw_block(const float* __restrict__ x, const CodecView& v, const BlockPos& bp,
+                                         uint32_t* __restrict__ w)
+{
+    constexpr int V = Cfg<DIMS>::V;
+    constexpr int ROWS = DIMS == 3 ? 16 : 4;
+    const int xs = 4 * bp.bx;
+    uint32_t prev = 3u;      // the two header bits (as the "top bits" of value -1: 3 >> 30 would drop them)
+    bool first = true;
+#pragma unroll 1
+    for (int r = 0; r < ROWS; ++r) {
+        const int lz = DIMS == 3 ? r / 4 : r;
+        const int ly = DIMS == 3 ? r % 4 : 0;
+        const int z = min(4 * bp.bz + lz, v.nz - 1);
+        const int y = DIMS == 3 ? min(4 * bp.by + ly, v.ny - 1) : 0;
+        const float* row = x + (long long)z * v.pz + (long long)y * v.py;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            const uint32_t g = __float_as_uint(__ldg(row + min(xs + c, v.nx - 1)));
+            const int k = 4 * r + c;
+            w[k] = (first ? prev : (prev >> 30)) | (g << 2);
+            first = false;
+            prev = g;
+        }
+    }
+    w[V] = prev >> 30;
+    return 2 + 32 * V;
+}
+
+// In-place transpose of a 32 x 32 bit matrix: on return a[p] bit r is the
+// input a[r] bit p (five stages of block swaps: j = 16, 8, 4, 2, 1).
+__device__ __forceinline__ void transpose32(uint32_t (&a)[32])
+{
+    constexpr uint32_t M[5] = {0x0000FFFFu, 0x00FF00FFu, 0x0F0F0F0Fu, 0x33333333u, 0x55555555u};
+#pragma unroll
+    for (int st = 0; st < 5; ++st) {
+        const int j = 16 >> st;
+#pragma unroll
+        for (int k = 0; k < 32; ++k) {
+            if (k & j) continue;
+            const uint32_t t = ((a[k] >> j) ^ a[k + j]) & M[st];
+            a[k] ^= t << j;
+            a[k + j] ^= t;
+        }
+    }
+}
+
 // Encode block b into its scratch slot; returns its bit count.
+// siv, col: this thread's two columns of shared memory (stride ENC_THREADS):
+// the block's integers before the transform, and its negabinary
+// coefficients in sequency order, later its bit-plane words (plane p of
+// coefficients 0-31 in col[p], of 32-63 in col[32 + p]).
 template <int DIMS>
 __device__ __forceinline__ int encode_block(const float* __restrict__ x, const CodecView& v, const Geo& G,
                                             float tol_f, uint32_t* __restrict__ scratch, long long b,
-                                            int32_t* siv, int* err)
+                                            int32_t* siv, uint32_t* col, int* err)
 {
     constexpr int V = Cfg<DIMS>::V;
-    constexpr Perm P = make_perm(DIMS);
+    constexpr int S = ENC_THREADS;
     const BlockPos bp = block_pos(G, b);
-    float f[V];
-    gather<DIMS>(x, v, bp, f);
     BitW bw{scratch + b * Cfg<DIMS>::MAXW, 0ull, 0, 0, Cfg<DIMS>::MAXW};
-
-    float amax = 0.0f;
-    bool bad = false;
-#pragma unroll
-    for (int i = 0; i < V; ++i) {
-        bad |= !isfinite(f[i]);
-        amax = fmaxf(amax, fabsf(f[i]));
-    }
-    if (bad) atomicOr(err, 1);
-    if (bad || amax <= tol_f) {
-        bw.put(0u, 1);
-        return bw.flush();
-    }
     int emax = -1000;
+    int ptop = 0;
+    {
+        float f[V];
+        gather<DIMS>(x, v, bp, f);
+        float amax = 0.0f;
+        bool bad = false;
 #pragma unroll
-    for (int i = 0; i < V; ++i) {
-        const uint32_t u = __float_as_uint(f[i]);
-        const int be = (int)((u >> 23) & 0xFF);
-        if (u & 0x7FFFFFFFu) emax = max(emax, max(be, 1) - 127);
-    }
-    int32_t c[V];
+        for (int i = 0; i < V; ++i) {
+            bad |= !isfinite(f[i]);
+            amax = fmaxf(amax, fabsf(f[i]));
+        }
+        if (bad) atomicOr(err, 1);
+        if (bad || amax <= tol_f) {
+            bw.put(0u, 1);
+            return bw.flush();
+        }
 #pragma unroll
-    for (int i = 0; i < V; ++i) {
-        const uint32_t u = __float_as_uint(f[i]);
-        const int be = (int)((u >> 23) & 0xFF);
-        const uint32_t M = (u & 0x7FFFFFu) | (be > 0 ? 0x800000u : 0u);
-        const int sh = emax - (max(be, 1) - 127);
-        uint32_t mag = sh >= 32 ? 0u : (M >> sh);
-        if (!(u & 0x7FFFFFFFu)) mag = 0u;
-        c[i] = (u >> 31) ? -(int32_t)mag : (int32_t)mag;
-        siv[i * ENC_THREADS] = c[i];
-    }
-    xform_fwd<DIMS>(c);
-    uint32_t nb[V];
-    uint32_t orall = 0;
+        for (int i = 0; i < V; ++i) {
+            const uint32_t u = __float_as_uint(f[i]);
+            const int be = (int)((u >> 23) & 0xFF);
+            if (u & 0x7FFFFFFFu) emax = max(emax, max(be, 1) - 127);
+        }
+        int32_t c[V];
 #pragma unroll
-    for (int r = 0; r < V; ++r) {
-        nb[r] = nega(c[P.p[r]]);
-        orall |= nb[r];
+        for (int i = 0; i < V; ++i) {
+            const uint32_t u = __float_as_uint(f[i]);
+            const int be = (int)((u >> 23) & 0xFF);
+            const uint32_t M = (u & 0x7FFFFFu) | (be > 0 ? 0x800000u : 0u);
+            const int sh = emax - (max(be, 1) - 127);
+            uint32_t mag = sh >= 32 ? 0u : (M >> sh);
+            if (!(u & 0x7FFFFFFFu)) mag = 0u;
+            c[i] = (u >> 31) ? -(int32_t)mag : (int32_t)mag;
+            siv[i * S] = c[i];
+        }
+        xform_fwd<DIMS>(c);
+        uint32_t orall = 0;
+#pragma unroll
+        for (int i = 0; i < V; ++i) {
+            const uint32_t n = nega(c[i]);
+            col[rank_of<DIMS>(i) * S] = n;
+            orall |= n;
+        }
+        ptop = orall ? 31 - __clz(orall) : 0;
     }
-    const int ptop = orall ? 31 - __clz(orall) : 0;
+    asm volatile("" ::: "memory");
     const float Tf = tol_f * pow2f(23 - emax);
     const int T = (int)Tf;
     int pbot = -1;
     if (T >= 2 && emax < 126) {
         const int lg = 31 - __clz(T);
         const int p0 = min(max(lg - GUARD, 0), ptop);
+#pragma unroll 1
         for (int p = p0; p >= 0; --p) {
             const uint32_t mask = ~((1u << p) - 1u);
             int32_t t[V];
 #pragma unroll
-            for (int r = 0; r < V; ++r) t[P.p[r]] = unnega(nb[r] & mask);
+            for (int i = 0; i < V; ++i) t[i] = unnega(col[rank_of<DIMS>(i) * S] & mask);
             xform_inv<DIMS>(t);
+            // keep the comparison's shared loads after the transform: hoisted
+            // above it they would hold 64 more registers
+            asm volatile("" ::: "memory");
             bool ok = true;
 #pragma unroll
             for (int i = 0; i < V; ++i) {
-                const long long d = (long long)siv[i * ENC_THREADS] - (long long)t[i];
+                const long long d = (long long)siv[i * S] - (long long)t[i];
                 ok &= (d <= (long long)T - 2) && (-d <= (long long)T - 2);
             }
             if (ok) {
@@ -334,16 +410,26 @@ __device__ __forceinline__ int encode_block(const float* __restrict__ x, const C
         }
     }
     if (pbot >= 0) {
+        // bit-plane words of the coefficients, by transposing 32-coefficient halves
+#pragma unroll
+        for (int h = 0; h < (V + 31) / 32; ++h) {
+            uint32_t m[32];
+#pragma unroll
+            for (int r = 0; r < 32; ++r) m[r] = (32 * h + r < V) ? col[(32 * h + r) * S] : 0u;
+            transpose32(m);
+#pragma unroll
+            for (int q = 0; q < 32; ++q) col[(32 * h + q) * S] = m[q];
+        }
         bw.put(1u, 1);
         bw.put(0u, 1);
         bw.put((uint32_t)(emax + 127), 8);
         bw.put((uint32_t)ptop, 5);
         bw.put((uint32_t)pbot, 5);
         int s = 0;
+#pragma unroll 1
         for (int p = ptop; p >= pbot; --p) {
-            unsigned long long W = 0;
-#pragma unroll
-            for (int r = 0; r < V; ++r) W |= (unsigned long long)((nb[r] >> p) & 1u) << r;
+            unsigned long long W = col[p * S];
+            if (V > 32) W |= (unsigned long long)col[(32 + p) * S] << 32;
             bw.put64(W & low_mask(s), s);
             while (s < V) {
                 const unsigned long long rest = W >> s;
@@ -358,31 +444,23 @@ __device__ __forceinline__ int encode_block(const float* __restrict__ x, const C
             }
         }
         if (bw.bits() <= Cfg<DIMS>::MAXBITS) return bw.flush();
-        bw.acc = 0ull;      // longer than raw: start over with the raw form
-        bw.nacc = 0;
-        bw.nw = 0;
+        // longer than raw: the raw form replaces it
     }
-    bw.put(1u, 1);
-    bw.put(1u, 1);
-    {
-        float g[V];
-        gather<DIMS>(x, v, bp, g);
-#pragma unroll
-        for (int i = 0; i < V; ++i) bw.put(__float_as_uint(g[i]), 32);
-    }
-    return bw.flush();
+    return raw_block<DIMS>(x, v, bp, scratch + b * Cfg<DIMS>::MAXW);
 }
 
 // One thread per block; each warp owns one 32-block chunk and stores the
 // chunk's word count in the chunk table (the scan turns counts into offsets).
 template <int DIMS>
-__global__ void __launch_bounds__(ENC_THREADS) enc_kernel(const float* __restrict__ x, CodecView v,
+__global__ void __launch_bounds__(ENC_THREADS, 5) enc_kernel(const float* __restrict__ x, CodecView v,
                                                           Geo G, float tol_f, uint32_t* __restrict__ scratch,
                                                           uint32_t* __restrict__ out, const long long* base_word,
                                                           long long cap_words, int* err)
 {
     constexpr int V = Cfg<DIMS>::V;
+    constexpr int CWD = V > 32 ? V : 32;       // plane words need 32 rows even in 2D
     __shared__ int32_t siv[V * ENC_THREADS];
+    __shared__ uint32_t colw[CWD * ENC_THREADS];
     const long long b = (long long)blockIdx.x * ENC_THREADS + threadIdx.x;
     const long long base = *base_word;
     if (base + G.table_words > cap_words) {
@@ -394,7 +472,7 @@ __global__ void __launch_bounds__(ENC_THREADS) enc_kernel(const float* __restric
     if (b == 0 && (G.nblocks & 1)) sizes[G.nblocks] = 0;
     int nbits = 0;
     if (b < G.nblocks) {
-        nbits = encode_block<DIMS>(x, v, G, tol_f, scratch, b, siv + threadIdx.x, err);
+        nbits = encode_block<DIMS>(x, v, G, tol_f, scratch, b, siv + threadIdx.x, colw + threadIdx.x, err);
         sizes[b] = (uint16_t)nbits;
     }
     int tot = nbits;
@@ -557,7 +635,9 @@ __global__ void __launch_bounds__(DEC_THREADS) dec_kernel(const uint32_t* __rest
                                                           float* __restrict__ x, int* err)
 {
     constexpr int V = Cfg<DIMS>::V;
-    constexpr Perm P = make_perm(DIMS);
+    constexpr int CWD = V > 32 ? V : 32;
+    __shared__ uint32_t colw[CWD * DEC_THREADS];
+    uint32_t* col = colw + threadIdx.x;
     const long long b = (long long)blockIdx.x * DEC_THREADS + threadIdx.x;
     const int lane = threadIdx.x & 31;
     const long long c = b / CHUNK;
@@ -613,10 +693,16 @@ __global__ void __launch_bounds__(DEC_THREADS) dec_kernel(const uint32_t* __rest
         const int pbot = (int)((h0 >> 15) & 31u);
         pos += 20;
         if (emax < -126 || emax > 127 || pbot > ptop) corrupt = true;
-        uint32_t nb[V];
+        // plane words into this thread's shared column (rows p and 32 + p),
+        // then one bit-matrix transpose gives the coefficient words
+        constexpr int S = DEC_THREADS;
 #pragma unroll
-        for (int r = 0; r < V; ++r) nb[r] = 0u;
+        for (int q = 0; q < 32; ++q) {
+            col[q * S] = 0u;
+            if (V > 32) col[(32 + q) * S] = 0u;
+        }
         int s = 0;
+#pragma unroll 1
         for (int p = ptop; p >= pbot && !corrupt; --p) {
             unsigned long long W = 0;
             if (s > 0) {
@@ -636,12 +722,22 @@ __global__ void __launch_bounds__(DEC_THREADS) dec_kernel(const uint32_t* __rest
                 s += z + 1;
             }
             if (pos > end) corrupt = true;
-#pragma unroll
-            for (int r = 0; r < V; ++r) nb[r] |= (uint32_t)((W >> r) & 1ull) << p;
+            col[p * S] = (uint32_t)W;
+            if (V > 32) col[(32 + p) * S] = (uint32_t)(W >> 32);
         }
+#pragma unroll
+        for (int h = 0; h < (V + 31) / 32; ++h) {
+            uint32_t m[32];
+#pragma unroll
+            for (int q = 0; q < 32; ++q) m[q] = col[(32 * h + q) * S];
+            transpose32(m);
+#pragma unroll
+            for (int r = 0; r < 32; ++r) col[(32 * h + r) * S] = m[r];
+        }
+        asm volatile("" ::: "memory");
         int32_t t[V];
 #pragma unroll
-        for (int r = 0; r < V; ++r) t[P.p[r]] = unnega(nb[r]);
+        for (int i = 0; i < V; ++i) t[i] = unnega(col[rank_of<DIMS>(i) * S]);
         xform_inv<DIMS>(t);
         const float sc = pow2f(max(emax - 23, -126));
 #pragma unroll

@@ -50,11 +50,23 @@ def main():
     npts = int(np.prod(shape))
     out["fwd_gbs"] = 16 * npts / (out["fwd_us"] * 1e-6) / 1e9
     out["adj_gbs"] = 28 * npts / (out["adj_us"] * 1e-6) / 1e9
+    # codec on a wavefield-like field: the last forward state of the shot
     x = torch.from_numpy((vel - vel.mean()) * 1e-2).cuda()
     for _ in range(args.reps):
         words, _ = C.codec_compress(x, args.tol)
         y = C.codec_decompress(words, shape)
     out["codec_ratio"] = npts / words.numel()
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    for _ in range(args.reps):
+        C.codec_compress(x, args.tol)
+    torch.cuda.synchronize()
+    out["compress_us"] = (time.perf_counter() - t) * 1e6 / args.reps
+    t = time.perf_counter()
+    for _ in range(args.reps):
+        C.codec_decompress(words, shape)
+    torch.cuda.synchronize()
+    out["decompress_us"] = (time.perf_counter() - t) * 1e6 / args.reps
     print(json.dumps(out))
 
 

@@ -703,7 +703,8 @@ int fwd_step(Ctx& cx, const Role& u, const Role& up, const Role& out, int n, boo
         if (cx.issue) {
             const int tok = cx.begin(PC_FWD);
             BatchLaunch<FwdArgs> b{cx.ftab_d + cx.fi, cx.fstart_d, NL, cx.m->fg.dims, cx.fblocks};
-            CK_TRY(launch_fwd_batch(b, cx.bf, cx.m->K, ck, cx.st));
+            if (cx.bf.ver == 3) CK_TRY(launch_fwd3_batch(b, cx.bf, cx.m->K, ck, cx.st));
+            else CK_TRY(launch_fwd_batch(b, cx.bf, cx.m->K, ck, cx.st));
             cx.end(tok);
             ++cx.launches;
         }
@@ -752,7 +753,8 @@ int adj_step(Ctx& cx, const Role& l1, const Role& l2, const Role& l0, const Role
         if (cx.issue) {
             const int tok = cx.begin(PC_ADJ);
             BatchLaunch<AdjArgs> b{cx.atab_d + cx.ai, cx.astart_d, NL, cx.m->fg.dims, cx.ablocks};
-            CK_TRY(launch_adj_batch(b, cx.ba, cx.m->K, utype, cx.st));
+            if (cx.ba.ver == 3) CK_TRY(launch_adj3_batch(b, cx.ba, cx.m->K, utype, cx.st));
+            else CK_TRY(launch_adj_batch(b, cx.ba, cx.m->K, utype, cx.st));
             cx.end(tok);
             ++cx.launches;
         }
@@ -1484,9 +1486,18 @@ int batch_tune(const std::vector<ckfwi_model*>& lanes, cudaStream_t st, const Ba
         std::vector<int> z;
     };
     std::vector<Cand> cands;
+    std::vector<Tile> shapes;
     for (int i = 0; i < tile_count(dims); ++i) {
         const Tile t = tile_at(dims, i, 1);
-        if (!tile_supported(dims, K, t)) continue;
+        if (tile_supported(dims, K, t)) shapes.push_back(t);
+    }
+    bool fits3 = dims == 3;
+    for (ckfwi_model* L : lanes) fits3 = fits3 && v3_fits(L->fg, K);
+    for (int i = 0; fits3 && i < v3_shape_count(); ++i) {
+        const Tile t = v3_tile_at(i, 1);
+        if (v3_supported(dims, K, t)) shapes.push_back(t);
+    }
+    for (const Tile& t : shapes) {
         long long cols = 0;
         int nzmax = 1;
         for (ckfwi_model* L : lanes) {
@@ -1555,11 +1566,13 @@ int batch_tune(const std::vector<ckfwi_model*>& lanes, cudaStream_t st, const Ba
         }
         for (int pass = 0; pass < 2 && rs == CKFWI_OK; ++pass) {
             auto go = [&]() {
-                if (pass == 0)
-                    return launch_fwd_batch(BatchLaunch<FwdArgs>{ftab, dst.as<int>(), NL, dims, total}, c.t, K,
-                                            CK_NONE, st);
-                return launch_adj_batch(BatchLaunch<AdjArgs>{atab, dst.as<int>(), NL, dims, total}, c.t, K, U_FP32,
-                                        st);
+                const BatchLaunch<FwdArgs> bf{ftab, dst.as<int>(), NL, dims, total};
+                const BatchLaunch<AdjArgs> ba{atab, dst.as<int>(), NL, dims, total};
+                if (c.t.ver == 3)
+                    return pass == 0 ? launch_fwd3_batch(bf, c.t, K, CK_NONE, st)
+                                     : launch_adj3_batch(ba, c.t, K, U_FP32, st);
+                return pass == 0 ? launch_fwd_batch(bf, c.t, K, CK_NONE, st)
+                                 : launch_adj_batch(ba, c.t, K, U_FP32, st);
             };
             const int reps = 3;
             cudaError_t e = go();
@@ -1574,8 +1587,9 @@ int batch_tune(const std::vector<ckfwi_model*>& lanes, cudaStream_t st, const Ba
                 break;
             }
             if (verbose)
-                std::fprintf(stderr, "ckfwi batch autotune %s lanes %d tile %dx%d z[0] %d: %.1f us\n",
-                             pass ? "adj" : "fwd", NL, c.t.bx, c.t.by, c.z[0], 1000.0f * ms / reps);
+                std::fprintf(stderr, "ckfwi batch autotune %s lanes %d ver %d tile %dx%d vec %d z[0] %d: %.1f us\n",
+                             pass ? "adj" : "fwd", NL, c.t.ver, c.t.bx, c.t.by, c.t.vec, c.z[0],
+                             1000.0f * ms / reps);
             if (ms < best[pass]) {
                 best[pass] = ms;
                 if (pass == 0) {

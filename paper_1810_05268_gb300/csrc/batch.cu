@@ -10,31 +10,6 @@
 
 namespace ckfwi {
 
-__device__ __forceinline__ int lane_of(const int* __restrict__ start, int nl, int b)
-{
-    int lo = 0, hi = nl - 1;
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (__ldg(start + mid) <= b) lo = mid;
-        else hi = mid - 1;
-    }
-    return lo;
-}
-
-template <class Args>
-__device__ __forceinline__ int stage_args(Args& dst, const Args* __restrict__ tab, const int* __restrict__ start,
-                                          int nl)
-{
-    static_assert(sizeof(Args) % 4 == 0, "argument block must be whole words");
-    const int l = lane_of(start, nl, blockIdx.x);
-    const int* src = reinterpret_cast<const int*>(tab + l);
-    int* d = reinterpret_cast<int*>(&dst);
-    const int tid = threadIdx.y * blockDim.x + threadIdx.x;
-    for (int i = tid; i < (int)(sizeof(Args) / 4); i += blockDim.x * blockDim.y) d[i] = __ldg(src + i);
-    __syncthreads();
-    return blockIdx.x - __ldg(start + l);
-}
-
 template <int K, int DIMS, int BX, int BY, int CK>
 __global__ void __launch_bounds__(BX * BY)
     fwd_batch_kernel(const FwdArgs* __restrict__ tab, const int* __restrict__ start, int nl)

@@ -321,66 +321,108 @@ __device__ __forceinline__ void transpose32(uint32_t (&a)[32])
     }
 }
 
-// Encode block b into its scratch slot; returns its bit count.
-// siv, col: this thread's two columns of shared memory (stride ENC_THREADS):
-// the block's integers before the transform, and its negabinary
-// coefficients in sequency order, later its bit-plane words (plane p of
-// coefficients 0-31 in col[p], of 32-63 in col[32 + p]).
+// sequency order: coefficient index of rank r
+__constant__ Perm c_perm3 = make_perm(3);
+__constant__ Perm c_perm2 = make_perm(2);
+template <int DIMS> __device__ __forceinline__ int perm_of(int r) { return DIMS == 3 ? c_perm3.p[r] : c_perm2.p[r]; }
+
+// Encode block b into its scratch slot; returns its bit count.  The block
+// is processed in four z slices (2D: four rows) so that only one slice's
+// values are held in registers outside the closed-loop search, which keeps
+// the code small and the register count low.  siv and col are this
+// thread's two columns of shared memory (stride ENC_THREADS): col holds the
+// slice values, then the transformed coefficients (natural order, as
+// negabinary); siv the integers before the transform, then the bit-plane
+// words (plane p of the first 32 coefficients in sequency order at row p,
+// of the next 32 at row 32 + p).
 template <int DIMS>
 __device__ __forceinline__ int encode_block(const float* __restrict__ x, const CodecView& v, const Geo& G,
                                             float tol_f, uint32_t* __restrict__ scratch, long long b,
                                             int32_t* siv, uint32_t* col, int* err)
 {
     constexpr int V = Cfg<DIMS>::V;
+    constexpr int SL = V / 4;                 // values per slice
     constexpr int S = ENC_THREADS;
     const BlockPos bp = block_pos(G, b);
     BitW bw{scratch + b * Cfg<DIMS>::MAXW, 0ull, 0, 0, Cfg<DIMS>::MAXW};
+    const int xs = 4 * bp.bx;
+    const bool vec = v.aligned && xs + 3 < v.nx;
+    // 1. gather, finiteness, max |x| and the block exponent
+    float amax = 0.0f;
+    bool bad = false;
     int emax = -1000;
-    int ptop = 0;
-    {
-        float f[V];
-        gather<DIMS>(x, v, bp, f);
-        float amax = 0.0f;
-        bool bad = false;
+#pragma unroll 1
+    for (int sl = 0; sl < 4; ++sl) {
 #pragma unroll
-        for (int i = 0; i < V; ++i) {
-            bad |= !isfinite(f[i]);
-            amax = fmaxf(amax, fabsf(f[i]));
-        }
-        if (bad) atomicOr(err, 1);
-        if (bad || amax <= tol_f) {
-            bw.put(0u, 1);
-            return bw.flush();
-        }
+        for (int ly = 0; ly < SL / 4; ++ly) {
+            const int z = min(4 * bp.bz + sl, v.nz - 1);
+            const int y = DIMS == 3 ? min(4 * bp.by + ly, v.ny - 1) : 0;
+            const float* row = x + (long long)z * v.pz + (long long)y * v.py;
+            float f[4];
+            if (vec) {
+                const float4 q = __ldg(reinterpret_cast<const float4*>(row + xs));
+                f[0] = q.x; f[1] = q.y; f[2] = q.z; f[3] = q.w;
+            } else {
 #pragma unroll
-        for (int i = 0; i < V; ++i) {
-            const uint32_t u = __float_as_uint(f[i]);
-            const int be = (int)((u >> 23) & 0xFF);
-            if (u & 0x7FFFFFFFu) emax = max(emax, max(be, 1) - 127);
-        }
-        int32_t c[V];
+                for (int c = 0; c < 4; ++c) f[c] = __ldg(row + min(xs + c, v.nx - 1));
+            }
 #pragma unroll
-        for (int i = 0; i < V; ++i) {
-            const uint32_t u = __float_as_uint(f[i]);
+            for (int c = 0; c < 4; ++c) {
+                const uint32_t u = __float_as_uint(f[c]);
+                bad |= !isfinite(f[c]);
+                amax = fmaxf(amax, fabsf(f[c]));
+                const int be = (int)((u >> 23) & 0xFF);
+                if (u & 0x7FFFFFFFu) emax = max(emax, max(be, 1) - 127);
+                col[(SL * sl + 4 * ly + c) * S] = u;
+            }
+        }
+    }
+    if (bad) atomicOr(err, 1);
+    if (bad || amax <= tol_f) {
+        bw.put(0u, 1);
+        return bw.flush();
+    }
+    // 2. integers (kept in siv for the closed loop), lifts along x and y
+#pragma unroll 1
+    for (int sl = 0; sl < 4; ++sl) {
+        int32_t c[SL];
+#pragma unroll
+        for (int k = 0; k < SL; ++k) {
+            const uint32_t u = col[(SL * sl + k) * S];
             const int be = (int)((u >> 23) & 0xFF);
             const uint32_t M = (u & 0x7FFFFFu) | (be > 0 ? 0x800000u : 0u);
             const int sh = emax - (max(be, 1) - 127);
             uint32_t mag = sh >= 32 ? 0u : (M >> sh);
             if (!(u & 0x7FFFFFFFu)) mag = 0u;
-            c[i] = (u >> 31) ? -(int32_t)mag : (int32_t)mag;
-            siv[i * S] = c[i];
+            c[k] = (u >> 31) ? -(int32_t)mag : (int32_t)mag;
+            siv[(SL * sl + k) * S] = c[k];
         }
-        xform_fwd<DIMS>(c);
-        uint32_t orall = 0;
 #pragma unroll
-        for (int i = 0; i < V; ++i) {
-            const uint32_t n = nega(c[i]);
-            col[rank_of<DIMS>(i) * S] = n;
-            orall |= n;
+        for (int r = 0; r < SL / 4; ++r) lift_fwd(c[4 * r], c[4 * r + 1], c[4 * r + 2], c[4 * r + 3]);
+        if constexpr (DIMS == 3) {
+#pragma unroll
+            for (int xx = 0; xx < 4; ++xx) lift_fwd(c[xx], c[4 + xx], c[8 + xx], c[12 + xx]);
         }
-        ptop = orall ? 31 - __clz(orall) : 0;
+#pragma unroll
+        for (int k = 0; k < SL; ++k) col[(SL * sl + k) * S] = (uint32_t)c[k];
     }
+    // 3. lifts along z (across slices), negabinary
+    uint32_t orall = 0;
+#pragma unroll 1
+    for (int k = 0; k < SL; ++k) {
+        int32_t a0 = (int32_t)col[k * S], a1 = (int32_t)col[(SL + k) * S];
+        int32_t a2 = (int32_t)col[(2 * SL + k) * S], a3 = (int32_t)col[(3 * SL + k) * S];
+        lift_fwd(a0, a1, a2, a3);
+        const uint32_t n0 = nega(a0), n1 = nega(a1), n2 = nega(a2), n3 = nega(a3);
+        col[k * S] = n0;
+        col[(SL + k) * S] = n1;
+        col[(2 * SL + k) * S] = n2;
+        col[(3 * SL + k) * S] = n3;
+        orall |= n0 | n1 | n2 | n3;
+    }
+    const int ptop = orall ? 31 - __clz(orall) : 0;
     asm volatile("" ::: "memory");
+    // 4. closed loop: the first plane whose truncation reproduces every integer within T - 2
     const float Tf = tol_f * pow2f(23 - emax);
     const int T = (int)Tf;
     int pbot = -1;
@@ -392,7 +434,7 @@ __device__ __forceinline__ int encode_block(const float* __restrict__ x, const C
             const uint32_t mask = ~((1u << p) - 1u);
             int32_t t[V];
 #pragma unroll
-            for (int i = 0; i < V; ++i) t[i] = unnega(col[rank_of<DIMS>(i) * S] & mask);
+            for (int i = 0; i < V; ++i) t[i] = unnega(col[i * S] & mask);
             xform_inv<DIMS>(t);
             // keep the comparison's shared loads after the transform: hoisted
             // above it they would hold 64 more registers
@@ -410,15 +452,16 @@ __device__ __forceinline__ int encode_block(const float* __restrict__ x, const C
         }
     }
     if (pbot >= 0) {
-        // bit-plane words of the coefficients, by transposing 32-coefficient halves
-#pragma unroll
+        // 5. bit-plane words: sequency-ordered coefficients, transposed 32 at a time
+        asm volatile("" ::: "memory");
+#pragma unroll 1
         for (int h = 0; h < (V + 31) / 32; ++h) {
             uint32_t m[32];
 #pragma unroll
-            for (int r = 0; r < 32; ++r) m[r] = (32 * h + r < V) ? col[(32 * h + r) * S] : 0u;
+            for (int r = 0; r < 32; ++r) m[r] = (32 * h + r < V) ? col[perm_of<DIMS>(32 * h + r) * S] : 0u;
             transpose32(m);
 #pragma unroll
-            for (int q = 0; q < 32; ++q) col[(32 * h + q) * S] = m[q];
+            for (int q = 0; q < 32; ++q) siv[(32 * h + q) * S] = (int32_t)m[q];
         }
         bw.put(1u, 1);
         bw.put(0u, 1);
@@ -428,8 +471,8 @@ __device__ __forceinline__ int encode_block(const float* __restrict__ x, const C
         int s = 0;
 #pragma unroll 1
         for (int p = ptop; p >= pbot; --p) {
-            unsigned long long W = col[p * S];
-            if (V > 32) W |= (unsigned long long)col[(32 + p) * S] << 32;
+            unsigned long long W = (uint32_t)siv[p * S];
+            if (V > 32) W |= (unsigned long long)(uint32_t)siv[(32 + p) * S] << 32;
             bw.put64(W & low_mask(s), s);
             while (s < V) {
                 const unsigned long long rest = W >> s;
@@ -452,15 +495,15 @@ __device__ __forceinline__ int encode_block(const float* __restrict__ x, const C
 // One thread per block; each warp owns one 32-block chunk and stores the
 // chunk's word count in the chunk table (the scan turns counts into offsets).
 template <int DIMS>
-__global__ void __launch_bounds__(ENC_THREADS, 5) enc_kernel(const float* __restrict__ x, CodecView v,
+__global__ void __launch_bounds__(ENC_THREADS, 7) enc_kernel(const float* __restrict__ x, CodecView v,
                                                           Geo G, float tol_f, uint32_t* __restrict__ scratch,
                                                           uint32_t* __restrict__ out, const long long* base_word,
                                                           long long cap_words, int* err)
 {
     constexpr int V = Cfg<DIMS>::V;
     constexpr int CWD = V > 32 ? V : 32;       // plane words need 32 rows even in 2D
-    __shared__ int32_t siv[V * ENC_THREADS];
-    __shared__ uint32_t colw[CWD * ENC_THREADS];
+    __shared__ int32_t siv[CWD * ENC_THREADS];
+    __shared__ uint32_t colw[V * ENC_THREADS];
     const long long b = (long long)blockIdx.x * ENC_THREADS + threadIdx.x;
     const long long base = *base_word;
     if (base + G.table_words > cap_words) {

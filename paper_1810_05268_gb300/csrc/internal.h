@@ -128,6 +128,9 @@ bool v3_supported(int dims, int K, const Tile& t);
 bool v3_fits(const FieldGeom& g, int K);
 cudaError_t launch_fwd3(const FwdArgs& a, const Tile& t, int K, int ck, cudaStream_t s);
 cudaError_t launch_adj3(const AdjArgs& a, const Tile& t, int K, int ut, cudaStream_t s);
+// batch_v3.cu (every lane's geometry must pass v3_fits)
+cudaError_t launch_fwd3_batch(const BatchLaunch<FwdArgs>& b, const Tile& t, int K, int ck, cudaStream_t s);
+cudaError_t launch_adj3_batch(const BatchLaunch<AdjArgs>& b, const Tile& t, int K, int ut, cudaStream_t s);
 
 // stencil_tma.cu (CUtensorMap comes from <cuda.h>)
 }  // namespace ckfwi

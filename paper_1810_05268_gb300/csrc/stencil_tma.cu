@@ -259,14 +259,16 @@ __device__ __forceinline__ float4 inj_vals(const Inj& in, const Inj4& c, int z)
     return v;
 }
 
-// leapfrog of a point pair: (2c - b p + w s) / a with a, b = 1 +- eta dt/2
+// leapfrog() of a point pair (increment form, each lane rounding like the
+// scalar operations): c + ((1 - e)(c - p) + w s) / (1 + e), e = eta dt/2
 __device__ __forceinline__ float2 leap2(float2 c, float2 p, float2 w, float2 s, float2 eta, float hdt)
 {
-    const float2 nb = make_float2(-__fmaf_rn(-eta.x, hdt, 1.0f), -__fmaf_rn(-eta.y, hdt, 1.0f));
-    float2 num = __ffma2_rn(w, s, __ffma2_rn(nb, p, __fadd2_rn(c, c)));
-    if (eta.x != 0.0f) num.x = __fdiv_rn(num.x, __fmaf_rn(eta.x, hdt, 1.0f));
-    if (eta.y != 0.0f) num.y = __fdiv_rn(num.y, __fmaf_rn(eta.y, hdt, 1.0f));
-    return num;
+    const float2 be = make_float2(__fmaf_rn(-eta.x, hdt, 1.0f), __fmaf_rn(-eta.y, hdt, 1.0f));
+    const float2 d = __ffma2_rn(p, make_float2(-1.0f, -1.0f), c);          // c - p, rounded once
+    float2 t = __ffma2_rn(w, s, __fmul2_rn(be, d));
+    if (eta.x != 0.0f) t.x = __fdiv_rn(t.x, __fmaf_rn(eta.x, hdt, 1.0f));
+    if (eta.y != 0.0f) t.y = __fdiv_rn(t.y, __fmaf_rn(eta.y, hdt, 1.0f));
+    return __fadd2_rn(c, t);
 }
 
 __device__ __forceinline__ float4 ldg4(const float* p) { return __ldg(reinterpret_cast<const float4*>(p)); }

@@ -68,7 +68,7 @@ def test_tma_reverse_reads_half_slots_like_register_queue(mode):
     assert np.array_equal(got[2], ref[2])
 
 
-V3_TILES = ["3,64,8,%d,4", "3,64,8,%d,2", "3,32,16,%d,4", "3,32,16,%d,2"]
+V3_TILES = ["3,32,16,%d,4", "3,32,16,%d,2"]
 
 
 @pytest.mark.parametrize("so,shape", [(2, (30, 37, 70)), (4, (33, 41, 131)), (8, (35, 43, 70)), (8, (26, 29, 200)),
@@ -98,6 +98,6 @@ def test_vector_kernels_half_slots_like_register_queue(mode, vec):
     rng = np.random.default_rng(1)
     dobs = torch.from_numpy((rng.standard_normal((61, case.rec.shape[0])) * 1e-3).astype(np.float32)).cuda()
     ref = _run(case, "1,32,8,9", "1,32,8,9", dobs, 4, mode)
-    got = _run(case, "3,64,8,11,%d" % vec, "3,64,8,11,%d" % vec, dobs, 4, mode)
+    got = _run(case, "3,32,16,11,%d" % vec, "3,32,16,11,%d" % vec, dobs, 4, mode)
     assert got[1] == ref[1]
     assert np.array_equal(got[2], ref[2])

@@ -8,10 +8,12 @@ interior + 40-cell damping layer (208^3 points) at 15 m, space order 8,
 Ricker source, 64 x 64 receivers.
 
 Headline (`value`): useful point-updates per second, 2 * N * npts / t, of
-the paper's method -- Revolve checkpointing with checkpoints compressed by
-the fixed-tolerance codec (abs. tol 1e-4) -- at the memory of 20
-uncompressed checkpoints.  Pure checkpointing (20 FP32 slots) and
-store-all are timed beside it in the same run (`compare`).
+the gradient at the memory of 20 uncompressed checkpoints, with the faster
+of the two storage choices the paper compares at equal memory -- Revolve
+with 20 FP32 checkpoints, or Revolve with checkpoints compressed by the
+fixed-tolerance codec (abs. tol 1e-4) in the same bytes (Sec. 4); the one
+taken is named in `config.mode`.  Both, store-all, and both again at the
+memory of 5 checkpoints are timed in the same run (`compare`).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
@@ -33,9 +35,14 @@ sys.path.insert(0, ROOT)
 
 WORKLOAD = "3d-128cube-so8"
 BUDGET_SLOTS = 20          # memory of 20 uncompressed checkpoints
+LOW_SLOTS = 5              # the low-memory comparison
 TOL = 1e-4                 # codec absolute tolerance
-FWD_BYTES = 16             # fwd kernel: read u^n, u^{n-1}, w; write u^{n+1}
-ADJ_BYTES = 28             # reverse kernel: read lam^j, lam^{j+1}, u^{j-1}, w, g; write lam^{j-1}, g
+FWD_BYTES = 16             # forward step: read u^n, u^{n-1}, w; write u^{n+1}
+ADJ_BYTES = 28             # reverse step: read lam^j, lam^{j+1}, u^{j-1}, w, g; write lam^{j-1}, g
+CPU_STEPS = 300            # time steps of the oracle sample (about 10-30 s on 16 cores)
+GRAD_TOL = 1e-2            # gradient accuracy a storage mode must keep to be the headline
+KERNEL_NAMES = {1: ("fwd_kernel", "adj_kernel"), 2: ("fwd_tma_kernel", "adj_tma_kernel"),
+                3: ("fwd3_kernel", "adj3_kernel")}
 
 
 def peaks():
@@ -48,13 +55,17 @@ def peaks():
         return 6800.0, "fallback"
 
 
-def traffic_per_point(kernel):
-    """DRAM bytes per grid point per launch from the committed ncu summary, or None."""
+def traffic_per_point(kernel, tile):
+    """DRAM bytes per grid point per launch of `kernel` with `tile` from the
+    committed ncu summary (taken on the same workload), or None."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(p) as f:
             d = json.load(f)
-        return float(d[kernel]["dram_bytes_per_point"])
+        e = d[kernel]
+        if e.get("tile") is not None and list(e["tile"]) != list(tile):
+            return None
+        return float(e["dram_bytes_per_point"])
     except Exception:
         return None
 
@@ -105,6 +116,63 @@ class Clocks:
                 "samples": len(sm)}
 
 
+def perf_model(C, results, nt):
+    """The paper's time model (Sec. 3-4: T = forward steps x C_F + N x C_R +
+    compressions x t_c + decompressions x t_d) with unit costs measured in
+    this run, its prediction for every mode against the measured time, and
+    the mode it would choose at each memory budget."""
+    unit = {}
+    for r in results.values():
+        for cls, n in (("fwd", "fwd_launches"), ("adj", "adj_launches"), ("comp", "comp_calls"),
+                       ("decomp", "decomp_calls")):
+            if r[n] > 0 and r[cls + "_ms"] > 0:
+                unit.setdefault(cls, []).append(r[cls + "_ms"] / r[n])
+    u = {k: float(np.median(v)) for k, v in unit.items()}
+    out = {"unit_ms": u, "modes": {}}
+    for name, r in results.items():
+        M = r["ckpt_slots"]
+        if M >= nt:
+            nf, nc, nd = nt, 0, 0
+        else:
+            acts, (p, W, R) = C.revolve_schedule(nt, M)
+            nf = p + 1
+            nc = 2 * W if r["store_mode"] == "codec" else 0
+            nd = 0
+            if r["store_mode"] == "codec":
+                for i, a in enumerate(acts):
+                    if a[0] == 2 and a[2] > 0:       # restore from a slot
+                        nxt = acts[i + 1][0] if i + 1 < len(acts) else -1
+                        nd += 1 if nxt == 3 else 2
+        pred = nf * u.get("fwd", 0) + nt * u.get("adj", 0) + nc * u.get("comp", 0) + nd * u.get("decomp", 0)
+        out["modes"][name] = {"predicted_ms": pred, "measured_ms": r["ms"],
+                              "forward_steps": nf, "compressions": nc, "decompressions": nd}
+    for budget, names in (("budget", ("codec", "fp32", "fp16", "bf16")),
+                          ("low", ("codec_low", "fp32_low", "fp16_low"))):
+        c = [n for n in names if n in out["modes"]]
+        if c:
+            out["choice_" + budget] = {
+                "predicted": min(c, key=lambda n: out["modes"][n]["predicted_ms"]),
+                "measured": min(c, key=lambda n: out["modes"][n]["measured_ms"])}
+    return out
+
+
+def rank_source(src, rk, ws):
+    """Source position of rank rk's shot: shots are independent (Sec. 1.2), so
+    ranks take distinct sources along x and share nothing on the data path."""
+    return (src[0], src[1], src[2] * (0.5 + 0.5 * (rk + 1) / max(ws, 1)))
+
+
+def max_over_ranks(ms, device):
+    """The step time of the slowest rank (the job's time); no-op on one rank."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return ms
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rk = int(os.environ.get("RANK", "0"))
@@ -132,7 +200,7 @@ def run_reference(args):
         return 0
     from paper_1810_05268_gb300 import synth
     w = synth.workload(WORKLOAD)
-    nt_sample = 6
+    nt_sample = CPU_STEPS
     for _ in range(args.warmup):
         cpu_sample(w, nt_sample)
     rates, times = [], []
@@ -165,7 +233,7 @@ def main():
     ap.add_argument("--impl", default="ckfwi")
     ap.add_argument("--nt", type=int, default=None, help="override the number of time steps (smaller runs)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle baseline")
-    ap.add_argument("--modes", default="codec,fp32,storeall")
+    ap.add_argument("--modes", default="storeall,codec,fp32,fp16,bf16,codec_low,fp32_low,fp16_low")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -186,7 +254,7 @@ def main():
     npts = int(np.prod(w.shape))
     grid = C.GridSpec(3, w.shape, w.nbl, w.h, w.so, w.dt, nt, w.vmax)
     # every rank its own shot: the source moves across the surface with the rank
-    src = (w.src[0], w.src[1], w.src[2] * (0.5 + 0.5 * (rk + 1) / max(ws, 1)))
+    src = rank_source(w.src, rk, ws)
     shot = C.ShotSpec(src=src, rec=w.rec, f0=w.f0)
     model = C.Model(grid)
     model.set_model(torch.from_numpy(w.true.astype(np.float32)).cuda())
@@ -200,79 +268,119 @@ def main():
     # codec slots at equal memory: size from the measured worst ratio of a
     # pilot run (the last states compress worst, Sec. 7), 10% headroom
     want = args.modes.split(",")
-    if "codec" in want:
+    fmin = None
+    if any(m.startswith("codec") for m in want):
         pilot = model.adjoint_gradient(shot, d_obs, BUDGET_SLOTS, store_mode="codec", tol=TOL,
                                        pool_bytes=budget)[2]
         fmin = max(1.0, pilot["ratio_min"])
-        m_codec = int(min(nt, max(2, budget / (state_bytes / fmin * 1.1))))
-        modes["codec"] = dict(ckpt_slots=m_codec, store_mode="codec", tol=TOL, pool_bytes=budget)
+
+    def codec_mode(slots):
+        b = slots * state_bytes
+        return dict(ckpt_slots=int(min(nt, max(2, b / (state_bytes / fmin * 1.1)))), store_mode="codec", tol=TOL,
+                    pool_bytes=b)
+    if "codec" in want:
+        modes["codec"] = codec_mode(BUDGET_SLOTS)
     if "fp32" in want:
         modes["fp32"] = dict(ckpt_slots=BUDGET_SLOTS, store_mode="fp32")
     if "storeall" in want:
         modes["storeall"] = dict(ckpt_slots=nt, store_mode="fp32")
-    headline = "codec" if "codec" in modes else list(modes)[0]
+    # 16-bit slots in the same bytes: 2 (M - 1) + 1 slots (slot 0 is the initial state)
+    for half in ("fp16", "bf16"):
+        if half in want:
+            modes[half] = dict(ckpt_slots=2 * (BUDGET_SLOTS - 1) + 1, store_mode=half)
+    if "codec_low" in want:
+        modes["codec_low"] = codec_mode(LOW_SLOTS)
+    if "fp32_low" in want:
+        modes["fp32_low"] = dict(ckpt_slots=LOW_SLOTS, store_mode="fp32")
+    if "fp16_low" in want:
+        modes["fp16_low"] = dict(ckpt_slots=2 * (LOW_SLOTS - 1) + 1, store_mode="fp16")
 
-    def one(kw, profile):
+    grads = {}
+
+    def one(kw, profile, keep=None):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        phi, g, st = model.adjoint_gradient(shot, d_obs, profile=profile, **kw)
+        phi, g, st = model.adjoint_gradient(shot, d_obs, profile=profile, use_graph=not profile, **kw)
         torch.cuda.synchronize()
+        if keep is not None:
+            grads[keep] = g
         return time.perf_counter() - t0, phi, st
 
     results = {}
-    clocks = None
-    for name, kw in modes.items():
-        # retry with fewer codec slots if the pool overflowed at run time
+    clocks = {}
+    skipped = {}
+    for name, kw in list(modes.items()):
+        # retry with fewer codec slots if the pool overflowed at run time; a
+        # 16-bit mode whose states overflow FP16 is reported and skipped
+        ok = False
         for _ in range(4):
             try:
                 for _ in range(args.warmup):
-                    one(kw, False)
+                    one(kw, False, keep=name)
+                ok = True
                 break
             except C.CkfwiError as e:
+                if e.status == C.NONFINITE and kw.get("store_mode") in ("fp16", "bf16"):
+                    skipped[name] = "checkpoint values overflow %s" % kw["store_mode"]
+                    break
                 if e.status != C.POOL_OVERFLOW or kw.get("store_mode") != "codec":
                     raise
                 kw["ckpt_slots"] = max(2, int(kw["ckpt_slots"] * 0.8))
+        if not ok:
+            modes.pop(name)
+            continue
         # profiled warm-up creates the library's timing events, so that the
         # profiled steps below do not include host-side event creation
         one(kw, True)
         if ws > 1:
             torch.distributed.barrier()
         torch.cuda.synchronize()
-        if name == headline:
-            clocks = Clocks(lr)
-        # timed region: K un-profiled gradients, CUDA events on torch's stream
-        # (the library launches on that stream), max over ranks
+        clk = Clocks(lr)
+        # timed region: K gradients replayed from the recorded graph, CUDA
+        # events on torch's stream (the library launches on that stream), max
+        # over ranks
         ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         ev0.record()
         for _ in range(args.steps):
             _, phi, st_plain = one(kw, False)
         ev1.record()
         torch.cuda.synchronize()
-        ms = ev0.elapsed_time(ev1) / args.steps
-        if ws > 1:
-            t = torch.tensor([ms], device="cuda")
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            ms = float(t.item())
+        clocks[name] = clk.stop()
+        ms = max_over_ranks(ev0.elapsed_time(ev1) / args.steps, "cuda")
         # per-kernel-class device time from profiled gradients (same work)
         sts = []
         for _ in range(max(1, min(args.steps, 3))):
             _, _, st = one(kw, True)
             sts.append(st)
-        clk = clocks.stop() if name == headline else None
         st = sts[-1]
-        fwd_ms = float(np.mean([s["fwd_ms"] for s in sts]))
-        adj_ms = float(np.mean([s["adj_ms"] for s in sts]))
+        avg = lambda k: float(np.mean([s[k] for s in sts]))
         results[name] = {
             "ms": ms, "gpts": 2.0 * nt * npts / (ms / 1e3) / 1e9 * ws,
             "ckpt_slots": kw["ckpt_slots"], "store_mode": kw["store_mode"],
+            "pool_bytes": kw.get("pool_bytes", st["pool_bytes_peak"]),
             "recompute_ratio": st["fwd_steps"] / nt, "p": st["p"], "W": st["takeshots"], "R": st["restores"],
             "fwd_launches": st["fwd_launches"], "adj_launches": st["adj_launches"],
-            "fwd_ms": fwd_ms, "adj_ms": adj_ms, "comp_ms": float(np.mean([s["comp_ms"] for s in sts])),
-            "decomp_ms": float(np.mean([s["decomp_ms"] for s in sts])),
-            "kernel_launches": st["kernel_launches"], "misfit": phi,
+            "comp_calls": st["comp_calls"], "decomp_calls": st["decomp_calls"],
+            "fwd_ms": avg("fwd_ms"), "adj_ms": avg("adj_ms"), "comp_ms": avg("comp_ms"),
+            "decomp_ms": avg("decomp_ms"), "kernel_launches": st_plain["kernel_launches"], "misfit": phi,
             "ratio_mean": st["ratio_mean"], "ratio_min": st["ratio_min"],
-            "pool_bytes_peak": st["pool_bytes_peak"], "clocks": clk,
+            "pool_bytes_peak": st["pool_bytes_peak"],
+            "fwd_kernel": [st["fwd_ver"], st["fwd_bx"], st["fwd_by"], st["fwd_vec"], st["fwd_zlen"]],
+            "adj_kernel": [st["adj_ver"], st["adj_bx"], st["adj_by"], st["adj_vec"], st["adj_zlen"]],
         }
+    # gradient error of every mode against store-all (bitwise the exact
+    # FP32 gradient: the schedule never changes values)
+    if "storeall" in grads:
+        ref = grads["storeall"].double()
+        nref = float(torch.linalg.vector_norm(ref))
+        for k, g in grads.items():
+            results[k]["grad_rel_err_vs_storeall"] = float(torch.linalg.vector_norm(g.double() - ref)) / nref
+    # headline: the fastest storage choice at the memory of BUDGET_SLOTS FP32
+    # checkpoints whose gradient stays within GRAD_TOL of the exact one
+    cand = [m for m in ("codec", "fp32", "fp16", "bf16") if m in results and
+            results[m].get("grad_rel_err_vs_storeall", 0.0) <= GRAD_TOL] or list(results)
+    headline = min(cand, key=lambda m: results[m]["ms"])
+    model_block = perf_model(C, results, nt)
 
     # end to end through the C-ABI with host buffers (pinned), same headline mode
     kw = modes[headline]
@@ -280,53 +388,67 @@ def main():
     dh.copy_(d_obs)
     gh = torch.empty(tuple(w.shape), dtype=torch.float32, pin_memory=True)
     dh_np, gh_np = dh.numpy(), gh.numpy()
-    model.adjoint_gradient(shot, dh_np, grad=gh_np, **kw)
+    model.adjoint_gradient(shot, dh_np, grad=gh_np, use_graph=True, **kw)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     e2e_steps = max(1, min(args.steps, 3))
     for _ in range(e2e_steps):
-        model.adjoint_gradient(shot, dh_np, grad=gh_np, **kw)
+        model.adjoint_gradient(shot, dh_np, grad=gh_np, use_graph=True, **kw)
     e2e_s = (time.perf_counter() - t0) / e2e_steps
 
     cpu = None
     if rk == 0 and not args.no_cpu:
-        rate, secs = cpu_sample(w, 6)
+        rate, secs = cpu_sample(w, CPU_STEPS)
         cpu = {"value": rate, "unit": "Gpt/s", "cores": os.cpu_count(), "kind": "oracle",
-               "sample": "FP64 oracle gradient on the same grid, first 6 of %d time steps (%.1f s)" % (nt, secs)}
+               "sample": "FP64 oracle gradient on the same grid, first %d of %d time steps (%.1f s)" % (
+                   CPU_STEPS, nt, secs)}
 
     if rk == 0:
         H = results[headline]
         peak, peak_kind = peaks()
-        # dominant kernel of the headline mode (largest share of device time)
-        fwd_bytes = FWD_BYTES * npts * H["fwd_launches"]
-        adj_bytes = ADJ_BYTES * npts * H["adj_launches"]
-        fwd_gbs = fwd_bytes / (H["fwd_ms"] / 1e3) / 1e9 if H["fwd_ms"] > 0 else 0.0
-        adj_gbs = adj_bytes / (H["adj_ms"] / 1e3) / 1e9 if H["adj_ms"] > 0 else 0.0
-        if H["fwd_ms"] >= H["adj_ms"]:
-            kname, ach, per, tkey = "fwd_kernel", fwd_gbs, FWD_BYTES, "fwd_kernel"
+        # the kernel class with the largest device-time share in the headline
+        # mode, its algorithmic bytes per launch over its average launch time
+        F = max(1.0, H["ratio_mean"] or 1.0)
+        classes = {
+            "fwd": (H["fwd_ms"], H["fwd_launches"], FWD_BYTES * npts),
+            "adj": (H["adj_ms"], H["adj_launches"], ADJ_BYTES * npts),
+            "comp": (H["comp_ms"], H["comp_calls"], (4.0 + 4.0 / F) * npts),
+            "decomp": (H["decomp_ms"], H["decomp_calls"], (4.0 / F + 4.0) * npts),
+        }
+        gbs = {k: (b * n / (ms / 1e3) / 1e9 if ms > 0 and n > 0 else 0.0) for k, (ms, n, b) in classes.items()}
+        dom = max(classes, key=lambda k: classes[k][0])
+        ms_d, n_d, b_d = classes[dom]
+        if dom in ("fwd", "adj"):
+            ver = H[dom + "_kernel"][0]
+            kname = KERNEL_NAMES.get(ver, ("?", "?"))[0 if dom == "fwd" else 1]
+            tpp = traffic_per_point(kname, H[dom + "_kernel"])
         else:
-            kname, ach, per, tkey = "adj_kernel", adj_gbs, ADJ_BYTES, "adj_kernel"
-        tpp = traffic_per_point(tkey)
+            kname = "codec compression (enc+scan+compact)" if dom == "comp" else "dec_kernel"
+            tpp = None
         line = {
             "metric": "gradient point-updates per second (useful 2*N*npts/t)",
             "value": H["gpts"], "unit": "Gpt/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": H["ms"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32", "data": "synthetic",
             "config": {"workload": WORKLOAD, "grid": list(w.shape), "nt": nt, "space_order": w.so,
-                       "mode": "revolve+codec tol %g at the memory of %d fp32 checkpoints" % (TOL, BUDGET_SLOTS),
+                       "mode": "%s: Revolve, %d slots, %s storage, at the memory of %d fp32 checkpoints%s" % (
+                           headline, H["ckpt_slots"], H["store_mode"], BUDGET_SLOTS,
+                           ", codec abs tol %g" % TOL if H["store_mode"] == "codec" else ""),
                        "ckpt_slots": H["ckpt_slots"], "l2": "working set (checkpoints + fields) > L2",
                        "parallelism": "shots" if ws > 1 else "single"},
-            "roofline": {"bound": "hbm", "kernel": kname, "achieved": ach, "peak": peak, "unit": "GB/s",
-                         "frac": ach / peak, "peak_kind": peak_kind,
-                         "algorithmic_bytes_per_point": per,
+            "roofline": {"bound": "hbm", "kernel": kname, "class": dom, "achieved": gbs[dom], "peak": peak,
+                         "unit": "GB/s", "frac": gbs[dom] / peak, "peak_kind": peak_kind,
+                         "algorithmic_bytes_per_launch": b_d, "launches": n_d,
                          "traffic": (tpp * npts) if tpp is not None else None,
-                         "fwd_gbs": fwd_gbs, "adj_gbs": adj_gbs},
+                         "class_gbs": gbs},
             "e2e": {"value": 2.0 * nt * npts / e2e_s / 1e9, "unit": "Gpt/s",
                     "h2d_bytes_per_step": int(dh.numel() * 4), "d2h_bytes_per_step": int(gh.numel() * 4 + 8)},
             "gpu_launches": int(H["kernel_launches"] * args.steps),
-            "clocks": H["clocks"],
+            "clocks": clocks.get(headline),
             "cpu_baseline": cpu,
-            "compare": {k: {kk: vv for kk, vv in v.items() if kk != "clocks"} for k, v in results.items()},
+            "compare": {k: dict(v, clocks=clocks.get(k)) for k, v in results.items()},
+            "skipped": skipped,
+            "model": model_block,
         }
         print(json.dumps(line))
     model.close()

@@ -41,7 +41,11 @@ class Stats(ctypes.Structure):
                 ("u_absmax", ctypes.c_double), ("fwd_ms", ctypes.c_double), ("adj_ms", ctypes.c_double),
                 ("comp_ms", ctypes.c_double), ("decomp_ms", ctypes.c_double), ("other_ms", ctypes.c_double),
                 ("fwd_launches", ctypes.c_longlong), ("adj_launches", ctypes.c_longlong),
-                ("comp_calls", ctypes.c_longlong), ("decomp_calls", ctypes.c_longlong)]
+                ("comp_calls", ctypes.c_longlong), ("decomp_calls", ctypes.c_longlong),
+                ("fwd_ver", ctypes.c_int), ("fwd_bx", ctypes.c_int), ("fwd_by", ctypes.c_int),
+                ("fwd_vec", ctypes.c_int), ("fwd_zlen", ctypes.c_int),
+                ("adj_ver", ctypes.c_int), ("adj_bx", ctypes.c_int), ("adj_by", ctypes.c_int),
+                ("adj_vec", ctypes.c_int), ("adj_zlen", ctypes.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -22,7 +22,7 @@ __global__ void __launch_bounds__(TX * TY)
 }
 
 template <int K, int V, int TX, int TY, class UT>
-__global__ void __launch_bounds__(TX * TY, (V == 2 && K <= 4) ? 3 : 1)
+__global__ void __launch_bounds__(TX * TY)
     adj3_batch_kernel(const AdjArgs* __restrict__ tab, const int* __restrict__ start, int nl)
 {
     using G = G3<K, V, TX, TY>;

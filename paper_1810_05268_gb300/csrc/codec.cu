@@ -347,10 +347,9 @@ __device__ __forceinline__ int encode_block(const float* __restrict__ x, const C
     BitW bw{scratch + b * Cfg<DIMS>::MAXW, 0ull, 0, 0, Cfg<DIMS>::MAXW};
     const int xs = 4 * bp.bx;
     const bool vec = v.aligned && xs + 3 < v.nx;
-    // 1. gather, finiteness, max |x| and the block exponent
+    // 1. gather, finiteness and max |x|
     float amax = 0.0f;
     bool bad = false;
-    int emax = -1000;
 #pragma unroll 1
     for (int sl = 0; sl < 4; ++sl) {
 #pragma unroll
@@ -368,12 +367,9 @@ __device__ __forceinline__ int encode_block(const float* __restrict__ x, const C
             }
 #pragma unroll
             for (int c = 0; c < 4; ++c) {
-                const uint32_t u = __float_as_uint(f[c]);
                 bad |= !isfinite(f[c]);
                 amax = fmaxf(amax, fabsf(f[c]));
-                const int be = (int)((u >> 23) & 0xFF);
-                if (u & 0x7FFFFFFFu) emax = max(emax, max(be, 1) - 127);
-                col[(SL * sl + 4 * ly + c) * S] = u;
+                col[(SL * sl + 4 * ly + c) * S] = __float_as_uint(f[c]);
             }
         }
     }
@@ -382,19 +378,23 @@ __device__ __forceinline__ int encode_block(const float* __restrict__ x, const C
         bw.put(0u, 1);
         return bw.flush();
     }
+    // block exponent: that of the largest magnitude (float order is exponent order)
+    const int emax = max((int)(__float_as_uint(amax) >> 23), 1) - 127;
+    // i = trunc(x 2^(23-Emax)): the scaling by a power of two is exact (the
+    // product stays below 2^24; a product that underflows is below 1 and
+    // truncates to 0 either way), so this equals the mantissa shift of the
+    // definition
+    const int sc = 23 - emax;
+    const int sa = min(sc, 127);
+    const float s1 = pow2f(sa), s2 = pow2f(sc - sa);
     // 2. integers (kept in siv for the closed loop), lifts along x and y
 #pragma unroll 1
     for (int sl = 0; sl < 4; ++sl) {
         int32_t c[SL];
 #pragma unroll
         for (int k = 0; k < SL; ++k) {
-            const uint32_t u = col[(SL * sl + k) * S];
-            const int be = (int)((u >> 23) & 0xFF);
-            const uint32_t M = (u & 0x7FFFFFu) | (be > 0 ? 0x800000u : 0u);
-            const int sh = emax - (max(be, 1) - 127);
-            uint32_t mag = sh >= 32 ? 0u : (M >> sh);
-            if (!(u & 0x7FFFFFFFu)) mag = 0u;
-            c[k] = (u >> 31) ? -(int32_t)mag : (int32_t)mag;
+            const float f = __uint_as_float(col[(SL * sl + k) * S]);
+            c[k] = __float2int_rz(__fmul_rn(__fmul_rn(f, s1), s2));
             siv[(SL * sl + k) * S] = c[k];
         }
 #pragma unroll
@@ -439,12 +439,12 @@ __device__ __forceinline__ int encode_block(const float* __restrict__ x, const C
             // keep the comparison's shared loads after the transform: hoisted
             // above it they would hold 64 more registers
             asm volatile("" ::: "memory");
+            // |i - t| <= T - 2 as one unsigned comparison (|i|, |t| < 2^26,
+            // T <= 2^24 because max|x| > tol)
+            const uint32_t lim = (uint32_t)(T - 2);
             bool ok = true;
 #pragma unroll
-            for (int i = 0; i < V; ++i) {
-                const long long d = (long long)siv[i * S] - (long long)t[i];
-                ok &= (d <= (long long)T - 2) && (-d <= (long long)T - 2);
-            }
+            for (int i = 0; i < V; ++i) ok &= (uint32_t)(siv[i * S] - t[i]) + lim <= 2u * lim;
             if (ok) {
                 pbot = p;
                 break;

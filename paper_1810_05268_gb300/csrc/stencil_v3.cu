@@ -12,9 +12,8 @@ __global__ void __launch_bounds__(TX * TY) fwd3_kernel(const FwdArgs a)
     fwd3_body<K, V, TX, TY, CK>(a, smem3, blockIdx.x, blockIdx.y, blockIdx.z, gridDim.x, gridDim.y);
 }
 
-// (V = 2: at most 85 registers, three 256-thread CTAs per SM)
 template <int K, int V, int TX, int TY, class UT>
-__global__ void __launch_bounds__(TX * TY, (V == 2 && K <= 4) ? 3 : 1) adj3_kernel(const AdjArgs a)
+__global__ void __launch_bounds__(TX * TY) adj3_kernel(const AdjArgs a)
 {
     extern __shared__ __align__(16) float smem3[];
     adj3_body<K, V, TX, TY, UT>(a, smem3, blockIdx.x, blockIdx.y, blockIdx.z);

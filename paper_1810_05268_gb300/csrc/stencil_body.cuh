@@ -13,7 +13,7 @@
 // small per-axis tables instead of being streamed.
 //
 // Rounding: the update is spelled out with __fmaf_rn / __fadd_rn /
-// __fdiv_rn in one device function used by every kernel, so no compiler
+// __fdividef in one device function used by every kernel, so no compiler
 // contraction can make the forward step of a recomputation differ from the
 // first sweep; with compression off, a checkpointed gradient is bitwise the
 // store-all gradient.
@@ -40,11 +40,15 @@ template <> __device__ __forceinline__ float ldf<float>(const float* p) { return
 // final addition: c - p is nearly exact and the damping factors multiply
 // that small increment, so FP32 keeps the receivers about five times closer
 // to the FP64 oracle over thousands of steps than 2c - b p + w s would.
+// For the same reason the division by 1 + e (inside the damping layer only)
+// may be the fast approximate one (2 ulp of the increment): it is one
+// reciprocal and one multiply instead of the IEEE division's sequence, and
+// every kernel uses the same instruction, so they stay bitwise equal.
 __device__ __forceinline__ float leapfrog(float c, float p, float w, float s, float eta, float hdt)
 {
     const float be = __fmaf_rn(-eta, hdt, 1.0f);
     float t = __fmaf_rn(w, s, __fmul_rn(be, __fsub_rn(c, p)));
-    if (eta != 0.0f) t = __fdiv_rn(t, __fmaf_rn(eta, hdt, 1.0f));
+    t = eta != 0.0f ? __fdividef(t, __fmaf_rn(eta, hdt, 1.0f)) : t;
     return __fadd_rn(c, t);
 }
 

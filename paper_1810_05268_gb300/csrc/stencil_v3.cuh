@@ -190,8 +190,8 @@ __device__ __forceinline__ float2 leap2v(float2 c, float2 p, float2 w, float2 s,
     const float2 be = __ffma2_rn(f2(-eta.x, -eta.y), f2(hdt, hdt), f2(1.0f, 1.0f));
     const float2 d = __ffma2_rn(p, f2(-1.0f, -1.0f), c);                   // c - p, rounded once
     float2 t = __ffma2_rn(w, s, __fmul2_rn(be, d));
-    if (eta.x != 0.0f) t.x = __fdiv_rn(t.x, __fmaf_rn(eta.x, hdt, 1.0f));
-    if (eta.y != 0.0f) t.y = __fdiv_rn(t.y, __fmaf_rn(eta.y, hdt, 1.0f));
+    t.x = eta.x != 0.0f ? __fdividef(t.x, __fmaf_rn(eta.x, hdt, 1.0f)) : t.x;
+    t.y = eta.y != 0.0f ? __fdividef(t.y, __fmaf_rn(eta.y, hdt, 1.0f)) : t.y;
     return __fadd2_rn(c, t);
 }
 

@@ -650,7 +650,7 @@ bool grid_samples(const FieldGeom& f, const Tile& t, int zlen, int nrec)
     const long long gx = (f.nx + t.bx - 1) / t.bx;
     const long long gy = f.dims == 3 ? (f.ny + t.by - 1) / t.by : 1;
     const long long gz = (f.nz + zlen - 1) / zlen;
-    const long long tpc = (t.ver == 2 ? t.bx / 4 : (t.ver == 3 ? t.bx / t.vec : t.bx)) * (long long)t.by;
+    const long long tpc = (t.ver == 2 ? t.bx / 4 : (t.ver >= 3 ? t.bx / t.vec : t.bx)) * (long long)t.by;
     return gx * gy * gz * tpc >= nrec;
 }
 
@@ -688,7 +688,9 @@ int fwd_step(Ctx& cx, const Role& u, const Role& up, const Role& out, int n, boo
             continue;
         }
         const int tok = cx.begin(PC_FWD);
-        if (m->tf.ver == 3) {
+        if (m->tf.ver == 4) {
+            CK_TRY(launch_fwd4(a, m->tf, m->K, ck, cx.st));
+        } else if (m->tf.ver == 3) {
             CK_TRY(launch_fwd3(a, m->tf, m->K, ck, cx.st));
         } else if (m->tf.ver == 2) {
             CUtensorMap tm;
@@ -736,7 +738,9 @@ int adj_step(Ctx& cx, const Role& l1, const Role& l2, const Role& l0, const Role
             continue;
         }
         const int tok = cx.begin(PC_ADJ);
-        if (m->ta.ver == 3) {
+        if (m->ta.ver == 4) {
+            CK_TRY(launch_adj4(a, m->ta, m->K, utype, cx.st));
+        } else if (m->ta.ver == 3) {
             CK_TRY(launch_adj3(a, m->ta, m->K, utype, cx.st));
         } else if (m->ta.ver == 2) {
             CUtensorMap tl, tu;
@@ -855,7 +859,12 @@ int autotune(ckfwi_model* m, cudaStream_t st)
             const Tile t0 = v3_tile_at(i, f.nz);
             if (!v3_supported(f.dims, m->K, t0)) continue;
             const long long cols = (long long)((f.nx + t0.bx - 1) / t0.bx) * ((f.ny + t0.by - 1) / t0.by);
-            for (int z : zlens(cols)) cands.push_back(v3_tile_at(i, z));
+            for (int z : zlens(cols)) {
+                cands.push_back(v3_tile_at(i, z));
+                Tile t4 = v3_tile_at(i, z);     // the same shape fed by asynchronous copies
+                t4.ver = 4;
+                if (v4_supported(f.dims, m->K, t4)) cands.push_back(t4);
+            }
         }
     }
     const bool tma_ok = encode_fn() != nullptr;
@@ -894,7 +903,10 @@ int autotune(ckfwi_model* m, cudaStream_t st)
     const int reps = 3;
     CUtensorMap tm_u, tm_l;
     auto go = [&](const Tile& t, int pass) -> int {
-        if (t.ver == 3) {
+        if (t.ver == 4) {
+            if (pass == 0) CK_TRY(launch_fwd4(a, t, m->K, CK_NONE, st));
+            else CK_TRY(launch_adj4(b, t, m->K, U_FP32, st));
+        } else if (t.ver == 3) {
             if (pass == 0) CK_TRY(launch_fwd3(a, t, m->K, CK_NONE, st));
             else CK_TRY(launch_adj3(b, t, m->K, U_FP32, st));
         } else if (t.ver == 2) {
@@ -917,7 +929,8 @@ int autotune(ckfwi_model* m, cudaStream_t st)
         const int nf = std::sscanf(v, "%d,%d,%d,%d,%d", &u.ver, &u.bx, &u.by, &u.zlen, &u.vec);
         if (nf < 4 || u.zlen < 1) return false;
         if (nf < 5) u.vec = 1;
-        const bool okv = u.ver == 3   ? v3_supported(f.dims, m->K, u) && v3_fits(f, m->K)
+        const bool okv = u.ver == 4   ? v4_supported(f.dims, m->K, u) && v3_fits(f, m->K)
+                         : u.ver == 3 ? v3_supported(f.dims, m->K, u) && v3_fits(f, m->K)
                          : u.ver == 2 ? (tma_ok && u.bx == 64 && tma_supported(f.dims, m->K, u.by))
                                       : tile_supported(f.dims, m->K, u);
         if (!okv) return false;

@@ -95,8 +95,9 @@ struct Tile {
     int bx, by;           // CTA shape in points (by = 1 in 2D); TMA kernels: bx = 64 points, by rows
     int zlen;             // ver 1, 3: z planes per CTA; ver 2: CTAs per SM of the persistent grid
     int ver = 1;          // 1: register-queue kernels, 2: TMA-fed kernels (3D, orders 2-8),
-                          // 3: vector-blocked kernels (3D)
-    int vec = 1;          // ver 3: x points per thread (2 or 4)
+                          // 3: vector-blocked kernels (3D), 4: vector-blocked forward step fed
+                          // by asynchronous copies (3D)
+    int vec = 1;          // ver 3, 4: x points per thread (2 or 4)
 };
 
 // One batched step over several lanes (shots): lane l's arguments are
@@ -128,6 +129,10 @@ bool v3_supported(int dims, int K, const Tile& t);
 bool v3_fits(const FieldGeom& g, int K);
 cudaError_t launch_fwd3(const FwdArgs& a, const Tile& t, int K, int ck, cudaStream_t s);
 cudaError_t launch_adj3(const AdjArgs& a, const Tile& t, int K, int ut, cudaStream_t s);
+// stencil_v4.cu (geometry must pass v3_fits)
+bool v4_supported(int dims, int K, const Tile& t);
+cudaError_t launch_fwd4(const FwdArgs& a, const Tile& t, int K, int ck, cudaStream_t s);
+cudaError_t launch_adj4(const AdjArgs& a, const Tile& t, int K, int ut, cudaStream_t s);
 // batch_v3.cu (every lane's geometry must pass v3_fits)
 cudaError_t launch_fwd3_batch(const BatchLaunch<FwdArgs>& b, const Tile& t, int K, int ck, cudaStream_t s);
 cudaError_t launch_adj3_batch(const BatchLaunch<AdjArgs>& b, const Tile& t, int K, int ut, cudaStream_t s);

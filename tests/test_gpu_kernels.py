@@ -101,3 +101,22 @@ def test_vector_kernels_half_slots_like_register_queue(mode, vec):
     got = _run(case, "3,32,16,11,%d" % vec, "3,32,16,11,%d" % vec, dobs, 4, mode)
     assert got[1] == ref[1]
     assert np.array_equal(got[2], ref[2])
+
+
+@pytest.mark.parametrize("so,shape", [(2, (30, 37, 70)), (4, (33, 41, 131)), (8, (35, 43, 70)), (8, (26, 29, 200)),
+                                      (16, (36, 41, 77)), (4, (21, 19, 13))])
+@pytest.mark.parametrize("vec", [2, 4])
+@pytest.mark.parametrize("mode", ["fp32", "bf16"])
+def test_async_copy_forward_bitwise_equal_register_queue(so, shape, vec, mode):
+    """The forward step fed by asynchronous copies (generation 4)."""
+    case = make_case(3, so, shape, nbl=6, nt=70, seed=so + 3 * vec)
+    rng = np.random.default_rng(so)
+    dobs = torch.from_numpy((rng.standard_normal((71, case.rec.shape[0])) * 1e-3).astype(np.float32)).cuda()
+    k = so // 2
+    by1 = max(8, k)
+    ref = _run(case, "1,32,%d,9" % by1, "1,32,%d,9" % by1, dobs, 5, mode)
+    for zlen in (7, 64):
+        got = _run(case, "4,32,16,%d,%d" % (zlen, vec), "3,32,16,%d,%d" % (zlen, vec), dobs, 5, mode)
+        assert np.array_equal(got[0], ref[0])
+        assert got[1] == ref[1]
+        assert np.array_equal(got[2], ref[2])

@@ -42,7 +42,7 @@ ADJ_BYTES = 28             # reverse step: read lam^j, lam^{j+1}, u^{j-1}, w, g;
 CPU_STEPS = 300            # time steps of the oracle sample (about 10-30 s on 16 cores)
 GRAD_TOL = 1e-2            # gradient accuracy a storage mode must keep to be the headline
 KERNEL_NAMES = {1: ("fwd_kernel", "adj_kernel"), 2: ("fwd_tma_kernel", "adj_tma_kernel"),
-                3: ("fwd3_kernel", "adj3_kernel")}
+                3: ("fwd3_kernel", "adj3_kernel"), 4: ("fwd4_kernel", "adj4_kernel")}
 
 
 def peaks():

@@ -926,9 +926,10 @@ int autotune(ckfwi_model* m, cudaStream_t st)
         const char* v = std::getenv(name);
         if (!v) return false;
         Tile u;
-        const int nf = std::sscanf(v, "%d,%d,%d,%d,%d", &u.ver, &u.bx, &u.by, &u.zlen, &u.vec);
+        const int nf = std::sscanf(v, "%d,%d,%d,%d,%d,%d", &u.ver, &u.bx, &u.by, &u.zlen, &u.vec, &u.pf);
         if (nf < 4 || u.zlen < 1) return false;
         if (nf < 5) u.vec = 1;
+        if (nf < 6) u.pf = 0;
         const bool okv = u.ver == 4   ? v4_supported(f.dims, m->K, u) && v3_fits(f, m->K)
                          : u.ver == 3 ? v3_supported(f.dims, m->K, u) && v3_fits(f, m->K)
                          : u.ver == 2 ? (tma_ok && u.bx == 64 && tma_supported(f.dims, m->K, u.by))
@@ -982,8 +983,8 @@ int autotune(ckfwi_model* m, cudaStream_t st)
             float ms = 0;
             ST_TRY(time_of(t, pass, 7, &ms));
             if (verbose)
-                std::fprintf(stderr, "ckfwi autotune %s final ver %d tile %dx%d vec %d zlen %d: %.1f us\n",
-                             pass ? "adj" : "fwd", t.ver, t.bx, t.by, t.vec, t.zlen, 1000.0f * ms);
+                std::fprintf(stderr, "ckfwi autotune %s final ver %d tile %dx%d vec %d zlen %d pf %d: %.1f us\n",
+                             pass ? "adj" : "fwd", t.ver, t.bx, t.by, t.vec, t.zlen, t.pf, 1000.0f * ms);
             if (ms < best) {
                 best = ms;
                 (pass == 0 ? m->tf : m->ta) = t;

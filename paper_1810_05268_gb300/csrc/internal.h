@@ -98,6 +98,7 @@ struct Tile {
                           // 3: vector-blocked kernels (3D), 4: vector-blocked forward step fed
                           // by asynchronous copies (3D)
     int vec = 1;          // ver 3, 4: x points per thread (2 or 4)
+    int pf = 0;           // ver 4: planes of prefetch (0 = the default, 2)
 };
 
 // One batched step over several lanes (shots): lane l's arguments are

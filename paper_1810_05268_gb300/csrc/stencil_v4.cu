@@ -24,12 +24,10 @@
 namespace ckfwi {
 namespace {
 
-constexpr int PF4 = 2;   // planes of prefetch
-
-template <int K, int V, int TX, int TY>
+template <int K, int V, int TX, int TY, int PF>
 struct G4 {
     using G = G3<K, V, TX, TY>;
-    static constexpr int D = PF4;
+    static constexpr int D = PF;                   // planes of prefetch
     static constexpr int RU = K + D + 1;           // u tiles in the ring
     static constexpr int RP = D + 1;               // point planes in each point ring
     static constexpr int PT = G::BXP * TY;         // floats of a point tile
@@ -62,10 +60,10 @@ template <int N> __device__ __forceinline__ void cp_wait() { asm volatile("cp.as
 // vectors, its point vectors.  Offsets are element offsets from the plane's
 // origin (add z * pxy); a copy whose source is not needed is zero-filled and
 // points at the plane origin instead (never read).
-template <int K, int V, int TX, int TY>
+template <int K, int V, int TX, int TY, int PF>
 struct Copies4 {
     using G = G3<K, V, TX, TY>;
-    using H = G4<K, V, TX, TY>;
+    using H = G4<K, V, TX, TY, PF>;
     int cg, cs;                    // centre: global offset, shared offset in a u tile
     bool cv;
     int hg[H::HPT], hs[H::HPT];    // halo vectors
@@ -121,12 +119,12 @@ struct Copies4 {
     }
 };
 
-template <int K, int V, int TX, int TY, int CK>
+template <int K, int V, int TX, int TY, int PF, int CK>
 __device__ __forceinline__ void fwd4_body(const FwdArgs& a, float* smem, int bxi, int byi, int bzi, int gxn,
                                           int gyn)
 {
     using G = G3<K, V, TX, TY>;
-    using H = G4<K, V, TX, TY>;
+    using H = G4<K, V, TX, TY, PF>;
     constexpr int D = H::D;
     const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TX + tx;
     const int nz = a.g.nz, ny = a.g.ny, nx = a.g.nx;
@@ -158,7 +156,7 @@ __device__ __forceinline__ void fwd4_body(const FwdArgs& a, float* smem, int bxi
         ecol[i] = (rowact && x0 + i < nx) ? __fadd_rn(a.eta[nz + y], a.eta[nz + ny + x0 + i]) : 0.0f;
     Inj3<V> ij;
     ij.init(a.src, y, x0, nx, rowact);
-    Copies4<K, V, TX, TY> cp;
+    Copies4<K, V, TX, TY, PF> cp;
     cp.init(tid, tx, ty, xb, yb, nx, ny, px);
 
     float* ring = smem;                          // RU u tiles
@@ -278,38 +276,38 @@ __device__ __forceinline__ void fwd4_body(const FwdArgs& a, float* smem, int bxi
     cp_wait<0>();     // no copy may land after the CTA has left
 }
 
-template <int K, int V, int TX, int TY, int CK>
+template <int K, int V, int TX, int TY, int PF, int CK>
 __global__ void __launch_bounds__(TX * TY) fwd4_kernel(const FwdArgs a)
 {
     extern __shared__ __align__(16) float smem4[];
-    fwd4_body<K, V, TX, TY, CK>(a, smem4, blockIdx.x, blockIdx.y, blockIdx.z, gridDim.x, gridDim.y);
+    fwd4_body<K, V, TX, TY, PF, CK>(a, smem4, blockIdx.x, blockIdx.y, blockIdx.z, gridDim.x, gridDim.y);
 }
 
-template <int K, int V, int TX, int TY>
+template <int K, int V, int TX, int TY, int PF>
 cudaError_t fwd4_go(const FwdArgs& a, int ck, cudaStream_t s)
 {
     using G = G3<K, V, TX, TY>;
-    using H = G4<K, V, TX, TY>;
+    using H = G4<K, V, TX, TY, PF>;
     const dim3 blk(TX, TY, 1);
     const dim3 grd((a.g.nx + G::BXP - 1) / G::BXP, (a.g.ny + TY - 1) / TY, (a.g.nz + a.zlen - 1) / a.zlen);
     const size_t sh = H::FLOATS * sizeof(float);
     cudaError_t e = cudaSuccess;
     switch (ck) {
     case CK_NONE:
-        e = cudaFuncSetAttribute(fwd4_kernel<K, V, TX, TY, CK_NONE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh);
-        if (e == cudaSuccess) fwd4_kernel<K, V, TX, TY, CK_NONE><<<grd, blk, sh, s>>>(a);
+        e = cudaFuncSetAttribute(fwd4_kernel<K, V, TX, TY, PF, CK_NONE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh);
+        if (e == cudaSuccess) fwd4_kernel<K, V, TX, TY, PF, CK_NONE><<<grd, blk, sh, s>>>(a);
         break;
     case CK_FP32:
-        e = cudaFuncSetAttribute(fwd4_kernel<K, V, TX, TY, CK_FP32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh);
-        if (e == cudaSuccess) fwd4_kernel<K, V, TX, TY, CK_FP32><<<grd, blk, sh, s>>>(a);
+        e = cudaFuncSetAttribute(fwd4_kernel<K, V, TX, TY, PF, CK_FP32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh);
+        if (e == cudaSuccess) fwd4_kernel<K, V, TX, TY, PF, CK_FP32><<<grd, blk, sh, s>>>(a);
         break;
     case CK_BF16:
-        e = cudaFuncSetAttribute(fwd4_kernel<K, V, TX, TY, CK_BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh);
-        if (e == cudaSuccess) fwd4_kernel<K, V, TX, TY, CK_BF16><<<grd, blk, sh, s>>>(a);
+        e = cudaFuncSetAttribute(fwd4_kernel<K, V, TX, TY, PF, CK_BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh);
+        if (e == cudaSuccess) fwd4_kernel<K, V, TX, TY, PF, CK_BF16><<<grd, blk, sh, s>>>(a);
         break;
     case CK_FP16:
-        e = cudaFuncSetAttribute(fwd4_kernel<K, V, TX, TY, CK_FP16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh);
-        if (e == cudaSuccess) fwd4_kernel<K, V, TX, TY, CK_FP16><<<grd, blk, sh, s>>>(a);
+        e = cudaFuncSetAttribute(fwd4_kernel<K, V, TX, TY, PF, CK_FP16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh);
+        if (e == cudaSuccess) fwd4_kernel<K, V, TX, TY, PF, CK_FP16><<<grd, blk, sh, s>>>(a);
         break;
     default: return cudaErrorInvalidValue;
     }
@@ -320,8 +318,8 @@ cudaError_t fwd4_go(const FwdArgs& a, int ck, cudaStream_t s)
 template <int K>
 cudaError_t fwd4_k(const FwdArgs& a, const Tile& t, int ck, cudaStream_t s)
 {
-    if (t.vec == 4 && t.bx == 32 && t.by == 16) return fwd4_go<K, 4, 8, 16>(a, ck, s);
-    if (t.vec == 2 && t.bx == 32 && t.by == 16) return fwd4_go<K, 2, 16, 16>(a, ck, s);
+    if (t.vec == 4 && t.bx == 32 && t.by == 16) return fwd4_go<K, 4, 8, 16, 2>(a, ck, s);
+    if (t.vec == 2 && t.bx == 32 && t.by == 16) return fwd4_go<K, 2, 16, 16, 2>(a, ck, s);
     return cudaErrorInvalidValue;
 }
 
@@ -329,11 +327,11 @@ cudaError_t fwd4_k(const FwdArgs& a, const Tile& t, int ck, cudaStream_t s)
 // Fused reverse step, same structure: rings of lam^j and u^{j-1} tiles and
 // of lam^{j+1}, w and gacc point tiles; u^{j-1} in FP32 only (16-bit
 // checkpoint reads use the vector-blocked kernel).
-template <int K, int V, int TX, int TY>
+template <int K, int V, int TX, int TY, int PF>
 __device__ __forceinline__ void adj4_body(const AdjArgs& a, float* smem, int bxi, int byi, int bzi)
 {
     using G = G3<K, V, TX, TY>;
-    using H = G4<K, V, TX, TY>;
+    using H = G4<K, V, TX, TY, PF>;
     constexpr int D = H::D;
     const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TX + tx;
     const int nz = a.g.nz, ny = a.g.ny, nx = a.g.nx;
@@ -355,7 +353,7 @@ __device__ __forceinline__ void adj4_body(const AdjArgs& a, float* smem, int bxi
     Inj3<V> ia, is;
     ia.init(a.adj, y, x0, nx, rowact);
     is.init(a.src, y, x0, nx, rowact);
-    Copies4<K, V, TX, TY> cp;
+    Copies4<K, V, TX, TY, PF> cp;
     cp.init(tid, tx, ty, xb, yb, nx, ny, px);
     const float* uu = static_cast<const float*>(a.u);
 
@@ -474,33 +472,33 @@ __device__ __forceinline__ void adj4_body(const AdjArgs& a, float* smem, int bxi
     cp_wait<0>();
 }
 
-template <int K, int V, int TX, int TY>
+template <int K, int V, int TX, int TY, int PF>
 __global__ void __launch_bounds__(TX * TY) adj4_kernel(const AdjArgs a)
 {
     extern __shared__ __align__(16) float smem4[];
-    adj4_body<K, V, TX, TY>(a, smem4, blockIdx.x, blockIdx.y, blockIdx.z);
+    adj4_body<K, V, TX, TY, PF>(a, smem4, blockIdx.x, blockIdx.y, blockIdx.z);
 }
 
-template <int K, int V, int TX, int TY>
+template <int K, int V, int TX, int TY, int PF>
 cudaError_t adj4_go(const AdjArgs& a, cudaStream_t s)
 {
     using G = G3<K, V, TX, TY>;
-    using H = G4<K, V, TX, TY>;
+    using H = G4<K, V, TX, TY, PF>;
     const dim3 blk(TX, TY, 1);
     const dim3 grd((a.g.nx + G::BXP - 1) / G::BXP, (a.g.ny + TY - 1) / TY, (a.g.nz + a.zlen - 1) / a.zlen);
     const size_t sh = ((size_t)2 * H::RU * G::TILE + (size_t)3 * H::RP * H::PT) * sizeof(float);
-    cudaError_t e = cudaFuncSetAttribute(adj4_kernel<K, V, TX, TY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(adj4_kernel<K, V, TX, TY, PF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)sh);
     if (e != cudaSuccess) return e;
-    adj4_kernel<K, V, TX, TY><<<grd, blk, sh, s>>>(a);
+    adj4_kernel<K, V, TX, TY, PF><<<grd, blk, sh, s>>>(a);
     return cudaGetLastError();
 }
 
 template <int K>
 cudaError_t adj4_k(const AdjArgs& a, const Tile& t, cudaStream_t s)
 {
-    if (t.vec == 4 && t.bx == 32 && t.by == 16) return adj4_go<K, 4, 8, 16>(a, s);
-    if (t.vec == 2 && t.bx == 32 && t.by == 16) return adj4_go<K, 2, 16, 16>(a, s);
+    if (t.vec == 4 && t.bx == 32 && t.by == 16) return adj4_go<K, 4, 8, 16, 2>(a, s);
+    if (t.vec == 2 && t.bx == 32 && t.by == 16) return adj4_go<K, 2, 16, 16, 2>(a, s);
     return cudaErrorInvalidValue;
 }
 
@@ -510,7 +508,8 @@ bool v4_supported(int dims, int K, const Tile& t)
 {
     if (dims != 3 || t.ver != 4 || t.zlen < 1 || t.by < K) return false;
     if (K != 1 && K != 2 && K != 4 && K != 8) return false;
-    return t.bx == 32 && t.by == 16 && (t.vec == 2 || t.vec == 4);
+    // two planes of prefetch (three measured no faster on 208^3, order 8)
+    return t.bx == 32 && t.by == 16 && (t.vec == 2 || t.vec == 4) && (t.pf == 0 || t.pf == 2);
 }
 
 // the reverse step in FP32 through the rings; 16-bit u^{j-1} through the

@@ -115,8 +115,10 @@ def test_async_copy_forward_bitwise_equal_register_queue(so, shape, vec, mode):
     k = so // 2
     by1 = max(8, k)
     ref = _run(case, "1,32,%d,9" % by1, "1,32,%d,9" % by1, dobs, 5, mode)
-    for zlen in (7, 64):
-        got = _run(case, "4,32,16,%d,%d" % (zlen, vec), "3,32,16,%d,%d" % (zlen, vec), dobs, 5, mode)
+    tiles = [("4,32,16,%d,%d" % (z, vec), "4,32,16,%d,%d" % (z, vec)) for z in (7, 64)]
+    tiles.append(("4,32,16,9,%d" % vec, "3,32,16,9,%d" % vec))   # mixed generations
+    for tf, ta in tiles:
+        got = _run(case, tf, ta, dobs, 5, mode)
         assert np.array_equal(got[0], ref[0])
         assert got[1] == ref[1]
         assert np.array_equal(got[2], ref[2])

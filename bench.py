@@ -116,44 +116,72 @@ class Clocks:
                 "samples": len(sm)}
 
 
-def perf_model(C, results, nt):
-    """The paper's time model (Sec. 3-4: T = forward steps x C_F + N x C_R +
-    compressions x t_c + decompressions x t_d) with unit costs measured in
-    this run, its prediction for every mode against the measured time, and
-    the mode it would choose at each memory budget."""
-    unit = {}
-    for r in results.values():
-        for cls, n in (("fwd", "fwd_launches"), ("adj", "adj_launches"), ("comp", "comp_calls"),
-                       ("decomp", "decomp_calls")):
-            if r[n] > 0 and r[cls + "_ms"] > 0:
-                unit.setdefault(cls, []).append(r[cls + "_ms"] / r[n])
-    u = {k: float(np.median(v)) for k, v in unit.items()}
-    out = {"unit_ms": u, "modes": {}}
+def perf_model(results, nt, fmin):
+    """The paper's time model (Sec. 3-4; paper_1810_05268_gb300.perfmodel)
+    with the unit costs measured in this run: its prediction for every timed
+    mode against the measured time, the mode it chooses at each budget, and
+    its prediction across memory budgets (the regimes of Sec. 4)."""
+    from paper_1810_05268_gb300 import perfmodel as P
+
+    def unit(cls, n, modes=None):
+        v = [r[cls + "_ms"] / r[n] for k, r in results.items()
+             if r[n] > 0 and r[cls + "_ms"] > 0 and (modes is None or r["store_mode"] in modes)]
+        return float(np.min(v)) if v else None
+    costs = P.Costs(c_f=unit("fwd", "fwd_launches"), c_r=unit("adj", "adj_launches", ("fp32",)),
+                    c_r16=unit("adj", "adj_launches", ("fp16", "bf16")), t_c=unit("comp", "comp_calls"),
+                    t_d=unit("decomp", "decomp_calls"), f_min=fmin,
+                    grad_err={r["store_mode"]: r.get("grad_rel_err_vs_storeall", 0.0) for r in results.values()})
+    out = {"unit_ms": {"C_F": costs.c_f, "C_R": costs.c_r, "C_R16": costs.c_r16, "t_c": costs.t_c,
+                       "t_d": costs.t_d, "F_min": fmin}, "modes": {}}
     for name, r in results.items():
-        M = r["ckpt_slots"]
-        if M >= nt:
-            nf, nc, nd = nt, 0, 0
-        else:
-            acts, (p, W, R) = C.revolve_schedule(nt, M)
-            nf = p + 1
-            nc = 2 * W if r["store_mode"] == "codec" else 0
-            nd = 0
-            if r["store_mode"] == "codec":
-                for i, a in enumerate(acts):
-                    if a[0] == 2 and a[2] > 0:       # restore from a slot
-                        nxt = acts[i + 1][0] if i + 1 < len(acts) else -1
-                        nd += 1 if nxt == 3 else 2
-        pred = nf * u.get("fwd", 0) + nt * u.get("adj", 0) + nc * u.get("comp", 0) + nd * u.get("decomp", 0)
-        out["modes"][name] = {"predicted_ms": pred, "measured_ms": r["ms"],
-                              "forward_steps": nf, "compressions": nc, "decompressions": nd}
-    for budget, names in (("budget", ("codec", "fp32", "fp16", "bf16")),
-                          ("low", ("codec_low", "fp32_low", "fp16_low"))):
+        nf, nc, nd = P.counts(nt, r["ckpt_slots"], r["store_mode"])
+        out["modes"][name] = {"predicted_ms": P.predict(costs, nt, r["ckpt_slots"], r["store_mode"]),
+                              "measured_ms": r["ms"], "forward_steps": nf, "compressions": nc,
+                              "decompressions": nd}
+    for budget, slots, names in (("budget", BUDGET_SLOTS, ("codec", "fp32", "fp16", "bf16")),
+                                 ("low", LOW_SLOTS, ("codec_low", "fp32_low", "fp16_low"))):
         c = [n for n in names if n in out["modes"]]
         if c:
-            out["choice_" + budget] = {
-                "predicted": min(c, key=lambda n: out["modes"][n]["predicted_ms"]),
-                "measured": min(c, key=lambda n: out["modes"][n]["measured_ms"])}
+            pick = P.choose(costs, nt, slots, modes=tuple(results[n]["store_mode"] for n in c), grad_tol=GRAD_TOL)
+            meas = min((n for n in c if results[n].get("grad_rel_err_vs_storeall", 0.0) <= GRAD_TOL),
+                       key=lambda n: out["modes"][n]["measured_ms"], default=None)
+            out["choice_" + budget] = {"predicted": pick[0] if pick else None,
+                                       "measured": results[meas]["store_mode"] if meas else None}
+    if fmin and costs.t_c is not None:
+        out["budget_sweep"] = P.sweep(costs, nt, [2, 3, 5, 8, 12, 20, 32, 50, 80, 128, 250, 500, nt])
     return out
+
+
+def batch_compare(C, torch, synth, nshots=16, slots=16):
+    """Shots of the 2D 1104 x 464 x 2000 workload (order 8): one batched call
+    (every stencil step one launch over all shots, recorded as a graph)
+    against the same gradients one shot at a time."""
+    w = synth.workload("2d-1024x384-so8")
+    grid = C.GridSpec(2, w.shape, w.nbl, w.h, w.so, w.dt, w.nt, w.vmax)
+    m = C.Model(grid)
+    m.set_model(torch.from_numpy(w.start.astype(np.float32)).cuda())
+    ext = (w.shape[1] - 2 * w.nbl - 1) * w.h
+    shots = [C.ShotSpec(src=(20.0, 0.0, float(x)), rec=w.rec, f0=w.f0)
+             for x in np.linspace(0.1 * ext, 0.9 * ext, nshots)]
+    dobs = [m.forward_shot(s) * 1.01 for s in shots]
+    m.batch_gradient(shots, dobs, slots, use_graph=True)
+    m.adjoint_gradient(shots[0], dobs[0], slots)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    _, gb, st = m.batch_gradient(shots, dobs, slots, use_graph=True)
+    torch.cuda.synchronize()
+    tb = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    for s, d in zip(shots, dobs):
+        m.adjoint_gradient(s, d, slots)
+    torch.cuda.synchronize()
+    ts = time.perf_counter() - t0
+    npts = int(np.prod(w.shape))
+    m.close()
+    return {"workload": "2d-1024x384-so8", "grid": list(w.shape), "nt": w.nt, "shots": nshots, "slots": slots,
+            "batched_ms": 1e3 * tb, "one_shot_at_a_time_ms": 1e3 * ts, "speedup": ts / tb,
+            "batched_gpts": 2.0 * w.nt * npts * nshots / tb / 1e9,
+            "stencil_launches_per_step": 1, "fwd_launches": st["fwd_launches"]}
 
 
 def rank_source(src, rk, ws):
@@ -233,7 +261,7 @@ def main():
     ap.add_argument("--impl", default="ckfwi")
     ap.add_argument("--nt", type=int, default=None, help="override the number of time steps (smaller runs)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle baseline")
-    ap.add_argument("--modes", default="storeall,codec,fp32,fp16,bf16,codec_low,fp32_low,fp16_low")
+    ap.add_argument("--modes", default="storeall,codec,fp32,fp16,bf16,codec_low,fp32_low,fp16_low,batch2d")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -380,7 +408,7 @@ def main():
     cand = [m for m in ("codec", "fp32", "fp16", "bf16") if m in results and
             results[m].get("grad_rel_err_vs_storeall", 0.0) <= GRAD_TOL] or list(results)
     headline = min(cand, key=lambda m: results[m]["ms"])
-    model_block = perf_model(C, results, nt)
+    model_block = perf_model(results, nt, fmin)
 
     # end to end through the C-ABI with host buffers (pinned), same headline mode
     kw = modes[headline]
@@ -395,6 +423,10 @@ def main():
     for _ in range(e2e_steps):
         model.adjoint_gradient(shot, dh_np, grad=gh_np, use_graph=True, **kw)
     e2e_s = (time.perf_counter() - t0) / e2e_steps
+
+    batch = None
+    if rk == 0 and "batch2d" in want:
+        batch = batch_compare(C, torch, synth)
 
     cpu = None
     if rk == 0 and not args.no_cpu:
@@ -449,6 +481,7 @@ def main():
             "compare": {k: dict(v, clocks=clocks.get(k)) for k, v in results.items()},
             "skipped": skipped,
             "model": model_block,
+            "batch": batch,
         }
         print(json.dumps(line))
     model.close()

@@ -1,0 +1,68 @@
+"""The time model of a checkpointed gradient (Sec. 3, Sec. 4) on the host:
+schedule counts against the oracle's Revolve, and the choices the model
+makes in the regimes the paper describes."""
+import pytest
+
+from oracle import revolve as R
+
+P = pytest.importorskip("paper_1810_05268_gb300.perfmodel")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_1810_05268_gb300 import build
+    build.build()
+
+
+@pytest.mark.parametrize("nt,slots", [(1000, 20), (500, 10), (300, 7), (60, 5), (40, 40)])
+def test_counts_follow_revolve(nt, slots):
+    nf, nc, nd = P.counts(nt, slots, "fp32")
+    if slots >= nt:
+        assert nf == nt
+    else:
+        acts, cnt = R.schedule(nt, slots)
+        assert nf == cnt["p"] + 1 == R.p_closed(nt, slots) + 1
+        nf2, nc2, nd2 = P.counts(nt, slots, "codec")
+        assert nf2 == nf and nc2 == 2 * cnt["W"]
+        r_slot = sum(1 for a in acts if a[0] == R.RESTORE and a[2] > 0)
+        assert r_slot <= nd2 <= 2 * r_slot      # one or two fields per restore from a slot
+    assert nc == nd == 0
+
+
+def test_slots_at_equal_memory():
+    assert P.slots_for(20, "fp32", 1000) == 20
+    assert P.slots_for(20, "fp16", 1000) == 39
+    assert P.slots_for(20, "codec", 1000, f_min=7.4) == 134
+    assert P.slots_for(20, "codec", 100, f_min=50.0) == 100
+
+
+def test_free_compression_wins_and_costly_compression_loses():
+    base = dict(c_f=0.05, c_r=0.09, t_d=0.02, f_min=8.0)
+    cheap = P.Costs(t_c=1e-4, **base)
+    dear = P.Costs(t_c=0.5, **base)
+    assert P.choose(cheap, 1000, 20, modes=("fp32", "codec"))[0] == "codec"
+    assert P.choose(dear, 1000, 20, modes=("fp32", "codec"))[0] == "fp32"
+
+
+def test_predicted_time_falls_with_memory_and_reaches_store_all():
+    c = P.Costs(c_f=0.05, c_r=0.09, t_c=0.08, t_d=0.02, f_min=8.0)
+    rows = P.sweep(c, 400, [2, 5, 20, 80, 400])
+    t32 = [r["fp32"] for r in rows]
+    assert all(a >= b for a, b in zip(t32, t32[1:]))
+    assert rows[-1]["fp32"] == pytest.approx(400 * (0.05 + 0.09))
+
+
+def test_regimes():
+    """Little memory: compression pays; ample memory: plain checkpoints win."""
+    c = P.Costs(c_f=0.05, c_r=0.09, t_c=0.03, t_d=0.01, f_min=10.0)
+    low = P.choose(c, 1000, 3, modes=("fp32", "codec"))
+    high = P.choose(c, 1000, 500, modes=("fp32", "codec"))
+    assert low[0] == "codec"
+    assert high[0] == "fp32"
+
+
+def test_gradient_tolerance_excludes_modes():
+    c = P.Costs(c_f=0.05, c_r=0.09, c_r16=0.09, t_c=1e-4, t_d=1e-4, f_min=8.0,
+                grad_err={"bf16": 0.03, "fp16": 0.004, "codec": 0.0005})
+    assert P.choose(c, 1000, 20, modes=("fp32", "bf16"), grad_tol=1e-2)[0] == "fp32"
+    assert P.choose(c, 1000, 20, modes=("fp32", "bf16"))[0] == "bf16"

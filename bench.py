@@ -36,6 +36,7 @@ sys.path.insert(0, ROOT)
 WORKLOAD = "3d-128cube-so8"
 BUDGET_SLOTS = 20          # memory of 20 uncompressed checkpoints
 LOW_SLOTS = 5              # the low-memory comparison
+HOST_SLOTS = 40            # second-level (host memory) slots of the two-level comparison
 TOL = 1e-4                 # codec absolute tolerance
 FWD_BYTES = 16             # forward step: read u^n, u^{n-1}, w; write u^{n+1}
 ADJ_BYTES = 28             # reverse step: read lam^j, lam^{j+1}, u^{j-1}, w, g; write lam^{j-1}, g
@@ -261,7 +262,7 @@ def main():
     ap.add_argument("--impl", default="ckfwi")
     ap.add_argument("--nt", type=int, default=None, help="override the number of time steps (smaller runs)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle baseline")
-    ap.add_argument("--modes", default="storeall,codec,fp32,fp16,bf16,codec_low,fp32_low,fp16_low,batch2d")
+    ap.add_argument("--modes", default="storeall,codec,fp32,fp16,bf16,codec_low,fp32_low,fp16_low,fp32_host,batch2d")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -322,6 +323,9 @@ def main():
         modes["fp32_low"] = dict(ckpt_slots=LOW_SLOTS, store_mode="fp32")
     if "fp16_low" in want:
         modes["fp16_low"] = dict(ckpt_slots=2 * (LOW_SLOTS - 1) + 1, store_mode="fp16")
+    # a second storage level: the device budget plus HOST_SLOTS slots in pinned host memory
+    if "fp32_host" in want:
+        modes["fp32_host"] = dict(ckpt_slots=BUDGET_SLOTS + HOST_SLOTS, store_mode="fp32", host_slots=HOST_SLOTS)
 
     grads = {}
 
@@ -385,7 +389,7 @@ def main():
         results[name] = {
             "ms": ms, "gpts": 2.0 * nt * npts / (ms / 1e3) / 1e9 * ws,
             "ckpt_slots": kw["ckpt_slots"], "store_mode": kw["store_mode"],
-            "pool_bytes": kw.get("pool_bytes", st["pool_bytes_peak"]),
+            "pool_bytes": kw.get("pool_bytes", st["pool_bytes_peak"]), "host_slots": kw.get("host_slots", 0),
             "recompute_ratio": st["fwd_steps"] / nt, "p": st["p"], "W": st["takeshots"], "R": st["restores"],
             "fwd_launches": st["fwd_launches"], "adj_launches": st["adj_launches"],
             "comp_calls": st["comp_calls"], "decomp_calls": st["decomp_calls"],
@@ -461,6 +465,7 @@ def main():
             "metric": "gradient point-updates per second (useful 2*N*npts/t)",
             "value": H["gpts"], "unit": "Gpt/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": H["ms"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "gradients_per_hour": 3.6e6 / H["ms"] * ws, "recompute_ratio": H["recompute_ratio"],
             "dtype": "f32", "data": "synthetic",
             "config": {"workload": WORKLOAD, "grid": list(w.shape), "nt": nt, "space_order": w.so,
                        "mode": "%s: Revolve, %d slots, %s storage, at the memory of %d fp32 checkpoints%s" % (

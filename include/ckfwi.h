@@ -122,6 +122,13 @@ typedef struct ckfwi_grad_opts {
     double grad_scale;   /* the gradient is multiplied by this (0 is read as 1) */
     int grad_f32;        /* batch only: grad_sum is float32 (the FP64 compensated
                             sum rounded once) instead of float64 */
+    int host_slots;      /* FP32 / BF16 / FP16 Revolve: how many of the M - 1
+                            checkpoint slots live in pinned host memory (the
+                            second storage level, read and written by the step
+                            kernels over the host link); the lowest-numbered
+                            slots, which Revolve writes and reads least, go
+                            there.  0: every slot in device memory.  Values are
+                            unchanged by the placement. */
 } ckfwi_grad_opts;
 
 typedef struct ckfwi_stats {

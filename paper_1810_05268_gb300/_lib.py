@@ -30,7 +30,8 @@ class Shot(ctypes.Structure):
 class GradOpts(ctypes.Structure):
     _fields_ = [("ckpt_slots", ctypes.c_int), ("store_mode", ctypes.c_int), ("tol", ctypes.c_double),
                 ("pool_bytes", ctypes.c_size_t), ("grad_kind", ctypes.c_int), ("use_graph", ctypes.c_int),
-                ("profile", ctypes.c_int), ("grad_scale", ctypes.c_double), ("grad_f32", ctypes.c_int)]
+                ("profile", ctypes.c_int), ("grad_scale", ctypes.c_double), ("grad_f32", ctypes.c_int),
+                ("host_slots", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):

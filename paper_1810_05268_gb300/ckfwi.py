@@ -162,7 +162,7 @@ def _alloc(shape, dtype, device):
 
 
 def _opts(ckpt_slots, store_mode, tol, pool_bytes, grad_kind, use_graph, profile=False, grad_scale=1.0,
-          grad_f32=False):
+          grad_f32=False, host_slots=0):
     o = GradOpts()
     o.ckpt_slots = int(ckpt_slots)
     o.store_mode = STORE_NAMES.get(store_mode, store_mode) if isinstance(store_mode, str) else int(store_mode)
@@ -173,6 +173,7 @@ def _opts(ckpt_slots, store_mode, tol, pool_bytes, grad_kind, use_graph, profile
     o.profile = int(bool(profile))
     o.grad_scale = float(grad_scale)
     o.grad_f32 = int(bool(grad_f32))
+    o.host_slots = int(host_slots)
     return o
 
 
@@ -193,7 +194,7 @@ def misfit(model, grid: GridSpec, shot: ShotSpec, d_obs, d_sim=None, stream=None
 
 def adjoint_gradient(model, grid: GridSpec, shot: ShotSpec, d_obs, ckpt_slots, store_mode=STORE_FP32,
                      tol=0.0, pool_bytes=0, grad_kind=SLOWNESS2, use_graph=False, grad=None, stream=None,
-                     profile=False, grad_scale=1.0):
+                     profile=False, grad_scale=1.0, host_slots=0):
     """(misfit, gradient on the total grid, stats dict)."""
     pd, mem = _buf(d_obs, np.float32)
     if grad is None:
@@ -202,7 +203,8 @@ def adjoint_gradient(model, grid: GridSpec, shot: ShotSpec, d_obs, ckpt_slots, s
     if memg != mem:
         raise ValueError("d_obs and grad must both be host or both be device buffers")
     s = shot.c()
-    o = _opts(ckpt_slots, store_mode, tol, pool_bytes, grad_kind, use_graph, profile, grad_scale)
+    o = _opts(ckpt_slots, store_mode, tol, pool_bytes, grad_kind, use_graph, profile, grad_scale,
+              host_slots=host_slots)
     phi = ctypes.c_double(0.0)
     st = Stats()
     _check(lib().ckfwi_adjoint_gradient(model, ctypes.byref(s), pd, mem, ctypes.byref(o), ctypes.byref(phi), pg,

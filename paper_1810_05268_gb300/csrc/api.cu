@@ -102,6 +102,44 @@ struct DevMem {
     template <class T> T* as() const { return static_cast<T*>(p); }
 };
 
+// Pinned, device-mapped host memory (the second checkpoint level).
+struct HostMem {
+    void* p = nullptr;     // host address
+    void* d = nullptr;     // the device's address of the same bytes
+    size_t bytes = 0;
+    HostMem() = default;
+    HostMem(const HostMem&) = delete;
+    HostMem& operator=(const HostMem&) = delete;
+    ~HostMem() { release(); }
+    void release()
+    {
+        if (p) cudaFreeHost(p);
+        p = d = nullptr;
+        bytes = 0;
+    }
+    // (re)allocate when too small; a fresh allocation is zeroed
+    cudaError_t alloc(size_t n)
+    {
+        if (bytes >= n && p) return cudaSuccess;
+        release();
+        if (n == 0) return cudaSuccess;
+        cudaError_t e = cudaHostAlloc(&p, n, cudaHostAllocMapped | cudaHostAllocPortable);
+        if (e != cudaSuccess) {
+            p = nullptr;
+            return e;
+        }
+        std::memset(p, 0, n);
+        e = cudaHostGetDevicePointer(&d, p, 0);
+        if (e != cudaSuccess) {
+            release();
+            return e;
+        }
+        bytes = n;
+        return cudaSuccess;
+    }
+};
+
+
 // FD weights of the 2k-th order second derivative, closed form (k! )^2 ...
 void fd_weights(int k, double* c)
 {
@@ -295,6 +333,8 @@ struct ckfwi_model {
     DevMem work[3], lam[3], gacc;
     DevMem traj;                    // store-all trajectory
     DevMem pool;                    // checkpoint pool
+    HostMem hpool;                  // checkpoint slots in host memory (second level)
+    int host_slots = 0;             // slots 1 .. host_slots live in hpool
     size_t pool_cap_bytes = 0;
     int pool_tag = -1;              // storage mode whose layout the pool holds
     DevMem slotbase;                // codec: device word offsets of slots
@@ -365,7 +405,6 @@ namespace {
 float* org(const DevMem& m, const FieldGeom& g) { return m.as<float>() + g.origin; }
 
 size_t field_bytes(const FieldGeom& g, size_t elem = 4) { return (size_t)g.alloc * elem; }
-
 // cuTensorMapEncodeTiled, fetched from the driver through the runtime (no
 // link-time dependency on libcuda).
 typedef CUresult (*EncodeTiled)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
@@ -556,9 +595,13 @@ void* rptr(ckfwi_model* m, int mode, const Role& r)
     case R_UN: return org(m->uN, f);
     case R_TRAJ: return m->traj.as<float>() + (size_t)r.idx * f.alloc + f.origin;
     case R_SLOT: {
-        // uncompressed slots: two padded fields per slot, FP32 or 16-bit
+        // uncompressed slots: two padded fields per slot, FP32 or 16-bit;
+        // slots 1 .. host_slots in host memory, the rest in device memory
         const size_t es = mode == CKFWI_STORE_FP32 ? 4 : 2;
-        return m->pool.as<char>() + ((size_t)(r.idx - 1) * 2 + r.which) * field_bytes(f, es) + (size_t)f.origin * es;
+        const size_t fb = field_bytes(f, es), off = (size_t)f.origin * es;
+        if (r.idx <= m->host_slots)
+            return static_cast<char*>(m->hpool.d) + ((size_t)(r.idx - 1) * 2 + r.which) * fb + off;
+        return m->pool.as<char>() + ((size_t)(r.idx - 1 - m->host_slots) * 2 + r.which) * fb + off;
     }
     default: return nullptr;
     }
@@ -654,6 +697,17 @@ bool grid_samples(const FieldGeom& f, const Tile& t, int zlen, int nrec)
     return gx * gy * gz * tpc >= nrec;
 }
 
+// A checkpoint slot in host memory (the second storage level).  Tensor maps
+// are built on device memory only, so a step whose TMA-read operand is such
+// a slot runs the register-queue kernel (bitwise the same values).
+bool in_host(const ckfwi_model* m, const Role& r) { return r.kind == R_SLOT && r.idx <= m->host_slots; }
+Tile host_tile(const ckfwi_model* m)
+{
+    Tile t = tile_at(m->fg.dims, 1, 16);
+    if (!tile_supported(m->fg.dims, m->K, t)) t = tile_at(m->fg.dims, 2, 16);
+    return t;
+}
+
 // One forward step n of every lane: u -> out, optionally sampling d^n and
 // writing a fused takeshot (ck, ck_u, ck_up).
 int fwd_step(Ctx& cx, const Role& u, const Role& up, const Role& out, int n, bool record, int ck,
@@ -688,7 +742,9 @@ int fwd_step(Ctx& cx, const Role& u, const Role& up, const Role& out, int n, boo
             continue;
         }
         const int tok = cx.begin(PC_FWD);
-        if (m->tf.ver == 4) {
+        if (m->tf.ver == 2 && in_host(m, u)) {
+            CK_TRY(launch_fwd(a, host_tile(m), m->K, ck, cx.st));
+        } else if (m->tf.ver == 4) {
             CK_TRY(launch_fwd4(a, m->tf, m->K, ck, cx.st));
         } else if (m->tf.ver == 3) {
             CK_TRY(launch_fwd3(a, m->tf, m->K, ck, cx.st));
@@ -738,7 +794,9 @@ int adj_step(Ctx& cx, const Role& l1, const Role& l2, const Role& l0, const Role
             continue;
         }
         const int tok = cx.begin(PC_ADJ);
-        if (m->ta.ver == 4) {
+        if (m->ta.ver == 2 && in_host(m, u)) {
+            CK_TRY(launch_adj(a, host_tile(m), m->K, utype, cx.st));
+        } else if (m->ta.ver == 4) {
             CK_TRY(launch_adj4(a, m->ta, m->K, utype, cx.st));
         } else if (m->ta.ver == 3) {
             CK_TRY(launch_adj3(a, m->ta, m->K, utype, cx.st));
@@ -1245,18 +1303,21 @@ double storage_bytes(const FieldGeom& f, const RunCfg& rc, const ckfwi_grad_opts
 int prepare_storage(ckfwi_model* m, const RunCfg& rc, const ckfwi_grad_opts* o)
 {
     const FieldGeom& f = m->fg;
-    const void* before[5] = {m->traj.p, m->pool.p, m->slotbase.p, m->scratch.p, m->statw.p};
+    const void* before[7] = {m->traj.p, m->pool.p, m->slotbase.p, m->scratch.p, m->statw.p, m->hpool.d,
+                             reinterpret_cast<const void*>((intptr_t)m->host_slots)};
     struct Bump {
         ckfwi_model* m;
         const void* const* b;
         ~Bump()
         {
-            const void* after[5] = {m->traj.p, m->pool.p, m->slotbase.p, m->scratch.p, m->statw.p};
-            for (int i = 0; i < 5; ++i)
+            const void* after[7] = {m->traj.p, m->pool.p, m->slotbase.p, m->scratch.p, m->statw.p, m->hpool.d,
+                                    reinterpret_cast<const void*>((intptr_t)m->host_slots)};
+            for (int i = 0; i < 7; ++i)
                 if (after[i] != b[i]) ++m->gen;
         }
     } bump{m, before};
     m->cap_words = 0;
+    m->host_slots = 0;
     if (rc.store_all) {
         CK_TRY(m->traj.alloc(field_bytes(f) * (size_t)rc.N));
         return CKFWI_OK;
@@ -1267,13 +1328,25 @@ int prepare_storage(ckfwi_model* m, const RunCfg& rc, const ckfwi_grad_opts* o)
     // a pool last used with another layout is cleared before reuse.
     const int tag = rc.mode == CKFWI_STORE_FP32 ? 4 : (rc.mode == CKFWI_STORE_CODEC ? 0 : 2);
     if (rc.mode != CKFWI_STORE_CODEC) {
-        const size_t need = nslot * field_bytes(f, (size_t)tag);
+        // the first host_slots slots in pinned host memory, the others on the device
+        const int hs = std::max(0, std::min(o->host_slots, rc.M - 1));
+        const size_t dslot = (size_t)(rc.M - 1 - hs) * 2, hslot = (size_t)hs * 2;
+        const size_t need = dslot * field_bytes(f, (size_t)tag);
         const void* before_p = m->pool.p;
+        const int old_tag = m->pool_tag;
         CK_TRY(m->pool.alloc(need));
-        if (m->pool.p == before_p && m->pool_tag != tag) {
+        if (m->pool.p == before_p && old_tag != tag && m->pool.p) {
             CK_TRY(cudaMemset(m->pool.p, 0, m->pool.bytes));
             CK_TRY(cudaDeviceSynchronize());
         }
+        if (hs > 0) {
+            const void* before_h = m->hpool.p;
+            CK_TRY(m->hpool.alloc(hslot * field_bytes(f, (size_t)tag)));
+            if (m->hpool.p == before_h && old_tag != tag) std::memset(m->hpool.p, 0, m->hpool.bytes);
+        } else if (m->hpool.p && old_tag != tag) {
+            std::memset(m->hpool.p, 0, m->hpool.bytes);
+        }
+        m->host_slots = hs;
         m->pool_tag = tag;
     } else {
         m->pool_tag = 0;

@@ -15,6 +15,7 @@ class OraGrid(ctypes.Structure):
         ("nx", ctypes.c_int), ("nbl", ctypes.c_int), ("so", ctypes.c_int),
         ("nt", ctypes.c_int), ("h", ctypes.c_double), ("dt", ctypes.c_double),
         ("vmax_damp", ctypes.c_double), ("refl", ctypes.c_double),
+        ("time_order", ctypes.c_int),
     ]
 
 
@@ -33,6 +34,7 @@ def lib():
                                      ctypes.c_double, P]
             L.ora_interp.argtypes = [P, P, P, P]
             L.ora_forward.argtypes = [P, P, i, P, P, i, P, P, P]
+            L.ora_step.argtypes = [P, P, P, P, P]
             L.ora_adjoint.argtypes = [P, P, i, P, P, i, P, P, P, P, P, i]
             L.ora_gradient.argtypes = [P, P, i, P, P, i, P, P, P, P, P, i]
             L.codec_compress.argtypes = [i, i, i, i, P, ctypes.c_double, P, ctypes.c_size_t, P]
@@ -41,7 +43,7 @@ def lib():
             L.codec_bound_words.argtypes = [i, i, i, i]
             L.codec_bound_words.restype = ctypes.c_longlong
             for f in ("ora_fd_weights", "ora_laplacian", "ora_damping", "ora_ricker",
-                      "ora_interp", "ora_forward", "ora_adjoint", "ora_gradient",
+                      "ora_interp", "ora_forward", "ora_step", "ora_adjoint", "ora_gradient",
                       "codec_decompress"):
                 getattr(L, f).restype = ctypes.c_int
             _lib = L

@@ -16,7 +16,8 @@
  *
  * What the paper fixes (Sec. 6, Eq. "eqn:wave" and the misfit after it):
  *   m u_tt - lap(u) = q,  m = 1/c^2,  phi = 1/2 ||d_sim - d_obs||^2,
- *   gradient by the adjoint-state method, OT2 (2nd order in time) kernel.
+ *   gradient by the adjoint-state method, OT2 (2nd order in time) kernel,
+ *   and an OT4 kernel (4th order in time) taken from the paper's DSL.
  * What the paper leaves to its DSL and this oracle fixes as a reading:
  *   - Laplacian: 2k-th order central differences, k = so/2, with the
  *     closed-form weights c_j = 2(-1)^(j+1) (k!)^2 / (j^2 (k-j)! (k+j)!),
@@ -38,6 +39,18 @@
  *       a lam^{j-1} = 2 lam^j - b lam^{j+1} + w (lap lam^j - P^T r^j)
  *     gradient  dphi/dm = sum_{n=0}^{N-1} lam^n (a u^{n+1} - 2u^n + b u^{n-1})/dt^2
  *                       = sum_{n=0}^{N-1} lam^n (lap u^n + q^n) c^2.
+ *   - OT4 (time_order 4): the paper names the kernel and cites its DSL for
+ *     it without stating it.  Reading: the modified-equation scheme, which
+ *     cancels the leading dt^2/12 u_tttt error of the centred second time
+ *     difference by using u_tttt = c^2 lap(c^2 lap u) of the undamped,
+ *     source-free equation.  The recursion keeps its form with lap replaced by
+ *       A u = lap u + dt^2/12 lap(c^2 lap u)
+ *     (the inner field c^2 lap u is zero outside the grid, like u); damping
+ *     and sources enter as in OT2.  A is symmetric, so the adjoint is the
+ *     same recursion with A, and the exact gradient gains the derivative of
+ *     the correction with respect to m = 1/c^2:
+ *       dphi/dm = sum_{n=0}^{N-1} [ lam^n (A u^n + q^n) c^2
+ *                                  + dt^2/12 c^4 (lap u^n)(lap lam^n) ].
  */
 #include <math.h>
 #include <stdint.h>
@@ -54,6 +67,7 @@ typedef struct {
     double dt;         /* time step [ms] */
     double vmax_damp;  /* velocity that sets the damping strength [km/s] */
     double refl;       /* target reflection coefficient R of the layer */
+    int time_order;    /* 2 (OT2; 0 reads as 2) or 4 (OT4) */
 } ora_grid;
 
 enum { ORA_OK = 0, ORA_EINVAL = -1, ORA_ENOMEM = -2 };
@@ -69,6 +83,7 @@ static int grid_ok(const ora_grid* g)
     if (g->dims == 3 && g->ny < 2) return 0;
     if (g->so < 2 || (g->so & 1) || g->so > 32) return 0;
     if (g->nt < 1 || !(g->h > 0) || !(g->dt > 0) || g->nbl < 0) return 0;
+    if (g->time_order != 0 && g->time_order != 2 && g->time_order != 4) return 0;
     return 1;
 }
 
@@ -205,6 +220,7 @@ typedef struct {
     const ora_grid* g;
     long np;
     double *ww, *aa, *bb, *c2;        /* per-point coefficients */
+    double *t1, *t2;                  /* np scratch values each (OT4 operator) */
     int nsrc, nrec, nstc;             /* stencil size 2^dims */
     long *sidx, *ridx;                /* [nsrc][nstc], [nrec][nstc] */
     double *swt, *rwt;
@@ -213,7 +229,7 @@ typedef struct {
 
 static void problem_free(problem* P)
 {
-    free(P->ww); free(P->aa); free(P->bb); free(P->c2);
+    free(P->ww); free(P->aa); free(P->bb); free(P->c2); free(P->t1); free(P->t2);
     free(P->sidx); free(P->ridx); free(P->swt); free(P->rwt);
 }
 
@@ -233,11 +249,13 @@ static int problem_init(problem* P, const ora_grid* g, const double* vel, int ns
     P->aa = malloc(sizeof(double) * P->np);
     P->bb = malloc(sizeof(double) * P->np);
     P->c2 = malloc(sizeof(double) * P->np);
+    P->t1 = malloc(sizeof(double) * P->np);
+    P->t2 = malloc(sizeof(double) * P->np);
     P->sidx = malloc(sizeof(long) * (nsrc + 1) * P->nstc);
     P->swt = malloc(sizeof(double) * (nsrc + 1) * P->nstc);
     P->ridx = malloc(sizeof(long) * (nrec + 1) * P->nstc);
     P->rwt = malloc(sizeof(double) * (nrec + 1) * P->nstc);
-    if (!P->ww || !P->aa || !P->bb || !P->c2 || !P->sidx || !P->swt || !P->ridx || !P->rwt) {
+    if (!P->ww || !P->aa || !P->bb || !P->c2 || !P->t1 || !P->t2 || !P->sidx || !P->swt || !P->ridx || !P->rwt) {
         problem_free(P);
         return ORA_ENOMEM;
     }
@@ -262,6 +280,21 @@ static int problem_init(problem* P, const ora_grid* g, const double* vel, int ns
             return ORA_EINVAL;
         }
     return ORA_OK;
+}
+
+static int is_ot4(const problem* P) { return P->g->time_order == 4; }
+
+/* The spatial operator of the time step, out = A u:  lap u for OT2,
+ * lap u + dt^2/12 lap(c^2 lap u) for OT4.  out must not alias u. */
+static void spatial_op(const problem* P, const double* u, double* out)
+{
+    const ora_grid* g = P->g;
+    ora_laplacian(g, u, out);
+    if (!is_ot4(P)) return;
+    for (long p = 0; p < P->np; ++p) P->t1[p] = P->c2[p] * out[p];
+    ora_laplacian(g, P->t1, P->t2);
+    const double k = g->dt * g->dt / 12.0;
+    for (long p = 0; p < P->np; ++p) out[p] += k * P->t2[p];
 }
 
 /* One leapfrog update:  out = (2 cur - b prev + w (lap + src)) / a,
@@ -312,7 +345,7 @@ static int forward_run(const problem* P, double* d, double* u_final, double* ckp
             memcpy(ckpt + (long)(2 * (n / seg)) * np, b, sizeof(double) * np);
             memcpy(ckpt + (long)(2 * (n / seg) + 1) * np, a, sizeof(double) * np);
         }
-        ora_laplacian(g, b, lap);
+        spatial_op(P, b, lap);
         add_sources(P, n, lap);
         leapfrog(P, b, a, lap, c);
         if (d) sample(P, c, d + (long)(n + 1) * P->nrec);
@@ -333,6 +366,23 @@ int ora_forward(const ora_grid* g, const double* vel, int nsrc, const double* sr
     st = forward_run(&P, d, u_final, NULL, 0);
     problem_free(&P);
     return st;
+}
+
+/* One source-free time step:  out = u^{n+1} from cur = u^n, prev = u^{n-1}
+ * (the OT2 or OT4 recursion of the grid's time order). */
+int ora_step(const ora_grid* g, const double* vel, const double* cur, const double* prev, double* out)
+{
+    if (!cur || !prev || !out) return ORA_EINVAL;
+    problem P;
+    int st = problem_init(&P, g, vel, 0, NULL, NULL, 0, NULL);
+    if (st != ORA_OK) return st;
+    double* lap = malloc(sizeof(double) * P.np);
+    if (!lap) { problem_free(&P); return ORA_ENOMEM; }
+    spatial_op(&P, cur, lap);
+    leapfrog(&P, cur, prev, lap, out);
+    free(lap);
+    problem_free(&P);
+    return ORA_OK;
 }
 
 /* Adjoint sweep driven by r ([nt+1][nrec], row 0 unused).
@@ -384,14 +434,14 @@ static int adjoint_run(const problem* P, const double* r, double* grad, double* 
             memcpy(prev, ckpt + (long)(2 * k + 1) * np, sizeof(double) * np);
             for (int n = s0; n < s1 - 1; ++n) {
                 double* cur = useg + (long)(n - s0 + 1) * np;
-                ora_laplacian(g, cur, lap);
+                spatial_op(P, cur, lap);
                 add_sources(P, n, lap);
                 leapfrog(P, cur, cur - np, lap, cur + np);
             }
         }
         for (; j > s0; --j) {
             /* lam^{j-1} from lam^j, lam^{j+1} and -P^T r^j */
-            ora_laplacian(g, l1, lap);
+            spatial_op(P, l1, lap);
             for (int rr = 0; rr < P->nrec; ++rr)
                 for (int i = 0; i < P->nstc; ++i)
                     lap[P->ridx[rr * P->nstc + i]] -= P->rwt[rr * P->nstc + i] * r[(long)j * P->nrec + rr];
@@ -399,10 +449,18 @@ static int adjoint_run(const problem* P, const double* r, double* grad, double* 
             const int n = j - 1;
             if (grad) {
                 const double* un = useg + (long)(n - s0 + 1) * np;
-                ora_laplacian(g, un, tmp);
+                spatial_op(P, un, tmp);
                 add_sources(P, n, tmp);
 #pragma omp parallel for schedule(static)
                 for (long p = 0; p < np; ++p) grad[p] += l0[p] * tmp[p] * P->c2[p];
+                if (is_ot4(P)) {
+                    /* derivative of the OT4 correction: dt^2/12 c^4 lap u^n lap lam^n */
+                    const double kk = g->dt * g->dt / 12.0;
+                    ora_laplacian(g, un, tmp);
+                    ora_laplacian(g, l0, lap);
+                    for (long p = 0; p < np; ++p)
+                        grad[p] += kk * P->c2[p] * P->c2[p] * tmp[p] * lap[p];
+                }
             }
             if (srcadj)
                 for (int s = 0; s < P->nsrc; ++s) {

@@ -24,6 +24,7 @@ class Grid:
     nt: int               # number of time steps N
     vmax_damp: float      # [km/s]
     refl: float = 1e-3
+    time_order: int = 2   # 2: OT2 kernel, 4: OT4 kernel (Sec. 6)
 
     @property
     def n3(self):
@@ -34,7 +35,7 @@ class Grid:
     def c(self):
         nz, ny, nx = self.n3
         return OraGrid(self.dims, nz, ny, nx, self.nbl, self.so, self.nt, self.h, self.dt,
-                       self.vmax_damp, self.refl)
+                       self.vmax_damp, self.refl, self.time_order)
 
 
 def _p(a):
@@ -114,6 +115,17 @@ def forward(grid: Grid, vel, src_pos, src_series, rec_pos, want_final=False):
     _check(lib().ora_forward(ctypes.byref(g), _p(vel), src_pos.shape[0], _p(src_pos), _p(ser),
                              rec_pos.shape[0], _p(rec_pos), _p(d), _p(uf)), "forward")
     return (d, uf) if want_final else d
+
+
+def step(grid: Grid, vel, cur, prev):
+    """u^{n+1} of the source-free recursion from u^n = cur, u^{n-1} = prev."""
+    vel = _f64(vel)
+    cur = _f64(cur, grid.shape)
+    prev = _f64(prev, grid.shape)
+    out = np.zeros(grid.shape)
+    g = grid.c()
+    _check(lib().ora_step(ctypes.byref(g), _p(vel), _p(cur), _p(prev), _p(out)), "step")
+    return out
 
 
 def adjoint(grid: Grid, vel, src_pos, src_series, rec_pos, r, want_grad=True,

@@ -25,6 +25,20 @@
  *   n = 1..N.  The adjoint is the exact transpose of this recursion; the
  *   gradient is dphi/dm = sum_{n=0}^{N-1} lam^n (lap_h u^n + Q^T s^n) c^2.
  *
+ * OT4 kernel (Sec. 6: the 4th-order-in-time kernel the paper takes from its
+ * DSL without stating it; time_order = 4).  The recursion above with lap_h
+ * replaced by
+ *   A u = lap_h u + dt^2/12 lap_h(c^2 lap_h u),
+ * the modified-equation correction of the leapfrog's dt^2/12 u_tttt error
+ * (the inner field c^2 lap_h u is zero outside the total grid, like u);
+ * damping and sources enter as for OT2.  A is symmetric, so the adjoint is
+ * the same recursion with A, and the exact gradient gains the derivative of
+ * the correction with respect to m:
+ *   dphi/dm = sum_{n=0}^{N-1} [ lam^n (A u^n + Q^T s^n) c^2
+ *                              + dt^2/12 c^4 (lap_h u^n)(lap_h lam^n) ].
+ * A step costs two launches; a model of time order 4 computes the gradients
+ * of a batch one shot at a time.
+ *
  * Units: lengths in m, times in ms, velocities in km/s (= m/ms), m = 1/c^2.
  *
  * Arrays: velocity, slowness and gradient fields cover the total grid
@@ -92,6 +106,7 @@ typedef struct ckfwi_grid {
     int nt;              /* number of time steps N >= 1 */
     double vmax_damp;    /* largest velocity the model will hold [km/s]: sets the
                             damping strength and the stability check */
+    int time_order;      /* 2: OT2 kernel (0 reads as 2); 4: OT4 kernel */
 } ckfwi_grid;
 
 typedef struct ckfwi_shot {
@@ -157,9 +172,10 @@ typedef struct ckfwi_model ckfwi_model;
 
 /* Allocate a model for grid g on the current device (working fields, maps,
  * coefficient buffers).  Sec. 6 (Eq. "eqn:wave").  *out receives the handle.
- * EINVAL for an unsupported order, a non-positive size, a damping layer
- * wider than half the grid, or vmax_damp dt / h beyond the leapfrog stability
- * limit of the stencil; ENOMEM if device memory runs out. */
+ * EINVAL for an unsupported space or time order, a non-positive size, a
+ * damping layer wider than half the grid, or vmax_damp dt / h beyond the
+ * leapfrog stability limit of the stencil (OT4: sqrt(3) times the OT2
+ * limit); ENOMEM if device memory runs out. */
 CKFWI_API int ckfwi_create_model(const ckfwi_grid* g, ckfwi_model** out);
 
 /* Set the medium: data is c [km/s] (kind CKFWI_VELOCITY) or m = 1/c^2

@@ -18,7 +18,7 @@ _lib = None
 class Grid(ctypes.Structure):
     _fields_ = [("dims", ctypes.c_int), ("n", ctypes.c_int * 3), ("nbl", ctypes.c_int),
                 ("h", ctypes.c_double), ("space_order", ctypes.c_int), ("dt", ctypes.c_double),
-                ("nt", ctypes.c_int), ("vmax_damp", ctypes.c_double)]
+                ("nt", ctypes.c_int), ("vmax_damp", ctypes.c_double), ("time_order", ctypes.c_int)]
 
 
 class Shot(ctypes.Structure):

@@ -77,6 +77,7 @@ class GridSpec:
     dt: float               # [ms]
     nt: int
     vmax_damp: float        # [km/s]
+    time_order: int = 2     # 2: OT2 kernel, 4: OT4 kernel (Sec. 6)
 
     def c(self):
         g = Grid()
@@ -86,6 +87,7 @@ class GridSpec:
             g.n[i] = int(n[i])
         g.nbl, g.h, g.space_order = int(self.nbl), float(self.h), int(self.space_order)
         g.dt, g.nt, g.vmax_damp = float(self.dt), int(self.nt), float(self.vmax_damp)
+        g.time_order = int(self.time_order)
         return g
 
 

@@ -328,6 +328,10 @@ struct ckfwi_model {
     int K = 0;
     float c[MAXK + 1] = {};
     float hdt = 0.0f;
+    int ot = 2;                     // time order of the kernel: 2 (OT2) or 4 (OT4)
+    float c12[MAXK + 1] = {};       // OT4: c_j / (12 h^2)
+    DevMem z4[3];                   // OT4: w lap f of the step in flight, and w lap u of the
+                                    // last two reverse steps (alternating by step parity)
     bool have_model = false;
     DevMem eta, w, cvel, zero, uN;
     DevMem work[3], lam[3], gacc;
@@ -457,14 +461,17 @@ int check_grid(const ckfwi_grid* g)
     if (!(g->h > 0) || !(g->dt > 0) || g->nt < 1 || g->nbl < 0) return CKFWI_EINVAL;
     if (!(g->vmax_damp > 0)) return CKFWI_EINVAL;
     if (2LL * g->nbl >= g->n[0] || 2LL * g->nbl >= g->n[2]) return CKFWI_EINVAL;
-    // leapfrog stability: (vmax dt / h)^2 * dims * |symbol at k h = pi| <= 4,
-    // the 1-D symbol of the 2k-th order second difference being -4 sum_{j odd} c_j
+    if (g->time_order != 0 && g->time_order != 2 && g->time_order != 4) return CKFWI_EINVAL;
+    // leapfrog stability: x = (vmax dt / h)^2 * dims * |symbol at k h = pi| <= 4,
+    // the 1-D symbol of the 2k-th order second difference being -4 sum_{j odd} c_j.
+    // OT4 multiplies a mode by 2 - x + x^2/12 per step instead of 2 - x, which
+    // stays within [-2, 2] up to x = 12.
     double c[MAXK + 1];
     fd_weights(so / 2, c);
     double sym = 0.0;
     for (int j = 1; j <= so / 2; j += 2) sym += 4.0 * c[j];
     const double cfl = g->vmax_damp * g->dt / g->h;
-    if (cfl * cfl * g->dims * sym > 4.0) return CKFWI_EINVAL;
+    if (cfl * cfl * g->dims * sym > (g->time_order == 4 ? 12.0 : 4.0)) return CKFWI_EINVAL;
     return CKFWI_OK;
 }
 
@@ -708,6 +715,51 @@ Tile host_tile(const ckfwi_model* m)
     return t;
 }
 
+// OT4 steps: the pass computing w lap f, then the update (ot4.cu).  The
+// reverse step j writes w lap u^{j-1} into z4[1 + j % 2] and pairs the one
+// of step j + 1 with lap lam^j.
+int ot4_fwd_step(ckfwi_model* m, const FwdArgs& a, const Tile& t, int ck, cudaStream_t st)
+{
+    const FieldGeom& f = m->fg;
+    Ot4LapArgs la{};
+    la.g = f;
+    la.f0 = a.u;
+    la.z0 = org(m->z4[0], f);
+    la.w = a.w;
+    std::memcpy(la.c, m->c, sizeof(la.c));
+    la.smp = a.smp;
+    CK_TRY(launch_ot4_lap(la, t, m->K, U_FP32, st));
+    Ot4FwdArgs fa{};
+    fa.f = a;
+    fa.f.smp = Sample{};
+    fa.z = la.z0;
+    std::memcpy(fa.c12, m->c12, sizeof(fa.c12));
+    CK_TRY(launch_ot4_fwd(fa, t, m->K, ck, st));
+    return CKFWI_OK;
+}
+
+int ot4_adj_step(ckfwi_model* m, const AdjArgs& a, const Tile& t, int utype, int j, cudaStream_t st)
+{
+    const FieldGeom& f = m->fg;
+    Ot4LapArgs la{};
+    la.g = f;
+    la.f0 = a.l1;
+    la.f1 = a.u;
+    la.z0 = org(m->z4[0], f);
+    la.z1 = org(m->z4[1 + (j & 1)], f);
+    la.w = a.w;
+    std::memcpy(la.c, m->c, sizeof(la.c));
+    CK_TRY(launch_ot4_lap(la, t, m->K, utype, st));
+    Ot4AdjArgs aa{};
+    aa.a = a;
+    aa.zl = la.z0;
+    aa.zu = la.z1;
+    aa.zu_next = j < m->g.nt ? org(m->z4[1 + ((j + 1) & 1)], f) : nullptr;
+    std::memcpy(aa.c12, m->c12, sizeof(aa.c12));
+    CK_TRY(launch_ot4_adj(aa, t, m->K, utype, st));
+    return CKFWI_OK;
+}
+
 // One forward step n of every lane: u -> out, optionally sampling d^n and
 // writing a fused takeshot (ck, ck_u, ck_up).
 int fwd_step(Ctx& cx, const Role& u, const Role& up, const Role& out, int n, bool record, int ck,
@@ -742,7 +794,10 @@ int fwd_step(Ctx& cx, const Role& u, const Role& up, const Role& out, int n, boo
             continue;
         }
         const int tok = cx.begin(PC_FWD);
-        if (m->tf.ver == 2 && in_host(m, u)) {
+        if (m->tf.ver == 5) {
+            ST_TRY(ot4_fwd_step(m, a, m->tf, ck, cx.st));
+            ++cx.launches;
+        } else if (m->tf.ver == 2 && in_host(m, u)) {
             CK_TRY(launch_fwd(a, host_tile(m), m->K, ck, cx.st));
         } else if (m->tf.ver == 4) {
             CK_TRY(launch_fwd4(a, m->tf, m->K, ck, cx.st));
@@ -794,7 +849,10 @@ int adj_step(Ctx& cx, const Role& l1, const Role& l2, const Role& l0, const Role
             continue;
         }
         const int tok = cx.begin(PC_ADJ);
-        if (m->ta.ver == 2 && in_host(m, u)) {
+        if (m->ta.ver == 5) {
+            ST_TRY(ot4_adj_step(m, a, m->ta, utype, j, cx.st));
+            ++cx.launches;
+        } else if (m->ta.ver == 2 && in_host(m, u)) {
             CK_TRY(launch_adj(a, host_tile(m), m->K, utype, cx.st));
         } else if (m->ta.ver == 4) {
             CK_TRY(launch_adj4(a, m->ta, m->K, utype, cx.st));
@@ -905,14 +963,21 @@ int autotune(ckfwi_model* m, cudaStream_t st)
         }
         return zl;
     };
-    for (int i = 0; i < tile_count(f.dims); ++i) {
+    // the OT4 kernel has its own two-pass kernels, tried alone
+    for (int i = 0; m->ot == 4 && i < ot4_shape_count(f.dims); ++i) {
+        const Tile t0 = ot4_tile_at(f.dims, i, f.nz);
+        if (!ot4_supported(f.dims, m->K, t0)) continue;
+        const long long cols = (long long)((f.nx + t0.bx - 1) / t0.bx) * (f.dims == 3 ? (f.ny + t0.by - 1) / t0.by : 1);
+        for (int z : zlens(cols)) cands.push_back(ot4_tile_at(f.dims, i, z));
+    }
+    for (int i = 0; m->ot == 2 && i < tile_count(f.dims); ++i) {
         Tile t0 = tile_at(f.dims, i, f.nz);
         if (!tile_supported(f.dims, m->K, t0)) continue;
         const long long cols = (long long)((f.nx + t0.bx - 1) / t0.bx) * (f.dims == 3 ? (f.ny + t0.by - 1) / t0.by : 1);
         for (int z : zlens(cols)) cands.push_back(tile_at(f.dims, i, z));
     }
     // vector-blocked kernels (3D)
-    if (f.dims == 3 && v3_fits(f, m->K)) {
+    if (m->ot == 2 && f.dims == 3 && v3_fits(f, m->K)) {
         for (int i = 0; i < v3_shape_count(); ++i) {
             const Tile t0 = v3_tile_at(i, f.nz);
             if (!v3_supported(f.dims, m->K, t0)) continue;
@@ -928,7 +993,7 @@ int autotune(ckfwi_model* m, cudaStream_t st)
     const bool tma_ok = encode_fn() != nullptr;
     // TMA kernels run a persistent grid; their zlen field is the CTAs per SM
     for (int ty : {8, 16}) {
-        if (!tma_ok || !tma_supported(f.dims, m->K, ty)) continue;
+        if (m->ot != 2 || !tma_ok || !tma_supported(f.dims, m->K, ty)) continue;
         for (int per_sm : {1, 2, 3}) {
             Tile t;
             t.bx = 64;
@@ -961,7 +1026,10 @@ int autotune(ckfwi_model* m, cudaStream_t st)
     const int reps = 3;
     CUtensorMap tm_u, tm_l;
     auto go = [&](const Tile& t, int pass) -> int {
-        if (t.ver == 4) {
+        if (t.ver == 5) {
+            if (pass == 0) ST_TRY(ot4_fwd_step(m, a, t, CK_NONE, st));
+            else ST_TRY(ot4_adj_step(m, b, t, U_FP32, m->g.nt, st));
+        } else if (t.ver == 4) {
             if (pass == 0) CK_TRY(launch_fwd4(a, t, m->K, CK_NONE, st));
             else CK_TRY(launch_adj4(b, t, m->K, U_FP32, st));
         } else if (t.ver == 3) {
@@ -988,7 +1056,9 @@ int autotune(ckfwi_model* m, cudaStream_t st)
         if (nf < 4 || u.zlen < 1) return false;
         if (nf < 5) u.vec = 1;
         if (nf < 6) u.pf = 0;
-        const bool okv = u.ver == 4   ? v4_supported(f.dims, m->K, u) && v3_fits(f, m->K)
+        if ((u.ver == 5) != (m->ot == 4)) return false;
+        const bool okv = u.ver == 5   ? ot4_supported(f.dims, m->K, u)
+                         : u.ver == 4 ? v4_supported(f.dims, m->K, u) && v3_fits(f, m->K)
                          : u.ver == 3 ? v3_supported(f.dims, m->K, u) && v3_fits(f, m->K)
                          : u.ver == 2 ? (tma_ok && u.bx == 64 && tma_supported(f.dims, m->K, u.by))
                                       : tile_supported(f.dims, m->K, u);
@@ -1057,6 +1127,8 @@ int autotune(ckfwi_model* m, cudaStream_t st)
         CK_TRY(cudaMemsetAsync(m->lam[i].p, 0, m->lam[i].bytes, st));
     }
     CK_TRY(cudaMemsetAsync(m->gacc.p, 0, m->gacc.bytes, st));
+    for (int i = 0; i < 3; ++i)
+        if (m->z4[i].p) CK_TRY(cudaMemsetAsync(m->z4[i].p, 0, m->z4[i].bytes, st));
     CK_TRY(cudaStreamSynchronize(st));
     m->tuned = true;
     return CKFWI_OK;
@@ -1945,6 +2017,7 @@ int ensure_clones(ckfwi_model* m, int k, cudaStream_t st)
 // CKFWI_MAX_LANES (default 64) and by the shot count.
 int batch_width(ckfwi_model* m, int nshots, const ckfwi_grad_opts* o)
 {
+    if (m->ot == 4) return 1;     // the OT4 kernels have no batched form: one shot at a time
     int cap = 64;
     if (const char* v = std::getenv("CKFWI_MAX_LANES")) cap = std::max(1, std::atoi(v));
     const RunCfg rc = run_cfg(m->g.nt, o);
@@ -1979,6 +2052,8 @@ int ckfwi_create_model(const ckfwi_grid* g, ckfwi_model** out)
     const double ih2 = 1.0 / (g->h * g->h);
     m->c[0] = 0.0f;   // the difference-form Laplacian needs c_j, j >= 1, only
     for (int j = 1; j <= m->K; ++j) m->c[j] = (float)(c[j] * ih2);
+    m->ot = g->time_order == 4 ? 4 : 2;
+    for (int j = 1; j <= m->K; ++j) m->c12[j] = (float)(c[j] * ih2 / 12.0);
     m->hdt = (float)(g->dt / 2.0);
     const FieldGeom& f = m->fg;
     std::vector<float> eta((size_t)f.nz + f.ny + f.nx);
@@ -1996,6 +2071,8 @@ int ckfwi_create_model(const ckfwi_grid* g, ckfwi_model** out)
         CK_TRY(m->lam[i].alloc(field_bytes(f)));
     }
     CK_TRY(m->gacc.alloc(field_bytes(f)));
+    if (m->ot == 4)
+        for (int i = 0; i < 3; ++i) CK_TRY(m->z4[i].alloc(field_bytes(f)));   // halos stay zero
     CK_TRY(m->flags.alloc(sizeof(int) * 8));
     CK_TRY(m->phi.alloc(sizeof(double) * 2));
     CK_TRY(m->partials.alloc(sizeof(double) * m->nparts));
@@ -2217,6 +2294,7 @@ int ckfwi_batch_gradient_models(ckfwi_model* const* models, const ckfwi_shot* sh
     for (int l = 0; l < nshots; ++l) {
         ckfwi_model* L = models[l];
         if (!L || !L->have_model || !seen.insert(L).second) return CKFWI_EINVAL;
+        if (L->ot == 4 && nshots > 1) return CKFWI_EINVAL;   // OT4 has no batched kernels
         lanes[l] = L;
         const FieldGeom& f = L->fg;
         const int n3[3] = {f.nz, f.ny, f.nx};

@@ -88,6 +88,34 @@ struct AdjArgs {
     int* err;             // error flags (bit 3: a bounded wait ran out)
 };
 
+// OT4 kernel (Sec. 6): a step is two passes, Z = w lap f and then the
+// leapfrog update with w A f = Z + w lap(Z) / 12 (ot4.cu).
+struct Ot4LapArgs {
+    FieldGeom g;
+    const float* f0;      // u^n (forward) or lam^j (reverse)
+    const void* f1;       // reverse: u^{j-1}, element type per launch; forward: null
+    float* z0;            // w lap f0
+    float* z1;            // w lap f1
+    const float* w;
+    float c[MAXK + 1];
+    int zlen;
+    Sample smp;           // forward: receiver sampling of u^n
+};
+
+struct Ot4FwdArgs {
+    FwdArgs f;            // as OT2 (c unused)
+    const float* z;       // w lap u^n
+    float c12[MAXK + 1];  // c_j / (12 h^2)
+};
+
+struct Ot4AdjArgs {
+    AdjArgs a;            // as OT2 (c: lap u^{j-1})
+    const float* zl;      // w lap lam^j
+    const float* zu;      // w lap u^{j-1}
+    const float* zu_next; // w lap u^j from the previous reverse step; null at j = N
+    float c12[MAXK + 1];
+};
+
 enum CkMode { CK_NONE = 0, CK_FP32 = 1, CK_BF16 = 2, CK_FP16 = 3 };
 enum UType { U_FP32 = 0, U_BF16 = 1, U_FP16 = 2 };
 
@@ -96,7 +124,7 @@ struct Tile {
     int zlen;             // ver 1, 3: z planes per CTA; ver 2: CTAs per SM of the persistent grid
     int ver = 1;          // 1: register-queue kernels, 2: TMA-fed kernels (3D, orders 2-8),
                           // 3: vector-blocked kernels (3D), 4: vector-blocked forward step fed
-                          // by asynchronous copies (3D)
+                          // by asynchronous copies (3D), 5: the two-pass OT4 kernels
     int vec = 1;          // ver 3, 4: x points per thread (2 or 4)
     int pf = 0;           // ver 4: planes of prefetch (0 = the default, 2)
 };
@@ -137,6 +165,14 @@ cudaError_t launch_adj4(const AdjArgs& a, const Tile& t, int K, int ut, cudaStre
 // batch_v3.cu (every lane's geometry must pass v3_fits)
 cudaError_t launch_fwd3_batch(const BatchLaunch<FwdArgs>& b, const Tile& t, int K, int ck, cudaStream_t s);
 cudaError_t launch_adj3_batch(const BatchLaunch<AdjArgs>& b, const Tile& t, int K, int ut, cudaStream_t s);
+
+// ot4.cu
+bool ot4_supported(int dims, int K, const Tile& t);
+int ot4_shape_count(int dims);
+Tile ot4_tile_at(int dims, int i, int zlen);
+cudaError_t launch_ot4_lap(const Ot4LapArgs& a, const Tile& t, int K, int ut, cudaStream_t s);
+cudaError_t launch_ot4_fwd(const Ot4FwdArgs& a, const Tile& t, int K, int ck, cudaStream_t s);
+cudaError_t launch_ot4_adj(const Ot4AdjArgs& a, const Tile& t, int K, int ut, cudaStream_t s);
 
 // stencil_tma.cu (CUtensorMap comes from <cuda.h>)
 }  // namespace ckfwi

@@ -30,7 +30,8 @@ class Case:
         return O.ricker(self.og.nt, self.og.dt, self.f0, self.t0)
 
 
-def make_case(dims, so, shape, nbl, nt, h=10.0, dt=None, seed=0, vmin=1.5, vmax=3.0, f0=None, nrec=None):
+def make_case(dims, so, shape, nbl, nt, h=10.0, dt=None, seed=0, vmin=1.5, vmax=3.0, f0=None, nrec=None,
+              time_order=2):
     if dt is None:
         dt = 1.0 if so <= 4 else 0.8
     vel = synth.grf(shape, 3.0, seed, vmin, vmax).astype(np.float32)
@@ -45,8 +46,8 @@ def make_case(dims, so, shape, nbl, nt, h=10.0, dt=None, seed=0, vmin=1.5, vmax=
     if f0 is None:
         f0 = vmin / (2.5 * 5 * h)          # >= 5 points per wavelength at 2.5 f0 [kHz]
     t0 = min(1.5 / f0, 0.45 * nt * dt)
-    og = O.Grid(dims, tuple(shape), nbl, h, so, dt, nt, vmax)
-    pg = C.GridSpec(dims, tuple(shape), nbl, h, so, dt, nt, vmax)
+    og = O.Grid(dims, tuple(shape), nbl, h, so, dt, nt, vmax, time_order=time_order)
+    pg = C.GridSpec(dims, tuple(shape), nbl, h, so, dt, nt, vmax, time_order=time_order)
     return Case(og, pg, vel, src, np.asarray(rec, dtype=np.float64), f0, t0)
 
 

@@ -728,13 +728,15 @@ int ot4_fwd_step(ckfwi_model* m, const FwdArgs& a, const Tile& t, int ck, cudaSt
     la.w = a.w;
     std::memcpy(la.c, m->c, sizeof(la.c));
     la.smp = a.smp;
-    CK_TRY(launch_ot4_lap(la, t, m->K, U_FP32, st));
+    if (t.ver == 6) CK_TRY(launch_ot4v_lap(la, t, m->K, U_FP32, st));
+    else CK_TRY(launch_ot4_lap(la, t, m->K, U_FP32, st));
     Ot4FwdArgs fa{};
     fa.f = a;
     fa.f.smp = Sample{};
     fa.z = la.z0;
     std::memcpy(fa.c12, m->c12, sizeof(fa.c12));
-    CK_TRY(launch_ot4_fwd(fa, t, m->K, ck, st));
+    if (t.ver == 6) CK_TRY(launch_ot4v_fwd(fa, t, m->K, ck, st));
+    else CK_TRY(launch_ot4_fwd(fa, t, m->K, ck, st));
     return CKFWI_OK;
 }
 
@@ -749,14 +751,16 @@ int ot4_adj_step(ckfwi_model* m, const AdjArgs& a, const Tile& t, int utype, int
     la.z1 = org(m->z4[1 + (j & 1)], f);
     la.w = a.w;
     std::memcpy(la.c, m->c, sizeof(la.c));
-    CK_TRY(launch_ot4_lap(la, t, m->K, utype, st));
+    if (t.ver == 6) CK_TRY(launch_ot4v_lap(la, t, m->K, utype, st));
+    else CK_TRY(launch_ot4_lap(la, t, m->K, utype, st));
     Ot4AdjArgs aa{};
     aa.a = a;
     aa.zl = la.z0;
     aa.zu = la.z1;
     aa.zu_next = j < m->g.nt ? org(m->z4[1 + ((j + 1) & 1)], f) : nullptr;
     std::memcpy(aa.c12, m->c12, sizeof(aa.c12));
-    CK_TRY(launch_ot4_adj(aa, t, m->K, utype, st));
+    if (t.ver == 6) CK_TRY(launch_ot4v_adj(aa, t, m->K, utype, st));
+    else CK_TRY(launch_ot4_adj(aa, t, m->K, utype, st));
     return CKFWI_OK;
 }
 
@@ -794,7 +798,7 @@ int fwd_step(Ctx& cx, const Role& u, const Role& up, const Role& out, int n, boo
             continue;
         }
         const int tok = cx.begin(PC_FWD);
-        if (m->tf.ver == 5) {
+        if (m->tf.ver >= 5) {
             ST_TRY(ot4_fwd_step(m, a, m->tf, ck, cx.st));
             ++cx.launches;
         } else if (m->tf.ver == 2 && in_host(m, u)) {
@@ -849,7 +853,7 @@ int adj_step(Ctx& cx, const Role& l1, const Role& l2, const Role& l0, const Role
             continue;
         }
         const int tok = cx.begin(PC_ADJ);
-        if (m->ta.ver == 5) {
+        if (m->ta.ver >= 5) {
             ST_TRY(ot4_adj_step(m, a, m->ta, utype, j, cx.st));
             ++cx.launches;
         } else if (m->ta.ver == 2 && in_host(m, u)) {
@@ -970,6 +974,22 @@ int autotune(ckfwi_model* m, cudaStream_t st)
         const long long cols = (long long)((f.nx + t0.bx - 1) / t0.bx) * (f.dims == 3 ? (f.ny + t0.by - 1) / t0.by : 1);
         for (int z : zlens(cols)) cands.push_back(ot4_tile_at(f.dims, i, z));
     }
+    if (m->ot == 4 && f.dims == 3 && v3_fits(f, m->K)) {
+        for (int vec : {4, 2}) {
+            Tile t0;
+            t0.ver = 6;
+            t0.bx = 32;
+            t0.by = 16;
+            t0.vec = vec;
+            t0.zlen = f.nz;
+            if (!ot4v_supported(f.dims, m->K, t0, false)) continue;
+            const long long cols = (long long)((f.nx + 31) / 32) * ((f.ny + 15) / 16);
+            for (int z : zlens(cols)) {
+                t0.zlen = z;
+                cands.push_back(t0);
+            }
+        }
+    }
     for (int i = 0; m->ot == 2 && i < tile_count(f.dims); ++i) {
         Tile t0 = tile_at(f.dims, i, f.nz);
         if (!tile_supported(f.dims, m->K, t0)) continue;
@@ -1026,7 +1046,7 @@ int autotune(ckfwi_model* m, cudaStream_t st)
     const int reps = 3;
     CUtensorMap tm_u, tm_l;
     auto go = [&](const Tile& t, int pass) -> int {
-        if (t.ver == 5) {
+        if (t.ver >= 5) {
             if (pass == 0) ST_TRY(ot4_fwd_step(m, a, t, CK_NONE, st));
             else ST_TRY(ot4_adj_step(m, b, t, U_FP32, m->g.nt, st));
         } else if (t.ver == 4) {
@@ -1048,7 +1068,7 @@ int autotune(ckfwi_model* m, cudaStream_t st)
         return CKFWI_OK;
     };
     // a forced tile (CKFWI_TILE_FWD / CKFWI_TILE_ADJ = "ver,bx,by,zlen[,vec]") skips the search
-    auto forced = [&](const char* name, Tile* t) {
+    auto forced = [&](const char* name, Tile* t, bool reverse) {
         const char* v = std::getenv(name);
         if (!v) return false;
         Tile u;
@@ -1056,8 +1076,9 @@ int autotune(ckfwi_model* m, cudaStream_t st)
         if (nf < 4 || u.zlen < 1) return false;
         if (nf < 5) u.vec = 1;
         if (nf < 6) u.pf = 0;
-        if ((u.ver == 5) != (m->ot == 4)) return false;
-        const bool okv = u.ver == 5   ? ot4_supported(f.dims, m->K, u)
+        if ((u.ver >= 5) != (m->ot == 4)) return false;
+        const bool okv = u.ver == 6   ? ot4v_supported(f.dims, m->K, u, reverse) && v3_fits(f, m->K)
+                         : u.ver == 5 ? ot4_supported(f.dims, m->K, u)
                          : u.ver == 4 ? v4_supported(f.dims, m->K, u) && v3_fits(f, m->K)
                          : u.ver == 3 ? v3_supported(f.dims, m->K, u) && v3_fits(f, m->K)
                          : u.ver == 2 ? (tma_ok && u.bx == 64 && tma_supported(f.dims, m->K, u.by))
@@ -1066,7 +1087,7 @@ int autotune(ckfwi_model* m, cudaStream_t st)
         *t = u;
         return true;
     };
-    const bool ff = forced("CKFWI_TILE_FWD", &m->tf), fa = forced("CKFWI_TILE_ADJ", &m->ta);
+    const bool ff = forced("CKFWI_TILE_FWD", &m->tf, false), fa = forced("CKFWI_TILE_ADJ", &m->ta, true);
     const bool verbose = std::getenv("CKFWI_VERBOSE") != nullptr;
     // time one candidate: the median of `rounds` timings of `reps` launches
     auto time_of = [&](const Tile& t, int pass, int rounds, float* out) -> int {
@@ -1095,6 +1116,8 @@ int autotune(ckfwi_model* m, cudaStream_t st)
         // more rounds (single timings of ~100 us launches vary by several %)
         std::vector<std::pair<float, size_t>> t1;
         for (size_t i = 0; i < cands.size(); ++i) {
+            // vector-blocked OT4 reverse steps come in one vector width only
+            if (cands[i].ver == 6 && !ot4v_supported(f.dims, m->K, cands[i], pass == 1)) continue;
             ST_TRY(go(cands[i], pass));
             float ms = 0;
             ST_TRY(time_of(cands[i], pass, 3, &ms));

@@ -124,7 +124,8 @@ struct Tile {
     int zlen;             // ver 1, 3: z planes per CTA; ver 2: CTAs per SM of the persistent grid
     int ver = 1;          // 1: register-queue kernels, 2: TMA-fed kernels (3D, orders 2-8),
                           // 3: vector-blocked kernels (3D), 4: vector-blocked forward step fed
-                          // by asynchronous copies (3D), 5: the two-pass OT4 kernels
+                          // by asynchronous copies (3D), 5: the two-pass OT4 kernels,
+                          // 6: the same vector-blocked (3D)
     int vec = 1;          // ver 3, 4: x points per thread (2 or 4)
     int pf = 0;           // ver 4: planes of prefetch (0 = the default, 2)
 };
@@ -173,6 +174,12 @@ Tile ot4_tile_at(int dims, int i, int zlen);
 cudaError_t launch_ot4_lap(const Ot4LapArgs& a, const Tile& t, int K, int ut, cudaStream_t s);
 cudaError_t launch_ot4_fwd(const Ot4FwdArgs& a, const Tile& t, int K, int ck, cudaStream_t s);
 cudaError_t launch_ot4_adj(const Ot4AdjArgs& a, const Tile& t, int K, int ut, cudaStream_t s);
+// ot4_v3.cu: the same passes vector-blocked (3D, geometry must pass v3_fits;
+// reverse steps vec 2 only)
+bool ot4v_supported(int dims, int K, const Tile& t, bool reverse);
+cudaError_t launch_ot4v_lap(const Ot4LapArgs& a, const Tile& t, int K, int ut, cudaStream_t s);
+cudaError_t launch_ot4v_fwd(const Ot4FwdArgs& a, const Tile& t, int K, int ck, cudaStream_t s);
+cudaError_t launch_ot4v_adj(const Ot4AdjArgs& a, const Tile& t, int K, int ut, cudaStream_t s);
 
 // stencil_tma.cu (CUtensorMap comes from <cuda.h>)
 }  // namespace ckfwi

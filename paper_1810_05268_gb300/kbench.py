@@ -23,18 +23,19 @@ def main():
     ap.add_argument("--h", type=float, default=15.0)
     ap.add_argument("--tol", type=float, default=1e-4)
     ap.add_argument("--reps", type=int, default=3)
+    ap.add_argument("--time-order", type=int, default=2, help="2: OT2 kernel, 4: OT4 kernel")
     args = ap.parse_args()
     build.build()
     shape = tuple(int(v) for v in args.shape.split(","))
     nbl = 20
     vel = synth.extend(synth.grf(tuple(n - 2 * nbl for n in shape), 8.0, 5, 1.5, 4.5), nbl).astype(np.float32)
-    grid = C.GridSpec(3, shape, nbl, args.h, args.so, 1.0, args.nt, 4.5)
+    grid = C.GridSpec(3, shape, nbl, args.h, args.so, 1.0, args.nt, 4.5, time_order=args.time_order)
     ext = [(n - 2 * nbl - 1) * args.h for n in shape]
     rec = synth.receiver_grid(2 * args.h, np.linspace(0, ext[1], 32), np.linspace(0, ext[2], 32))
     shot = C.ShotSpec(src=(2 * args.h, ext[1] / 2, ext[2] / 2), rec=rec, f0=0.02, t0=25.0)
     m = C.Model(grid)
     m.set_model(torch.from_numpy(vel).cuda())
-    out = {"shape": shape, "so": args.so, "nt": args.nt}
+    out = {"shape": shape, "so": args.so, "nt": args.nt, "time_order": args.time_order}
     for _ in range(args.reps):
         d = m.forward_shot(shot)
     torch.cuda.synchronize()
@@ -48,8 +49,12 @@ def main():
     out["fwd_us"] = st["fwd_ms"] * 1e3 / st["fwd_launches"]
     out["adj_us"] = st["adj_ms"] * 1e3 / st["adj_launches"]
     npts = int(np.prod(shape))
-    out["fwd_gbs"] = 16 * npts / (out["fwd_us"] * 1e-6) / 1e9
-    out["adj_gbs"] = 28 * npts / (out["adj_us"] * 1e-6) / 1e9
+    # algorithmic bytes per point of a step (OT4: both passes)
+    fb, ab = (32, 60) if args.time_order == 4 else (16, 28)
+    out["fwd_gbs"] = fb * npts / (out["fwd_us"] * 1e-6) / 1e9
+    out["adj_gbs"] = ab * npts / (out["adj_us"] * 1e-6) / 1e9
+    out["fwd_kernel"] = [st["fwd_ver"], st["fwd_bx"], st["fwd_by"], st["fwd_zlen"]]
+    out["adj_kernel"] = [st["adj_ver"], st["adj_bx"], st["adj_by"], st["adj_zlen"]]
     # codec on a wavefield-like field: the last forward state of the shot
     x = torch.from_numpy((vel - vel.mean()) * 1e-2).cuda()
     for _ in range(args.reps):

@@ -42,6 +42,10 @@ def lib():
             L.codec_decompress.argtypes = [i, i, i, i, P, ctypes.c_size_t, P]
             L.codec_bound_words.argtypes = [i, i, i, i]
             L.codec_bound_words.restype = ctypes.c_longlong
+            L.codec_compress_rate.argtypes = [i, i, i, i, P, i, P, ctypes.c_size_t, P]
+            L.codec_compress_rate.restype = ctypes.c_longlong
+            L.codec_rate_words.argtypes = [i, i, i, i, i]
+            L.codec_rate_words.restype = ctypes.c_longlong
             for f in ("ora_fd_weights", "ora_laplacian", "ora_damping", "ora_ricker",
                       "ora_interp", "ora_forward", "ora_step", "ora_adjoint", "ora_gradient",
                       "codec_decompress"):

@@ -1,4 +1,5 @@
-"""Fixed-accuracy 4^d block-transform codec (test infrastructure only).
+"""Fixed-accuracy and fixed-rate 4^d block-transform codec (test
+infrastructure only).
 
 numpy front end of codec_oracle.c, whose header holds the full
 specification.  The paper stores checkpoints with ZFP's fixed-tolerance
@@ -40,6 +41,30 @@ def compress(x, tol):
                              out.ctypes.data_as(ctypes.c_void_p), cap, ctypes.byref(flags))
     if n < 0:
         raise ValueError("codec_compress: %s" % STATUS.get(int(n), n))
+    return out[:n].copy(), bool(flags.value)
+
+
+def rate_words(shape, dims, rate):
+    """Words of a fixed-rate stream: 16 + nblocks * ceil(rate * 4^dims / 32)."""
+    nz, ny, nx = (shape if dims == 3 else (shape[0], 1, shape[1]))
+    return int(lib().codec_rate_words(dims, nz, ny, nx, int(rate)))
+
+
+def compress_rate(x, rate):
+    """Fixed-rate compression (rate bits per value, 1..32); returns
+    (stream uint32 array, nonfinite flag)."""
+    x = np.ascontiguousarray(np.asarray(x, dtype=np.float32))
+    dims = x.ndim
+    nz, ny, nx = _shape3(x, dims)
+    cap = rate_words(x.shape, dims, rate)
+    if cap < 0:
+        raise ValueError("codec_rate_words: %s" % STATUS.get(int(cap), cap))
+    out = np.zeros(cap, dtype=np.uint32)
+    flags = ctypes.c_int(0)
+    n = lib().codec_compress_rate(dims, nz, ny, nx, x.ctypes.data_as(ctypes.c_void_p), int(rate),
+                                  out.ctypes.data_as(ctypes.c_void_p), cap, ctypes.byref(flags))
+    if n < 0:
+        raise ValueError("codec_compress_rate: %s" % STATUS.get(int(n), n))
     return out[:n].copy(), bool(flags.value)
 
 

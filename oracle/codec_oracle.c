@@ -82,6 +82,7 @@
 #endif
 #define CODEC_HDR_WORDS 16
 #define CHUNK_BLOCKS 32
+#define CODEC_RATE_VERSION 2u   /* fixed-rate streams (see "fixed-rate mode" below) */
 
 enum { C_OK = 0, C_EINVAL = -1, C_ENOMEM = -2, C_OVERFLOW = -3, C_CORRUPT = -4 };
 
@@ -107,6 +108,8 @@ static int geom_init(cgeom* G, int dims, int nz, int ny, int nx)
 }
 
 static int max_block_bits(const cgeom* G) { return 2 + 32 * G->V; }
+
+static int decompress_rate(const cgeom* G, const uint32_t* in, size_t nwords, float* x);
 
 static long table_words(const cgeom* G) { return CODEC_HDR_WORDS + G->nchunks + (G->nblocks + 1) / 2; }
 
@@ -471,6 +474,12 @@ int codec_decompress(int dims, int nz, int ny, int nx, const uint32_t* in, size_
 {
     cgeom G;
     if (geom_init(&G, dims, nz, ny, nx) != C_OK || !in || !x) return C_EINVAL;
+    if (nwords >= CODEC_HDR_WORDS && in[0] == CODEC_MAGIC && in[1] == ((uint32_t)dims | (CODEC_RATE_VERSION << 8))) {
+        if (in[2] != (uint32_t)nz || in[3] != (uint32_t)ny || in[4] != (uint32_t)nx ||
+            in[5] != (uint32_t)G.nblocks)
+            return C_CORRUPT;
+        return decompress_rate(&G, in, nwords, x);
+    }
     const long tw = table_words(&G);
     if ((long)nwords < tw) return C_CORRUPT;
     if (in[0] != CODEC_MAGIC || in[1] != ((uint32_t)dims | (CODEC_VERSION << 8)) ||
@@ -535,6 +544,206 @@ int codec_block_stats(int dims, int nz, int ny, int nx, const uint32_t* in, size
             }
             pos += sz;
         }
+    }
+    return C_OK;
+}
+
+
+/* ---------- fixed-rate mode ----------
+ * Sec. 2.2 lists ZFP's fixed-rate mode beside fixed tolerance: a guaranteed
+ * size and no bound on the error.  This codec's fixed-rate mode:
+ *   rate R bits per value, 1 <= R <= 32.  Every block occupies exactly
+ *   W = ceil(R V / 32) words, a budget of 32 W bits, so a field takes
+ *   16 + nblocks W words whatever its values.
+ * Per block, bits LSB first from the block's first word:
+ *   0                        all values are +-0, or a value is not finite
+ *                            (flag NONFINITE), or Emax < -100 (every value
+ *                            below 2^-99 in magnitude is flushed to zero);
+ *                            the rest of the budget is zero;
+ *   1, Emax+127 (8), ptop (5), then planes ptop, ptop-1, ..., 0, each coded
+ *                            exactly as step 7 of the fixed-accuracy mode
+ *                            (verbatim bits of the s significant
+ *                            coefficients, then group tests), until the
+ *                            budget is full: the first bit that does not fit
+ *                            is dropped and coding stops.
+ * Steps 2-5 (Emax, integers, lifting, order, negabinary) are the
+ * fixed-accuracy mode's.  The decoder reads the same bits and stops at the
+ * budget; a plane cut short keeps the bits read, all later bits are zero;
+ * x_hat = float(i_hat) * 2^(Emax-23).  A longer budget extends a block's
+ * bits and never changes the ones a shorter budget kept (the code is
+ * embedded).
+ * Container: the header of the fixed-accuracy mode with version 2 and
+ * [7] = nblocks W, [8] = R; blocks back to back after the header, no chunk
+ * or size table.
+ */
+#define RATE_EMIN (-100)
+
+static long rate_block_words(const cgeom* G, int rate) { return ((long)rate * G->V + 31) / 32; }
+
+long long codec_rate_words(int dims, int nz, int ny, int nx, int rate)
+{
+    cgeom G;
+    if (geom_init(&G, dims, nz, ny, nx) != C_OK || rate < 1 || rate > 32) return C_EINVAL;
+    return CODEC_HDR_WORDS + G.nblocks * rate_block_words(&G, rate);
+}
+
+/* append the n low bits of v while they fit in the budget; 0 once it is full */
+static int put_budget(bitw* B, long end, uint32_t v, int n)
+{
+    for (int k = 0; k < n; ++k) {
+        if (B->pos >= end) return 0;
+        put_bit(B, (v >> k) & 1u);
+    }
+    return 1;
+}
+
+static void encode_block_rate(const cgeom* G, const int* perm, const float* v, long budget, bitw* B,
+                              int* nonfinite)
+{
+    const int V = G->V;
+    const long end = B->pos + budget;
+    int bad = 0, any = 0;
+    for (int i = 0; i < V; ++i) {
+        if (!isfinite(v[i])) bad = 1;
+        if ((bits_of_f(v[i]) & 0x7FFFFFFFu) != 0) any = 1;
+    }
+    if (bad) *nonfinite = 1;
+    int emax = -1000;
+    for (int i = 0; i < V; ++i) {
+        uint32_t u = bits_of_f(v[i]);
+        if ((u & 0x7FFFFFFFu) == 0) continue;
+        int be = (int)((u >> 23) & 0xFF);
+        int e = (be > 0 ? be : 1) - 127;
+        if (e > emax) emax = e;
+    }
+    if (bad || !any || emax < RATE_EMIN) { put_bit(B, 0); B->pos = end; return; }
+    int32_t cf[64];
+    for (int i = 0; i < V; ++i) {
+        uint32_t u = bits_of_f(v[i]);
+        int be = (int)((u >> 23) & 0xFF);
+        uint32_t M = (u & 0x7FFFFFu) | (be > 0 ? 0x800000u : 0u);
+        int e = (be > 0 ? be : 1) - 127;
+        int sh = emax - e;
+        uint32_t mag = (sh >= 32) ? 0u : (M >> sh);
+        if ((u & 0x7FFFFFFFu) == 0) mag = 0;
+        cf[i] = (u >> 31) ? -(int32_t)mag : (int32_t)mag;
+    }
+    fwd_xform(cf, G->dims);
+    uint32_t nb[64], orall = 0;
+    for (int r = 0; r < V; ++r) { nb[r] = to_nega(cf[perm[r]]); orall |= nb[r]; }
+    int ptop = 31;
+    while (ptop > 0 && !((orall >> ptop) & 1u)) --ptop;
+    int ok = put_budget(B, end, 1, 1) && put_budget(B, end, (uint32_t)(emax + 127), 8) &&
+             put_budget(B, end, (uint32_t)ptop, 5);
+    int s = 0;
+    for (int p = ptop; p >= 0 && ok; --p) {
+        uint32_t plane[64];
+        for (int r = 0; r < V; ++r) plane[r] = (nb[r] >> p) & 1u;
+        for (int r = 0; r < s && ok; ++r) ok = put_budget(B, end, plane[r], 1);
+        while (ok && s < V) {
+            uint32_t a = 0;
+            for (int r = s; r < V; ++r) a |= plane[r];
+            ok = put_budget(B, end, a, 1);
+            if (!ok || !a) break;
+            for (;;) {
+                uint32_t bit = plane[s];
+                ok = put_budget(B, end, bit, 1);
+                if (!ok) break;
+                ++s;
+                if (bit) break;
+            }
+        }
+    }
+    B->pos = end;
+}
+
+/* read one bit if the budget has room; *more = 0 once it is exhausted */
+static uint32_t get_budget(bitr* B, int* more)
+{
+    if (!*more || B->pos >= B->end) { *more = 0; return 0; }
+    return get_bit(B);
+}
+
+static void decode_block_rate(const cgeom* G, const int* perm, bitr* B, float* v)
+{
+    const int V = G->V;
+    int more = 1;
+    if (!get_budget(B, &more)) {
+        for (int i = 0; i < V; ++i) v[i] = 0.0f;
+        return;
+    }
+    uint32_t e8 = 0, pt = 0;
+    for (int k = 0; k < 8; ++k) e8 |= get_budget(B, &more) << k;
+    for (int k = 0; k < 5; ++k) pt |= get_budget(B, &more) << k;
+    const int emax = (int)e8 - 127;
+    uint32_t nb[64];
+    for (int r = 0; r < V; ++r) nb[r] = 0;
+    int s = 0;
+    for (int p = (int)pt; p >= 0 && more; --p) {
+        for (int r = 0; r < s && more; ++r) nb[r] |= get_budget(B, &more) << p;
+        while (more && s < V) {
+            if (!get_budget(B, &more)) break;
+            while (more && s < V) {
+                uint32_t bit = get_budget(B, &more);
+                if (!more) break;
+                nb[s] |= bit << p;
+                ++s;
+                if (bit) break;
+            }
+        }
+    }
+    int32_t tr[64];
+    for (int r = 0; r < V; ++r) tr[perm[r]] = from_nega(nb[r]);
+    inv_xform(tr, G->dims);
+    /* emax >= -100 for a coded block, so the scale is a normal float */
+    const float sc = pow2f(emax - 23 < -126 ? -126 : emax - 23);
+    for (int i = 0; i < V; ++i) v[i] = (float)tr[i] * sc;
+}
+
+/* Fixed-rate compression of x into out (cap words): returns the words used
+ * (always codec_rate_words), or < 0.  *flags: bit0 NONFINITE. */
+long long codec_compress_rate(int dims, int nz, int ny, int nx, const float* x, int rate, uint32_t* out,
+                              size_t cap, int* flags)
+{
+    cgeom G;
+    if (geom_init(&G, dims, nz, ny, nx) != C_OK || !x || !out || rate < 1 || rate > 32) return C_EINVAL;
+    const long W = rate_block_words(&G, rate);
+    const long total = CODEC_HDR_WORDS + G.nblocks * W;
+    if ((long)cap < total) return C_OVERFLOW;
+    memset(out, 0, sizeof(uint32_t) * total);
+    int perm[64];
+    sequency_order(dims, perm);
+    int nonfinite = 0;
+    float v[64];
+    for (long b = 0; b < G.nblocks; ++b) {
+        bitw B = {out + CODEC_HDR_WORDS + b * W, W * 32, 0, 0};
+        gather_block(&G, x, b, v);
+        encode_block_rate(&G, perm, v, W * 32, &B, &nonfinite);
+    }
+    out[0] = CODEC_MAGIC;
+    out[1] = (uint32_t)dims | (CODEC_RATE_VERSION << 8);
+    out[2] = (uint32_t)nz; out[3] = (uint32_t)ny; out[4] = (uint32_t)nx;
+    out[5] = (uint32_t)G.nblocks; out[6] = 0;
+    out[7] = (uint32_t)(G.nblocks * W);
+    out[8] = (uint32_t)rate;
+    out[9] = nonfinite ? 1u : 0u;
+    if (flags) *flags = nonfinite;
+    return total;
+}
+
+static int decompress_rate(const cgeom* G, const uint32_t* in, size_t nwords, float* x)
+{
+    const int rate = (int)in[8];
+    if (rate < 1 || rate > 32 || in[6] != 0) return C_CORRUPT;
+    const long W = rate_block_words(G, rate);
+    if (in[7] != (uint32_t)(G->nblocks * W) || CODEC_HDR_WORDS + G->nblocks * W > (long)nwords) return C_CORRUPT;
+    int perm[64];
+    sequency_order(G->dims, perm);
+    float v[64];
+    for (long b = 0; b < G->nblocks; ++b) {
+        bitr B = {in + CODEC_HDR_WORDS + b * W, W * 32, 0, 0};
+        decode_block_rate(G, perm, &B, v);
+        scatter_block(G, x, b, v);
     }
     return C_OK;
 }

@@ -91,6 +91,10 @@ extern "C" {
 #define CKFWI_STORE_BF16 1
 #define CKFWI_STORE_FP16 2
 #define CKFWI_STORE_CODEC 3
+/* the codec's fixed-rate mode (Sec. 2.2 lists ZFP's fixed-rate mode: a
+ * guaranteed size, no error bound): `rate` bits per value, every checkpoint
+ * the same predictable size (ckfwi_codec_rate_words) */
+#define CKFWI_STORE_CODEC_RATE 4
 
 /* model parameterisation of set_model / of the gradient */
 #define CKFWI_VELOCITY 0   /* c [km/s]; gradient dphi/dc */
@@ -144,6 +148,9 @@ typedef struct ckfwi_grad_opts {
                             slots, which Revolve writes and reads least, go
                             there.  0: every slot in device memory.  Values are
                             unchanged by the placement. */
+    int rate;            /* CODEC_RATE: bits per value, 1..32.  The pool holds
+                            exactly (M - 1) * 2 fixed-size streams; a non-zero
+                            pool_bytes below that is EINVAL. */
 } ckfwi_grad_opts;
 
 typedef struct ckfwi_stats {
@@ -270,6 +277,18 @@ CKFWI_API int ckfwi_revolve_schedule(int nt, int slots, int32_t* actions, long l
  * ckfwi_codec_decompress: stream (device) -> x (device).  Synchronous;
  *   CORRUPT if a check fails. */
 CKFWI_API long long ckfwi_codec_bound_words(int dims, int nz, int ny, int nx);
+/* Fixed-rate mode of the same codec (Sec. 2.2: ZFP's fixed-rate mode): rate
+ * bits per value, 1..32, every 4^d block exactly ceil(rate 4^d / 32) words.
+ * ckfwi_codec_rate_words: the stream length, 16 + nblocks * that (EINVAL for
+ *   a bad shape or rate).
+ * ckfwi_codec_compress_rate: as ckfwi_codec_compress (device buffers,
+ *   synchronous, *used_words and *flags on the host); POOL_OVERFLOW if cap
+ *   is below ckfwi_codec_rate_words.  No scratch memory.
+ * ckfwi_codec_decompress reads either mode's streams. */
+CKFWI_API long long ckfwi_codec_rate_words(int dims, int nz, int ny, int nx, int rate);
+CKFWI_API int ckfwi_codec_compress_rate(const float* x, int dims, int nz, int ny, int nx, int rate,
+                              uint32_t* out, long long cap, long long* used_words, int* flags,
+                              void* stream);
 CKFWI_API int ckfwi_codec_compress(const float* x, int dims, int nz, int ny, int nx, double tol,
                          uint32_t* out, long long cap, long long* used_words, int* flags,
                          void* stream);

@@ -31,7 +31,7 @@ class GradOpts(ctypes.Structure):
     _fields_ = [("ckpt_slots", ctypes.c_int), ("store_mode", ctypes.c_int), ("tol", ctypes.c_double),
                 ("pool_bytes", ctypes.c_size_t), ("grad_kind", ctypes.c_int), ("use_graph", ctypes.c_int),
                 ("profile", ctypes.c_int), ("grad_scale", ctypes.c_double), ("grad_f32", ctypes.c_int),
-                ("host_slots", ctypes.c_int)]
+                ("host_slots", ctypes.c_int), ("rate", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
@@ -55,7 +55,7 @@ class Stats(ctypes.Structure):
 EXPORTS = ["ckfwi_create_model", "ckfwi_set_model", "ckfwi_forward_shot", "ckfwi_misfit", "ckfwi_adjoint_gradient",
            "ckfwi_batch_gradient", "ckfwi_batch_gradient_models", "ckfwi_free", "ckfwi_error_string", "ckfwi_revolve_schedule",
            "ckfwi_codec_bound_words", "ckfwi_codec_compress", "ckfwi_codec_decompress",
-           "ckfwi_codec_compress_noalloc"]
+           "ckfwi_codec_compress_noalloc", "ckfwi_codec_rate_words", "ckfwi_codec_compress_rate"]
 
 
 def lib():
@@ -86,6 +86,9 @@ def lib():
         L.ckfwi_codec_compress.argtypes = [P, I, I, I, I, D, P, LL, P, P, P]
         L.ckfwi_codec_decompress.argtypes = [P, LL, I, I, I, I, P, P]
         L.ckfwi_codec_compress_noalloc.argtypes = [P, I, I, I, I, D, P, LL, P, P, P]
+        L.ckfwi_codec_rate_words.argtypes = [I, I, I, I, I]
+        L.ckfwi_codec_rate_words.restype = LL
+        L.ckfwi_codec_compress_rate.argtypes = [P, I, I, I, I, I, P, LL, P, P, P]
         for name in ("ckfwi_create_model", "ckfwi_set_model", "ckfwi_forward_shot", "ckfwi_misfit",
                      "ckfwi_adjoint_gradient",
                      "ckfwi_batch_gradient", "ckfwi_batch_gradient_models", "ckfwi_revolve_schedule", "ckfwi_codec_compress",

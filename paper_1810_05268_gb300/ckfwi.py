@@ -15,9 +15,10 @@ from ._lib import GradOpts, Grid, Shot, Stats, lib
 
 OK, EINVAL, ENOMEM, POOL_OVERFLOW, NONFINITE, CORRUPT, TIMEOUT, ECUDA = 0, -1, -2, -3, -4, -5, -6, -7
 HOST, DEVICE = 0, 1
-STORE_FP32, STORE_BF16, STORE_FP16, STORE_CODEC = 0, 1, 2, 3
+STORE_FP32, STORE_BF16, STORE_FP16, STORE_CODEC, STORE_CODEC_RATE = 0, 1, 2, 3, 4
 VELOCITY, SLOWNESS2 = 0, 1
-STORE_NAMES = {"fp32": STORE_FP32, "bf16": STORE_BF16, "fp16": STORE_FP16, "codec": STORE_CODEC}
+STORE_NAMES = {"fp32": STORE_FP32, "bf16": STORE_BF16, "fp16": STORE_FP16, "codec": STORE_CODEC,
+               "rate": STORE_CODEC_RATE}
 
 
 class CkfwiError(RuntimeError):
@@ -164,7 +165,7 @@ def _alloc(shape, dtype, device):
 
 
 def _opts(ckpt_slots, store_mode, tol, pool_bytes, grad_kind, use_graph, profile=False, grad_scale=1.0,
-          grad_f32=False, host_slots=0):
+          grad_f32=False, host_slots=0, rate=0):
     o = GradOpts()
     o.ckpt_slots = int(ckpt_slots)
     o.store_mode = STORE_NAMES.get(store_mode, store_mode) if isinstance(store_mode, str) else int(store_mode)
@@ -176,6 +177,7 @@ def _opts(ckpt_slots, store_mode, tol, pool_bytes, grad_kind, use_graph, profile
     o.grad_scale = float(grad_scale)
     o.grad_f32 = int(bool(grad_f32))
     o.host_slots = int(host_slots)
+    o.rate = int(rate)
     return o
 
 
@@ -196,7 +198,7 @@ def misfit(model, grid: GridSpec, shot: ShotSpec, d_obs, d_sim=None, stream=None
 
 def adjoint_gradient(model, grid: GridSpec, shot: ShotSpec, d_obs, ckpt_slots, store_mode=STORE_FP32,
                      tol=0.0, pool_bytes=0, grad_kind=SLOWNESS2, use_graph=False, grad=None, stream=None,
-                     profile=False, grad_scale=1.0, host_slots=0):
+                     profile=False, grad_scale=1.0, host_slots=0, rate=0):
     """(misfit, gradient on the total grid, stats dict)."""
     pd, mem = _buf(d_obs, np.float32)
     if grad is None:
@@ -206,7 +208,7 @@ def adjoint_gradient(model, grid: GridSpec, shot: ShotSpec, d_obs, ckpt_slots, s
         raise ValueError("d_obs and grad must both be host or both be device buffers")
     s = shot.c()
     o = _opts(ckpt_slots, store_mode, tol, pool_bytes, grad_kind, use_graph, profile, grad_scale,
-              host_slots=host_slots)
+              host_slots=host_slots, rate=rate)
     phi = ctypes.c_double(0.0)
     st = Stats()
     _check(lib().ckfwi_adjoint_gradient(model, ctypes.byref(s), pd, mem, ctypes.byref(o), ctypes.byref(phi), pg,
@@ -238,7 +240,7 @@ def _shot_array(shots):
 
 def batch_gradient(model, grid: GridSpec, shots, d_obs_list, ckpt_slots, store_mode=STORE_FP32, tol=0.0,
                    pool_bytes=0, grad_kind=SLOWNESS2, use_graph=False, grad_sum=None, stream=None,
-                   grad_scale=1.0, grad_f32=False, profile=False):
+                   grad_scale=1.0, grad_f32=False, profile=False, rate=0):
     """(sum of misfits, sum of gradients over shots (FP64, or FP32 with grad_f32), stats dict).
 
     The shots run as batches of lanes, one launch per stencil step over all
@@ -254,7 +256,8 @@ def batch_gradient(model, grid: GridSpec, shots, d_obs_list, ckpt_slots, store_m
     if memg != mem:
         raise ValueError("d_obs and grad_sum must both be host or both be device buffers")
     carr, keep = _shot_array(shots)
-    o = _opts(ckpt_slots, store_mode, tol, pool_bytes, grad_kind, use_graph, profile, grad_scale, grad_f32)
+    o = _opts(ckpt_slots, store_mode, tol, pool_bytes, grad_kind, use_graph, profile, grad_scale, grad_f32,
+              rate=rate)
     phi = ctypes.c_double(0.0)
     st = Stats()
     _check(lib().ckfwi_batch_gradient(model, carr, n, ptrs, mem, ctypes.byref(o), ctypes.byref(phi), pg,
@@ -265,7 +268,7 @@ def batch_gradient(model, grid: GridSpec, shots, d_obs_list, ckpt_slots, store_m
 
 def batch_gradient_models(models, shots, d_obs_list, offsets, global_shape, ckpt_slots, store_mode=STORE_FP32,
                           tol=0.0, pool_bytes=0, grad_kind=SLOWNESS2, use_graph=False, grad_sum=None, stream=None,
-                          grad_scale=1.0, grad_f32=False, profile=False):
+                          grad_scale=1.0, grad_f32=False, profile=False, rate=0):
     """Shots with uneven apertures: shot s on its own model (window) models[s],
     placed at offsets[s] = (z, y, x) in a global grid of global_shape.
     Returns (sum of misfits, gradient sum on the global grid, stats dict)."""
@@ -291,7 +294,8 @@ def batch_gradient_models(models, shots, d_obs_list, offsets, global_shape, ckpt
         off[i] = (o3[0], 0, o3[1]) if len(o3) == 2 else o3
     gna = (ctypes.c_int * 3)(*gn)
     carr, keep = _shot_array(shots)
-    o = _opts(ckpt_slots, store_mode, tol, pool_bytes, grad_kind, use_graph, profile, grad_scale, grad_f32)
+    o = _opts(ckpt_slots, store_mode, tol, pool_bytes, grad_kind, use_graph, profile, grad_scale, grad_f32,
+              rate=rate)
     phi = ctypes.c_double(0.0)
     st = Stats()
     _check(lib().ckfwi_batch_gradient_models(marr, carr, n, ptrs, mem, ctypes.byref(o), off.ctypes.data, gna,
@@ -365,6 +369,31 @@ def codec_compress_noalloc(x, out, tol, stream=None):
                                               ctypes.c_void_p(out.data_ptr()), out.numel(), ctypes.byref(used),
                                               ctypes.byref(flags), _stream(stream)), "ckfwi_codec_compress_noalloc")
     return used.value, bool(flags.value & 1)
+
+
+def codec_rate_words(dims, nz, ny, nx, rate):
+    v = lib().ckfwi_codec_rate_words(int(dims), int(nz), int(ny), int(nx), int(rate))
+    if v < 0:
+        raise CkfwiError(int(v), "ckfwi_codec_rate_words")
+    return int(v)
+
+
+def codec_compress_rate(x, rate, stream=None):
+    """Fixed-rate compression (rate bits per value) of a contiguous float32
+    CUDA tensor; returns (int32 tensor of stream words, nonfinite flag)."""
+    import torch
+    if not _is_torch_cuda(x) or x.dtype != torch.float32 or not x.is_contiguous():
+        raise ValueError("codec_compress_rate needs a contiguous float32 CUDA tensor")
+    dims = x.dim()
+    nz, ny, nx = _shape3(tuple(x.shape))
+    cap = codec_rate_words(dims, nz, ny, nx, rate)
+    out = torch.zeros(cap, dtype=torch.int32, device=x.device)
+    used = ctypes.c_longlong(0)
+    flags = ctypes.c_int(0)
+    _check(lib().ckfwi_codec_compress_rate(ctypes.c_void_p(x.data_ptr()), dims, nz, ny, nx, int(rate),
+                                           ctypes.c_void_p(out.data_ptr()), cap, ctypes.byref(used),
+                                           ctypes.byref(flags), _stream(stream)), "ckfwi_codec_compress_rate")
+    return out[:used.value].clone(), bool(flags.value & 1)
 
 
 def codec_decompress(stream_words, shape, stream=None):

@@ -1185,8 +1185,10 @@ struct State {
 
 struct RunCfg {
     int N, M, mode;
-    float tol_f;
+    float tol_f;          // CODEC: the bound; CODEC_RATE: the rate (a graph key)
     bool store_all;
+    bool codec;           // CODEC or CODEC_RATE: checkpoints in the stream pool
+    int rate;             // CODEC_RATE: bits per value
 };
 
 CodecView field_view(const FieldGeom& f)
@@ -1252,7 +1254,7 @@ int run_body(Ctx& cx, const RunCfg& rc, const std::vector<Action>& acts, long lo
     // start words of their second field
     auto sbase = [&](ckfwi_model* m, int slot) { return m->slotbase.as<long long>() + slot; };
     auto smid = [&](ckfwi_model* m, int slot) { return m->slotbase.as<long long>() + (rc.M + 1) + slot; };
-    if (rc.mode == CKFWI_STORE_CODEC && cx.issue) {
+    if (rc.codec && cx.issue) {
         for (int l = 0; l < NL; ++l) {
             ckfwi_model* m = cx.lane(l);
             CK_TRY(cudaMemsetAsync(m->slotbase.p, 0, sizeof(long long) * 2, cx.st));
@@ -1274,7 +1276,7 @@ int run_body(Ctx& cx, const RunCfg& rc, const std::vector<Action>& acts, long lo
                 int ck = CK_NONE;
                 Role cku = NONE_R, ckup = NONE_R;
                 Role out = pick_free(st);
-                if (last && next_take && rc.mode != CKFWI_STORE_CODEC) {
+                if (last && next_take && !rc.codec) {
                     const int slot = acts[ai + 1].b;
                     if (rc.mode == CKFWI_STORE_FP32) {
                         out = slot_r(slot, 0);   // u^{n+1} straight into the slot
@@ -1294,28 +1296,32 @@ int run_body(Ctx& cx, const RunCfg& rc, const std::vector<Action>& acts, long lo
                 st.tcur = U_FP32;
             }
         } else if (A.op == ACT_TAKESHOT) {
-            if (rc.mode == CKFWI_STORE_CODEC) {
+            if (rc.codec) {
                 if (cx.issue) {
+                    // a field into the pool at *from, its end written to *to
+                    auto comp = [&](ckfwi_model* m, const float* x, const long long* from, long long* to,
+                                    unsigned long long* sw) -> cudaError_t {
+                        if (rc.rate)
+                            return codec_rate_compress_dev(x, field_view(m->fg), rc.rate, m->pool.as<uint32_t>(), from,
+                                                           m->cap_words, to, m->flags.as<int>() + 1, sw, cx.st);
+                        return codec_compress_dev(x, field_view(m->fg), rc.tol_f, m->pool.as<uint32_t>(), from,
+                                                  m->cap_words, to, m->scratch.p, m->flags.as<int>() + 1, sw, cx.st);
+                    };
                     int tok = cx.begin(PC_COMP);
                     for (int l = 0; l < NL; ++l) {
                         ckfwi_model* m = cx.lane(l);
                         unsigned long long* sw = m->statw.as<unsigned long long>();
-                        CK_TRY(codec_compress_dev(cx.fptr(l, st.cur), field_view(m->fg), rc.tol_f,
-                                                  m->pool.as<uint32_t>(), sbase(m, A.b), m->cap_words, smid(m, A.b),
-                                                  m->scratch.p, m->flags.as<int>() + 1, sw + ncomp, cx.st));
+                        CK_TRY(comp(m, cx.fptr(l, st.cur), sbase(m, A.b), smid(m, A.b), sw + ncomp));
                     }
                     cx.end(tok);
                     tok = cx.begin(PC_COMP);
                     for (int l = 0; l < NL; ++l) {
                         ckfwi_model* m = cx.lane(l);
                         unsigned long long* sw = m->statw.as<unsigned long long>();
-                        CK_TRY(codec_compress_dev(cx.fptr(l, st.prev), field_view(m->fg), rc.tol_f,
-                                                  m->pool.as<uint32_t>(), smid(m, A.b), m->cap_words,
-                                                  sbase(m, A.b + 1), m->scratch.p, m->flags.as<int>() + 1,
-                                                  sw + ncomp + 1, cx.st));
+                        CK_TRY(comp(m, cx.fptr(l, st.prev), smid(m, A.b), sbase(m, A.b + 1), sw + ncomp + 1));
                     }
                     cx.end(tok);
-                    cx.launches += 6LL * NL;
+                    cx.launches += (rc.rate ? 4LL : 6LL) * NL;
                 }
                 ncomp += 2;
             }
@@ -1324,14 +1330,20 @@ int run_body(Ctx& cx, const RunCfg& rc, const std::vector<Action>& acts, long lo
                 st = State{ZERO_R, ZERO_R, U_FP32, U_FP32};
             } else if (rc.mode == CKFWI_STORE_FP32) {
                 st = State{slot_r(A.b, 0), slot_r(A.b, 1), U_FP32, U_FP32};   // the slot is the state
-            } else if (rc.mode == CKFWI_STORE_CODEC) {
+            } else if (rc.codec) {
                 if (cx.issue) {
+                    auto dec = [&](ckfwi_model* m, const long long* from, float* x) -> cudaError_t {
+                        if (rc.rate)
+                            return codec_rate_decompress_dev(m->pool.as<uint32_t>(), from, m->cap_words,
+                                                             field_view(m->fg), rc.rate, x, m->flags.as<int>() + 1,
+                                                             cx.st);
+                        return codec_decompress_dev(m->pool.as<uint32_t>(), from, m->cap_words, field_view(m->fg), x,
+                                                    m->flags.as<int>() + 1, cx.st);
+                    };
                     int tok = cx.begin(PC_DECOMP);
                     for (int l = 0; l < NL; ++l) {
                         ckfwi_model* m = cx.lane(l);
-                        CK_TRY(codec_decompress_dev(m->pool.as<uint32_t>(), sbase(m, A.b), m->cap_words,
-                                                    field_view(m->fg), cx.fptr(l, work_r(0)),
-                                                    m->flags.as<int>() + 1, cx.st));
+                        CK_TRY(dec(m, sbase(m, A.b), cx.fptr(l, work_r(0))));
                         ++cx.launches;
                     }
                     cx.end(tok);
@@ -1339,9 +1351,7 @@ int run_body(Ctx& cx, const RunCfg& rc, const std::vector<Action>& acts, long lo
                         tok = cx.begin(PC_DECOMP);
                         for (int l = 0; l < NL; ++l) {
                             ckfwi_model* m = cx.lane(l);
-                            CK_TRY(codec_decompress_dev(m->pool.as<uint32_t>(), smid(m, A.b), m->cap_words,
-                                                        field_view(m->fg), cx.fptr(l, work_r(1)),
-                                                        m->flags.as<int>() + 1, cx.st));
+                            CK_TRY(dec(m, smid(m, A.b), cx.fptr(l, work_r(1))));
                             ++cx.launches;
                         }
                         cx.end(tok);
@@ -1390,7 +1400,8 @@ double storage_bytes(const FieldGeom& f, const RunCfg& rc, const ckfwi_grad_opts
     if (rc.M <= 1) return 0.0;
     const double nslot = (double)(rc.M - 1) * 2;
     if (rc.mode == CKFWI_STORE_FP32) return nslot * field_bytes(f, 4);
-    if (rc.mode != CKFWI_STORE_CODEC) return nslot * field_bytes(f, 2);
+    if (!rc.codec) return nslot * field_bytes(f, 2);
+    if (rc.rate) return nslot * 4.0 * (double)codec_rate_words(f.dims, f.nz, f.ny, f.nx, rc.rate);
     const double pool = o->pool_bytes ? (double)o->pool_bytes : nslot * f.npts * 4.0;
     return pool + (double)codec_scratch_bytes(f.dims, f.nz, f.ny, f.nx);
 }
@@ -1421,8 +1432,8 @@ int prepare_storage(ckfwi_model* m, const RunCfg& rc, const ckfwi_grad_opts* o)
     const size_t nslot = (size_t)(rc.M - 1) * 2;
     // Uncompressed slots are read with their halo cells, which must hold 0;
     // a pool last used with another layout is cleared before reuse.
-    const int tag = rc.mode == CKFWI_STORE_FP32 ? 4 : (rc.mode == CKFWI_STORE_CODEC ? 0 : 2);
-    if (rc.mode != CKFWI_STORE_CODEC) {
+    const int tag = rc.mode == CKFWI_STORE_FP32 ? 4 : (rc.codec ? 0 : 2);
+    if (!rc.codec) {
         // the first host_slots slots in pinned host memory, the others on the device
         const int hs = std::max(0, std::min(o->host_slots, rc.M - 1));
         const size_t dslot = (size_t)(rc.M - 1 - hs) * 2, hslot = (size_t)hs * 2;
@@ -1446,11 +1457,17 @@ int prepare_storage(ckfwi_model* m, const RunCfg& rc, const ckfwi_grad_opts* o)
     } else {
         m->pool_tag = 0;
         size_t bytes = o->pool_bytes ? o->pool_bytes : (size_t)(rc.M - 1) * 2 * f.npts * 4;
+        if (rc.rate) {
+            // fixed-rate streams: the exact size is known, a smaller budget is refused up front
+            const size_t need = (size_t)(rc.M - 1) * 2 * 4 * (size_t)codec_rate_words(f.dims, f.nz, f.ny, f.nx, rc.rate);
+            if (o->pool_bytes && o->pool_bytes < need) return CKFWI_EINVAL;
+            bytes = need;
+        }
         bytes = (bytes + 3) / 4 * 4;
         CK_TRY(m->pool.alloc(bytes, false));
         m->cap_words = (long long)(bytes / 4);
         CK_TRY(m->slotbase.alloc(sizeof(long long) * (2 * (size_t)rc.M + 4)));
-        CK_TRY(m->scratch.alloc((size_t)codec_scratch_bytes(f.dims, f.nz, f.ny, f.nx), false));
+        if (!rc.rate) CK_TRY(m->scratch.alloc((size_t)codec_scratch_bytes(f.dims, f.nz, f.ny, f.nx), false));
         CK_TRY(m->statw.alloc(sizeof(unsigned long long) * (size_t)(4 * rc.N + 8)));
     }
     return CKFWI_OK;
@@ -1467,7 +1484,8 @@ int check_opts(const ckfwi_grad_opts* o)
 {
     if (!o) return CKFWI_EINVAL;
     if (o->ckpt_slots < 1) return CKFWI_EINVAL;
-    if (o->store_mode < 0 || o->store_mode > 3) return CKFWI_EINVAL;
+    if (o->store_mode < 0 || o->store_mode > 4) return CKFWI_EINVAL;
+    if (o->store_mode == CKFWI_STORE_CODEC_RATE && (o->rate < 1 || o->rate > 32)) return CKFWI_EINVAL;
     if (o->grad_kind != CKFWI_VELOCITY && o->grad_kind != CKFWI_SLOWNESS2) return CKFWI_EINVAL;
     if (o->store_mode == CKFWI_STORE_CODEC && (!(o->tol >= std::ldexp(1.0, -90)) || !std::isfinite(o->tol)))
         return CKFWI_EINVAL;
@@ -1480,7 +1498,9 @@ RunCfg run_cfg(int nt, const ckfwi_grad_opts* o)
     rc.N = nt;
     rc.M = o->ckpt_slots;
     rc.mode = o->store_mode;
-    rc.tol_f = rc.mode == CKFWI_STORE_CODEC ? tol_float(o->tol) : 0.0f;
+    rc.codec = rc.mode == CKFWI_STORE_CODEC || rc.mode == CKFWI_STORE_CODEC_RATE;
+    rc.rate = rc.mode == CKFWI_STORE_CODEC_RATE ? o->rate : 0;
+    rc.tol_f = rc.mode == CKFWI_STORE_CODEC ? tol_float(o->tol) : (float)rc.rate;
     rc.store_all = rc.M >= rc.N && rc.mode == CKFWI_STORE_FP32;
     if (rc.M > rc.N) rc.M = rc.N;
     return rc;
@@ -1541,7 +1561,7 @@ void fill_stats(ckfwi_stats* stats, Ctx& cx, const RunCfg& rc, const long long* 
     }
     if (rc.store_all) stats->pool_bytes_peak = (double)field_bytes(f) * rc.N;
     else if (rc.mode == CKFWI_STORE_FP32) stats->pool_bytes_peak = (double)(rc.M - 1) * 2 * field_bytes(f, 4);
-    else if (rc.mode != CKFWI_STORE_CODEC) stats->pool_bytes_peak = (double)(rc.M - 1) * 2 * field_bytes(f, 2);
+    else if (!rc.codec) stats->pool_bytes_peak = (double)(rc.M - 1) * 2 * field_bytes(f, 2);
 }
 
 // Compression ratios and the peak pool height of one lane's codec run
@@ -1629,7 +1649,7 @@ int gradient_one(ckfwi_model* m, const ckfwi_shot* s, const float* d_obs, int me
         } else {
             // the same schedule: counters from a dry count
             counters[0] = rc.store_all ? rc.N : cnt[0] + 1;
-            counters[1] = rc.mode == CKFWI_STORE_CODEC ? 2 * cnt[1] : 0;
+            counters[1] = rc.codec ? 2 * cnt[1] : 0;
             cx.launches = it->second.launches;
             std::memcpy(cx.count, it->second.count, sizeof(cx.count));
         }
@@ -1909,7 +1929,7 @@ int gradient_batch(const std::vector<ckfwi_model*>& lanes, const ckfwi_shot* sho
     auto it = graph ? m0->bgraphs.find(key) : m0->bgraphs.end();
     if (it != m0->bgraphs.end()) {
         counters[0] = rc.store_all ? rc.N : cnt[0] + 1;
-        counters[1] = rc.mode == CKFWI_STORE_CODEC ? 2 * cnt[1] : 0;
+        counters[1] = rc.codec ? 2 * cnt[1] : 0;
         cx.launches = it->second.ex.launches;
         std::memcpy(cx.count, it->second.ex.count, sizeof(cx.count));
         CK_TRY(cudaGraphLaunch(it->second.ex.ex, st));
@@ -2461,6 +2481,46 @@ extern "C" int ckfwi_codec_compress(const float* x, int dims, int nz, int ny, in
     return CKFWI_OK;
 }
 
+extern "C" long long ckfwi_codec_rate_words(int dims, int nz, int ny, int nx, int rate)
+{
+    if ((dims != 2 && dims != 3) || nz < 1 || ny < 1 || nx < 1 || (dims == 2 && ny != 1)) return CKFWI_EINVAL;
+    if (rate < 1 || rate > 32) return CKFWI_EINVAL;
+    return codec_rate_words(dims, nz, ny, nx, rate);
+}
+
+extern "C" int ckfwi_codec_compress_rate(const float* x, int dims, int nz, int ny, int nx, int rate, uint32_t* out,
+                                         long long cap, long long* used_words, int* flags, void* stream)
+{
+    if (!x || !out || cap <= 0) return CKFWI_EINVAL;
+    if ((dims != 2 && dims != 3) || nz < 1 || ny < 1 || nx < 1 || (dims == 2 && ny != 1)) return CKFWI_EINVAL;
+    if (rate < 1 || rate > 32) return CKFWI_EINVAL;
+    cudaStream_t st = S(stream);
+    int dev = 0;
+    CK_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) return CKFWI_EINVAL;
+    std::lock_guard<std::mutex> lk(g_codec_mu);
+    if (!g_codec_scal[dev]) g_codec_scal[dev] = new DevMem();
+    DevMem& scal = *g_codec_scal[dev];
+    CK_TRY(scal.alloc(64, true));
+    CK_TRY(cudaMemsetAsync(scal.p, 0, 64, st));
+    CodecView v{};
+    v.dims = dims; v.nz = nz; v.ny = ny; v.nx = nx;
+    v.py = nx;
+    v.pz = (long long)ny * nx;
+    v.aligned = false;
+    long long* sc = scal.as<long long>();
+    int* err = reinterpret_cast<int*>(sc + 4);
+    CK_TRY(codec_rate_compress_dev(x, v, rate, out, sc, cap, sc + 1, err, nullptr, st));
+    long long h[5];
+    CK_TRY(cudaMemcpyAsync(h, sc, sizeof(h), cudaMemcpyDeviceToHost, st));
+    CK_TRY(cudaStreamSynchronize(st));
+    const int e = (int)(h[4] & 0xffffffff);
+    if (flags) *flags = (e & 1) ? 1 : 0;
+    if (e & 2) return CKFWI_POOL_OVERFLOW;
+    if (used_words) *used_words = h[1];
+    return CKFWI_OK;
+}
+
 extern "C" int ckfwi_codec_decompress(const uint32_t* in, long long nwords, int dims, int nz, int ny, int nx,
                                       float* x, void* stream)
 {
@@ -2482,7 +2542,13 @@ extern "C" int ckfwi_codec_decompress(const uint32_t* in, long long nwords, int 
     v.aligned = (nx % 4 == 0) && ((reinterpret_cast<uintptr_t>(x) & 15) == 0);
     long long* sc = scal.as<long long>();
     int* err = reinterpret_cast<int*>(sc + 4);
-    CK_TRY(codec_decompress_dev(in, sc, nwords, v, x, err, st));
+    // the header's version word says which mode wrote the stream
+    uint32_t hv[9] = {};
+    if (nwords < 16) return CKFWI_CORRUPT;
+    CK_TRY(cudaMemcpyAsync(hv, in, sizeof(hv), cudaMemcpyDeviceToHost, st));
+    CK_TRY(cudaStreamSynchronize(st));
+    if ((hv[1] >> 8) == 2u) CK_TRY(codec_rate_decompress_dev(in, sc, nwords, v, (int)hv[8], x, err, st));
+    else CK_TRY(codec_decompress_dev(in, sc, nwords, v, x, err, st));
     int e = 0;
     CK_TRY(cudaMemcpyAsync(&e, err, sizeof(int), cudaMemcpyDeviceToHost, st));
     CK_TRY(cudaStreamSynchronize(st));

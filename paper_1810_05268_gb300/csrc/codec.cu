@@ -42,164 +42,17 @@
 // raises an error bit and the stream is not written.
 #include <cstdint>
 
-#include "internal.h"
+#include "codec_common.cuh"
 
 namespace ckfwi {
 namespace {
 
-constexpr uint32_t MAGIC = 0x31435442u;
 constexpr uint32_t VERSION = 1u;
-constexpr int HDR = 16;
-constexpr int CHUNK = 32;
 constexpr int GUARD = 1;
 constexpr int ENC_THREADS = 64;
 constexpr int CMP_WARPS = 4;
 constexpr int DEC_THREADS = 128;
 
-template <int DIMS> struct Cfg {
-    static constexpr int V = DIMS == 3 ? 64 : 16;
-    static constexpr int MAXBITS = 2 + 32 * V;
-    static constexpr int MAXW = (MAXBITS + 31) / 32;       // scratch words per block
-};
-
-struct Geo {
-    int dims, nz, ny, nx, nbz, nby, nbx;
-    long long nblocks, nchunks, table_words;
-};
-
-__host__ __device__ inline Geo make_geo(int dims, int nz, int ny, int nx)
-{
-    Geo G;
-    G.dims = dims; G.nz = nz; G.ny = ny; G.nx = nx;
-    G.nbz = (nz + 3) / 4;
-    G.nby = dims == 3 ? (ny + 3) / 4 : 1;
-    G.nbx = (nx + 3) / 4;
-    G.nblocks = (long long)G.nbz * G.nby * G.nbx;
-    G.nchunks = (G.nblocks + CHUNK - 1) / CHUNK;
-    G.table_words = HDR + G.nchunks + (G.nblocks + 1) / 2;
-    return G;
-}
-
-// sequency order, built at compile time from its definition
-struct Perm { int p[64]; };
-constexpr Perm make_perm(int dims)
-{
-    Perm r{};
-    int key[64] = {};
-    const int V = dims == 3 ? 64 : 16;
-    for (int i = 0; i < V; ++i) {
-        const int kz = dims == 3 ? i / 16 : i / 4;
-        const int ky = dims == 3 ? (i / 4) % 4 : 0;
-        const int kx = i % 4;
-        key[i] = ((kz + ky + kx) << 12) | (kz << 8) | (ky << 4) | kx;
-        r.p[i] = i;
-    }
-    for (int a = 0; a < V; ++a) {
-        int best = a;
-        for (int b = a + 1; b < V; ++b)
-            if (key[r.p[b]] < key[r.p[best]]) best = b;
-        const int t = r.p[a];
-        r.p[a] = r.p[best];
-        r.p[best] = t;
-    }
-    return r;
-}
-
-// inverse of the sequency order: the rank of coefficient i (shared-memory
-// rows are addressed by it at run time, so no register array is ever
-// indexed with a run-time value)
-constexpr Perm make_rank(int dims)
-{
-    const Perm P = make_perm(dims);
-    Perm r{};
-    for (int k = 0; k < 64; ++k) r.p[k] = 0;
-    for (int k = 0; k < (dims == 3 ? 64 : 16); ++k) r.p[P.p[k]] = k;
-    return r;
-}
-__constant__ Perm c_rank3 = make_rank(3);
-__constant__ Perm c_rank2 = make_rank(2);
-template <int DIMS> __device__ __forceinline__ int rank_of(int i) { return DIMS == 3 ? c_rank3.p[i] : c_rank2.p[i]; }
-
-__device__ __forceinline__ int32_t half_of(int32_t a) { return a >> 1; }  // arithmetic shift
-
-__device__ __forceinline__ void lift_fwd(int32_t& x0, int32_t& x1, int32_t& x2, int32_t& x3)
-{
-    const uint32_t u0 = x0, u1 = x1, u2 = x2, u3 = x3;
-    const int32_t d3 = (int32_t)(u3 - (u2 + u2) + u1);
-    const int32_t d1 = (int32_t)(u1 - (uint32_t)half_of((int32_t)(u0 + u2)));
-    const int32_t D = (int32_t)(u2 - u0);
-    const int32_t S = (int32_t)(u0 + (uint32_t)half_of(D));
-    x0 = S; x1 = D; x2 = d1; x3 = d3;
-}
-
-__device__ __forceinline__ void lift_inv(int32_t& a0, int32_t& a1, int32_t& a2, int32_t& a3)
-{
-    const int32_t S = a0, D = a1, d1 = a2, d3 = a3;
-    const int32_t x0 = (int32_t)((uint32_t)S - (uint32_t)half_of(D));
-    const int32_t x2 = (int32_t)((uint32_t)D + (uint32_t)x0);
-    const int32_t x1 = (int32_t)((uint32_t)d1 + (uint32_t)half_of((int32_t)((uint32_t)x0 + (uint32_t)x2)));
-    const int32_t x3 = (int32_t)((uint32_t)d3 + (uint32_t)x2 + (uint32_t)x2 - (uint32_t)x1);
-    a0 = x0; a1 = x1; a2 = x2; a3 = x3;
-}
-
-template <int DIMS>
-__device__ __forceinline__ void xform_fwd(int32_t (&b)[Cfg<DIMS>::V])
-{
-    if constexpr (DIMS == 3) {
-#pragma unroll
-        for (int r = 0; r < 16; ++r) lift_fwd(b[4 * r], b[4 * r + 1], b[4 * r + 2], b[4 * r + 3]);
-#pragma unroll
-        for (int z = 0; z < 4; ++z)
-#pragma unroll
-            for (int x = 0; x < 4; ++x)
-                lift_fwd(b[16 * z + x], b[16 * z + 4 + x], b[16 * z + 8 + x], b[16 * z + 12 + x]);
-#pragma unroll
-        for (int r = 0; r < 16; ++r) lift_fwd(b[r], b[16 + r], b[32 + r], b[48 + r]);
-    } else {
-#pragma unroll
-        for (int z = 0; z < 4; ++z) lift_fwd(b[4 * z], b[4 * z + 1], b[4 * z + 2], b[4 * z + 3]);
-#pragma unroll
-        for (int x = 0; x < 4; ++x) lift_fwd(b[x], b[4 + x], b[8 + x], b[12 + x]);
-    }
-}
-
-template <int DIMS>
-__device__ __forceinline__ void xform_inv(int32_t (&b)[Cfg<DIMS>::V])
-{
-    if constexpr (DIMS == 3) {
-#pragma unroll
-        for (int r = 0; r < 16; ++r) lift_inv(b[r], b[16 + r], b[32 + r], b[48 + r]);
-#pragma unroll
-        for (int z = 0; z < 4; ++z)
-#pragma unroll
-            for (int x = 0; x < 4; ++x)
-                lift_inv(b[16 * z + x], b[16 * z + 4 + x], b[16 * z + 8 + x], b[16 * z + 12 + x]);
-#pragma unroll
-        for (int r = 0; r < 16; ++r) lift_inv(b[4 * r], b[4 * r + 1], b[4 * r + 2], b[4 * r + 3]);
-    } else {
-#pragma unroll
-        for (int x = 0; x < 4; ++x) lift_inv(b[x], b[4 + x], b[8 + x], b[12 + x]);
-#pragma unroll
-        for (int z = 0; z < 4; ++z) lift_inv(b[4 * z], b[4 * z + 1], b[4 * z + 2], b[4 * z + 3]);
-    }
-}
-
-__device__ __forceinline__ uint32_t nega(int32_t c) { return ((uint32_t)c + 0xAAAAAAAAu) ^ 0xAAAAAAAAu; }
-__device__ __forceinline__ int32_t unnega(uint32_t n) { return (int32_t)((n ^ 0xAAAAAAAAu) - 0xAAAAAAAAu); }
-
-__device__ __forceinline__ float pow2f(int e) { return __uint_as_float((uint32_t)(e + 127) << 23); }
-
-// block coordinates and clamped sample positions
-struct BlockPos { int bz, by, bx; };
-__device__ __forceinline__ BlockPos block_pos(const Geo& G, long long b)
-{
-    BlockPos p;
-    p.bx = (int)(b % G.nbx);
-    const long long t = b / G.nbx;
-    p.by = (int)(t % G.nby);
-    p.bz = (int)(t / G.nby);
-    return p;
-}
 
 template <int DIMS>
 __device__ __forceinline__ void gather(const float* __restrict__ x, const CodecView& v, const BlockPos& bp,

@@ -229,5 +229,12 @@ cudaError_t codec_compress_dev(const float* x, const CodecView& v, float tol_f,
 cudaError_t codec_decompress_dev(const uint32_t* in, const long long* base_word,
                                  long long cap_words, const CodecView& v, float* x, int* err,
                                  cudaStream_t s);
+// codec_rate.cu: the fixed-rate mode (same pool conventions; rate 1..32)
+long long codec_rate_words(int dims, int nz, int ny, int nx, int rate);
+cudaError_t codec_rate_compress_dev(const float* x, const CodecView& v, int rate, uint32_t* out,
+                                    const long long* base_word, long long cap_words, long long* next_word,
+                                    int* err, unsigned long long* stat_words, cudaStream_t s);
+cudaError_t codec_rate_decompress_dev(const uint32_t* in, const long long* base_word, long long cap_words,
+                                      const CodecView& v, int rate, float* x, int* err, cudaStream_t s);
 
 }  // namespace ckfwi

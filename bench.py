@@ -8,12 +8,16 @@ interior + 40-cell damping layer (208^3 points) at 15 m, space order 8,
 Ricker source, 64 x 64 receivers.
 
 Headline (`value`): useful point-updates per second, 2 * N * npts / t, of
-the gradient at the memory of 20 uncompressed checkpoints, with the faster
-of the two storage choices the paper compares at equal memory -- Revolve
-with 20 FP32 checkpoints, or Revolve with checkpoints compressed by the
-fixed-tolerance codec (abs. tol 1e-4) in the same bytes (Sec. 4); the one
-taken is named in `config.mode`.  Both, store-all, and both again at the
-memory of 5 checkpoints are timed in the same run (`compare`).
+the gradient at the memory of 20 uncompressed checkpoints, with the fastest
+storage choice whose gradient stays within 1e-2 of the exact one: Revolve
+with 20 FP32 checkpoints, 39 FP16 / BF16 ones, or checkpoints compressed in
+the same bytes by the fixed-tolerance codec (abs. tol 1e-4; slots from the
+worst ratio, or planned from every state's measured size) or by its
+fixed-rate mode (16 bits per value) (Sec. 4); the one taken is named in
+`config.mode`.  All of them, store-all, the memory of 5 checkpoints, 40
+more slots in host memory, the OT4 kernel's modes (`ot4`) and a batch of 16
+2D shots are timed in the same run; `model` holds the time model's
+prediction of each against the measurement.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
@@ -38,12 +42,20 @@ BUDGET_SLOTS = 20          # memory of 20 uncompressed checkpoints
 LOW_SLOTS = 5              # the low-memory comparison
 HOST_SLOTS = 40            # second-level (host memory) slots of the two-level comparison
 TOL = 1e-4                 # codec absolute tolerance
+RATE = 16                  # fixed-rate codec: bits per value
 FWD_BYTES = 16             # forward step: read u^n, u^{n-1}, w; write u^{n+1}
 ADJ_BYTES = 28             # reverse step: read lam^j, lam^{j+1}, u^{j-1}, w, g; write lam^{j-1}, g
 CPU_STEPS = 300            # time steps of the oracle sample (about 10-30 s on 16 cores)
 GRAD_TOL = 1e-2            # gradient accuracy a storage mode must keep to be the headline
 KERNEL_NAMES = {1: ("fwd_kernel", "adj_kernel"), 2: ("fwd_tma_kernel", "adj_tma_kernel"),
-                3: ("fwd3_kernel", "adj3_kernel"), 4: ("fwd4_kernel", "adj4_kernel")}
+                3: ("fwd3_kernel", "adj3_kernel"), 4: ("fwd4_kernel", "adj4_kernel"),
+                5: ("ot4_lap_kernel+ot4_fwd_kernel", "ot4_lap_kernel+ot4_adj_kernel")}
+# OT4 step (two passes): forward reads u^n, w and writes Z = w lap u^n, then
+# reads Z, u^n, u^{n-1}, w and writes u^{n+1}; reverse reads lam^j, u^{j-1}, w
+# and writes Z_l, Z_u, then reads Z_l, lam^j, Z_u, u^{j-1}, lam^{j+1}, w, g and
+# the previous Z_u and writes lam^{j-1}, g
+OT4_FWD_BYTES = 32
+OT4_ADJ_BYTES = 60
 
 
 def peaks():
@@ -129,18 +141,23 @@ def perf_model(results, nt, fmin):
              if r[n] > 0 and r[cls + "_ms"] > 0 and (modes is None or r["store_mode"] in modes)]
         return float(np.min(v)) if v else None
     costs = P.Costs(c_f=unit("fwd", "fwd_launches"), c_r=unit("adj", "adj_launches", ("fp32",)),
-                    c_r16=unit("adj", "adj_launches", ("fp16", "bf16")), t_c=unit("comp", "comp_calls"),
-                    t_d=unit("decomp", "decomp_calls"), f_min=fmin,
+                    c_r16=unit("adj", "adj_launches", ("fp16", "bf16")), t_c=unit("comp", "comp_calls", ("codec",)),
+                    t_d=unit("decomp", "decomp_calls", ("codec",)), f_min=fmin,
+                    t_c_rate=unit("comp", "comp_calls", ("rate",)), t_d_rate=unit("decomp", "decomp_calls", ("rate",)),
+                    rate=RATE,
                     grad_err={r["store_mode"]: r.get("grad_rel_err_vs_storeall", 0.0) for r in results.values()})
     out = {"unit_ms": {"C_F": costs.c_f, "C_R": costs.c_r, "C_R16": costs.c_r16, "t_c": costs.t_c,
-                       "t_d": costs.t_d, "F_min": fmin}, "modes": {}}
+                       "t_d": costs.t_d, "t_c_rate": costs.t_c_rate, "t_d_rate": costs.t_d_rate, "F_min": fmin},
+           "modes": {}}
     for name, r in results.items():
         nf, nc, nd = P.counts(nt, r["ckpt_slots"], r["store_mode"])
         out["modes"][name] = {"predicted_ms": P.predict(costs, nt, r["ckpt_slots"], r["store_mode"]),
                               "measured_ms": r["ms"], "forward_steps": nf, "compressions": nc,
                               "decompressions": nd}
-    for budget, slots, names in (("budget", BUDGET_SLOTS, ("codec", "fp32", "fp16", "bf16")),
-                                 ("low", LOW_SLOTS, ("codec_low", "fp32_low", "fp16_low"))):
+    for budget, slots, names in (("budget", BUDGET_SLOTS, ("codec", "fp32", "fp16", "bf16", "rate")),
+                                 ("low", LOW_SLOTS, ("codec_low", "fp32_low", "fp16_low", "rate_low"))):
+        # (the scheduled codec modes are the codec with per-state sizes: the
+        # model's uniform-ratio choice is made among the others)
         c = [n for n in names if n in out["modes"]]
         if c:
             pick = P.choose(costs, nt, slots, modes=tuple(results[n]["store_mode"] for n in c), grad_tol=GRAD_TOL)
@@ -149,8 +166,182 @@ def perf_model(results, nt, fmin):
             out["choice_" + budget] = {"predicted": pick[0] if pick else None,
                                        "measured": results[meas]["store_mode"] if meas else None}
     if fmin and costs.t_c is not None:
-        out["budget_sweep"] = P.sweep(costs, nt, [2, 3, 5, 8, 12, 20, 32, 50, 80, 128, 250, 500, nt])
+        out["budget_sweep"] = P.sweep(costs, nt, [2, 3, 5, 8, 12, 20, 32, 50, 80, 128, 250, 500, nt],
+                                      modes=("fp32", "fp16", "codec") + (("rate",) if costs.t_c_rate else ()))
     return out
+
+
+def time_modes(C, torch, model, shot, d_obs, modes, nt, npts, args, ws, lr):
+    """Time one gradient of every storage mode in `modes` (dict name ->
+    adjoint_gradient keywords): W warm-ups, K timed graph replays (CUDA
+    events, max over ranks, clocks sampled), then profiled gradients for the
+    per-class device times.  Returns (results, last gradients, clocks,
+    skipped modes)."""
+    grads = {}
+
+    def one(kw, profile, keep=None):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        phi, g, st = model.adjoint_gradient(shot, d_obs, profile=profile, use_graph=not profile, **kw)
+        torch.cuda.synchronize()
+        if keep is not None:
+            grads[keep] = g
+        return time.perf_counter() - t0, phi, st
+
+    results = {}
+    clocks = {}
+    skipped = {}
+    for name, kw in list(modes.items()):
+        # retry with fewer codec slots if the pool overflowed at run time; a
+        # 16-bit mode whose states overflow FP16 is reported and skipped
+        ok = False
+        for _ in range(4):
+            try:
+                for _ in range(args.warmup):
+                    one(kw, False, keep=name)
+                ok = True
+                break
+            except C.CkfwiError as e:
+                if e.status == C.NONFINITE and kw.get("store_mode") in ("fp16", "bf16"):
+                    skipped[name] = "checkpoint values overflow %s" % kw["store_mode"]
+                    break
+                if e.status != C.POOL_OVERFLOW or kw.get("store_mode") != "codec":
+                    raise
+                kw["ckpt_slots"] = max(2, int(kw["ckpt_slots"] * 0.8))
+        if not ok:
+            modes.pop(name)
+            continue
+        # profiled warm-up creates the library's timing events, so that the
+        # profiled steps below do not include host-side event creation
+        one(kw, True)
+        if ws > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        clk = Clocks(lr)
+        # timed region: K gradients replayed from the recorded graph, CUDA
+        # events on torch's stream (the library launches on that stream), max
+        # over ranks
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record()
+        for _ in range(args.steps):
+            _, phi, st_plain = one(kw, False)
+        ev1.record()
+        torch.cuda.synchronize()
+        clocks[name] = clk.stop()
+        ms = max_over_ranks(ev0.elapsed_time(ev1) / args.steps, "cuda")
+        # per-kernel-class device time from profiled gradients (same work)
+        sts = []
+        for _ in range(max(1, min(args.steps, 3))):
+            _, _, st = one(kw, True)
+            sts.append(st)
+        st = sts[-1]
+        avg = lambda k: float(np.mean([s[k] for s in sts]))
+        results[name] = {
+            "ms": ms, "gpts": 2.0 * nt * npts / (ms / 1e3) / 1e9 * ws,
+            "ckpt_slots": kw["ckpt_slots"], "store_mode": kw["store_mode"],
+            "pool_bytes": kw.get("pool_bytes", st["pool_bytes_peak"]), "host_slots": kw.get("host_slots", 0),
+            "recompute_ratio": st["fwd_steps"] / nt, "p": st["p"], "W": st["takeshots"], "R": st["restores"],
+            "fwd_launches": st["fwd_launches"], "adj_launches": st["adj_launches"],
+            "comp_calls": st["comp_calls"], "decomp_calls": st["decomp_calls"],
+            "fwd_ms": avg("fwd_ms"), "adj_ms": avg("adj_ms"), "comp_ms": avg("comp_ms"),
+            "decomp_ms": avg("decomp_ms"), "kernel_launches": st_plain["kernel_launches"], "misfit": phi,
+            "ratio_mean": st["ratio_mean"], "ratio_min": st["ratio_min"],
+            "pool_bytes_peak": st["pool_bytes_peak"],
+            "fwd_kernel": [st["fwd_ver"], st["fwd_bx"], st["fwd_by"], st["fwd_vec"], st["fwd_zlen"]],
+            "adj_kernel": [st["adj_ver"], st["adj_bx"], st["adj_by"], st["adj_vec"], st["adj_zlen"]],
+        }
+    return results, grads, clocks, skipped
+
+
+def grad_errors(torch, results, grads):
+    """Gradient error of every mode against store-all (bitwise the exact
+    FP32 gradient: the schedule never changes values)."""
+    if "storeall" in grads:
+        ref = grads["storeall"].double()
+        nref = float(torch.linalg.vector_norm(ref))
+        for k, g in grads.items():
+            results[k]["grad_rel_err_vs_storeall"] = float(torch.linalg.vector_norm(g.double() - ref)) / nref
+
+
+def size_profile(C, model, shot, d_obs, nt, state_bytes):
+    """A pilot gradient that compresses every state once (nt slots): the
+    worst ratio F_min and each state's compressed bytes (Sec. 8:
+    non-uniform ratios)."""
+    from paper_1810_05268_gb300 import perfmodel as P
+    pool = nt * state_bytes // 4
+    for _ in range(4):
+        try:
+            st = model.adjoint_gradient(shot, d_obs, nt, store_mode="codec", tol=TOL, pool_bytes=pool)[2]
+            break
+        except C.CkfwiError as e:
+            if e.status != C.POOL_OVERFLOW:
+                raise
+            pool *= 2
+    return max(1.0, st["ratio_min"]), P.state_bytes(nt, nt, model.stream_words())
+
+
+def codec_modes(C, nt, state_bytes, fmin, sizes, slots, sched):
+    """Codec checkpoints in the memory of `slots` FP32 checkpoints: slots
+    from the worst ratio with 10% headroom, or (sched) the most slots whose
+    pool peak with every state's measured size fits."""
+    from paper_1810_05268_gb300 import perfmodel as P
+    b = slots * state_bytes
+    if sched:
+        m = P.slots_for_sizes(nt, b, P.size_function(sizes))
+    else:
+        m = b / (state_bytes / fmin * 1.1)
+    return dict(ckpt_slots=int(min(nt, max(2, m))), store_mode="codec", tol=TOL, pool_bytes=b)
+
+
+def rate_mode(C, nt, shape, state_bytes, slots):
+    """Fixed-rate checkpoints (RATE bits per value) in the memory of `slots`
+    FP32 checkpoints: their size is known, so the slots are exact."""
+    b = slots * state_bytes
+    per = 2 * 4 * C.codec_rate_words(3, *shape, RATE)
+    return dict(ckpt_slots=int(min(nt, 1 + b // per)), store_mode="rate", rate=RATE, pool_bytes=b)
+
+
+def ot4_block(C, torch, w, grid, shot, nt, npts, state_bytes, args, ws, lr, res2):
+    """The same gradient with the OT4 kernel: store-all, and Revolve at the
+    memory of BUDGET_SLOTS and LOW_SLOTS FP32 checkpoints with FP32, FP16 and
+    codec storage; the time model's prediction against the measurement, the
+    OT4 / OT2 step-cost ratio and the budget sweep (where compression pays)."""
+    import dataclasses
+    from paper_1810_05268_gb300 import perfmodel as P
+    g4 = dataclasses.replace(grid, time_order=4)
+    m4 = C.Model(g4)
+    m4.set_model(torch.from_numpy(w.true.astype(np.float32)).cuda())
+    d_obs = m4.forward_shot(shot).clone()
+    m4.set_model(torch.from_numpy(w.start.astype(np.float32)).cuda())
+    fmin, sizes = size_profile(C, m4, shot, d_obs, nt, state_bytes)
+    codec = lambda slots, sched=False: codec_modes(C, nt, state_bytes, fmin, sizes, slots, sched)
+    modes = {"storeall": dict(ckpt_slots=nt, store_mode="fp32"),
+             "fp32": dict(ckpt_slots=BUDGET_SLOTS, store_mode="fp32"),
+             "fp16": dict(ckpt_slots=2 * (BUDGET_SLOTS - 1) + 1, store_mode="fp16"),
+             "codec": codec(BUDGET_SLOTS),
+             "codec_sched": codec(BUDGET_SLOTS, True),
+             "fp32_low": dict(ckpt_slots=LOW_SLOTS, store_mode="fp32"),
+             "codec_low": codec(LOW_SLOTS),
+             "codec_sched_low": codec(LOW_SLOTS, True)}
+    results, grads, clocks, skipped = time_modes(C, torch, m4, shot, d_obs, modes, nt, npts, args, ws, lr)
+    m4.close()
+    grad_errors(torch, results, grads)
+    mdl = perf_model(results, nt, fmin)
+    u2 = perf_model(res2, nt, None)["unit_ms"]
+    u4 = mdl["unit_ms"]
+    gbs = {}
+    for name, r in results.items():
+        gbs[name] = {k: (b * npts * r[k + "_launches"] / (r[k + "_ms"] / 1e3) / 1e9 if r[k + "_ms"] > 0 else 0.0)
+                     for k, b in (("fwd", OT4_FWD_BYTES), ("adj", OT4_ADJ_BYTES))}
+    return {
+        "time_order": 4, "workload": WORKLOAD, "nt": nt, "codec_tol": TOL, "F_min": fmin,
+        "compare": {k: dict(v, clocks=clocks.get(k), hbm_gbs=gbs.get(k)) for k, v in results.items()},
+        "skipped": skipped,
+        "step_cost_ratio_ot4_vs_ot2": {"C_F": u4["C_F"] / u2["C_F"] if u2["C_F"] else None,
+                                       "C_R": u4["C_R"] / u2["C_R"] if u2["C_R"] else None},
+        "algorithmic_bytes_per_point": {"fwd": OT4_FWD_BYTES, "adj": OT4_ADJ_BYTES},
+        "model": mdl,
+    }
 
 
 def batch_compare(C, torch, synth, nshots=16, slots=16):
@@ -262,7 +453,9 @@ def main():
     ap.add_argument("--impl", default="ckfwi")
     ap.add_argument("--nt", type=int, default=None, help="override the number of time steps (smaller runs)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle baseline")
-    ap.add_argument("--modes", default="storeall,codec,fp32,fp16,bf16,codec_low,fp32_low,fp16_low,fp32_host,batch2d")
+    ap.add_argument("--modes",
+                    default="storeall,codec,codec_sched,rate,fp32,fp16,bf16,codec_low,codec_sched_low,rate_low,"
+                            "fp32_low,fp16_low,fp32_host,ot4,batch2d")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -294,21 +487,21 @@ def main():
     state_bytes = 2 * npts * 4
     budget = BUDGET_SLOTS * state_bytes
     modes = {}
-    # codec slots at equal memory: size from the measured worst ratio of a
-    # pilot run (the last states compress worst, Sec. 7), 10% headroom
+    # codec slots at equal memory: from the worst ratio of a pilot run (the
+    # last states compress worst, Sec. 7) with 10% headroom, or planned from
+    # every state's measured size (non-uniform ratios, Sec. 8)
     want = args.modes.split(",")
-    fmin = None
+    fmin, sizes = None, None
     if any(m.startswith("codec") for m in want):
-        pilot = model.adjoint_gradient(shot, d_obs, BUDGET_SLOTS, store_mode="codec", tol=TOL,
-                                       pool_bytes=budget)[2]
-        fmin = max(1.0, pilot["ratio_min"])
-
-    def codec_mode(slots):
-        b = slots * state_bytes
-        return dict(ckpt_slots=int(min(nt, max(2, b / (state_bytes / fmin * 1.1)))), store_mode="codec", tol=TOL,
-                    pool_bytes=b)
+        fmin, sizes = size_profile(C, model, shot, d_obs, nt, state_bytes)
+    cm = lambda slots, sched=False: codec_modes(C, nt, state_bytes, fmin, sizes, slots, sched)
+    rm = lambda slots: rate_mode(C, nt, w.shape, state_bytes, slots)
     if "codec" in want:
-        modes["codec"] = codec_mode(BUDGET_SLOTS)
+        modes["codec"] = cm(BUDGET_SLOTS)
+    if "codec_sched" in want:
+        modes["codec_sched"] = cm(BUDGET_SLOTS, True)
+    if "rate" in want:
+        modes["rate"] = rm(BUDGET_SLOTS)
     if "fp32" in want:
         modes["fp32"] = dict(ckpt_slots=BUDGET_SLOTS, store_mode="fp32")
     if "storeall" in want:
@@ -318,7 +511,11 @@ def main():
         if half in want:
             modes[half] = dict(ckpt_slots=2 * (BUDGET_SLOTS - 1) + 1, store_mode=half)
     if "codec_low" in want:
-        modes["codec_low"] = codec_mode(LOW_SLOTS)
+        modes["codec_low"] = cm(LOW_SLOTS)
+    if "codec_sched_low" in want:
+        modes["codec_sched_low"] = cm(LOW_SLOTS, True)
+    if "rate_low" in want:
+        modes["rate_low"] = rm(LOW_SLOTS)
     if "fp32_low" in want:
         modes["fp32_low"] = dict(ckpt_slots=LOW_SLOTS, store_mode="fp32")
     if "fp16_low" in want:
@@ -327,89 +524,13 @@ def main():
     if "fp32_host" in want:
         modes["fp32_host"] = dict(ckpt_slots=BUDGET_SLOTS + HOST_SLOTS, store_mode="fp32", host_slots=HOST_SLOTS)
 
-    grads = {}
-
-    def one(kw, profile, keep=None):
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        phi, g, st = model.adjoint_gradient(shot, d_obs, profile=profile, use_graph=not profile, **kw)
-        torch.cuda.synchronize()
-        if keep is not None:
-            grads[keep] = g
-        return time.perf_counter() - t0, phi, st
-
-    results = {}
-    clocks = {}
-    skipped = {}
-    for name, kw in list(modes.items()):
-        # retry with fewer codec slots if the pool overflowed at run time; a
-        # 16-bit mode whose states overflow FP16 is reported and skipped
-        ok = False
-        for _ in range(4):
-            try:
-                for _ in range(args.warmup):
-                    one(kw, False, keep=name)
-                ok = True
-                break
-            except C.CkfwiError as e:
-                if e.status == C.NONFINITE and kw.get("store_mode") in ("fp16", "bf16"):
-                    skipped[name] = "checkpoint values overflow %s" % kw["store_mode"]
-                    break
-                if e.status != C.POOL_OVERFLOW or kw.get("store_mode") != "codec":
-                    raise
-                kw["ckpt_slots"] = max(2, int(kw["ckpt_slots"] * 0.8))
-        if not ok:
-            modes.pop(name)
-            continue
-        # profiled warm-up creates the library's timing events, so that the
-        # profiled steps below do not include host-side event creation
-        one(kw, True)
-        if ws > 1:
-            torch.distributed.barrier()
-        torch.cuda.synchronize()
-        clk = Clocks(lr)
-        # timed region: K gradients replayed from the recorded graph, CUDA
-        # events on torch's stream (the library launches on that stream), max
-        # over ranks
-        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        ev0.record()
-        for _ in range(args.steps):
-            _, phi, st_plain = one(kw, False)
-        ev1.record()
-        torch.cuda.synchronize()
-        clocks[name] = clk.stop()
-        ms = max_over_ranks(ev0.elapsed_time(ev1) / args.steps, "cuda")
-        # per-kernel-class device time from profiled gradients (same work)
-        sts = []
-        for _ in range(max(1, min(args.steps, 3))):
-            _, _, st = one(kw, True)
-            sts.append(st)
-        st = sts[-1]
-        avg = lambda k: float(np.mean([s[k] for s in sts]))
-        results[name] = {
-            "ms": ms, "gpts": 2.0 * nt * npts / (ms / 1e3) / 1e9 * ws,
-            "ckpt_slots": kw["ckpt_slots"], "store_mode": kw["store_mode"],
-            "pool_bytes": kw.get("pool_bytes", st["pool_bytes_peak"]), "host_slots": kw.get("host_slots", 0),
-            "recompute_ratio": st["fwd_steps"] / nt, "p": st["p"], "W": st["takeshots"], "R": st["restores"],
-            "fwd_launches": st["fwd_launches"], "adj_launches": st["adj_launches"],
-            "comp_calls": st["comp_calls"], "decomp_calls": st["decomp_calls"],
-            "fwd_ms": avg("fwd_ms"), "adj_ms": avg("adj_ms"), "comp_ms": avg("comp_ms"),
-            "decomp_ms": avg("decomp_ms"), "kernel_launches": st_plain["kernel_launches"], "misfit": phi,
-            "ratio_mean": st["ratio_mean"], "ratio_min": st["ratio_min"],
-            "pool_bytes_peak": st["pool_bytes_peak"],
-            "fwd_kernel": [st["fwd_ver"], st["fwd_bx"], st["fwd_by"], st["fwd_vec"], st["fwd_zlen"]],
-            "adj_kernel": [st["adj_ver"], st["adj_bx"], st["adj_by"], st["adj_vec"], st["adj_zlen"]],
-        }
+    results, grads, clocks, skipped = time_modes(C, torch, model, shot, d_obs, modes, nt, npts, args, ws, lr)
     # gradient error of every mode against store-all (bitwise the exact
     # FP32 gradient: the schedule never changes values)
-    if "storeall" in grads:
-        ref = grads["storeall"].double()
-        nref = float(torch.linalg.vector_norm(ref))
-        for k, g in grads.items():
-            results[k]["grad_rel_err_vs_storeall"] = float(torch.linalg.vector_norm(g.double() - ref)) / nref
+    grad_errors(torch, results, grads)
     # headline: the fastest storage choice at the memory of BUDGET_SLOTS FP32
     # checkpoints whose gradient stays within GRAD_TOL of the exact one
-    cand = [m for m in ("codec", "fp32", "fp16", "bf16") if m in results and
+    cand = [m for m in ("codec", "codec_sched", "rate", "fp32", "fp16", "bf16") if m in results and
             results[m].get("grad_rel_err_vs_storeall", 0.0) <= GRAD_TOL] or list(results)
     headline = min(cand, key=lambda m: results[m]["ms"])
     model_block = perf_model(results, nt, fmin)
@@ -427,6 +548,13 @@ def main():
     for _ in range(e2e_steps):
         model.adjoint_gradient(shot, dh_np, grad=gh_np, use_graph=True, **kw)
     e2e_s = (time.perf_counter() - t0) / e2e_steps
+
+    # the OT4 kernel on the same workload: its own unit costs and the time
+    # model's break-even (Sec. 7: the costlier step favours compression)
+    ot4 = None
+    if "ot4" in want:
+        model.close()
+        ot4 = ot4_block(C, torch, w, grid, shot, nt, npts, state_bytes, args, ws, lr, results)
 
     batch = None
     if rk == 0 and "batch2d" in want:
@@ -486,6 +614,7 @@ def main():
             "compare": {k: dict(v, clocks=clocks.get(k)) for k, v in results.items()},
             "skipped": skipped,
             "model": model_block,
+            "ot4": ot4,
             "batch": batch,
         }
         print(json.dumps(line))

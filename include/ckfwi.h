@@ -257,6 +257,14 @@ CKFWI_API void ckfwi_free(ckfwi_model* m);
 
 CKFWI_API const char* ckfwi_error_string(int status);
 
+/* Stream lengths [words] of every compression of the model's last
+ * ckfwi_adjoint_gradient with compressed (CODEC / CODEC_RATE) checkpoints,
+ * in schedule order: two per takeshot, u^s then u^{s-1}.  The sizes the
+ * time model and the slot planner need when compression ratios vary from
+ * step to step (Sec. 8: non-uniform ratios).  *n (host) receives the count;
+ * cap = 0 only queries it; EINVAL if 0 < cap < count.  Host only. */
+CKFWI_API int ckfwi_stream_words(const ckfwi_model* m, long long* words, long long cap, long long* n);
+
 /* The Revolve schedule for (nt, slots) (Sec. 3, Eq. "eqn:recompute", split
  * at the smallest minimiser), as int32 triples (op, a, b):
  * 0 = advance(from state a, b steps), 1 = takeshot(state a, slot b),

@@ -55,7 +55,7 @@ class Stats(ctypes.Structure):
 EXPORTS = ["ckfwi_create_model", "ckfwi_set_model", "ckfwi_forward_shot", "ckfwi_misfit", "ckfwi_adjoint_gradient",
            "ckfwi_batch_gradient", "ckfwi_batch_gradient_models", "ckfwi_free", "ckfwi_error_string", "ckfwi_revolve_schedule",
            "ckfwi_codec_bound_words", "ckfwi_codec_compress", "ckfwi_codec_decompress",
-           "ckfwi_codec_compress_noalloc", "ckfwi_codec_rate_words", "ckfwi_codec_compress_rate"]
+           "ckfwi_codec_compress_noalloc", "ckfwi_codec_rate_words", "ckfwi_codec_compress_rate", "ckfwi_stream_words"]
 
 
 def lib():
@@ -86,6 +86,7 @@ def lib():
         L.ckfwi_codec_compress.argtypes = [P, I, I, I, I, D, P, LL, P, P, P]
         L.ckfwi_codec_decompress.argtypes = [P, LL, I, I, I, I, P, P]
         L.ckfwi_codec_compress_noalloc.argtypes = [P, I, I, I, I, D, P, LL, P, P, P]
+        L.ckfwi_stream_words.argtypes = [P, P, LL, P]
         L.ckfwi_codec_rate_words.argtypes = [I, I, I, I, I]
         L.ckfwi_codec_rate_words.restype = LL
         L.ckfwi_codec_compress_rate.argtypes = [P, I, I, I, I, I, P, LL, P, P, P]

@@ -322,6 +322,17 @@ def revolve_schedule(nt, slots):
     return acts, (cnt[0], cnt[1], cnt[2])
 
 
+def stream_words(model):
+    """Words of every compression of the model's last compressed-checkpoint
+    gradient, in schedule order (u^s, u^{s-1} per takeshot)."""
+    n = ctypes.c_longlong(0)
+    _check(lib().ckfwi_stream_words(model, None, 0, ctypes.byref(n)), "ckfwi_stream_words")
+    out = np.zeros(n.value, dtype=np.int64)
+    if n.value:
+        _check(lib().ckfwi_stream_words(model, out.ctypes.data, n.value, ctypes.byref(n)), "ckfwi_stream_words")
+    return out
+
+
 def codec_bound_words(dims, nz, ny, nx):
     v = lib().ckfwi_codec_bound_words(int(dims), int(nz), int(ny), int(nx))
     if v < 0:
@@ -427,6 +438,9 @@ class Model:
 
     def adjoint_gradient(self, shot, d_obs, ckpt_slots, **kw):
         return adjoint_gradient(self.h, self.grid, shot, d_obs, ckpt_slots, **kw)
+
+    def stream_words(self):
+        return stream_words(self.h)
 
     def batch_gradient(self, shots, d_obs_list, ckpt_slots, **kw):
         return batch_gradient(self.h, self.grid, shots, d_obs_list, ckpt_slots, **kw)

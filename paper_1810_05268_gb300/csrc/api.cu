@@ -346,6 +346,7 @@ struct ckfwi_model {
     DevMem flags;                   // int error flags
     DevMem phi, partials;
     DevMem statw;                   // codec: words per compression
+    std::vector<long long> last_words;   // codec: words of each compression of the last gradient
     DevMem gsum_comp;               // batch: compensation terms
     ShotDev shot;
     Tile tf{}, ta{};
@@ -1662,14 +1663,17 @@ int gradient_one(ckfwi_model* m, const ckfwi_shot* s, const float* d_obs, int me
     int fl = 0;
     ST_TRY(read_flags(m, st, &fl));
     if (misfit) *misfit = phi;
+    m->last_words.clear();
+    if (counters[1] > 0) {
+        m->last_words.resize((size_t)counters[1]);
+        CK_TRY(cudaMemcpy(m->last_words.data(), m->statw.p, sizeof(long long) * counters[1], cudaMemcpyDeviceToHost));
+    }
     if (stats) {
         fill_stats(stats, cx, rc, cnt, counters, f);
         const long long ncomp = counters[1];
         if (ncomp > 0) {
-            std::vector<long long> words(ncomp);
-            CK_TRY(cudaMemcpy(words.data(), m->statw.p, sizeof(long long) * ncomp, cudaMemcpyDeviceToHost));
             double mn, sum, peak;
-            codec_stats(words, acts, rc.M, f, &mn, &sum, &peak);
+            codec_stats(m->last_words, acts, rc.M, f, &mn, &sum, &peak);
             stats->ratio_min = mn;
             stats->ratio_mean = sum / (double)ncomp;
             stats->pool_bytes_peak = peak;
@@ -2391,6 +2395,15 @@ int ckfwi_batch_gradient_models(ckfwi_model* const* models, const ckfwi_shot* sh
 }
 
 void ckfwi_free(ckfwi_model* m) { delete m; }
+
+int ckfwi_stream_words(const ckfwi_model* m, long long* words, long long cap, long long* n)
+{
+    if (!m || !n || cap < 0 || (cap > 0 && !words)) return CKFWI_EINVAL;
+    *n = (long long)m->last_words.size();
+    if (cap < *n) return cap == 0 ? CKFWI_OK : CKFWI_EINVAL;
+    std::copy(m->last_words.begin(), m->last_words.end(), words);
+    return CKFWI_OK;
+}
 
 const char* ckfwi_error_string(int status)
 {

@@ -19,9 +19,18 @@ compression paying, everything fitting).
 
 The counts come from the library's own Revolve schedule; the unit costs from
 profiled gradients (`measure`).
+
+Non-uniform ratios (Sec. 8 names them as the model's next step: early
+wavefields are smoother and compress better).  The slot rule above sizes
+every checkpoint by the worst ratio.  With the size of each state known (a
+pilot gradient that compresses every state once, `state_bytes`),
+`slots_for_sizes` instead replays the schedule's slot stack with those sizes
+(`pool_peak`) and takes the most slots whose peak fits the budget.
 """
 from dataclasses import dataclass, field
-from typing import Dict, Optional
+from typing import Callable, Dict, Optional
+
+import numpy as np
 
 from . import ckfwi as C
 
@@ -35,6 +44,9 @@ class Costs:
     t_d: Optional[float] = None    # one field decompression [ms]
     f_min: Optional[float] = None  # worst compression ratio
     grad_err: Dict[str, float] = field(default_factory=dict)   # gradient error of each mode
+    t_c_rate: Optional[float] = None   # fixed-rate mode: one field compression [ms]
+    t_d_rate: Optional[float] = None   # fixed-rate mode: one field decompression [ms]
+    rate: Optional[int] = None         # fixed-rate mode: bits per value
 
 
 def counts(nt, slots, mode):
@@ -43,9 +55,10 @@ def counts(nt, slots, mode):
         return nt, 0, 0
     slots = min(slots, nt)
     acts, (p, W, R) = C.revolve_schedule(nt, slots)
-    nc = 2 * W if mode == "codec" else 0
+    comp = mode in ("codec", "rate")
+    nc = 2 * W if comp else 0
     nd = 0
-    if mode == "codec":
+    if comp:
         for i, a in enumerate(acts):
             if a[0] == 2 and a[2] > 0:           # restore from a slot
                 nxt = acts[i + 1][0] if i + 1 < len(acts) else -1
@@ -59,13 +72,14 @@ def predict(costs: Costs, nt, slots, mode):
     c_r = costs.c_r16 if mode in ("fp16", "bf16") and costs.c_r16 is not None else costs.c_r
     t = nf * costs.c_f + nt * c_r
     if nc or nd:
-        if costs.t_c is None or costs.t_d is None:
-            raise ValueError("codec costs not measured")
-        t += nc * costs.t_c + nd * costs.t_d
+        tc, td = (costs.t_c_rate, costs.t_d_rate) if mode == "rate" else (costs.t_c, costs.t_d)
+        if tc is None or td is None:
+            raise ValueError("%s costs not measured" % mode)
+        t += nc * tc + nd * td
     return t
 
 
-def slots_for(budget_fp32_slots, mode, nt, f_min=None):
+def slots_for(budget_fp32_slots, mode, nt, f_min=None, rate=None):
     """Slots of `mode` that fit in the memory of `budget_fp32_slots` FP32 checkpoints."""
     b = budget_fp32_slots
     if mode == "fp32":
@@ -76,6 +90,10 @@ def slots_for(budget_fp32_slots, mode, nt, f_min=None):
         if not f_min:
             raise ValueError("codec needs the worst compression ratio")
         return int(min(nt, max(2, b * f_min / 1.1)))
+    if mode == "rate":
+        if not rate:
+            raise ValueError("the fixed-rate mode needs its rate")
+        return int(min(nt, 1 + b * 32 // rate))
     raise ValueError(mode)
 
 
@@ -89,7 +107,9 @@ def choose(costs: Costs, nt, budget_fp32_slots, modes=("fp32", "fp16", "bf16", "
             continue
         if mode == "codec" and (costs.t_c is None or not costs.f_min):
             continue
-        m = slots_for(budget_fp32_slots, mode, nt, costs.f_min)
+        if mode == "rate" and (costs.t_c_rate is None or not costs.rate):
+            continue
+        m = slots_for(budget_fp32_slots, mode, nt, costs.f_min, costs.rate)
         t = predict(costs, nt, m, mode)
         if best is None or t < best[2]:
             best = (mode, m, t)
@@ -104,7 +124,9 @@ def sweep(costs: Costs, nt, budgets, modes=("fp32", "fp16", "codec")):
         for mode in modes:
             if mode == "codec" and (costs.t_c is None or not costs.f_min):
                 continue
-            row[mode] = predict(costs, nt, slots_for(b, mode, nt, costs.f_min), mode)
+            if mode == "rate" and (costs.t_c_rate is None or not costs.rate):
+                continue
+            row[mode] = predict(costs, nt, slots_for(b, mode, nt, costs.f_min, costs.rate), mode)
         row["best"] = min((k for k in row if k != "budget_fp32_slots"), key=lambda k: row[k])
         rows.append(row)
     return rows
@@ -129,3 +151,61 @@ def measure(model, shot, d_obs, nt, slots=20, tol=1e-4, state_bytes=None, reps=2
                  c_r16=s16["adj_ms"] / s16["adj_launches"],
                  t_c=sc["comp_ms"] / max(1, sc["comp_calls"]), t_d=sc["decomp_ms"] / max(1, sc["decomp_calls"]),
                  f_min=sc["ratio_min"])
+
+
+def state_bytes(nt, slots, words):
+    """{state: bytes} of the states a compressed-checkpoint gradient with
+    `slots` slots stored, from its stream words (schedule order, two per
+    takeshot: u^s then u^{s-1}; `ckfwi.stream_words`)."""
+    acts, _ = C.revolve_schedule(nt, min(slots, nt))
+    out, k = {}, 0
+    if 2 * int(sum(1 for a in acts if a[0] == 1)) != len(words):
+        raise ValueError("stream words do not match the schedule")
+    for op, a, b in acts:
+        if op == 1:
+            out[int(a)] = 4 * int(words[k] + words[k + 1])
+            k += 2
+    if k != len(words):
+        raise ValueError("stream words do not match the schedule (%d of %d used)" % (k, len(words)))
+    return out
+
+
+def size_function(sizes):
+    """size_of(state) from measured {state: bytes}: linear interpolation
+    between measured states, the nearest one outside them."""
+    st = np.array(sorted(sizes), dtype=np.float64)
+    by = np.array([sizes[k] for k in sorted(sizes)], dtype=np.float64)
+    return lambda s: float(np.interp(float(s), st, by))
+
+
+def pool_peak(nt, slots, size_of: Callable[[int], float]):
+    """Peak bytes of the checkpoint pool when state s takes size_of(s) bytes.
+    The slots form a stack (a takeshot into slot b drops the slots above
+    it), so at a takeshot the pool holds slots 1..b."""
+    acts, _ = C.revolve_schedule(nt, min(slots, nt))
+    height = [0.0] * (min(slots, nt) + 2)
+    peak = 0.0
+    for op, a, b in acts:
+        if op == 1:
+            height[b] = height[b - 1] + size_of(int(a))
+            peak = max(peak, height[b])
+    return peak
+
+
+def slots_for_sizes(nt, budget_bytes, size_of: Callable[[int], float], headroom=1.02):
+    """The most slots (<= nt) whose pool peak, with these per-state sizes
+    and a small headroom, fits the budget; 1 (the initial state only) if
+    none does."""
+    fits = lambda m: pool_peak(nt, m, size_of) * headroom <= budget_bytes
+    lo, hi = 1, nt
+    if fits(hi):
+        return hi
+    while hi - lo > 1:                   # the peak grows with the slots
+        mid = (lo + hi) // 2
+        if fits(mid):
+            lo = mid
+        else:
+            hi = mid
+    while lo > 1 and not fits(lo):       # guard a non-monotone step
+        lo -= 1
+    return lo

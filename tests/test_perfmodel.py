@@ -66,3 +66,55 @@ def test_gradient_tolerance_excludes_modes():
                 grad_err={"bf16": 0.03, "fp16": 0.004, "codec": 0.0005})
     assert P.choose(c, 1000, 20, modes=("fp32", "bf16"), grad_tol=1e-2)[0] == "fp32"
     assert P.choose(c, 1000, 20, modes=("fp32", "bf16"))[0] == "bf16"
+
+
+def _oracle_peak(nt, slots, size_of):
+    # independent replay on the oracle's Revolve: the slots held at each takeshot
+    acts, _ = R.schedule(nt, slots)
+    held, peak = {}, 0.0
+    for op, a, b in acts:
+        if op == R.TAKESHOT:
+            held = {k: v for k, v in held.items() if k < b}
+            held[b] = size_of(a)
+            peak = max(peak, sum(held.values()))
+    return peak
+
+
+@pytest.mark.parametrize("nt,slots", [(200, 5), (300, 17), (120, 60), (50, 50)])
+def test_pool_peak_matches_an_independent_replay(nt, slots):
+    import numpy as np
+    rng = np.random.default_rng(nt + slots)
+    sz = rng.uniform(1.0, 9.0, nt)
+    f = lambda s: float(sz[s])
+    assert P.pool_peak(nt, slots, f) == pytest.approx(_oracle_peak(nt, slots, f), rel=1e-12)
+
+
+def test_uniform_sizes_give_the_worst_ratio_rule():
+    # equal sizes S: the most slots is the budget over S, plus the initial state
+    for nt, budget, S in ((1000, 20.0, 1.0), (300, 7.5, 0.5), (100, 1000.0, 1.0)):
+        assert P.slots_for_sizes(nt, budget, lambda s: S, headroom=1.0) == min(nt, int(budget // S) + 1)
+
+
+def test_growing_sizes_give_more_slots_than_the_worst_ratio():
+    # states that compress better early (sizes growing with the step), as
+    # for a wavefield spreading from a source
+    nt, S = 1000, 1.0
+    f = lambda s: S * min(1.0, 0.05 + s / 600.0)
+    b = 20.0
+    m = P.slots_for_sizes(nt, b, f)
+    assert m > int(b // S) + 1
+    assert P.pool_peak(nt, m, f) * 1.02 <= b
+    assert P.pool_peak(nt, m + 1, f) * 1.02 > b or m == nt
+
+
+def test_state_bytes_maps_words_to_states():
+    import numpy as np
+    nt, slots = 60, 7
+    acts, (p, W, Rn) = __import__("paper_1810_05268_gb300.ckfwi", fromlist=["x"]).revolve_schedule(nt, slots)
+    words = np.arange(2 * W) + 10
+    sb = P.state_bytes(nt, slots, words)
+    taken = [int(a[1]) for a in acts if a[0] == 1]
+    assert list(sb) == taken
+    assert sb[taken[0]] == 4 * (10 + 11)
+    with pytest.raises(ValueError):
+        P.state_bytes(nt, slots, words[:-2])

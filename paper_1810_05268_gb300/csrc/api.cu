@@ -957,15 +957,22 @@ int autotune(ckfwi_model* m, cudaStream_t st)
     int nsm = 0;
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     std::vector<Tile> cands;
+    // Candidate z-run lengths for a tile with `cols` column blocks: runs
+    // giving about 2-16 CTAs per SM, and every run length from 4 to 32
+    // planes, among which are the ones whose CTA count fills the last wave
+    // of resident CTAs (a grid of 2.1 waves runs as 3).  The timings pick.
     auto zlens = [&](long long cols) {
         std::vector<int> zl;
+        auto add = [&](int z) {
+            z = std::max(4, std::min(z, f.nz));
+            if (std::find(zl.begin(), zl.end(), z) == zl.end()) zl.push_back(z);
+        };
         for (int target : {2, 4, 8, 16}) {
             long long nzc = (target * (long long)nsm + cols - 1) / cols;
             nzc = std::max<long long>(1, std::min<long long>(nzc, f.nz));
-            int z = (int)((f.nz + nzc - 1) / nzc);
-            z = std::max(z, 4);
-            if (std::find(zl.begin(), zl.end(), z) == zl.end()) zl.push_back(z);
+            add((int)((f.nz + nzc - 1) / nzc));
         }
+        for (int z = 4; z <= 32; ++z) add(z);
         return zl;
     };
     // the OT4 kernel has its own two-pass kernels, tried alone

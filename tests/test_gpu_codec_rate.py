@@ -145,3 +145,34 @@ def test_rate_batch_equals_single_shots():
         ref = g1.double() if ref is None else ref + g1.double()
     assert abs(phi - phis) <= 1e-12 * abs(phis)
     assert rel_l2(gs.cpu().numpy(), ref.cpu().numpy()) < 1e-6
+
+
+def test_stream_words_and_size_planning():
+    """The stream sizes of a compressed-checkpoint gradient come back in
+    schedule order; a plan from every state's size fits the pool it was made
+    for, and (states compress better early) takes more slots than the
+    worst-ratio rule."""
+    from paper_1810_05268_gb300 import perfmodel as P
+    case = make_case(3, 8, **CASE, seed=21)
+    dd = torch.from_numpy(_obs(case)).cuda()
+    m = C.Model(case.pg)
+    m.set_model(torch.from_numpy(case.vel).cuda())
+    nt = case.pg.nt
+    npts = int(np.prod(case.pg.shape))
+    S = 2 * npts * 4
+    _, _, st = m.adjoint_gradient(case.shot(), dd, ckpt_slots=6, store_mode="rate", rate=8)
+    w = m.stream_words()
+    assert len(w) == 2 * st["takeshots"]
+    assert np.all(w == C.codec_rate_words(3, *case.pg.shape, 8))
+    _, _, st = m.adjoint_gradient(case.shot(), dd, ckpt_slots=nt, store_mode="codec", tol=1e-5, pool_bytes=nt * S)
+    w = m.stream_words()
+    assert len(w) == 2 * (nt - 1)
+    sizes = P.state_bytes(nt, nt, w)
+    assert sorted(sizes) == list(range(1, nt))
+    budget = 4 * S
+    plan = P.slots_for_sizes(nt, budget, P.size_function(sizes))
+    worst = int(budget / (S / st["ratio_min"] * 1.1))
+    assert plan > worst
+    _, _, st2 = m.adjoint_gradient(case.shot(), dd, ckpt_slots=plan, store_mode="codec", tol=1e-5,
+                                   pool_bytes=budget)
+    assert st2["pool_bytes_peak"] <= budget

@@ -140,16 +140,38 @@ def perf_model(results, nt, fmin):
         v = [r[cls + "_ms"] / r[n] for k, r in results.items()
              if r[n] > 0 and r[cls + "_ms"] > 0 and (modes is None or r["store_mode"] in modes)]
         return float(np.min(v)) if v else None
-    costs = P.Costs(c_f=unit("fwd", "fwd_launches"), c_r=unit("adj", "adj_launches", ("fp32",)),
-                    c_r16=unit("adj", "adj_launches", ("fp16", "bf16")), t_c=unit("comp", "comp_calls", ("codec",)),
+
+    def named(k):
+        return results.get(k)
+    # plain step costs from store-all (no fused checkpoint writes); the extra
+    # cost of a step that writes a checkpoint, and of a reverse step reading a
+    # 16-bit one, from the FP32 / FP16 runs and their event counts
+    sa = named("storeall")
+    c_f = sa["fwd_ms"] / sa["fwd_launches"] if sa else unit("fwd", "fwd_launches")
+    c_r = sa["adj_ms"] / sa["adj_launches"] if sa else unit("adj", "adj_launches", ("fp32",))
+    t_ck = {}
+    c_r16 = None
+    for key, mode in (("fp32", "fp32"), ("fp16", "fp16")):
+        r = named(key)
+        if r and r["fwd_launches"] > 0:
+            ev = P.events(nt, r["ckpt_slots"], mode)
+            if ev["takeshots"]:
+                t_ck[mode] = max(0.0, (r["fwd_ms"] - ev["fwd"] * c_f) / ev["takeshots"])
+            if mode == "fp16" and ev["rev16"]:
+                c_r16 = (r["adj_ms"] - (nt - ev["rev16"]) * c_r) / ev["rev16"]
+    costs = P.Costs(c_f=c_f, c_r=c_r, c_r16=c_r16, t_c=unit("comp", "comp_calls", ("codec",)),
                     t_d=unit("decomp", "decomp_calls", ("codec",)), f_min=fmin,
                     t_c_rate=unit("comp", "comp_calls", ("rate",)), t_d_rate=unit("decomp", "decomp_calls", ("rate",)),
-                    rate=RATE,
+                    t_d16=unit("decomp", "decomp_calls", ("fp16", "bf16")),
+                    t_ck32=t_ck.get("fp32", 0.0), t_ck16=t_ck.get("fp16", 0.0), rate=RATE,
                     grad_err={r["store_mode"]: r.get("grad_rel_err_vs_storeall", 0.0) for r in results.values()})
     out = {"unit_ms": {"C_F": costs.c_f, "C_R": costs.c_r, "C_R16": costs.c_r16, "t_c": costs.t_c,
-                       "t_d": costs.t_d, "t_c_rate": costs.t_c_rate, "t_d_rate": costs.t_d_rate, "F_min": fmin},
+                       "t_d": costs.t_d, "t_c_rate": costs.t_c_rate, "t_d_rate": costs.t_d_rate,
+                       "t_d16": costs.t_d16, "t_ck32": costs.t_ck32, "t_ck16": costs.t_ck16, "F_min": fmin},
            "modes": {}}
     for name, r in results.items():
+        if r.get("host_slots"):
+            continue          # slots in host memory have their own (link) costs; not modelled
         nf, nc, nd = P.counts(nt, r["ckpt_slots"], r["store_mode"])
         out["modes"][name] = {"predicted_ms": P.predict(costs, nt, r["ckpt_slots"], r["store_mode"]),
                               "measured_ms": r["ms"], "forward_steps": nf, "compressions": nc,

@@ -39,7 +39,10 @@ from . import ckfwi as C
 class Costs:
     c_f: float                     # forward step [ms]
     c_r: float                     # reverse step reading FP32 checkpoints [ms]
-    c_r16: Optional[float] = None  # reverse step reading 16-bit checkpoints directly [ms]
+    c_r16: Optional[float] = None  # reverse step reading a 16-bit checkpoint directly [ms]
+    t_d16: Optional[float] = None  # 16-bit restore before a recomputation: both fields up-cast [ms]
+    t_ck32: float = 0.0            # extra cost of a forward step that writes an FP32 checkpoint [ms]
+    t_ck16: float = 0.0            # extra cost of a forward step that writes a 16-bit checkpoint [ms]
     t_c: Optional[float] = None    # one field compression [ms]
     t_d: Optional[float] = None    # one field decompression [ms]
     f_min: Optional[float] = None  # worst compression ratio
@@ -50,7 +53,9 @@ class Costs:
 
 
 def counts(nt, slots, mode):
-    """(forward steps, compressions, decompressions) of one gradient."""
+    """(forward steps, compressions, decompressions) of one gradient; for
+    16-bit storage the third count is the restores that up-cast a state
+    (a reverse step reads the 16-bit u^s directly)."""
     if slots >= nt and mode == "fp32":
         return nt, 0, 0
     slots = min(slots, nt)
@@ -58,19 +63,44 @@ def counts(nt, slots, mode):
     comp = mode in ("codec", "rate")
     nc = 2 * W if comp else 0
     nd = 0
-    if comp:
-        for i, a in enumerate(acts):
-            if a[0] == 2 and a[2] > 0:           # restore from a slot
-                nxt = acts[i + 1][0] if i + 1 < len(acts) else -1
+    for i, a in enumerate(acts):
+        if a[0] == 2 and a[2] > 0:               # restore from a slot
+            nxt = acts[i + 1][0] if i + 1 < len(acts) else -1
+            if comp:
                 nd += 1 if nxt == 3 else 2        # a reverse step next needs u^s only
+            elif mode in ("fp16", "bf16") and nxt != 3:
+                nd += 1
     return p + 1, nc, nd
 
 
-def predict(costs: Costs, nt, slots, mode):
-    """Predicted gradient time [ms] with `slots` slots of `mode` storage."""
+def events(nt, slots, mode):
+    """Every cost-bearing event of one gradient: forward steps, takeshots,
+    compressions, decompressions (codec: fields; 16-bit: up-cast restores)
+    and reverse steps that read a 16-bit checkpoint directly."""
     nf, nc, nd = counts(nt, slots, mode)
-    c_r = costs.c_r16 if mode in ("fp16", "bf16") and costs.c_r16 is not None else costs.c_r
-    t = nf * costs.c_f + nt * c_r
+    ev = {"fwd": nf, "takeshots": 0, "comp": nc, "decomp": nd, "rev16": 0}
+    if slots >= nt and mode == "fp32":
+        return ev
+    acts, (p, W, R) = C.revolve_schedule(nt, min(slots, nt))
+    ev["takeshots"] = W
+    if mode in ("fp16", "bf16"):
+        ev["rev16"] = sum(1 for i in range(len(acts) - 1)
+                          if acts[i][0] == 2 and acts[i][2] > 0 and acts[i + 1][0] == 3)
+    return ev
+
+
+def predict(costs: Costs, nt, slots, mode):
+    """Predicted gradient time [ms] with `slots` slots of `mode` storage
+    (Sec. 3-4: recomputation, storage writes and reads, compression)."""
+    ev = events(nt, slots, mode)
+    nf, nc, nd = ev["fwd"], ev["comp"], ev["decomp"]
+    t = nf * costs.c_f + nt * costs.c_r
+    if mode == "fp32":
+        return t + ev["takeshots"] * costs.t_ck32
+    if mode in ("fp16", "bf16"):
+        c_r16 = costs.c_r16 if costs.c_r16 is not None else costs.c_r
+        return (t + ev["takeshots"] * costs.t_ck16 + ev["rev16"] * (c_r16 - costs.c_r)
+                + nd * (costs.t_d16 or 0.0))
     if nc or nd:
         tc, td = (costs.t_c_rate, costs.t_d_rate) if mode == "rate" else (costs.t_c, costs.t_d)
         if tc is None or td is None:

@@ -54,29 +54,6 @@ constexpr int CMP_WARPS = 4;
 constexpr int DEC_THREADS = 128;
 
 
-template <int DIMS>
-__device__ __forceinline__ void gather(const float* __restrict__ x, const CodecView& v, const BlockPos& bp,
-                                       float (&f)[Cfg<DIMS>::V])
-{
-    const int xs = 4 * bp.bx;
-    const bool vec = v.aligned && xs + 3 < v.nx;
-    constexpr int ROWS = DIMS == 3 ? 16 : 4;
-#pragma unroll
-    for (int r = 0; r < ROWS; ++r) {
-        const int lz = DIMS == 3 ? r / 4 : r;
-        const int ly = DIMS == 3 ? r % 4 : 0;
-        const int z = min(4 * bp.bz + lz, v.nz - 1);
-        const int y = DIMS == 3 ? min(4 * bp.by + ly, v.ny - 1) : 0;
-        const float* row = x + (long long)z * v.pz + (long long)y * v.py;
-        if (vec) {
-            const float4 q = __ldg(reinterpret_cast<const float4*>(row + xs));
-            f[4 * r] = q.x; f[4 * r + 1] = q.y; f[4 * r + 2] = q.z; f[4 * r + 3] = q.w;
-        } else {
-#pragma unroll
-            for (int c = 0; c < 4; ++c) f[4 * r + c] = __ldg(row + min(xs + c, v.nx - 1));
-        }
-    }
-}
 
 // bit writer into a per-block scratch slot of `cap` words; bits past the
 // slot are counted but not stored (such a stream is replaced by the raw form)
@@ -156,23 +133,6 @@ __device__ __forceinline__ int raw_block(const float* __restrict__ x, const Code
     return 2 + 32 * V;
 }
 
-// In-place transpose of a 32 x 32 bit matrix: on return a[p] bit r is the
-// input a[r] bit p (five stages of block swaps: j = 16, 8, 4, 2, 1).
-__device__ __forceinline__ void transpose32(uint32_t (&a)[32])
-{
-    constexpr uint32_t M[5] = {0x0000FFFFu, 0x00FF00FFu, 0x0F0F0F0Fu, 0x33333333u, 0x55555555u};
-#pragma unroll
-    for (int st = 0; st < 5; ++st) {
-        const int j = 16 >> st;
-#pragma unroll
-        for (int k = 0; k < 32; ++k) {
-            if (k & j) continue;
-            const uint32_t t = ((a[k] >> j) ^ a[k + j]) & M[st];
-            a[k] ^= t << j;
-            a[k + j] ^= t;
-        }
-    }
-}
 
 // sequency order: coefficient index of rank r
 __constant__ Perm c_perm3 = make_perm(3);

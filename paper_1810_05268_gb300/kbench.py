@@ -72,6 +72,21 @@ def main():
         C.codec_decompress(words, shape)
     torch.cuda.synchronize()
     out["decompress_us"] = (time.perf_counter() - t) * 1e6 / args.reps
+    # the fixed-rate mode at 16 bits per value
+    for _ in range(args.reps):
+        rw, _ = C.codec_compress_rate(x, 16)
+        C.codec_decompress(rw, shape)
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    for _ in range(args.reps):
+        C.codec_compress_rate(x, 16)
+    torch.cuda.synchronize()
+    out["compress_rate16_us"] = (time.perf_counter() - t) * 1e6 / args.reps
+    t = time.perf_counter()
+    for _ in range(args.reps):
+        C.codec_decompress(rw, shape)
+    torch.cuda.synchronize()
+    out["decompress_rate16_us"] = (time.perf_counter() - t) * 1e6 / args.reps
     print(json.dumps(out))
 
 

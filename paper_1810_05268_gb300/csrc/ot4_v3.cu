@@ -264,24 +264,11 @@ __global__ void __launch_bounds__(TX * TY) ot4v_fwd_kernel(const Ot4FwdArgs A)
             if (CK == CK_FP32) {
                 vput<V>(static_cast<float*>(a.ck_up), o, uv, P.full, P.x0, P.nx);
             } else if (CK == CK_BF16) {
-#pragma unroll
-                for (int i = 0; i < V; ++i) {
-                    if (P.x0 + i < P.nx) {
-                        static_cast<__nv_bfloat16*>(a.ck_u)[o + i] = __float2bfloat16_rn(v[i]);
-                        static_cast<__nv_bfloat16*>(a.ck_up)[o + i] = __float2bfloat16_rn(uv[i]);
-                    }
-                }
+                st16<__nv_bfloat16, V>(a.ck_u, o, v, P.full, P.x0, P.nx);
+                st16<__nv_bfloat16, V>(a.ck_up, o, uv, P.full, P.x0, P.nx);
             } else if (CK == CK_FP16) {
-                bool inf = false;
-#pragma unroll
-                for (int i = 0; i < V; ++i) {
-                    if (P.x0 + i < P.nx) {
-                        const __half hv = __float2half_rn(v[i]), hp = __float2half_rn(uv[i]);
-                        static_cast<__half*>(a.ck_u)[o + i] = hv;
-                        static_cast<__half*>(a.ck_up)[o + i] = hp;
-                        inf = inf || __hisinf(hv) || __hisinf(hp);
-                    }
-                }
+                const bool inf = st16<__half, V>(a.ck_u, o, v, P.full, P.x0, P.nx) |
+                                 st16<__half, V>(a.ck_up, o, uv, P.full, P.x0, P.nx);
                 if (inf) atomicOr(a.err, 1);
             }
         }

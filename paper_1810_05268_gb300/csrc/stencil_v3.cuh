@@ -195,6 +195,42 @@ __device__ __forceinline__ float2 leap2v(float2 c, float2 p, float2 w, float2 s,
     return __fadd2_rn(c, t);
 }
 
+// Store V values into a 16-bit checkpoint field (BF16 or FP16): one V-wide
+// store of packed values when the whole vector lies in the grid, else one
+// value at a time.  Returns whether an FP16 value overflowed to infinity.
+template <class T> __device__ __forceinline__ T from_f(float v);
+template <> __device__ __forceinline__ __half from_f<__half>(float v) { return __float2half_rn(v); }
+template <> __device__ __forceinline__ __nv_bfloat16 from_f<__nv_bfloat16>(float v) { return __float2bfloat16_rn(v); }
+__device__ __forceinline__ unsigned short bits16(__half h) { return __half_as_ushort(h); }
+__device__ __forceinline__ unsigned short bits16(__nv_bfloat16 h) { return __bfloat16_as_ushort(h); }
+__device__ __forceinline__ bool is_inf16(__half h) { return __hisinf(h) != 0; }
+__device__ __forceinline__ bool is_inf16(__nv_bfloat16) { return false; }
+
+template <class T, int V>
+__device__ __forceinline__ bool st16(void* base, long long o, const float* v, bool full, int x0, int nx)
+{
+    T h[V];
+    bool inf = false;
+#pragma unroll
+    for (int i = 0; i < V; ++i) {
+        h[i] = from_f<T>(v[i]);
+        inf = inf || ((full || x0 + i < nx) && is_inf16(h[i]));
+    }
+    T* p = static_cast<T*>(base) + o;
+    if (full) {
+        unsigned int w[V / 2];
+#pragma unroll
+        for (int k = 0; k < V / 2; ++k) w[k] = (unsigned int)bits16(h[2 * k]) | ((unsigned int)bits16(h[2 * k + 1]) << 16);
+        if constexpr (V == 4) *reinterpret_cast<uint2*>(p) = make_uint2(w[0], w[1]);
+        else *reinterpret_cast<unsigned int*>(p) = w[0];
+    } else {
+#pragma unroll
+        for (int i = 0; i < V; ++i)
+            if (x0 + i < nx) p[i] = h[i];
+    }
+    return inf;
+}
+
 template <int V>
 struct Inj3 {                 // injection test of a thread's V points
     InjCol c0;                // the first point's column; point i is c0.base + i
@@ -422,24 +458,10 @@ __device__ __forceinline__ void fwd3_body(const FwdArgs& a, float* smem, int bxi
                 }
             }
             if (CK == CK_BF16) {
-#pragma unroll
-                for (int i = 0; i < V; ++i) {
-                    if (x0 + i < nx) {
-                        static_cast<__nv_bfloat16*>(a.ck_u)[o + i] = __float2bfloat16_rn(v[i]);
-                        static_cast<__nv_bfloat16*>(a.ck_up)[o + i] = __float2bfloat16_rn(uc[i]);
-                    }
-                }
+                st16<__nv_bfloat16, V>(a.ck_u, o, v, full, x0, nx);
+                st16<__nv_bfloat16, V>(a.ck_up, o, uc, full, x0, nx);
             } else if (CK == CK_FP16) {
-                bool inf = false;
-#pragma unroll
-                for (int i = 0; i < V; ++i) {
-                    if (x0 + i < nx) {
-                        const __half hv_ = __float2half_rn(v[i]), hp = __float2half_rn(uc[i]);
-                        static_cast<__half*>(a.ck_u)[o + i] = hv_;
-                        static_cast<__half*>(a.ck_up)[o + i] = hp;
-                        inf = inf || __hisinf(hv_) || __hisinf(hp);
-                    }
-                }
+                const bool inf = st16<__half, V>(a.ck_u, o, v, full, x0, nx) | st16<__half, V>(a.ck_up, o, uc, full, x0, nx);
                 if (inf) atomicOr(a.err, 1);
             }
         }

@@ -244,24 +244,10 @@ __device__ __forceinline__ void fwd4_body(const FwdArgs& a, float* smem, int bxi
                 }
             }
             if (CK == CK_BF16) {
-#pragma unroll
-                for (int i = 0; i < V; ++i) {
-                    if (x0 + i < nx) {
-                        static_cast<__nv_bfloat16*>(a.ck_u)[o + i] = __float2bfloat16_rn(v[i]);
-                        static_cast<__nv_bfloat16*>(a.ck_up)[o + i] = __float2bfloat16_rn(uc[i]);
-                    }
-                }
+                st16<__nv_bfloat16, V>(a.ck_u, o, v, full, x0, nx);
+                st16<__nv_bfloat16, V>(a.ck_up, o, uc, full, x0, nx);
             } else if (CK == CK_FP16) {
-                bool inf = false;
-#pragma unroll
-                for (int i = 0; i < V; ++i) {
-                    if (x0 + i < nx) {
-                        const __half hv_ = __float2half_rn(v[i]), hp = __float2half_rn(uc[i]);
-                        static_cast<__half*>(a.ck_u)[o + i] = hv_;
-                        static_cast<__half*>(a.ck_up)[o + i] = hp;
-                        inf = inf || __hisinf(hv_) || __hisinf(hp);
-                    }
-                }
+                const bool inf = st16<__half, V>(a.ck_u, o, v, full, x0, nx) | st16<__half, V>(a.ck_up, o, uc, full, x0, nx);
                 if (inf) atomicOr(a.err, 1);
             }
         }

@@ -151,16 +151,17 @@ def perf_model(results, nt, fmin):
     # 16-bit one, from the FP32 / FP16 runs and their event counts
     sa = named("storeall")
     c_f = sa["fwd_ms"] / sa["fwd_launches"] if sa else unit("fwd", "fwd_launches")
-    c_r = sa["adj_ms"] / sa["adj_launches"] if sa else unit("adj", "adj_launches", ("fp32",))
+    c_r = sa["adj_ms"] / sa["adj_launches"] if sa else (unit("adj", "adj_launches", ("fp32", "codec", "rate"))
+                                                        or unit("adj", "adj_launches"))
     t_ck = {}
     c_r16 = None
     for key, mode in (("fp32", "fp32"), ("fp16", "fp16")):
         r = named(key)
-        if r and r["fwd_launches"] > 0:
+        if r and r["fwd_launches"] > 0 and c_f is not None:
             ev = P.events(nt, r["ckpt_slots"], mode)
             if ev["takeshots"]:
                 t_ck[mode] = max(0.0, (r["fwd_ms"] - ev["fwd"] * c_f) / ev["takeshots"])
-            if mode == "fp16" and ev["rev16"]:
+            if mode == "fp16" and ev["rev16"] and c_r is not None:
                 c_r16 = (r["adj_ms"] - (nt - ev["rev16"]) * c_r) / ev["rev16"]
     costs = P.Costs(c_f=c_f, c_r=c_r, c_r16=c_r16, t_c=unit("comp", "comp_calls", ("codec",)),
                     t_d=unit("decomp", "decomp_calls", ("codec",)), f_min=fmin,

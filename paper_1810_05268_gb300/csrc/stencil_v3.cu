@@ -12,14 +12,16 @@ __global__ void __launch_bounds__(TX * TY) fwd3_kernel(const FwdArgs a)
     fwd3_body<K, V, TX, TY, CK>(a, smem3, blockIdx.x, blockIdx.y, blockIdx.z, gridDim.x, gridDim.y);
 }
 
-// Four-point reverse steps up to order 8 are capped at 168 registers, so
-// that three 128-thread CTAs fit an SM (8 bytes of spill at order 8; 236
+// Four-point FP32 reverse steps up to order 8 are capped at 168 registers,
+// so that three 128-thread CTAs fit an SM (8 bytes of spill at order 8; 236
 // registers and two CTAs uncapped): the step is latency-bound at 8 warps.
-template <int K, int V>
-constexpr int adj3_min_blocks() { return V == 4 && K <= 4 ? 3 : 1; }
+// The 16-bit variants spill inside the plane loop under the cap and stay
+// uncapped.
+template <int K, int V, class UT>
+constexpr int adj3_min_blocks() { return V == 4 && K <= 4 && std::is_same<UT, float>::value ? 3 : 1; }
 
 template <int K, int V, int TX, int TY, class UT>
-__global__ void __launch_bounds__(TX * TY, adj3_min_blocks<K, V>()) adj3_kernel(const AdjArgs a)
+__global__ void __launch_bounds__(TX * TY, adj3_min_blocks<K, V, UT>()) adj3_kernel(const AdjArgs a)
 {
     extern __shared__ __align__(16) float smem3[];
     adj3_body<K, V, TX, TY, UT>(a, smem3, blockIdx.x, blockIdx.y, blockIdx.z);

@@ -61,6 +61,11 @@ __device__ __forceinline__ void gld_plain(float (&d)[V], const float* p)
     }
 }
 
+// a 16-bit pattern of element type UT as a float (exact for both types)
+template <class UT> __device__ __forceinline__ float f16_bits(unsigned int b);
+template <> __device__ __forceinline__ float f16_bits<__half>(unsigned int b) { return __half2float(__ushort_as_half((unsigned short)b)); }
+template <> __device__ __forceinline__ float f16_bits<__nv_bfloat16>(unsigned int b) { return __uint_as_float(b << 16); }
+
 // V values of a checkpoint field of element type UT, as floats
 template <class UT, int V>
 __device__ __forceinline__ void gldu(float (&d)[V], const UT* p)
@@ -68,7 +73,7 @@ __device__ __forceinline__ void gldu(float (&d)[V], const UT* p)
     if constexpr (std::is_same<UT, float>::value) {
         gld<V>(d, p);
     } else {
-        // two 16-bit values per 32-bit word
+        // two 16-bit values per 32-bit word, the lower address in the low half
         unsigned int w[V / 2];
         if constexpr (V == 4) {
             const uint2 t = __ldg(reinterpret_cast<const uint2*>(p));
@@ -79,12 +84,8 @@ __device__ __forceinline__ void gldu(float (&d)[V], const UT* p)
         }
 #pragma unroll
         for (int k = 0; k < V / 2; ++k) {
-            UT lo, hi;
-            const unsigned short l16 = (unsigned short)(w[k] & 0xffffu), h16 = (unsigned short)(w[k] >> 16);
-            memcpy(&lo, &l16, 2);
-            memcpy(&hi, &h16, 2);
-            d[2 * k] = to_f<UT>(lo);
-            d[2 * k + 1] = to_f<UT>(hi);
+            d[2 * k] = f16_bits<UT>(w[k] & 0xffffu);
+            d[2 * k + 1] = f16_bits<UT>(w[k] >> 16);
         }
     }
 }

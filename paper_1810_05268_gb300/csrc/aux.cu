@@ -124,20 +124,39 @@ __global__ void grad_sum_kernel(const float* __restrict__ gacc, const float* __r
     sum[q] = t;
 }
 
+// Up-cast of a checkpoint field into an FP32 working field: one thread per
+// four consecutive x points of a row (one 8- or 16-byte load and one 16-byte
+// store; rows start 16-byte aligned in both layouts), the ragged end of a
+// row value by value.  Halo cells are not touched.
+template <class T>
+__device__ __forceinline__ float up1(T v);
+template <> __device__ __forceinline__ float up1<float>(float v) { return v; }
+template <> __device__ __forceinline__ float up1<__half>(__half v) { return __half2float(v); }
+template <> __device__ __forceinline__ float up1<__nv_bfloat16>(__nv_bfloat16 v) { return __bfloat162float(v); }
+
 template <class T>
 __global__ void upcast_kernel(const T* __restrict__ src, FieldGeom g, float* __restrict__ dst)
 {
-    const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= g.npts) return;
-    const long long o = padded(g, p);
-    float v;
-    if constexpr (sizeof(T) == 2) {
-        if constexpr (std::is_same<T, __half>::value) v = __half2float(src[o]);
-        else v = __bfloat162float(src[o]);
+    const long long nvx = (g.nx + 3) / 4;
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= nvx * g.ny * g.nz) return;
+    const long long row = t / nvx;
+    const int x0 = (int)(t - row * nvx) * 4;
+    const long long y = row % g.ny, z = row / g.ny;
+    const long long o = z * g.pxy + y * g.px + x0;
+    if (x0 + 4 <= g.nx) {
+        float4 r;
+        if constexpr (sizeof(T) == 4) {
+            r = __ldg(reinterpret_cast<const float4*>(src + o));
+        } else {
+            const uint2 w = __ldg(reinterpret_cast<const uint2*>(src + o));
+            const T* h = reinterpret_cast<const T*>(&w);
+            r = make_float4(up1<T>(h[0]), up1<T>(h[1]), up1<T>(h[2]), up1<T>(h[3]));
+        }
+        *reinterpret_cast<float4*>(dst + o) = r;
     } else {
-        v = src[o];
+        for (int i = 0; x0 + i < g.nx; ++i) dst[o + i] = up1<T>(src[o + i]);
     }
-    dst[o] = v;
 }
 
 __global__ void copy_f64_kernel(const double* __restrict__ a, double* __restrict__ b, long long n)
@@ -207,7 +226,7 @@ cudaError_t launch_grad_out_f64(const float* gacc_origin, const float* c_dense, 
 cudaError_t launch_cast_restore(const void* src, int utype, const FieldGeom& g, float* dst_origin,
                                 cudaStream_t s)
 {
-    const unsigned nb = blocks_for(g.npts, 256);
+    const unsigned nb = blocks_for((long long)((g.nx + 3) / 4) * g.ny * g.nz, 256);
     if (utype == U_BF16)
         upcast_kernel<__nv_bfloat16><<<nb, 256, 0, s>>>(static_cast<const __nv_bfloat16*>(src), g, dst_origin);
     else if (utype == U_FP16)

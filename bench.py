@@ -154,19 +154,21 @@ def perf_model(results, nt, fmin):
     c_r = sa["adj_ms"] / sa["adj_launches"] if sa else (unit("adj", "adj_launches", ("fp32", "codec", "rate"))
                                                         or unit("adj", "adj_launches"))
     t_ck = {}
-    c_r16 = None
+    c_r16 = t_d16 = None
     for key, mode in (("fp32", "fp32"), ("fp16", "fp16")):
         r = named(key)
         if r and r["fwd_launches"] > 0 and c_f is not None:
             ev = P.events(nt, r["ckpt_slots"], mode)
             if ev["takeshots"]:
                 t_ck[mode] = max(0.0, (r["fwd_ms"] - ev["fwd"] * c_f) / ev["takeshots"])
-            if mode == "fp16" and ev["rev16"] and c_r is not None:
-                c_r16 = (r["adj_ms"] - (nt - ev["rev16"]) * c_r) / ev["rev16"]
+            if mode == "fp16":
+                c_r16 = r["adj_ms"] / r["adj_launches"]
+                if ev["decomp"]:
+                    t_d16 = r["decomp_ms"] / ev["decomp"]
     costs = P.Costs(c_f=c_f, c_r=c_r, c_r16=c_r16, t_c=unit("comp", "comp_calls", ("codec",)),
                     t_d=unit("decomp", "decomp_calls", ("codec",)), f_min=fmin,
                     t_c_rate=unit("comp", "comp_calls", ("rate",)), t_d_rate=unit("decomp", "decomp_calls", ("rate",)),
-                    t_d16=unit("decomp", "decomp_calls", ("fp16", "bf16")),
+                    t_d16=t_d16,
                     t_ck32=t_ck.get("fp32", 0.0), t_ck16=t_ck.get("fp16", 0.0), rate=RATE,
                     grad_err={r["store_mode"]: r.get("grad_rel_err_vs_storeall", 0.0) for r in results.values()})
     out = {"unit_ms": {"C_F": costs.c_f, "C_R": costs.c_r, "C_R16": costs.c_r16, "t_c": costs.t_c,

@@ -1367,8 +1367,21 @@ int run_body(Ctx& cx, const RunCfg& rc, const std::vector<Action>& acts, long lo
                 }
                 st = State{work_r(0), work_r(1), U_FP32, U_FP32};
             } else if (next_turn) {
-                // the reverse step reads the 16-bit u^s directly
-                st = State{slot_r(A.b, 0), slot_r(A.b, 1), ut_slot, ut_slot};
+                // a reverse step needs u^s only: up-cast that field.  (The
+                // reverse kernels can read 16-bit u^s directly, but on this
+                // GPU the up-cast plus an FP32 step, whose u^s then comes
+                // from L2, is faster: 15 + 80 us against 105 us at 208^3.)
+                if (cx.issue) {
+                    const int tok = cx.begin(PC_DECOMP);
+                    for (int l = 0; l < NL; ++l) {
+                        ckfwi_model* m = cx.lane(l);
+                        CK_TRY(launch_cast_restore(cx.ptr(l, slot_r(A.b, 0)), ut_slot, m->fg, cx.fptr(l, work_r(0)),
+                                                   cx.st));
+                        cx.launches += 1;
+                    }
+                    cx.end(tok);
+                }
+                st = State{work_r(0), slot_r(A.b, 1), U_FP32, ut_slot};
             } else {
                 if (cx.issue) {
                     const int tok = cx.begin(PC_DECOMP);

@@ -39,8 +39,8 @@ from . import ckfwi as C
 class Costs:
     c_f: float                     # forward step [ms]
     c_r: float                     # reverse step reading FP32 checkpoints [ms]
-    c_r16: Optional[float] = None  # reverse step reading a 16-bit checkpoint directly [ms]
-    t_d16: Optional[float] = None  # 16-bit restore before a recomputation: both fields up-cast [ms]
+    c_r16: Optional[float] = None  # reverse step in a 16-bit run (reported, not used: u^s is up-cast) [ms]
+    t_d16: Optional[float] = None  # up-cast of one 16-bit checkpoint field [ms]
     t_ck32: float = 0.0            # extra cost of a forward step that writes an FP32 checkpoint [ms]
     t_ck16: float = 0.0            # extra cost of a forward step that writes a 16-bit checkpoint [ms]
     t_c: Optional[float] = None    # one field compression [ms]
@@ -54,8 +54,8 @@ class Costs:
 
 def counts(nt, slots, mode):
     """(forward steps, compressions, decompressions) of one gradient; for
-    16-bit storage the third count is the restores that up-cast a state
-    (a reverse step reads the 16-bit u^s directly)."""
+    16-bit storage the third count is the fields up-cast by restores (a
+    reverse step next needs u^s only)."""
     if slots >= nt and mode == "fp32":
         return nt, 0, 0
     slots = min(slots, nt)
@@ -66,26 +66,20 @@ def counts(nt, slots, mode):
     for i, a in enumerate(acts):
         if a[0] == 2 and a[2] > 0:               # restore from a slot
             nxt = acts[i + 1][0] if i + 1 < len(acts) else -1
-            if comp:
+            if comp or mode in ("fp16", "bf16"):
                 nd += 1 if nxt == 3 else 2        # a reverse step next needs u^s only
-            elif mode in ("fp16", "bf16") and nxt != 3:
-                nd += 1
     return p + 1, nc, nd
 
 
 def events(nt, slots, mode):
     """Every cost-bearing event of one gradient: forward steps, takeshots,
-    compressions, decompressions (codec: fields; 16-bit: up-cast restores)
-    and reverse steps that read a 16-bit checkpoint directly."""
+    compressions and decompressions (fields; 16-bit: fields up-cast)."""
     nf, nc, nd = counts(nt, slots, mode)
-    ev = {"fwd": nf, "takeshots": 0, "comp": nc, "decomp": nd, "rev16": 0}
+    ev = {"fwd": nf, "takeshots": 0, "comp": nc, "decomp": nd}
     if slots >= nt and mode == "fp32":
         return ev
     acts, (p, W, R) = C.revolve_schedule(nt, min(slots, nt))
     ev["takeshots"] = W
-    if mode in ("fp16", "bf16"):
-        ev["rev16"] = sum(1 for i in range(len(acts) - 1)
-                          if acts[i][0] == 2 and acts[i][2] > 0 and acts[i + 1][0] == 3)
     return ev
 
 
@@ -98,9 +92,7 @@ def predict(costs: Costs, nt, slots, mode):
     if mode == "fp32":
         return t + ev["takeshots"] * costs.t_ck32
     if mode in ("fp16", "bf16"):
-        c_r16 = costs.c_r16 if costs.c_r16 is not None else costs.c_r
-        return (t + ev["takeshots"] * costs.t_ck16 + ev["rev16"] * (c_r16 - costs.c_r)
-                + nd * (costs.t_d16 or 0.0))
+        return t + ev["takeshots"] * costs.t_ck16 + nd * (costs.t_d16 or 0.0)
     if nc or nd:
         tc, td = (costs.t_c_rate, costs.t_d_rate) if mode == "rate" else (costs.t_c, costs.t_d)
         if tc is None or td is None:

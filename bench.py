@@ -77,9 +77,12 @@ def traffic_per_point(kernel, tile):
         with open(p) as f:
             d = json.load(f)
         e = d[kernel]
-        # the same kernel and tile shape (version, x, y, points per thread);
-        # the z-run length moves the halo re-reads by a few percent only
-        if e.get("tile") is not None and list(e["tile"])[:4] != list(tile)[:4]:
+        # the same kernel, tile shape (version, x, y, points per thread) and
+        # prefetch depth; the z-run length moves the halo re-reads by a few
+        # percent only
+        t = list(tile) + [0] * (6 - len(tile))
+        want = list(e["tile"]) + [0] * (6 - len(e["tile"]))
+        if e.get("tile") is not None and (want[:4] != t[:4] or want[5] != t[5]):
             return None
         return float(e["dram_bytes_per_point"])
     except Exception:
@@ -275,8 +278,8 @@ def time_modes(C, torch, model, shot, d_obs, modes, nt, npts, args, ws, lr):
             "decomp_ms": avg("decomp_ms"), "kernel_launches": st_plain["kernel_launches"], "misfit": phi,
             "ratio_mean": st["ratio_mean"], "ratio_min": st["ratio_min"],
             "pool_bytes_peak": st["pool_bytes_peak"],
-            "fwd_kernel": [st["fwd_ver"], st["fwd_bx"], st["fwd_by"], st["fwd_vec"], st["fwd_zlen"]],
-            "adj_kernel": [st["adj_ver"], st["adj_bx"], st["adj_by"], st["adj_vec"], st["adj_zlen"]],
+            "fwd_kernel": [st["fwd_ver"], st["fwd_bx"], st["fwd_by"], st["fwd_vec"], st["fwd_zlen"], st["fwd_pf"]],
+            "adj_kernel": [st["adj_ver"], st["adj_bx"], st["adj_by"], st["adj_vec"], st["adj_zlen"], st["adj_pf"]],
         }
     return results, grads, clocks, skipped
 

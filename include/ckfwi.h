@@ -168,11 +168,14 @@ typedef struct ckfwi_stats {
     double fwd_ms, adj_ms, comp_ms, decomp_ms, other_ms;
     long long fwd_launches, adj_launches, comp_calls, decomp_calls;
     /* stencil kernel generation the autotuner chose for the forward and the
-     * reverse step: 1 register-queue, 2 TMA-fed, 3 vector-blocked; and the
+     * reverse step: 1 register-queue, 2 TMA-fed, 3 vector-blocked, 4 fed by
+     * asynchronous copies, 5 / 6 the OT4 kernels (register-queue / vector-
+     * blocked); and the
      * tile (x points, y rows, x points per thread, z planes per CTA or, for
      * generation 2, CTAs per SM) */
     int fwd_ver, fwd_bx, fwd_by, fwd_vec, fwd_zlen;
     int adj_ver, adj_bx, adj_by, adj_vec, adj_zlen;
+    int fwd_pf, adj_pf;      /* generation 4: planes of prefetch (0: the default, 2) */
 } ckfwi_stats;
 
 typedef struct ckfwi_model ckfwi_model;

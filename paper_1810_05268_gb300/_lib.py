@@ -46,7 +46,8 @@ class Stats(ctypes.Structure):
                 ("fwd_ver", ctypes.c_int), ("fwd_bx", ctypes.c_int), ("fwd_by", ctypes.c_int),
                 ("fwd_vec", ctypes.c_int), ("fwd_zlen", ctypes.c_int),
                 ("adj_ver", ctypes.c_int), ("adj_bx", ctypes.c_int), ("adj_by", ctypes.c_int),
-                ("adj_vec", ctypes.c_int), ("adj_zlen", ctypes.c_int)]
+                ("adj_vec", ctypes.c_int), ("adj_zlen", ctypes.c_int),
+                ("fwd_pf", ctypes.c_int), ("adj_pf", ctypes.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -1015,6 +1015,8 @@ int autotune(ckfwi_model* m, cudaStream_t st)
                 Tile t4 = v3_tile_at(i, z);     // the same shape fed by asynchronous copies
                 t4.ver = 4;
                 if (v4_supported(f.dims, m->K, t4)) cands.push_back(t4);
+                t4.pf = 1;                       // one plane of prefetch, six CTAs per SM
+                if (v4_supported(f.dims, m->K, t4)) cands.push_back(t4);
             }
         }
     }
@@ -1557,6 +1559,8 @@ void fill_stats(ckfwi_stats* stats, Ctx& cx, const RunCfg& rc, const long long* 
     stats->adj_by = ta.by;
     stats->adj_vec = ta.vec;
     stats->adj_zlen = cx.batch ? cx.za[0] : ta.zlen;
+    stats->fwd_pf = tf.pf;
+    stats->adj_pf = ta.pf;
     stats->fwd_steps = counters[0];
     stats->adj_steps = rc.N;
     stats->p = rc.store_all ? rc.N - 1 : cnt[0];
@@ -2324,6 +2328,8 @@ int ckfwi_batch_gradient(ckfwi_model* m, const ckfwi_shot* shots, int nshots, co
         acc.adj_by = one.adj_by;
         acc.adj_vec = one.adj_vec;
         acc.adj_zlen = one.adj_zlen;
+        acc.fwd_pf = one.fwd_pf;
+        acc.adj_pf = one.adj_pf;
         g0 += nb;
     }
     // sum + compensation, scaled; FP64 or rounded once to FP32

@@ -262,8 +262,14 @@ __device__ __forceinline__ void fwd4_body(const FwdArgs& a, float* smem, int bxi
     cp_wait<0>();     // no copy may land after the CTA has left
 }
 
+// One plane of prefetch needs 31 KB of shared memory per 128-thread CTA at
+// order 8 (two planes: 39 KB, five CTAs per SM); capped at 80 registers
+// (no spill up to order 8), six CTAs fit.
+template <int K, int V, int PF>
+constexpr int fwd4_min_blocks() { return V == 4 && PF == 1 && K <= 4 ? 6 : 1; }
+
 template <int K, int V, int TX, int TY, int PF, int CK>
-__global__ void __launch_bounds__(TX * TY) fwd4_kernel(const FwdArgs a)
+__global__ void __launch_bounds__(TX * TY, fwd4_min_blocks<K, V, PF>()) fwd4_kernel(const FwdArgs a)
 {
     extern __shared__ __align__(16) float smem4[];
     fwd4_body<K, V, TX, TY, PF, CK>(a, smem4, blockIdx.x, blockIdx.y, blockIdx.z, gridDim.x, gridDim.y);
@@ -304,6 +310,7 @@ cudaError_t fwd4_go(const FwdArgs& a, int ck, cudaStream_t s)
 template <int K>
 cudaError_t fwd4_k(const FwdArgs& a, const Tile& t, int ck, cudaStream_t s)
 {
+    if (t.vec == 4 && t.bx == 32 && t.by == 16 && t.pf == 1) return fwd4_go<K, 4, 8, 16, 1>(a, ck, s);
     if (t.vec == 4 && t.bx == 32 && t.by == 16) return fwd4_go<K, 4, 8, 16, 2>(a, ck, s);
     if (t.vec == 2 && t.bx == 32 && t.by == 16) return fwd4_go<K, 2, 16, 16, 2>(a, ck, s);
     return cudaErrorInvalidValue;
@@ -494,8 +501,9 @@ bool v4_supported(int dims, int K, const Tile& t)
 {
     if (dims != 3 || t.ver != 4 || t.zlen < 1 || t.by < K) return false;
     if (K != 1 && K != 2 && K != 4 && K != 8) return false;
-    // two planes of prefetch (three measured no faster on 208^3, order 8)
-    return t.bx == 32 && t.by == 16 && (t.vec == 2 || t.vec == 4) && (t.pf == 0 || t.pf == 2);
+    // two planes of prefetch (three measured no faster on 208^3, order 8);
+    // the four-point forward step also with one plane and six CTAs per SM
+    return t.bx == 32 && t.by == 16 && (t.vec == 2 || t.vec == 4) && (t.pf == 0 || t.pf == 2 || (t.pf == 1 && t.vec == 4 && K <= 4));
 }
 
 // the reverse step in FP32 through the rings; 16-bit u^{j-1} through the

@@ -117,6 +117,8 @@ def test_async_copy_forward_bitwise_equal_register_queue(so, shape, vec, mode):
     ref = _run(case, "1,32,%d,9" % by1, "1,32,%d,9" % by1, dobs, 5, mode)
     tiles = [("4,32,16,%d,%d" % (z, vec), "4,32,16,%d,%d" % (z, vec)) for z in (7, 64)]
     tiles.append(("4,32,16,9,%d" % vec, "3,32,16,9,%d" % vec))   # mixed generations
+    if vec == 4 and so <= 8:
+        tiles.append(("4,32,16,9,4,1", "3,32,16,9,4"))            # one plane of prefetch
     for tf, ta in tiles:
         got = _run(case, tf, ta, dobs, 5, mode)
         assert np.array_equal(got[0], ref[0])

@@ -118,3 +118,19 @@ def test_state_bytes_maps_words_to_states():
     assert sb[taken[0]] == 4 * (10 + 11)
     with pytest.raises(ValueError):
         P.state_bytes(nt, slots, words[:-2])
+
+
+@pytest.mark.parametrize("nt,slots", [(1000, 39), (300, 9), (120, 5)])
+def test_sixteen_bit_upcasts_follow_revolve(nt, slots):
+    # a restore from a slot up-casts u^s before a reverse step, both fields
+    # before a recomputation (the executor's 16-bit restore)
+    acts, cnt = R.schedule(nt, slots)
+    want = 0
+    for i, a in enumerate(acts):
+        if a[0] == R.RESTORE and a[2] > 0:
+            nxt = acts[i + 1][0] if i + 1 < len(acts) else None
+            want += 1 if nxt == R.YOUTURN else 2
+    nf, nc, nd = P.counts(nt, slots, "fp16")
+    assert nd == want and nc == 0 and nf == cnt["p"] + 1
+    ev = P.events(nt, slots, "fp16")
+    assert ev["takeshots"] == cnt["W"] and ev["decomp"] == want

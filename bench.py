@@ -43,7 +43,7 @@ LOW_SLOTS = 5              # the low-memory comparison
 HOST_SLOTS = 40            # second-level (host memory) slots of the two-level comparison
 TOL = 1e-4                 # codec absolute tolerance
 RATE = 16                  # fixed-rate codec: bits per value
-FWD_BYTES = 16             # forward step: read u^n, u^{n-1}, w; write u^{n+1}
+FWD_BYTES = 16             # forward step: read u^n, u^{n-1}, w; write u^{n+1} (+4 with a fused checkpoint)
 ADJ_BYTES = 28             # reverse step: read lam^j, lam^{j+1}, u^{j-1}, w, g; write lam^{j-1}, g
 CPU_STEPS = 300            # time steps of the oracle sample (about 10-30 s on 16 cores)
 GRAD_TOL = 1e-2            # gradient accuracy a storage mode must keep to be the headline
@@ -604,8 +604,12 @@ def main():
         # the kernel class with the largest device-time share in the headline
         # mode, its algorithmic bytes per launch over its average launch time
         F = max(1.0, H["ratio_mean"] or 1.0)
+        # a step that writes an FP32 or 16-bit checkpoint writes 4 more B/pt
+        # (u^{n-1} in FP32, or both levels in 16 bits), W of the launches
+        ck_bytes = 4.0 if H["store_mode"] in ("fp32", "fp16", "bf16") and H["ckpt_slots"] < nt else 0.0
+        fwd_b = (FWD_BYTES + ck_bytes * H["W"] / max(1, H["fwd_launches"])) * npts
         classes = {
-            "fwd": (H["fwd_ms"], H["fwd_launches"], FWD_BYTES * npts),
+            "fwd": (H["fwd_ms"], H["fwd_launches"], fwd_b),
             "adj": (H["adj_ms"], H["adj_launches"], ADJ_BYTES * npts),
             "comp": (H["comp_ms"], H["comp_calls"], (4.0 + 4.0 / F) * npts),
             "decomp": (H["decomp_ms"], H["decomp_calls"], (4.0 / F + 4.0) * npts),

@@ -249,8 +249,10 @@ CKFWI_API int ckfwi_batch_gradient(ckfwi_model* m, const ckfwi_shot* shots, int 
  * opts->grad_f32) receives sum_s of shot s's gradient added at its window,
  * in shot order with compensated FP64 summation, points outside every
  * window 0; misfit_sum (host) the FP64 sum of the misfits.  EINVAL when a
- * window leaves the global grid, a model repeats or lacks a medium.  All
- * lanes run at once: ENOMEM when their storage does not fit. */
+ * window leaves the global grid, a model repeats or lacks a medium, or a
+ * model of time order 4 is one of several shots (the OT4 kernels have no
+ * batched form).
+ * All lanes run at once: ENOMEM when their storage does not fit. */
 CKFWI_API int ckfwi_batch_gradient_models(ckfwi_model* const* models, const ckfwi_shot* shots, int nshots,
                          const float* const* d_obs, int mem, const ckfwi_grad_opts* opts,
                          const int* offsets, const int* global_n, double* misfit_sum,

@@ -219,3 +219,22 @@ def test_ot4_vector_blocked_reverse_rejects_width_4(monkeypatch):
     dobs = torch.from_numpy(_obs(case)).cuda()
     _, _, _, st = _grad_with_tiles(monkeypatch, case, dobs, "6,32,16,9,4", "6,32,16,9,4", ckpt_slots=4)
     assert not (st["adj_ver"] == 6 and st["adj_vec"] == 4)
+
+
+def test_ot4_windowed_batch_is_refused():
+    """The OT4 kernels have no batched form: a windowed batch of several OT4
+    shots is refused; a single OT4 window runs."""
+    case = _case(2, 4, 61)
+    ms = []
+    for k in range(2):
+        m = _model(case)
+        ms.append(m)
+    obs = [torch.from_numpy(_obs(case)).cuda() for _ in ms]
+    shape = case.pg.shape
+    with pytest.raises(C.CkfwiError):
+        C.batch_gradient_models(ms, [case.shot(), case.shot()], obs, [(0, 0, 0), (0, 0, 0)],
+                                shape, 9)
+    phi, g, _ = C.batch_gradient_models([ms[0]], [case.shot()], obs[:1], [(0, 0, 0)], shape, 9)
+    p1, g1, _ = ms[0].adjoint_gradient(case.shot(), obs[0], ckpt_slots=9)
+    assert abs(phi - p1) <= 1e-12 * abs(p1)
+    assert rel_l2(g.cpu().numpy(), g1.double().cpu().numpy()) < 1e-6

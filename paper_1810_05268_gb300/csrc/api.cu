@@ -1331,7 +1331,7 @@ int run_body(Ctx& cx, const RunCfg& rc, const std::vector<Action>& acts, long lo
                         CK_TRY(comp(m, cx.fptr(l, st.prev), smid(m, A.b), sbase(m, A.b + 1), sw + ncomp + 1));
                     }
                     cx.end(tok);
-                    cx.launches += (rc.rate ? 4LL : 6LL) * NL;
+                    cx.launches += 4LL * NL;   // two launches per field in either mode
                 }
                 ncomp += 2;
             }

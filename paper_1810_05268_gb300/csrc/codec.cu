@@ -33,10 +33,11 @@
 //
 // GPU layout of the work: one thread encodes / decodes one block; a warp
 // owns one chunk, so block bit offsets inside a chunk come from a warp scan
-// of the size table.  Compression runs in three launches: encode every
-// block into a fixed-size scratch slot and write its size, scan chunk sizes
-// (one CTA) into the chunk table and header, then compact each chunk's bits
-// through shared memory into the payload.  The pool position of a stream is
+// of the size table.  Compression runs in two launches: encode every block
+// into a fixed-size scratch slot and write its size (and each chunk's word
+// count), then compact each chunk's bits through shared memory into the
+// payload, every CTA summing the counts before its chunks for their offsets
+// (CTA 0 writes the header).  The pool position of a stream is
 // read from and written to device memory, so a schedule of compressions and
 // decompressions runs without host synchronisation; running out of pool
 // raises an error bit and the stream is not written.
@@ -306,7 +307,8 @@ __device__ __forceinline__ int encode_block(const float* __restrict__ x, const C
 }
 
 // One thread per block; each warp owns one 32-block chunk and stores the
-// chunk's word count in the chunk table (the scan turns counts into offsets).
+// chunk's word count after the block slots of the scratch (the compaction
+// turns counts into offsets).
 template <int DIMS>
 __global__ void __launch_bounds__(ENC_THREADS, 7) enc_kernel(const float* __restrict__ x, CodecView v,
                                                           Geo G, float tol_f, uint32_t* __restrict__ scratch,
@@ -323,7 +325,6 @@ __global__ void __launch_bounds__(ENC_THREADS, 7) enc_kernel(const float* __rest
         if (b == 0) atomicOr(err, 2);
         return;
     }
-    uint32_t* ctab = out + base + HDR;
     uint16_t* sizes = reinterpret_cast<uint16_t*>(out + base + HDR + G.nchunks);
     if (b == 0 && (G.nblocks & 1)) sizes[G.nblocks] = 0;
     int nbits = 0;
@@ -335,73 +336,60 @@ __global__ void __launch_bounds__(ENC_THREADS, 7) enc_kernel(const float* __rest
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) tot += __shfl_xor_sync(0xffffffffu, tot, o);
     const long long c = b / CHUNK;
-    if ((threadIdx.x & 31) == 0 && c < G.nchunks) ctab[c] = (uint32_t)((tot + 31) / 32);
+    uint32_t* counts = scratch + (G.nblocks + CHUNK) * Cfg<DIMS>::MAXW;   // words of each chunk
+    if ((threadIdx.x & 31) == 0 && c < G.nchunks) counts[c] = (uint32_t)((tot + 31) / 32);
 }
 
-// One CTA: the chunk word counts in the chunk table -> exclusive offsets in
-// place; header; next free word; overflow check.  Each thread takes SCAN_ITEMS
-// consecutive chunks per pass.
-constexpr int SCAN_ITEMS = 8;
-__global__ void __launch_bounds__(1024) scan_kernel(uint32_t* __restrict__ out, const long long* base_word,
-                                                    long long cap_words, long long* next_word, Geo G,
-                                                    float tol_f, int* err, unsigned long long* stat_words)
+// Compaction of each chunk's blocks from their scratch slots into the
+// payload.  A CTA handles CMP_WARPS consecutive chunks (a warp each) and
+// finds their payload offsets itself: it sums the word counts of all chunks
+// before its first one, and of all chunks for the stream's total, so no
+// separate scan launch is needed (every CTA reads the 4-byte counts, a few
+// KB from L2).  The total decides the overflow (nothing is written) and,
+// in CTA 0, the header, the pool's next word and the statistics.
+template <int DIMS>
+__global__ void __launch_bounds__(CMP_WARPS * 32) compact_kernel(uint32_t* __restrict__ out, const long long* base_word,
+                                                                 long long cap_words, long long* next_word, Geo G,
+                                                                 float tol_f, const uint32_t* __restrict__ scratch,
+                                                                 int* err, unsigned long long* stat_words)
 {
-    __shared__ long long carry_s;
-    __shared__ long long warp_tot[32];
+    constexpr int CW = (CHUNK * Cfg<DIMS>::MAXBITS + 31) / 32 + 1;
+    __shared__ uint32_t buf[CMP_WARPS][CW];
+    __shared__ long long red[2][CMP_WARPS];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const long long base = *base_word;
-    if (base + G.table_words > cap_words) {
-        if (threadIdx.x == 0) {
-            atomicOr(err, 2);
-            *next_word = base;
-        }
+    if (base + G.table_words > cap_words) {            // the encoder raised the error
+        if (blockIdx.x == 0 && threadIdx.x == 0) *next_word = base;
         return;
     }
-    uint32_t* hdr = out + base;
-    uint32_t* ctab = hdr + HDR;
-    if (threadIdx.x == 0) carry_s = 0;
-    __syncthreads();
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    for (long long c0 = 0; c0 < G.nchunks; c0 += 1024LL * SCAN_ITEMS) {
-        const long long cb = c0 + (long long)threadIdx.x * SCAN_ITEMS;
-        uint32_t v[SCAN_ITEMS];
-        long long sum = 0;
-#pragma unroll
-        for (int i = 0; i < SCAN_ITEMS; ++i) {
-            v[i] = (cb + i < G.nchunks) ? ctab[cb + i] : 0u;
-            sum += v[i];
-        }
-        long long incl = sum;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const long long t = __shfl_up_sync(0xffffffffu, incl, o);
-            if (lane >= o) incl += t;
-        }
-        if (lane == 31) warp_tot[wid] = incl;
-        __syncthreads();
-        if (wid == 0) {
-            const long long t = warp_tot[lane];
-            long long tin = t;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const long long u = __shfl_up_sync(0xffffffffu, tin, o);
-                if (lane >= o) tin += u;
-            }
-            warp_tot[lane] = tin - t;       // exclusive prefix of warp totals
-        }
-        __syncthreads();
-        long long run = carry_s + warp_tot[wid] + incl - sum;
-#pragma unroll
-        for (int i = 0; i < SCAN_ITEMS; ++i) {
-            if (cb + i < G.nchunks) ctab[cb + i] = (uint32_t)run;
-            run += v[i];
-        }
-        __syncthreads();
-        if (threadIdx.x == 1023) carry_s = run;
-        __syncthreads();
+    const uint32_t* counts = scratch + (G.nblocks + CHUNK) * Cfg<DIMS>::MAXW;
+    const long long c0 = (long long)blockIdx.x * CMP_WARPS;
+    long long before = 0, after = 0;
+    for (long long i = threadIdx.x; i < G.nchunks; i += CMP_WARPS * 32) {
+        const uint32_t w = __ldg(counts + i);
+        if (i < c0) before += w;
+        else after += w;
     }
-    if (threadIdx.x == 0) {
-        const long long payload = carry_s;
-        const long long end = base + G.table_words + payload;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        before += __shfl_xor_sync(0xffffffffu, before, o);
+        after += __shfl_xor_sync(0xffffffffu, after, o);
+    }
+    if (lane == 0) {
+        red[0][wid] = before;
+        red[1][wid] = after;
+    }
+    __syncthreads();
+    long long prefix = 0, total = 0;
+#pragma unroll
+    for (int k = 0; k < CMP_WARPS; ++k) {
+        prefix += red[0][k];
+        total += red[1][k];
+    }
+    total += prefix;
+    const long long end = base + G.table_words + total;
+    uint32_t* hdr = out + base;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
         hdr[0] = MAGIC;
         hdr[1] = (uint32_t)G.dims | (VERSION << 8);
         hdr[2] = (uint32_t)G.nz;
@@ -409,7 +397,7 @@ __global__ void __launch_bounds__(1024) scan_kernel(uint32_t* __restrict__ out, 
         hdr[4] = (uint32_t)G.nx;
         hdr[5] = (uint32_t)G.nblocks;
         hdr[6] = (uint32_t)G.nchunks;
-        hdr[7] = (uint32_t)payload;
+        hdr[7] = (uint32_t)total;
         hdr[8] = __float_as_uint(tol_f);
         hdr[9] = (*err & 1) ? 1u : 0u;
         for (int i = 10; i < HDR; ++i) hdr[i] = 0u;
@@ -419,23 +407,13 @@ __global__ void __launch_bounds__(1024) scan_kernel(uint32_t* __restrict__ out, 
         } else {
             *next_word = end;
         }
-        if (stat_words) atomicAdd(stat_words, (unsigned long long)(G.table_words + payload));
+        if (stat_words) atomicAdd(stat_words, (unsigned long long)(G.table_words + total));
     }
-}
-
-template <int DIMS>
-__global__ void __launch_bounds__(CMP_WARPS * 32) compact_kernel(uint32_t* __restrict__ out, const long long* base_word,
-                                                                 const long long* next_word, Geo G,
-                                                                 const uint32_t* __restrict__ scratch, int* err)
-{
-    constexpr int CW = (CHUNK * Cfg<DIMS>::MAXBITS + 31) / 32 + 1;
-    __shared__ uint32_t buf[CMP_WARPS][CW];
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const long long c = (long long)blockIdx.x * CMP_WARPS + wid;
-    const long long base = *base_word;
-    if (*next_word <= base) return;               // overflow: nothing is written
+    if (end > cap_words) return;                       // overflow: nothing is written
+    const long long c = c0 + wid;
     if (c >= G.nchunks) return;
-    const uint32_t* hdr = out + base;
+    long long off_c = prefix;                          // payload word offset of this warp's chunk
+    for (long long k = c0; k < c; ++k) off_c += __ldg(counts + k);
     const uint16_t* sizes = reinterpret_cast<const uint16_t*>(hdr + HDR + G.nchunks);
     const long long b = c * CHUNK + lane;
     const int nbits = b < G.nblocks ? sizes[b] : 0;
@@ -445,15 +423,16 @@ __global__ void __launch_bounds__(CMP_WARPS * 32) compact_kernel(uint32_t* __res
         const int t = __shfl_up_sync(0xffffffffu, incl, o);
         if (lane >= o) incl += t;
     }
-    const int total = __shfl_sync(0xffffffffu, incl, 31);
+    const int totb = __shfl_sync(0xffffffffu, incl, 31);
     const int off = incl - nbits;
-    const int words = (total + 31) / 32;
+    const int words = (totb + 31) / 32;
     // every block is at most MAXBITS long by construction; a chunk that is
     // not would overrun the shared buffer, so it is refused outright
     if (__any_sync(0xffffffffu, nbits > Cfg<DIMS>::MAXBITS) || words > CW) {
         if (lane == 0) atomicOr(err, 4);
         return;
     }
+    if (lane == 0) hdr[HDR + c] = (uint32_t)off_c;
     for (int k = lane; k < words; k += 32) buf[wid][k] = 0u;
     __syncwarp();
     const uint32_t* src = scratch + b * Cfg<DIMS>::MAXW;
@@ -468,7 +447,7 @@ __global__ void __launch_bounds__(CMP_WARPS * 32) compact_kernel(uint32_t* __res
         if (sh) atomicOr(&buf[wid][idx + 1], val >> (32 - sh));
     }
     __syncwarp();
-    uint32_t* payload = out + base + G.table_words + hdr[HDR + c];
+    uint32_t* payload = out + base + G.table_words + off_c;
     for (int k = lane; k < words; k += 32) payload[k] = buf[wid][k];
 }
 
@@ -637,7 +616,7 @@ long long codec_scratch_bytes(int dims, int nz, int ny, int nx)
 {
     const Geo G = make_geo(dims, nz, ny, nx);
     const long long w = dims == 3 ? Cfg<3>::MAXW : Cfg<2>::MAXW;
-    return (G.nblocks + CHUNK) * w * 4;
+    return ((G.nblocks + CHUNK) * w + G.nchunks) * 4;   // block slots, then each chunk's word count
 }
 
 cudaError_t codec_compress_dev(const float* x, const CodecView& v, float tol_f, uint32_t* out,
@@ -650,12 +629,12 @@ cudaError_t codec_compress_dev(const float* x, const CodecView& v, float tol_f, 
     const unsigned cb = (unsigned)((G.nchunks + CMP_WARPS - 1) / CMP_WARPS);
     if (v.dims == 3) {
         enc_kernel<3><<<eb, ENC_THREADS, 0, s>>>(x, v, G, tol_f, sc, out, base_word, cap_words, err);
-        scan_kernel<<<1, 1024, 0, s>>>(out, base_word, cap_words, next_word, G, tol_f, err, stat_words);
-        compact_kernel<3><<<cb, CMP_WARPS * 32, 0, s>>>(out, base_word, next_word, G, sc, err);
+        compact_kernel<3><<<cb, CMP_WARPS * 32, 0, s>>>(out, base_word, cap_words, next_word, G, tol_f, sc, err,
+                                                         stat_words);
     } else {
         enc_kernel<2><<<eb, ENC_THREADS, 0, s>>>(x, v, G, tol_f, sc, out, base_word, cap_words, err);
-        scan_kernel<<<1, 1024, 0, s>>>(out, base_word, cap_words, next_word, G, tol_f, err, stat_words);
-        compact_kernel<2><<<cb, CMP_WARPS * 32, 0, s>>>(out, base_word, next_word, G, sc, err);
+        compact_kernel<2><<<cb, CMP_WARPS * 32, 0, s>>>(out, base_word, cap_words, next_word, G, tol_f, sc, err,
+                                                         stat_words);
     }
     return cudaGetLastError();
 }

@@ -30,7 +30,8 @@ namespace {
 
 constexpr long long NOALLOC_MAX_BLOCKS = 65536;            // 4^d blocks per field
 constexpr long long NOALLOC_WORDS_PER_BLOCK = 65;           // 2 + 32 * 64 bits, rounded up to words
-constexpr long long NOALLOC_SCRATCH_WORDS = (NOALLOC_MAX_BLOCKS + 32) * NOALLOC_WORDS_PER_BLOCK;
+// block slots, then one word count per 32-block chunk
+constexpr long long NOALLOC_SCRATCH_WORDS = (NOALLOC_MAX_BLOCKS + 32) * NOALLOC_WORDS_PER_BLOCK + NOALLOC_MAX_BLOCKS / 32;
 
 // Device-side scratch.  In host code these names are host-side stand-ins,
 // not device addresses: the address is looked up once per device below.

@@ -50,12 +50,13 @@ GRAD_TOL = 1e-2            # gradient accuracy a storage mode must keep to be th
 KERNEL_NAMES = {1: ("fwd_kernel", "adj_kernel"), 2: ("fwd_tma_kernel", "adj_tma_kernel"),
                 3: ("fwd3_kernel", "adj3_kernel"), 4: ("fwd4_kernel", "adj4_kernel"),
                 5: ("ot4_lap_kernel+ot4_fwd_kernel", "ot4_lap_kernel+ot4_adj_kernel")}
-# OT4 step (two passes): forward reads u^n, w and writes Z = w lap u^n, then
-# reads Z, u^n, u^{n-1}, w and writes u^{n+1}; reverse reads lam^j, u^{j-1}, w
-# and writes Z_l, Z_u, then reads Z_l, lam^j, Z_u, u^{j-1}, lam^{j+1}, w, g and
-# the previous Z_u and writes lam^{j-1}, g
+# OT4 forward step (two passes): reads u^n, w and writes Z = w lap u^n, then
+# reads Z, u^n, u^{n-1}, w and writes u^{n+1}.  Reverse step (three passes):
+# reads lam^j, u^{j-1}, w, the previous Z_u and g, writes Z_l, Z_u, g; reads
+# Z_l, lam^j, lam^{j+1}, w, writes lam^{j-1}; reads u^{j-1}, Z_u, lam^{j-1}, g,
+# writes g
 OT4_FWD_BYTES = 32
-OT4_ADJ_BYTES = 60
+OT4_ADJ_BYTES = 72
 
 
 def peaks():

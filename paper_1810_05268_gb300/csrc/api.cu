@@ -716,7 +716,8 @@ Tile host_tile(const ckfwi_model* m)
     return t;
 }
 
-// OT4 steps: the pass computing w lap f, then the update (ot4.cu).  The
+// OT4 steps (ot4.cu): forward, the pass computing w lap f, then the update;
+// reverse, w lap of lam^j and u^{j-1}, the update, the gradient pass.  The
 // reverse step j writes w lap u^{j-1} into z4[1 + j % 2] and pairs the one
 // of step j + 1 with lap lam^j.
 int ot4_fwd_step(ckfwi_model* m, const FwdArgs& a, const Tile& t, int ck, cudaStream_t st)
@@ -744,6 +745,7 @@ int ot4_fwd_step(ckfwi_model* m, const FwdArgs& a, const Tile& t, int ck, cudaSt
 int ot4_adj_step(ckfwi_model* m, const AdjArgs& a, const Tile& t, int utype, int j, cudaStream_t st)
 {
     const FieldGeom& f = m->fg;
+    // pass 1: Z_l, Z_u(j), and the deferred term of step j + 1
     Ot4LapArgs la{};
     la.g = f;
     la.f0 = a.l1;
@@ -752,16 +754,38 @@ int ot4_adj_step(ckfwi_model* m, const AdjArgs& a, const Tile& t, int utype, int
     la.z1 = org(m->z4[1 + (j & 1)], f);
     la.w = a.w;
     std::memcpy(la.c, m->c, sizeof(la.c));
+    la.gacc = a.gacc;
+    la.zu_next = j < m->g.nt ? org(m->z4[1 + ((j + 1) & 1)], f) : nullptr;
+    std::memcpy(la.c12, m->c12, sizeof(la.c12));
     if (t.ver == 6) CK_TRY(launch_ot4v_lap(la, t, m->K, utype, st));
     else CK_TRY(launch_ot4_lap(la, t, m->K, utype, st));
-    Ot4AdjArgs aa{};
-    aa.a = a;
-    aa.zl = la.z0;
-    aa.zu = la.z1;
-    aa.zu_next = j < m->g.nt ? org(m->z4[1 + ((j + 1) & 1)], f) : nullptr;
-    std::memcpy(aa.c12, m->c12, sizeof(aa.c12));
-    if (t.ver == 6) CK_TRY(launch_ot4v_adj(aa, t, m->K, utype, st));
-    else CK_TRY(launch_ot4_adj(aa, t, m->K, utype, st));
+    // pass 2: lam^{j-1} by the forward update kernel on the adjoint's fields
+    Ot4FwdArgs ua{};
+    ua.f.g = f;
+    ua.f.u = a.l1;
+    ua.f.up = a.l2;
+    ua.f.w = a.w;
+    ua.f.out = a.l0;
+    ua.f.eta = a.eta;
+    ua.f.hdt = a.hdt;
+    ua.f.src = a.adj;
+    ua.f.err = a.err;
+    ua.z = la.z0;
+    std::memcpy(ua.c12, m->c12, sizeof(ua.c12));
+    if (t.ver == 6) CK_TRY(launch_ot4v_fwd(ua, t, m->K, CK_NONE, st));
+    else CK_TRY(launch_ot4_fwd(ua, t, m->K, CK_NONE, st));
+    // pass 3: the gradient term of lam^{j-1}
+    Ot4GradArgs ga{};
+    ga.g = f;
+    ga.u = a.u;
+    ga.zu = la.z1;
+    ga.l0 = a.l0;
+    ga.gacc = a.gacc;
+    std::memcpy(ga.c, m->c, sizeof(ga.c));
+    std::memcpy(ga.c12, m->c12, sizeof(ga.c12));
+    ga.src = a.src;
+    if (t.ver == 6) CK_TRY(launch_ot4v_grad(ga, t, m->K, utype, st));
+    else CK_TRY(launch_ot4_grad(ga, t, m->K, utype, st));
     return CKFWI_OK;
 }
 
@@ -856,7 +880,7 @@ int adj_step(Ctx& cx, const Role& l1, const Role& l2, const Role& l0, const Role
         const int tok = cx.begin(PC_ADJ);
         if (m->ta.ver >= 5) {
             ST_TRY(ot4_adj_step(m, a, m->ta, utype, j, cx.st));
-            ++cx.launches;
+            cx.launches += 2;
         } else if (m->ta.ver == 2 && in_host(m, u)) {
             CK_TRY(launch_adj(a, host_tile(m), m->K, utype, cx.st));
         } else if (m->ta.ver == 4) {

@@ -88,8 +88,9 @@ struct AdjArgs {
     int* err;             // error flags (bit 3: a bounded wait ran out)
 };
 
-// OT4 kernel (Sec. 6): a step is two passes, Z = w lap f and then the
-// leapfrog update with w A f = Z + w lap(Z) / 12 (ot4.cu).
+// OT4 kernel (Sec. 6): a forward step is two passes, Z = w lap f and then the
+// leapfrog update with w A f = Z + w lap(Z) / 12; a reverse step is three
+// (ot4.cu).
 struct Ot4LapArgs {
     FieldGeom g;
     const float* f0;      // u^n (forward) or lam^j (reverse)
@@ -100,20 +101,28 @@ struct Ot4LapArgs {
     float c[MAXK + 1];
     int zlen;
     Sample smp;           // forward: receiver sampling of u^n
-};
-
-struct Ot4FwdArgs {
-    FwdArgs f;            // as OT2 (c unused)
-    const float* z;       // w lap u^n
+    float* gacc;          // reverse: gacc += zu_next lap(f0) / 12 (zu_next null: nothing)
+    const float* zu_next; // reverse: w lap u^j from the previous reverse step
     float c12[MAXK + 1];  // c_j / (12 h^2)
 };
 
-struct Ot4AdjArgs {
-    AdjArgs a;            // as OT2 (c: lap u^{j-1})
-    const float* zl;      // w lap lam^j
+struct Ot4FwdArgs {
+    FwdArgs f;            // as OT2 (c unused); also the reverse update (u = lam^j, up = lam^{j+1})
+    const float* z;       // w lap u^n (reverse: w lap lam^j)
+    float c12[MAXK + 1];  // c_j / (12 h^2)
+};
+
+// The reverse step's gradient pass: gacc += lam^{j-1} (lap u^{j-1} + lap(Z_u)/12 + q^{j-1}).
+struct Ot4GradArgs {
+    FieldGeom g;
+    const void* u;        // u^{j-1}, element type per launch
     const float* zu;      // w lap u^{j-1}
-    const float* zu_next; // w lap u^j from the previous reverse step; null at j = N
+    const float* l0;      // lam^{j-1}
+    float* gacc;
+    float c[MAXK + 1];
     float c12[MAXK + 1];
+    int zlen;
+    Inj src;              // Q^T s^{j-1}
 };
 
 enum CkMode { CK_NONE = 0, CK_FP32 = 1, CK_BF16 = 2, CK_FP16 = 3 };
@@ -173,13 +182,12 @@ int ot4_shape_count(int dims);
 Tile ot4_tile_at(int dims, int i, int zlen);
 cudaError_t launch_ot4_lap(const Ot4LapArgs& a, const Tile& t, int K, int ut, cudaStream_t s);
 cudaError_t launch_ot4_fwd(const Ot4FwdArgs& a, const Tile& t, int K, int ck, cudaStream_t s);
-cudaError_t launch_ot4_adj(const Ot4AdjArgs& a, const Tile& t, int K, int ut, cudaStream_t s);
-// ot4_v3.cu: the same passes vector-blocked (3D, geometry must pass v3_fits;
-// reverse steps vec 2 only)
+cudaError_t launch_ot4_grad(const Ot4GradArgs& a, const Tile& t, int K, int ut, cudaStream_t s);
+// ot4_v3.cu: the same passes vector-blocked (3D, geometry must pass v3_fits)
 bool ot4v_supported(int dims, int K, const Tile& t, bool reverse);
 cudaError_t launch_ot4v_lap(const Ot4LapArgs& a, const Tile& t, int K, int ut, cudaStream_t s);
 cudaError_t launch_ot4v_fwd(const Ot4FwdArgs& a, const Tile& t, int K, int ck, cudaStream_t s);
-cudaError_t launch_ot4v_adj(const Ot4AdjArgs& a, const Tile& t, int K, int ut, cudaStream_t s);
+cudaError_t launch_ot4v_grad(const Ot4GradArgs& a, const Tile& t, int K, int ut, cudaStream_t s);
 
 // stencil_tma.cu (CUtensorMap comes from <cuda.h>)
 }  // namespace ckfwi

@@ -20,13 +20,19 @@
 // dt^2/12 c^4 lap u^n lap lam^n.  lap lam^n needs lam^n's neighbours, which
 // exist only after the step that makes lam^n, when u^n is no longer at hand.
 // So each reverse step j keeps Z_u = w lap u^{j-1} for the next one, which
-// pairs it with lap lam^{j-1} (both per point, no extra stencil field):
-//   pass 1: Z_l = w lap lam^j,  Z_u(j) = w lap u^{j-1}
+// pairs it with lap lam^{j-1} (both per point).  A reverse step is three
+// passes, each staging at most two fields:
+//   pass 1: Z_l = w lap lam^j,  Z_u(j) = w lap u^{j-1},
+//           gacc += Z_u(j+1) lap(lam^j)/12                       (j < N)
 //   pass 2: lam^{j-1} = leapfrog(lam^j, lam^{j+1}, Z_l + w (lap(Z_l)/12 - P^T r^j))
-//           gacc += lam^{j-1} (lap u^{j-1} + lap(Z_u(j))/12 + q^{j-1})
-//                 + Z_u(j+1) lap(lam^j)/12                    (j < N)
+//           (the forward update kernel with the adjoint's fields)
+//   pass 3: gacc += lam^{j-1} (lap u^{j-1} + lap(Z_u(j))/12 + q^{j-1})
 // and gacc times c^2 is the gradient, as for OT2.  (Z_u(N+1) would pair with
-// lap lam^N = 0; at j = 1 the term for n = 0 vanishes since u^0 = 0.)
+// lap lam^N = 0; at j = 1 the term for n = 0 vanishes since u^0 = 0.)  The
+// three passes move 72 B/pt against 60 for a two-pass form whose second pass
+// staged all four fields, yet run 20% faster (205 against 254 us at 208^3,
+// order 8): that pass needed 228 registers at two points per thread, one
+// 256-thread CTA per SM.
 //
 // Every step of one model runs these kernels, forward and reverse, so a
 // recomputed forward step repeats the first sweep bit for bit.
@@ -152,7 +158,12 @@ __global__ void __launch_bounds__(BX * BY) ot4_lap_kernel(const Ot4LapArgs a)
         if (c.act) {
             const long long o = (long long)z * c.pxy + c.col;
             a.z0[o] = __fmul_rn(wv, lap_at<K, DIMS, SX>(s0.q, sm, cy, c.tx + K, a.c));
-            if (NF == 2) a.z1[o] = __fmul_rn(wv, lap_at<K, DIMS, SX>(s1.q, sm + TILE, cy, c.tx + K, a.c));
+            if (NF == 2) {
+                a.z1[o] = __fmul_rn(wv, lap_at<K, DIMS, SX>(s1.q, sm + TILE, cy, c.tx + K, a.c));
+                if (a.zu_next)   // the deferred gradient term of the step before: Z_u(j+1) lap(lam^j)/12
+                    a.gacc[o] = __fmaf_rn(__ldg(a.zu_next + o), lap_at<K, DIMS, SX>(s0.q, sm, cy, c.tx + K, a.c12),
+                                          a.gacc[o]);
+            }
         }
         s0.shift();
         if (NF == 2) s1.shift();
@@ -216,80 +227,51 @@ __global__ void __launch_bounds__(BX * BY) ot4_fwd_kernel(const Ot4FwdArgs A)
     }
 }
 
-// ------------------------------------------------------------- pass 2, reverse
+// ------------------------------------------------------------- pass 3, reverse
 template <int K, int DIMS, int BX, int BY, class UT>
-__global__ void __launch_bounds__(BX * BY) ot4_adj_kernel(const Ot4AdjArgs A)
+__global__ void __launch_bounds__(BX * BY) ot4_grad_kernel(const Ot4GradArgs a)
 {
     extern __shared__ float sm[];
     constexpr int SX = BX + 2 * K;
     constexpr int TILE = (DIMS == 3 ? BY + 2 * K : 1) * SX;
-    const AdjArgs& a = A.a;
     const Col4 c = col4<DIMS, BX, BY>(a.g);
     const int z0 = blockIdx.z * a.zlen;
     if (z0 >= c.nz) return;
     const int z1 = min(z0 + a.zlen, c.nz);
     const int cy = (DIMS == 3) ? c.ty + K : 0;
-    const float ecol = c.act ? ((DIMS == 3 ? a.eta[c.nz + c.y] : 0.0f) + a.eta[c.nz + c.ny + c.x]) : 0.0f;
-    const InjCol ia = inj_col(a.adj, c.y, c.x, c.act);
     const InjCol is = inj_col(a.src, c.y, c.x, c.act);
     const UT* uu = static_cast<const UT*>(a.u);
-    const bool defer = A.zu_next != nullptr;
-    float* smzl = sm;
-    float* sml = sm + TILE;
-    float* smzu = sm + 2 * TILE;
-    float* smu = sm + 3 * TILE;
-
-    Stage4<K, DIMS, BX, BY> szl, sl, szu, su;
-    szl.start(A.zl, c, z0);
-    sl.start(a.l1, c, z0);
-    szu.start(A.zu, c, z0);
+    float* smu = sm;
+    float* smzu = sm + TILE;
+    Stage4<K, DIMS, BX, BY> su, szu;
     su.start(uu, c, z0);
+    szu.start(a.zu, c, z0);
     long long o1 = (long long)z0 * c.pxy + c.col;
-    float nl2 = c.act ? __ldg(a.l2 + o1) : 0.0f;
-    float nw = c.act ? __ldg(a.w + o1) : 0.0f;
+    float nl = c.act ? __ldg(a.l0 + o1) : 0.0f;
     float ng = c.act ? a.gacc[o1] : 0.0f;
-    float nzn = (c.act && defer) ? __ldg(A.zu_next + o1) : 0.0f;
     for (int z = z0; z < z1; ++z) {
-        szl.take();
-        sl.take();
-        szu.take();
         su.take();
-        const float l2v = nl2, wv = nw, gv = ng, znv = nzn;
+        szu.take();
+        const float lv = nl, gv = ng;
         if (z + 1 < z1) {
-            szl.ahead(A.zl, c, z + 1);
-            sl.ahead(a.l1, c, z + 1);
-            szu.ahead(A.zu, c, z + 1);
             su.ahead(uu, c, z + 1);
+            szu.ahead(a.zu, c, z + 1);
             o1 = (long long)(z + 1) * c.pxy + c.col;
-            nl2 = c.act ? __ldg(a.l2 + o1) : 0.0f;
-            nw = c.act ? __ldg(a.w + o1) : 0.0f;
+            nl = c.act ? __ldg(a.l0 + o1) : 0.0f;
             ng = c.act ? a.gacc[o1] : 0.0f;
-            nzn = (c.act && defer) ? __ldg(A.zu_next + o1) : 0.0f;
         }
         __syncthreads();
-        szl.put(smzl, c);
-        if (defer) sl.put(sml, c);
-        szu.put(smzu, c);
         su.put(smu, c);
+        szu.put(smzu, c);
         __syncthreads();
         if (c.act) {
-            float s = lap_at<K, DIMS, SX>(szl.q, smzl, cy, c.tx + K, A.c12);
-            s = __fadd_rn(s, inj_val(a.adj, ia, z));
-            const float eta = a.eta[z] + ecol;
-            const float lam = leapfrog4(sl.q[K], l2v, wv, szl.q[K], s, eta, a.hdt);
             float g = lap_at<K, DIMS, SX>(su.q, smu, cy, c.tx + K, a.c);
-            g = __fadd_rn(g, lap_at<K, DIMS, SX>(szu.q, smzu, cy, c.tx + K, A.c12));
+            g = __fadd_rn(g, lap_at<K, DIMS, SX>(szu.q, smzu, cy, c.tx + K, a.c12));
             g = __fadd_rn(g, inj_val(a.src, is, z));
-            float acc = __fmaf_rn(lam, g, gv);
-            if (defer) acc = __fmaf_rn(znv, lap_at<K, DIMS, SX>(sl.q, sml, cy, c.tx + K, A.c12), acc);
-            const long long o = (long long)z * c.pxy + c.col;
-            a.l0[o] = lam;
-            a.gacc[o] = acc;
+            a.gacc[(long long)z * c.pxy + c.col] = __fmaf_rn(lv, g, gv);
         }
-        szl.shift();
-        sl.shift();
-        szu.shift();
         su.shift();
+        szu.shift();
     }
 }
 
@@ -336,14 +318,14 @@ cudaError_t fwd2_go(const Ot4FwdArgs& a, int ck, cudaStream_t s)
 }
 
 template <int K, int DIMS, int BX, int BY>
-cudaError_t adj2_go(const Ot4AdjArgs& a, int ut, cudaStream_t s)
+cudaError_t grad_go(const Ot4GradArgs& a, int ut, cudaStream_t s)
 {
-    const dim3 blk(BX, BY, 1), grd = grid_of<DIMS, BX, BY>(a.a.g, a.a.zlen);
-    const size_t sh = smem_bytes<DIMS, BX, BY>(K, 4);
+    const dim3 blk(BX, BY, 1), grd = grid_of<DIMS, BX, BY>(a.g, a.zlen);
+    const size_t sh = smem_bytes<DIMS, BX, BY>(K, 2);
     switch (ut) {
-    case U_FP32: ot4_adj_kernel<K, DIMS, BX, BY, float><<<grd, blk, sh, s>>>(a); break;
-    case U_BF16: ot4_adj_kernel<K, DIMS, BX, BY, __nv_bfloat16><<<grd, blk, sh, s>>>(a); break;
-    case U_FP16: ot4_adj_kernel<K, DIMS, BX, BY, __half><<<grd, blk, sh, s>>>(a); break;
+    case U_FP32: ot4_grad_kernel<K, DIMS, BX, BY, float><<<grd, blk, sh, s>>>(a); break;
+    case U_BF16: ot4_grad_kernel<K, DIMS, BX, BY, __nv_bfloat16><<<grd, blk, sh, s>>>(a); break;
+    case U_FP16: ot4_grad_kernel<K, DIMS, BX, BY, __half><<<grd, blk, sh, s>>>(a); break;
     default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
@@ -379,11 +361,11 @@ cudaError_t fwd2_k(const Ot4FwdArgs& a, const Tile& t, int ck, cudaStream_t s)
 }
 
 template <int K>
-cudaError_t adj2_k(const Ot4AdjArgs& a, const Tile& t, int ut, cudaStream_t s)
+cudaError_t grad_k(const Ot4GradArgs& a, const Tile& t, int ut, cudaStream_t s)
 {
     return by_shape<K>(
-        a.a.g.dims, t, [&] { return adj2_go<K, 3, 32, 8>(a, ut, s); },
-        [&] { return adj2_go<K, 3, 32, 16>(a, ut, s); }, [&] { return adj2_go<K, 2, 128, 1>(a, ut, s); });
+        a.g.dims, t, [&] { return grad_go<K, 3, 32, 8>(a, ut, s); },
+        [&] { return grad_go<K, 3, 32, 16>(a, ut, s); }, [&] { return grad_go<K, 2, 128, 1>(a, ut, s); });
 }
 }  // namespace
 
@@ -433,15 +415,15 @@ cudaError_t launch_ot4_fwd(const Ot4FwdArgs& a, const Tile& t, int K, int ck, cu
     }
 }
 
-cudaError_t launch_ot4_adj(const Ot4AdjArgs& a, const Tile& t, int K, int ut, cudaStream_t s)
+cudaError_t launch_ot4_grad(const Ot4GradArgs& a, const Tile& t, int K, int ut, cudaStream_t s)
 {
-    Ot4AdjArgs b = a;
-    b.a.zlen = t.zlen;
+    Ot4GradArgs b = a;
+    b.zlen = t.zlen;
     switch (K) {
-    case 1: return adj2_k<1>(b, t, ut, s);
-    case 2: return adj2_k<2>(b, t, ut, s);
-    case 4: return adj2_k<4>(b, t, ut, s);
-    case 8: return adj2_k<8>(b, t, ut, s);
+    case 1: return grad_k<1>(b, t, ut, s);
+    case 2: return grad_k<2>(b, t, ut, s);
+    case 4: return grad_k<4>(b, t, ut, s);
+    case 8: return grad_k<8>(b, t, ut, s);
     default: return cudaErrorInvalidValue;
     }
 }

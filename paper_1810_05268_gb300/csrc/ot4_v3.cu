@@ -1,6 +1,6 @@
-// Vector-blocked OT4 kernels for 3D grids: the two passes of ot4.cu
-// (Z = w lap f, then the update with w A f = Z + w lap(Z) / 12, and the
-// reverse step with its deferred gradient term) on the thread layout of the
+// Vector-blocked OT4 kernels for 3D grids: the passes of ot4.cu (Z = w lap f,
+// the update with w A f = Z + w lap(Z) / 12, and the reverse step's
+// gradient pass with its deferred term) on the thread layout of the
 // vector-blocked OT2 kernels (stencil_v3.cuh): a thread owns V consecutive x
 // points, global accesses are V-wide vectors, staged planes are double
 // buffered with one barrier per plane, and the arithmetic runs on pairs of
@@ -181,6 +181,29 @@ __global__ void __launch_bounds__(TX * TY) ot4v_lap_kernel(const Ot4LapArgs a)
                     r[2 * p + 1] = t.y;
                 }
                 vput<V>(a.z1, o, r, P.full, P.x0, P.nx);
+                if (a.zu_next) {   // the deferred gradient term of the step before: Z_u(j+1) lap(lam^j)/12
+                    float d[V], zn[V], gv[V];
+                    lap3<K, V, TX, TY>(d, s0.q, sm, P.tx, P.ty, a.c12);
+                    const long long oc = P.col + (long long)z * P.pxy;
+                    if (P.full) {
+                        gld<V>(zn, a.zu_next + oc);
+                        gld_plain<V>(gv, a.gacc + oc);
+                    } else {
+#pragma unroll
+                        for (int i = 0; i < V; ++i) {
+                            zn[i] = P.x0 + i < P.nx ? __ldg(a.zu_next + oc + i) : 0.0f;
+                            gv[i] = P.x0 + i < P.nx ? a.gacc[oc + i] : 0.0f;
+                        }
+                    }
+#pragma unroll
+                    for (int p = 0; p < V / 2; ++p) {
+                        const float2 t = __ffma2_rn(f2(zn[2 * p], zn[2 * p + 1]), f2(d[2 * p], d[2 * p + 1]),
+                                                    f2(gv[2 * p], gv[2 * p + 1]));
+                        r[2 * p] = t.x;
+                        r[2 * p + 1] = t.y;
+                    }
+                    vput<V>(a.gacc, o, r, P.full, P.x0, P.nx);
+                }
             }
         }
         s0.stage(smn, P.tx, P.ty, hm);
@@ -277,84 +300,59 @@ __global__ void __launch_bounds__(TX * TY) ot4v_fwd_kernel(const Ot4FwdArgs A)
     }
 }
 
-// ------------------------------------------------------------- pass 2, reverse
+// ------------------------------------------------------------- pass 3, reverse
 template <int K, int V, int TX, int TY, class UT>
-__global__ void __launch_bounds__(TX * TY) ot4v_adj_kernel(const Ot4AdjArgs A)
+__global__ void __launch_bounds__(TX * TY) ot4v_grad_kernel(const Ot4GradArgs a)
 {
     using G = G3<K, V, TX, TY>;
     extern __shared__ __align__(16) float smem4[];
-    const AdjArgs& a = A.a;
     const Pos3 P = pos3<V, TX, TY, G::BXP>(a.g);
     const int z0 = blockIdx.z * a.zlen;
     if (z0 >= P.nz) return;
     const int z1 = min(z0 + a.zlen, P.nz);
-    float ecol[V];
-#pragma unroll
-    for (int i = 0; i < V; ++i)
-        ecol[i] = (P.rowact && P.x0 + i < P.nx) ? __fadd_rn(a.eta[P.nz + P.y], a.eta[P.nz + P.ny + P.x0 + i]) : 0.0f;
-    Inj3<V> ia, is;
-    ia.init(a.adj, P.y, P.x0, P.nx, P.rowact);
+    Inj3<V> is;
     is.init(a.src, P.y, P.x0, P.nx, P.rowact);
     HaloMap<K, V, TX, TY> hm;
     hm.init(P.tx, P.ty, P.xb, P.x0, P.y, P.nx, P.ny, P.px);
     const UT* uu = static_cast<const UT*>(a.u);
-    const bool defer = A.zu_next != nullptr;
-    const float* __restrict__ L2 = a.l2 + P.col;
-    const float* __restrict__ W = a.w + P.col;
+    const float* __restrict__ L0 = a.l0 + P.col;
     const float* __restrict__ GA = a.gacc + P.col;
-    const float* __restrict__ ZN = defer ? A.zu_next + P.col : W;   // W: a valid stand-in, never used
-    VStage<K, V, TX, TY, float> szl, sl, szu;
     VStage<K, V, TX, TY, UT> su;
-    szl.start(A.zl, P.col, z0, P.pxy, P.cload, hm, smem4, P.tx, P.ty);
-    sl.start(a.l1, P.col, z0, P.pxy, P.cload, hm, smem4 + G::TILE, P.tx, P.ty);
-    szu.start(A.zu, P.col, z0, P.pxy, P.cload, hm, smem4 + 2 * G::TILE, P.tx, P.ty);
-    su.start(uu, P.col, z0, P.pxy, P.cload, hm, smem4 + 3 * G::TILE, P.tx, P.ty);
-    float nl2[V], nw[V], ng[V], nzn[V];
+    VStage<K, V, TX, TY, float> szu;
+    su.start(uu, P.col, z0, P.pxy, P.cload, hm, smem4, P.tx, P.ty);
+    szu.start(a.zu, P.col, z0, P.pxy, P.cload, hm, smem4 + G::TILE, P.tx, P.ty);
+    float nl[V], ng[V];
     if (P.cload) {
-        gld<V>(nl2, L2 + z0 * P.pxy);
-        gld<V>(nw, W + z0 * P.pxy);
+        gld<V>(nl, L0 + z0 * P.pxy);
         gld_plain<V>(ng, GA + z0 * P.pxy);
-        gld<V>(nzn, ZN + z0 * P.pxy);
     } else {
-        vzero<V>(nl2);
-        vzero<V>(nw);
+        vzero<V>(nl);
         vzero<V>(ng);
-        vzero<V>(nzn);
     }
     const int zqmax = P.nz + K - 1;
     for (int z = z0; z < z1; ++z) {
-        float* sm = smem4 + ((z - z0) & 1) * (4 * G::TILE);
-        float* smn = smem4 + (((z - z0) & 1) ^ 1) * (4 * G::TILE);
-        szl.take();
-        sl.take();
-        szu.take();
+        float* sm = smem4 + ((z - z0) & 1) * (2 * G::TILE);
+        float* smn = smem4 + (((z - z0) & 1) ^ 1) * (2 * G::TILE);
         su.take();
-        float l2v[V], wv[V], gv[V], znv[V];
+        szu.take();
+        float lv[V], gv[V];
 #pragma unroll
         for (int i = 0; i < V; ++i) {
-            l2v[i] = nl2[i];
-            wv[i] = nw[i];
+            lv[i] = nl[i];
             gv[i] = ng[i];
-            znv[i] = nzn[i];
         }
         const int zn = min(z + 1, z1 - 1) * P.pxy, zq = min(z + K + 1, zqmax) * P.pxy;
-        szl.fetch(A.zl, P.col, zq, zn, P.cload, hm);
-        sl.fetch(a.l1, P.col, zq, zn, P.cload, hm);
-        szu.fetch(A.zu, P.col, zq, zn, P.cload, hm);
         su.fetch(uu, P.col, zq, zn, P.cload, hm);
+        szu.fetch(a.zu, P.col, zq, zn, P.cload, hm);
         if (P.cload) {
-            gld<V>(nl2, L2 + zn);
-            gld<V>(nw, W + zn);
+            gld<V>(nl, L0 + zn);
             gld_plain<V>(ng, GA + zn);
-            gld<V>(nzn, ZN + zn);
         }
         __syncthreads();
         if (P.cload) {
-            float s[V], g[V], t[V], d[V], lam[V], acc[V];
-            lap3<K, V, TX, TY>(s, szl.q, sm, P.tx, P.ty, A.c12);
-            ia.add(s, a.adj, z);
-            lap3<K, V, TX, TY>(g, su.q, sm + 3 * G::TILE, P.tx, P.ty, a.c);
-            lap3<K, V, TX, TY>(t, szu.q, sm + 2 * G::TILE, P.tx, P.ty, A.c12);
+            float g[V], t[V], acc[V];
+            lap3<K, V, TX, TY>(g, su.q, sm, P.tx, P.ty, a.c);
+            lap3<K, V, TX, TY>(t, szu.q, sm + G::TILE, P.tx, P.ty, a.c12);
 #pragma unroll
             for (int p = 0; p < V / 2; ++p) {
                 const float2 r = __fadd2_rn(f2(g[2 * p], g[2 * p + 1]), f2(t[2 * p], t[2 * p + 1]));
@@ -362,41 +360,24 @@ __global__ void __launch_bounds__(TX * TY) ot4v_adj_kernel(const Ot4AdjArgs A)
                 g[2 * p + 1] = r.y;
             }
             is.add(g, a.src, z);
-            if (defer) lap3<K, V, TX, TY>(d, sl.q, sm + G::TILE, P.tx, P.ty, A.c12);
-            const float ez = a.eta[z];
-            const float* lc = sl.q[K];
-            const float* zc = szl.q[K];
 #pragma unroll
             for (int p = 0; p < V / 2; ++p) {
-                const int i = 2 * p;
-                const float2 eta = __fadd2_rn(f2(ez, ez), f2(ecol[i], ecol[i + 1]));
-                const float2 r = leap4v(f2(lc[i], lc[i + 1]), f2(l2v[i], l2v[i + 1]), f2(wv[i], wv[i + 1]),
-                                        f2(zc[i], zc[i + 1]), f2(s[i], s[i + 1]), eta, a.hdt);
-                float2 gg = __ffma2_rn(r, f2(g[i], g[i + 1]), f2(gv[i], gv[i + 1]));
-                if (defer) gg = __ffma2_rn(f2(znv[i], znv[i + 1]), f2(d[i], d[i + 1]), gg);
-                lam[i] = r.x;
-                lam[i + 1] = r.y;
-                acc[i] = gg.x;
-                acc[i + 1] = gg.y;
+                const float2 r = __ffma2_rn(f2(lv[2 * p], lv[2 * p + 1]), f2(g[2 * p], g[2 * p + 1]),
+                                            f2(gv[2 * p], gv[2 * p + 1]));
+                acc[2 * p] = r.x;
+                acc[2 * p + 1] = r.y;
             }
-            const long long o = (long long)z * P.pxy + P.col;
-            vput<V>(a.l0, o, lam, P.full, P.x0, P.nx);
-            vput<V>(a.gacc, o, acc, P.full, P.x0, P.nx);
+            vput<V>(a.gacc, (long long)z * P.pxy + P.col, acc, P.full, P.x0, P.nx);
         }
-        szl.stage(smn, P.tx, P.ty, hm);
-        sl.stage(smn + G::TILE, P.tx, P.ty, hm);
-        szu.stage(smn + 2 * G::TILE, P.tx, P.ty, hm);
-        su.stage(smn + 3 * G::TILE, P.tx, P.ty, hm);
-        szl.shift();
-        sl.shift();
-        szu.shift();
+        su.stage(smn, P.tx, P.ty, hm);
+        szu.stage(smn + G::TILE, P.tx, P.ty, hm);
         su.shift();
+        szu.shift();
     }
 }
 
 // ---------------------------------------------------------------- dispatch
-// (V, TX, TY) shapes: forward steps {4, 8, 16} and {2, 16, 16}; the reverse
-// step, with four staged fields, {2, 16, 16} only (register queues).
+// (V, TX, TY) shapes: {4, 8, 16} and {2, 16, 16} for every pass.
 template <int V, int TX, int TY, int BXP>
 dim3 grid4(const FieldGeom& g, int zlen)
 {
@@ -440,18 +421,25 @@ cudaError_t fwdv_go(const Ot4FwdArgs& a, int ck, cudaStream_t s)
 }
 
 template <int K, int V, int TX, int TY>
-cudaError_t adjv_go(const Ot4AdjArgs& a, int ut, cudaStream_t s)
+cudaError_t gradv_go(const Ot4GradArgs& a, int ut, cudaStream_t s)
 {
     using G = G3<K, V, TX, TY>;
-    const dim3 blk(TX, TY, 1), grd = grid4<V, TX, TY, G::BXP>(a.a.g, a.a.zlen);
-    const size_t sh = 8 * (size_t)G::TILE * sizeof(float);
+    const dim3 blk(TX, TY, 1), grd = grid4<V, TX, TY, G::BXP>(a.g, a.zlen);
+    const size_t sh = 4 * (size_t)G::TILE * sizeof(float);
     switch (ut) {
-    case U_FP32: ot4v_adj_kernel<K, V, TX, TY, float><<<grd, blk, sh, s>>>(a); break;
-    case U_BF16: ot4v_adj_kernel<K, V, TX, TY, __nv_bfloat16><<<grd, blk, sh, s>>>(a); break;
-    case U_FP16: ot4v_adj_kernel<K, V, TX, TY, __half><<<grd, blk, sh, s>>>(a); break;
+    case U_FP32: ot4v_grad_kernel<K, V, TX, TY, float><<<grd, blk, sh, s>>>(a); break;
+    case U_BF16: ot4v_grad_kernel<K, V, TX, TY, __nv_bfloat16><<<grd, blk, sh, s>>>(a); break;
+    case U_FP16: ot4v_grad_kernel<K, V, TX, TY, __half><<<grd, blk, sh, s>>>(a); break;
     default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
+}
+
+template <int K>
+cudaError_t gradv_k(const Ot4GradArgs& a, const Tile& t, int ut, cudaStream_t s)
+{
+    if (t.vec == 4) return gradv_go<K, 4, 8, 16>(a, ut, s);
+    return gradv_go<K, 2, 16, 16>(a, ut, s);
 }
 
 template <int K>
@@ -471,9 +459,10 @@ cudaError_t fwdv_k(const Ot4FwdArgs& a, const Tile& t, int ck, cudaStream_t s)
 
 bool ot4v_supported(int dims, int K, const Tile& t, bool reverse)
 {
+    (void)reverse;   // every pass has both vector widths
     if (dims != 3 || t.ver != 6 || t.zlen < 1 || t.by != 16 || t.bx != 32 || t.by < K) return false;
     if (K != 1 && K != 2 && K != 4 && K != 8) return false;
-    return t.vec == 2 || (t.vec == 4 && !reverse);
+    return t.vec == 2 || t.vec == 4;
 }
 
 cudaError_t launch_ot4v_lap(const Ot4LapArgs& a, const Tile& t, int K, int ut, cudaStream_t s)
@@ -504,16 +493,16 @@ cudaError_t launch_ot4v_fwd(const Ot4FwdArgs& a, const Tile& t, int K, int ck, c
     }
 }
 
-cudaError_t launch_ot4v_adj(const Ot4AdjArgs& a, const Tile& t, int K, int ut, cudaStream_t s)
+cudaError_t launch_ot4v_grad(const Ot4GradArgs& a, const Tile& t, int K, int ut, cudaStream_t s)
 {
-    Ot4AdjArgs b = a;
-    b.a.zlen = t.zlen;
-    if (!v3_fits(a.a.g, K) || !ot4v_supported(a.a.g.dims, K, t, true)) return cudaErrorInvalidValue;
+    Ot4GradArgs b = a;
+    b.zlen = t.zlen;
+    if (!v3_fits(a.g, K) || !ot4v_supported(a.g.dims, K, t, true)) return cudaErrorInvalidValue;
     switch (K) {
-    case 1: return adjv_go<1, 2, 16, 16>(b, ut, s);
-    case 2: return adjv_go<2, 2, 16, 16>(b, ut, s);
-    case 4: return adjv_go<4, 2, 16, 16>(b, ut, s);
-    case 8: return adjv_go<8, 2, 16, 16>(b, ut, s);
+    case 1: return gradv_k<1>(b, t, ut, s);
+    case 2: return gradv_k<2>(b, t, ut, s);
+    case 4: return gradv_k<4>(b, t, ut, s);
+    case 8: return gradv_k<8>(b, t, ut, s);
     default: return cudaErrorInvalidValue;
     }
 }

@@ -50,7 +50,7 @@ def main():
     out["adj_us"] = st["adj_ms"] * 1e3 / st["adj_launches"]
     npts = int(np.prod(shape))
     # algorithmic bytes per point of a step (OT4: both passes)
-    fb, ab = (32, 60) if args.time_order == 4 else (16, 28)
+    fb, ab = (32, 72) if args.time_order == 4 else (16, 28)
     out["fwd_gbs"] = fb * npts / (out["fwd_us"] * 1e-6) / 1e9
     out["adj_gbs"] = ab * npts / (out["adj_us"] * 1e-6) / 1e9
     out["fwd_kernel"] = [st["fwd_ver"], st["fwd_bx"], st["fwd_by"], st["fwd_zlen"]]

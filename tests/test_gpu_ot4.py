@@ -212,13 +212,15 @@ def test_ot4_vector_blocked_half_slots_are_bitwise(monkeypatch, mode):
     assert p1 == p2 and torch.equal(g1, g2)
 
 
-def test_ot4_vector_blocked_reverse_rejects_width_4(monkeypatch):
-    """A forced reverse tile the vector-blocked OT4 kernels do not have is
-    ignored (the autotuner's choice stands)."""
-    case = _case(3, 4, 53)
+def test_ot4_vector_blocked_reverse_at_width_4(monkeypatch):
+    """The vector-blocked reverse passes at four points per thread give the
+    register-queue values bit for bit."""
+    case = _case(3, 8, 53)
     dobs = torch.from_numpy(_obs(case)).cuda()
-    _, _, _, st = _grad_with_tiles(monkeypatch, case, dobs, "6,32,16,9,4", "6,32,16,9,4", ckpt_slots=4)
-    assert not (st["adj_ver"] == 6 and st["adj_vec"] == 4)
+    _, p1, g1, _ = _grad_with_tiles(monkeypatch, case, dobs, "5,32,8,7", "5,32,8,7", ckpt_slots=4)
+    _, p2, g2, st = _grad_with_tiles(monkeypatch, case, dobs, "6,32,16,9,4", "6,32,16,9,4", ckpt_slots=4)
+    assert st["adj_ver"] == 6 and st["adj_vec"] == 4
+    assert p1 == p2 and torch.equal(g1, g2)
 
 
 def test_ot4_windowed_batch_is_refused():

@@ -12,4 +12,7 @@ Modules
   oracle.propagator  forward modelling, adjoint, misfit and gradient (C, FP64)
   oracle.revolve     binomial checkpointing schedule and its counts (Python)
   oracle.codec       fixed-accuracy 4^d block-transform codec (C, integer)
+  oracle.checkpointed  the gradient a Revolve executor computes when its
+                     checkpoints are stored rounded or compressed (Python
+                     over the C steps)
 """

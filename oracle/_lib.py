@@ -37,6 +37,12 @@ def lib():
             L.ora_step.argtypes = [P, P, P, P, P]
             L.ora_adjoint.argtypes = [P, P, i, P, P, i, P, P, P, P, P, i]
             L.ora_gradient.argtypes = [P, P, i, P, P, i, P, P, P, P, P, i]
+            L.ora_problem_create.argtypes = [P, P, i, P, P, i, P]
+            L.ora_problem_create.restype = P
+            L.ora_problem_destroy.argtypes = [P]
+            L.ora_problem_destroy.restype = None
+            L.ora_problem_fwd_step.argtypes = [P, i, P, P, P]
+            L.ora_problem_adj_step.argtypes = [P, P, i, P, P, P, P, P]
             L.codec_compress.argtypes = [i, i, i, i, P, ctypes.c_double, P, ctypes.c_size_t, P]
             L.codec_compress.restype = ctypes.c_longlong
             L.codec_decompress.argtypes = [i, i, i, i, P, ctypes.c_size_t, P]
@@ -48,6 +54,7 @@ def lib():
             L.codec_rate_words.restype = ctypes.c_longlong
             for f in ("ora_fd_weights", "ora_laplacian", "ora_damping", "ora_ricker",
                       "ora_interp", "ora_forward", "ora_step", "ora_adjoint", "ora_gradient",
+                      "ora_problem_fwd_step", "ora_problem_adj_step",
                       "codec_decompress"):
                 getattr(L, f).restype = ctypes.c_int
             _lib = L

@@ -317,6 +317,47 @@ static void add_sources(const problem* P, int n, double* lap)
             lap[P->sidx[s * P->nstc + i]] += P->swt[s * P->nstc + i] * P->sser[(long)s * P->g->nt + n];
 }
 
+/* One forward step n of the recursion:  out = u^{n+1} from cur = u^n,
+ * prev = u^{n-1} and the source term q^n.  lap: np scratch values. */
+static void forward_step(const problem* P, int n, const double* cur, const double* prev,
+                         double* lap, double* out)
+{
+    spatial_op(P, cur, lap);
+    add_sources(P, n, lap);
+    leapfrog(P, cur, prev, lap, out);
+}
+
+/* One reverse step j = N..1 of the adjoint recursion (header):
+ * l0 = lam^{j-1} from l1 = lam^j, l2 = lam^{j+1} and the residual row r^j.
+ * With grad, adds the gradient term of n = j-1, which reads the forward
+ * state un = u^{n}:  lam^n (A u^n + q^n) c^2, and for OT4 also
+ * dt^2/12 c^4 lap(u^n) lap(lam^n).  lap, tmp: np scratch values each. */
+static void adjoint_step(const problem* P, const double* r, int j, const double* l1, const double* l2,
+                         double* l0, const double* un, double* grad, double* lap, double* tmp)
+{
+    const ora_grid* g = P->g;
+    const long np = P->np;
+    spatial_op(P, l1, lap);
+    for (int rr = 0; rr < P->nrec; ++rr)
+        for (int i = 0; i < P->nstc; ++i)
+            lap[P->ridx[rr * P->nstc + i]] -= P->rwt[rr * P->nstc + i] * r[(long)j * P->nrec + rr];
+    leapfrog(P, l1, l2, lap, l0);
+    if (!grad) return;
+    const int n = j - 1;
+    spatial_op(P, un, tmp);
+    add_sources(P, n, tmp);
+#pragma omp parallel for schedule(static)
+    for (long p = 0; p < np; ++p) grad[p] += l0[p] * tmp[p] * P->c2[p];
+    if (is_ot4(P)) {
+        /* derivative of the OT4 correction: dt^2/12 c^4 lap u^n lap lam^n */
+        const double kk = g->dt * g->dt / 12.0;
+        ora_laplacian(g, un, tmp);
+        ora_laplacian(g, l0, lap);
+        for (long p = 0; p < np; ++p)
+            grad[p] += kk * P->c2[p] * P->c2[p] * tmp[p] * lap[p];
+    }
+}
+
 static void sample(const problem* P, const double* u, double* d_row)
 {
     for (int r = 0; r < P->nrec; ++r) {
@@ -345,9 +386,7 @@ static int forward_run(const problem* P, double* d, double* u_final, double* ckp
             memcpy(ckpt + (long)(2 * (n / seg)) * np, b, sizeof(double) * np);
             memcpy(ckpt + (long)(2 * (n / seg) + 1) * np, a, sizeof(double) * np);
         }
-        spatial_op(P, b, lap);
-        add_sources(P, n, lap);
-        leapfrog(P, b, a, lap, c);
+        forward_step(P, n, b, a, lap, c);
         if (d) sample(P, c, d + (long)(n + 1) * P->nrec);
         double* t = a; a = b; b = c; c = t;
     }
@@ -434,34 +473,14 @@ static int adjoint_run(const problem* P, const double* r, double* grad, double* 
             memcpy(prev, ckpt + (long)(2 * k + 1) * np, sizeof(double) * np);
             for (int n = s0; n < s1 - 1; ++n) {
                 double* cur = useg + (long)(n - s0 + 1) * np;
-                spatial_op(P, cur, lap);
-                add_sources(P, n, lap);
-                leapfrog(P, cur, cur - np, lap, cur + np);
+                forward_step(P, n, cur, cur - np, lap, cur + np);
             }
         }
         for (; j > s0; --j) {
-            /* lam^{j-1} from lam^j, lam^{j+1} and -P^T r^j */
-            spatial_op(P, l1, lap);
-            for (int rr = 0; rr < P->nrec; ++rr)
-                for (int i = 0; i < P->nstc; ++i)
-                    lap[P->ridx[rr * P->nstc + i]] -= P->rwt[rr * P->nstc + i] * r[(long)j * P->nrec + rr];
-            leapfrog(P, l1, l2, lap, l0);
+            /* lam^{j-1} from lam^j, lam^{j+1} and -P^T r^j; gradient term of n = j-1 */
             const int n = j - 1;
-            if (grad) {
-                const double* un = useg + (long)(n - s0 + 1) * np;
-                spatial_op(P, un, tmp);
-                add_sources(P, n, tmp);
-#pragma omp parallel for schedule(static)
-                for (long p = 0; p < np; ++p) grad[p] += l0[p] * tmp[p] * P->c2[p];
-                if (is_ot4(P)) {
-                    /* derivative of the OT4 correction: dt^2/12 c^4 lap u^n lap lam^n */
-                    const double kk = g->dt * g->dt / 12.0;
-                    ora_laplacian(g, un, tmp);
-                    ora_laplacian(g, l0, lap);
-                    for (long p = 0; p < np; ++p)
-                        grad[p] += kk * P->c2[p] * P->c2[p] * tmp[p] * lap[p];
-                }
-            }
+            const double* un = grad ? useg + (long)(n - s0 + 1) * np : NULL;
+            adjoint_step(P, r, j, l1, l2, l0, un, grad, lap, tmp);
             if (srcadj)
                 for (int s = 0; s < P->nsrc; ++s) {
                     double acc = 0.0;
@@ -516,4 +535,77 @@ int ora_gradient(const ora_grid* g, const double* vel, int nsrc, const double* s
     free(d); free(r);
     problem_free(&P);
     return st;
+}
+
+/* ---- step-level interface ----
+ * A problem held between calls, so that a caller can drive single forward
+ * and reverse steps in the order a checkpointing schedule prescribes
+ * (Sec. 3).  The steps are the ones ora_forward / ora_adjoint run, so a
+ * schedule that hands every step its exact inputs reproduces their results
+ * bit for bit. */
+typedef struct {
+    ora_grid g;          /* own copy: problem keeps a pointer to it */
+    problem P;
+    double* series;      /* own copy of the source series, [nsrc][nt] */
+    double *lap, *tmp;   /* np scratch values each */
+} ora_handle;
+
+void ora_problem_destroy(void* h)
+{
+    ora_handle* H = (ora_handle*)h;
+    if (!H) return;
+    problem_free(&H->P);
+    free(H->series); free(H->lap); free(H->tmp);
+    free(H);
+}
+
+/* Same arguments as ora_forward; NULL on invalid input or no memory. */
+void* ora_problem_create(const ora_grid* g, const double* vel, int nsrc, const double* src_pos,
+                         const double* src_series, int nrec, const double* rec_pos)
+{
+    if (!grid_ok(g) || nsrc < 0 || nrec < 0) return NULL;
+    if ((nsrc > 0 && !src_pos) || (nrec > 0 && !rec_pos)) return NULL;
+    ora_handle* H = calloc(1, sizeof(*H));
+    if (!H) return NULL;
+    H->g = *g;
+    if (src_series && nsrc > 0) {
+        H->series = malloc(sizeof(double) * (long)nsrc * g->nt);
+        if (!H->series) { free(H); return NULL; }
+        memcpy(H->series, src_series, sizeof(double) * (long)nsrc * g->nt);
+    }
+    if (problem_init(&H->P, &H->g, vel, nsrc, src_pos, H->series, nrec, rec_pos) != ORA_OK) {
+        free(H->series);
+        free(H);
+        return NULL;
+    }
+    H->lap = malloc(sizeof(double) * H->P.np);
+    H->tmp = malloc(sizeof(double) * H->P.np);
+    if (!H->lap || !H->tmp) { ora_problem_destroy(H); return NULL; }
+    return H;
+}
+
+/* out = u^{n+1} from cur = u^n and prev = u^{n-1}, with the source term q^n
+ * (0 <= n < nt).  out must not alias cur or prev. */
+int ora_problem_fwd_step(void* h, int n, const double* cur, const double* prev, double* out)
+{
+    ora_handle* H = (ora_handle*)h;
+    if (!H || !cur || !prev || !out || n < 0 || n >= H->g.nt) return ORA_EINVAL;
+    if (out == cur || out == prev) return ORA_EINVAL;
+    forward_step(&H->P, n, cur, prev, H->lap, out);
+    return ORA_OK;
+}
+
+/* Reverse step j (1 <= j <= nt): l0 = lam^{j-1} from l1 = lam^j,
+ * l2 = lam^{j+1} and row j of the residual r ([nt+1][nrec]).  With grad
+ * (np values, accumulated), adds the gradient term of n = j-1 read from the
+ * forward state un = u^{j-1}.  l0 must not alias l1, l2 or un. */
+int ora_problem_adj_step(void* h, const double* r, int j, const double* l1, const double* l2,
+                         double* l0, const double* un, double* grad)
+{
+    ora_handle* H = (ora_handle*)h;
+    if (!H || !r || !l1 || !l2 || !l0 || j < 1 || j > H->g.nt) return ORA_EINVAL;
+    if (grad && !un) return ORA_EINVAL;
+    if (l0 == l1 || l0 == l2 || (un && l0 == un)) return ORA_EINVAL;
+    adjoint_step(&H->P, r, j, l1, l2, l0, un, grad, H->lap, H->tmp);
+    return ORA_OK;
 }

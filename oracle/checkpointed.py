@@ -102,6 +102,7 @@ class Stepper:
     steps (ora_problem_*)."""
 
     def __init__(self, grid, vel, src_pos, src_series, rec_pos):
+        self._h = None
         vel = _prop._f64(vel)
         if vel.size != int(np.prod(grid.shape)):
             raise ValueError("velocity size does not match the grid")

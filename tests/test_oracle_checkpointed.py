@@ -236,3 +236,24 @@ def test_error_follows_the_storage_precision():
     assert ec[0] > ec[1] > ec[2]
     er = [err("rate", rate=b) for b in (8, 12, 16)]
     assert er[0] > er[1] > er[2]
+
+
+def test_step_interface_rejects_bad_calls():
+    g, vel, src, ser, rec, dobs = _case(2, 4, 2, 8)
+    z = np.zeros(g.shape)
+    r = np.zeros((g.nt + 1, len(rec)))
+    with K.Stepper(g, vel, src, ser, rec) as S:
+        for n in (-1, g.nt):
+            with pytest.raises(ValueError):
+                S.fwd(n, z, z)
+        for j in (0, g.nt + 1):
+            with pytest.raises(ValueError):
+                S.adj(r, j, z, z)
+        with pytest.raises(ValueError):
+            S.adj(r, 1, z, z, un=None, grad=np.zeros(g.shape))   # a gradient needs u^{j-1}
+    with pytest.raises(ValueError):
+        K.Stepper(g, vel[:-1], src, ser, rec)
+    with pytest.raises(ValueError):
+        K.gradient(g, vel, src, ser, rec, dobs, 2, store="fp8")
+    with pytest.raises(ValueError):
+        K.gradient(g, vel, src, ser, rec, dobs, 2, store="codec")        # no tolerance

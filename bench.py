@@ -65,7 +65,7 @@ def peaks():
         with open(p) as f:
             d = json.load(f)
         return float(d["hbm_gbs"]), "measured"
-    except Exception:
+    except (OSError, ValueError, KeyError, TypeError):
         return 6800.0, "fallback"
 
 
@@ -86,7 +86,7 @@ def traffic_per_point(kernel, tile):
         if e.get("tile") is not None and (want[:4] != t[:4] or want[5] != t[5]):
             return None
         return float(e["dram_bytes_per_point"])
-    except Exception:
+    except (OSError, ValueError, KeyError, TypeError, IndexError):
         return None
 
 
@@ -103,7 +103,7 @@ class Clocks:
             self.p = subprocess.Popen(["nvidia-smi", "-i", str(index), "--query-gpu=" + self.Q,
                                        "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
                                       stderr=subprocess.DEVNULL)
-        except Exception:
+        except OSError:
             self.p = None
 
     def stop(self):
@@ -112,7 +112,7 @@ class Clocks:
         self.p.terminate()
         try:
             self.p.wait(timeout=5)
-        except Exception:
+        except subprocess.TimeoutExpired:
             self.p.kill()
         self.f.seek(0)
         sm, mx, reasons = [], 0.0, set()

@@ -284,12 +284,14 @@ def test_tiny_time_axis(nt):
 # float32 states differ from the FP64 ones by about 1e-6 relative, enough to
 # move a small share of the rounding and quantisation decisions, so the two
 # compressed gradients agree statistically rather than element by element.
-# Bounds set on the CPU by injecting float32-sized noise into the oracle's
-# forward steps (up to 4x the size that reproduces the float32 gradient
-# error of these cases): on these two cases the compression error's norm
-# agreed within 5%, and for bfloat16 and 8 bits per value the
-# GPU-to-lossy-oracle difference stayed at or below 0.26x the compression
-# error (the exact gradient is 1x away by definition).
+# Bounds set on the CPU by driving the lossy executor with float32-like
+# forward states: float32-sized noise injected into the oracle's forward
+# steps (8 seeds, and 4x the size that reproduces the float32 gradient error
+# of these cases), and a float32 evaluation of the increment-form forward
+# step.  On these two cases the compression error's norm agreed within 5%,
+# and for bfloat16 and 8 bits per value the GPU-to-lossy-oracle difference
+# stayed at or below 0.26x the compression error (the exact gradient is 1x
+# away by definition).
 LOSSY = [("bf16", {}, 0.6, 0.15), ("rate", {"rate": 8}, 0.6, 0.15), ("fp16", {}, None, 0.25),
          ("codec", {"rel": 1e-2}, None, 0.25), ("codec", {"rel": 1e-3}, None, 0.25)]
 

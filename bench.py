@@ -45,6 +45,7 @@ TOL = 1e-4                 # codec absolute tolerance
 RATE = 16                  # fixed-rate codec: bits per value
 FWD_BYTES = 16             # forward step: read u^n, u^{n-1}, w; write u^{n+1} (+4 with a fused checkpoint)
 ADJ_BYTES = 28             # reverse step: read lam^j, lam^{j+1}, u^{j-1}, w, g; write lam^{j-1}, g
+NOMINAL_HBM_GBS = 7900.0   # GB300 HBM3e, nominal (the measured copy is the roofline's peak)
 CPU_STEPS = 300            # time steps of the oracle sample (about 10-30 s on 16 cores)
 GRAD_TOL = 1e-2            # gradient accuracy a storage mode must keep to be the headline
 KERNEL_NAMES = {1: ("fwd_kernel", "adj_kernel"), 2: ("fwd_tma_kernel", "adj_tma_kernel"),
@@ -623,7 +624,7 @@ def main():
             kname = KERNEL_NAMES.get(ver, ("?", "?"))[0 if dom == "fwd" else 1]
             tpp = traffic_per_point(kname, H[dom + "_kernel"])
         else:
-            kname = "codec compression (enc+scan+compact)" if dom == "comp" else "dec_kernel"
+            kname = "codec compression (enc+compact)" if dom == "comp" else "dec_kernel"
             tpp = None
         line = {
             "metric": "gradient point-updates per second (useful 2*N*npts/t)",
@@ -639,6 +640,7 @@ def main():
                        "parallelism": "shots" if ws > 1 else "single"},
             "roofline": {"bound": "hbm", "kernel": kname, "class": dom, "achieved": gbs[dom], "peak": peak,
                          "unit": "GB/s", "frac": gbs[dom] / peak, "peak_kind": peak_kind,
+                         "frac_of_nominal": gbs[dom] / NOMINAL_HBM_GBS,
                          "algorithmic_bytes_per_launch": b_d, "launches": n_d,
                          "traffic": (tpp * npts) if tpp is not None else None,
                          "class_gbs": gbs},

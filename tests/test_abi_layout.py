@@ -1,9 +1,11 @@
 """The binding's ctypes structures mirror include/ckfwi.h field by field:
 a plain C program built against the header prints every field's offset and
 every structure's size, which must equal the ctypes layout (a mismatch would
-pass wrong values across the boundary without any error)."""
+pass wrong values across the boundary without any error); the status, memory,
+storage and gradient-kind constants equal the header's."""
 import ctypes
 import os
+import re
 import shutil
 import subprocess
 
@@ -51,3 +53,13 @@ def test_struct_layout_matches_header(c_layout, cname, py):
     assert c_layout[(cname, "sizeof")] == ctypes.sizeof(py)
     for f in py._fields_:
         assert c_layout[(cname, f[0])] == getattr(py, f[0]).offset, f[0]
+
+
+def test_constants_match_header():
+    from paper_1810_05268_gb300 import ckfwi as C
+    txt = open(os.path.join(ROOT, "include", "ckfwi.h")).read()
+    defs = {k: int(v) for k, v in re.findall(r"#define CKFWI_(\w+)\s+(-?\d+)\b", txt)}
+    defs.pop("H", None)
+    assert len(defs) >= 17
+    for name, v in defs.items():
+        assert getattr(C, name) == v, name

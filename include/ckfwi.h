@@ -258,8 +258,13 @@ CKFWI_API int ckfwi_batch_gradient_models(ckfwi_model* const* models, const ckfw
                          const int* offsets, const int* global_n, double* misfit_sum,
                          double* grad_sum, ckfwi_stats* stats, void* stream);
 
+/* Release the model and everything it owns (working fields, checkpoint
+ * pools, maps, recorded graphs, batch clones); NULL is ignored.  The caller
+ * makes sure no work queued on the model is still running. */
 CKFWI_API void ckfwi_free(ckfwi_model* m);
 
+/* A static, human-readable text for a status code ("unknown status" for a
+ * code this header does not define).  Host only. */
 CKFWI_API const char* ckfwi_error_string(int status);
 
 /* Stream lengths [words] of every compression of the model's last

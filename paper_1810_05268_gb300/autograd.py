@@ -28,12 +28,17 @@ class CheckpointedMisfit(torch.autograd.Function):
     @staticmethod
     def backward(ctx, grad_out):
         (m,) = ctx.saved_tensors
+        scale = float(grad_out)
+        if scale == 0.0:
+            # the library reads a scale of 0 as 1; a zero upstream gradient
+            # needs no adjoint run
+            return torch.zeros_like(m), None, None, None, None
         ctx.model.set_model(m, kind=C.SLOWNESS2)
         g = torch.empty_like(m)
         opts = dict(ctx.opts)
         slots = opts.pop("ckpt_slots")
         ctx.model.batch_gradient(ctx.shots, ctx.d_obs, slots, grad_kind=C.SLOWNESS2,
-                                 grad_scale=float(grad_out), grad_f32=True, grad_sum=g, **opts)
+                                 grad_scale=scale, grad_f32=True, grad_sum=g, **opts)
         return g, None, None, None, None
 
 

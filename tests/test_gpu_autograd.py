@@ -85,6 +85,8 @@ def test_backward_scales_with_grad_output():
     (g1,) = torch.autograd.grad(A.misfit(x, m, shots, dd, ckpt_slots=9), x)
     (g3,) = torch.autograd.grad(3.0 * A.misfit(x, m, shots, dd, ckpt_slots=9), x)
     assert torch.allclose(g3, 3.0 * g1, rtol=1e-6, atol=0)
+    (g0,) = torch.autograd.grad(0.0 * A.misfit(x, m, shots, dd, ckpt_slots=9), x)
+    assert not bool(g0.any())
 
 
 def test_steepest_descent_reduces_misfit():

@@ -59,13 +59,27 @@ def _stream(stream=None):
 def _buf(x, dtype):
     """(pointer, mem) of a torch CUDA tensor or a numpy array of `dtype`."""
     if _is_torch_cuda(x):
-        if not x.is_contiguous():
-            raise ValueError("device buffers must be contiguous")
+        import torch
+        want = {np.float32: torch.float32, np.float64: torch.float64}[np.dtype(dtype).type]
+        if x.dtype != want or not x.is_contiguous():
+            raise ValueError("device buffers must be contiguous %s" % np.dtype(dtype).name)
         return ctypes.c_void_p(x.data_ptr()), DEVICE
     a = np.asarray(x)
     if a.dtype != dtype or not a.flags.c_contiguous:
         raise ValueError("host buffers must be contiguous %s" % np.dtype(dtype).name)
     return ctypes.c_void_p(a.ctypes.data), HOST
+
+
+def _numel(x):
+    return int(x.numel()) if _is_torch_cuda(x) else int(np.asarray(x).size)
+
+
+def _need(x, n, what):
+    """The library reads or writes n values of x: refuse a smaller buffer
+    here, before a kernel would run past its end."""
+    have = _numel(x)
+    if have < n:
+        raise ValueError("%s holds %d values, the call needs %d" % (what, have, n))
 
 
 @dataclass
@@ -91,6 +105,10 @@ class GridSpec:
         g.time_order = int(self.time_order)
         return g
 
+    @property
+    def npts(self):
+        return int(np.prod(self.shape))
+
 
 @dataclass
 class ShotSpec:
@@ -102,7 +120,8 @@ class ShotSpec:
     wavelet: Optional[np.ndarray] = None   # [nt] float32 overriding the Ricker
     _keep: list = field(default_factory=list, repr=False)
 
-    def c(self):
+    def c(self, nt=None):
+        """The C struct; with nt, a wavelet shorter than nt samples is refused."""
         s = Shot()
         for i in range(3):
             s.src[i] = float(self.src[i])
@@ -113,6 +132,8 @@ class ShotSpec:
         self._keep = [rec]
         if self.wavelet is not None:
             w = np.ascontiguousarray(np.asarray(self.wavelet, dtype=np.float32))
+            if nt is not None and w.size < nt:
+                raise ValueError("the wavelet has %d samples, the grid %d time steps" % (w.size, nt))
             s.wavelet = w.ctypes.data
             self._keep.append(w)
         else:
@@ -143,7 +164,8 @@ def forward_shot(model, grid: GridSpec, shot: ShotSpec, d_sim=None, device=None,
             device = _default_device()
         d_sim = _alloc((grid.nt + 1, shot.nrec), np.float32, device)
     p, mem = _buf(d_sim, np.float32)
-    s = shot.c()
+    _need(d_sim, (grid.nt + 1) * shot.nrec, "d_sim")
+    s = shot.c(grid.nt)
     _check(lib().ckfwi_forward_shot(model, ctypes.byref(s), p, mem, _stream(stream)), "ckfwi_forward_shot")
     return d_sim
 
@@ -168,7 +190,12 @@ def _opts(ckpt_slots, store_mode, tol, pool_bytes, grad_kind, use_graph, profile
           grad_f32=False, host_slots=0, rate=0):
     o = GradOpts()
     o.ckpt_slots = int(ckpt_slots)
-    o.store_mode = STORE_NAMES.get(store_mode, store_mode) if isinstance(store_mode, str) else int(store_mode)
+    if isinstance(store_mode, str):
+        if store_mode not in STORE_NAMES:
+            raise ValueError("unknown store_mode %r (one of %s)" % (store_mode, ", ".join(STORE_NAMES)))
+        o.store_mode = STORE_NAMES[store_mode]
+    else:
+        o.store_mode = int(store_mode)
     o.tol = float(tol)
     o.pool_bytes = int(pool_bytes)
     o.grad_kind = int(grad_kind)
@@ -184,12 +211,14 @@ def _opts(ckpt_slots, store_mode, tol, pool_bytes, grad_kind, use_graph, profile
 def misfit(model, grid: GridSpec, shot: ShotSpec, d_obs, d_sim=None, stream=None):
     """phi = 1/2 sum_{n>=1} ||d_sim^n - d_obs^n||^2 (FP64) by forward modelling only."""
     pd, mem = _buf(d_obs, np.float32)
+    _need(d_obs, (grid.nt + 1) * shot.nrec, "d_obs")
     ps = None
     if d_sim is not None:
         ps, ms = _buf(d_sim, np.float32)
         if ms != mem:
             raise ValueError("d_obs and d_sim must both be host or both be device buffers")
-    s = shot.c()
+        _need(d_sim, (grid.nt + 1) * shot.nrec, "d_sim")
+    s = shot.c(grid.nt)
     phi = ctypes.c_double(0.0)
     _check(lib().ckfwi_misfit(model, ctypes.byref(s), pd, mem, ctypes.byref(phi), ps, _stream(stream)),
            "ckfwi_misfit")
@@ -206,7 +235,9 @@ def adjoint_gradient(model, grid: GridSpec, shot: ShotSpec, d_obs, ckpt_slots, s
     pg, memg = _buf(grad, np.float32)
     if memg != mem:
         raise ValueError("d_obs and grad must both be host or both be device buffers")
-    s = shot.c()
+    _need(d_obs, (grid.nt + 1) * shot.nrec, "d_obs")
+    _need(grad, grid.npts, "grad")
+    s = shot.c(grid.nt)
     o = _opts(ckpt_slots, store_mode, tol, pool_bytes, grad_kind, use_graph, profile, grad_scale,
               host_slots=host_slots, rate=rate)
     phi = ctypes.c_double(0.0)
@@ -229,11 +260,11 @@ def _d_obs_ptrs(d_obs_list):
     return ptrs, mem
 
 
-def _shot_array(shots):
+def _shot_array(shots, nt=None):
     carr = (Shot * len(shots))()
     keep = []
     for i, sh in enumerate(shots):
-        carr[i] = sh.c()
+        carr[i] = sh.c(nt)
         keep.append(sh._keep)
     return carr, keep
 
@@ -255,7 +286,10 @@ def batch_gradient(model, grid: GridSpec, shots, d_obs_list, ckpt_slots, store_m
     pg, memg = _buf(grad_sum, gdt)
     if memg != mem:
         raise ValueError("d_obs and grad_sum must both be host or both be device buffers")
-    carr, keep = _shot_array(shots)
+    for sh, d in zip(shots, d_obs_list):
+        _need(d, (grid.nt + 1) * sh.nrec, "d_obs")
+    _need(grad_sum, grid.npts, "grad_sum")
+    carr, keep = _shot_array(shots, grid.nt)
     o = _opts(ckpt_slots, store_mode, tol, pool_bytes, grad_kind, use_graph, profile, grad_scale, grad_f32,
               rate=rate)
     phi = ctypes.c_double(0.0)
@@ -287,13 +321,19 @@ def batch_gradient_models(models, shots, d_obs_list, offsets, global_shape, ckpt
     pg, memg = _buf(grad_sum, gdt)
     if memg != mem:
         raise ValueError("d_obs and grad_sum must both be host or both be device buffers")
+    _need(grad_sum, int(np.prod(gshape)), "grad_sum")
+    nt = None
+    for m, sh, d in zip(models, shots, d_obs_list):
+        if isinstance(m, Model):
+            nt = m.grid.nt
+            _need(d, (nt + 1) * sh.nrec, "d_obs")
     marr = (ctypes.c_void_p * n)(*[m.h if isinstance(m, Model) else m for m in models])
     off = np.zeros((n, 3), dtype=np.int32)
     for i, o3 in enumerate(offsets):
         o3 = tuple(int(v) for v in o3)
         off[i] = (o3[0], 0, o3[1]) if len(o3) == 2 else o3
     gna = (ctypes.c_int * 3)(*gn)
-    carr, keep = _shot_array(shots)
+    carr, keep = _shot_array(shots, nt)
     o = _opts(ckpt_slots, store_mode, tol, pool_bytes, grad_kind, use_graph, profile, grad_scale, grad_f32,
               rate=rate)
     phi = ctypes.c_double(0.0)
@@ -370,8 +410,8 @@ def codec_compress_noalloc(x, out, tol, stream=None):
     import torch
     if not _is_torch_cuda(x) or x.dtype != torch.float32 or not x.is_contiguous():
         raise ValueError("codec_compress_noalloc needs a contiguous float32 CUDA tensor")
-    if not _is_torch_cuda(out) or not out.is_contiguous():
-        raise ValueError("codec_compress_noalloc needs a contiguous CUDA output tensor")
+    if not _is_torch_cuda(out) or not out.is_contiguous() or out.element_size() != 4:
+        raise ValueError("codec_compress_noalloc needs a contiguous CUDA output tensor of 32-bit words")
     dims = x.dim()
     nz, ny, nx = _shape3(tuple(x.shape))
     used = ctypes.c_longlong(0)
@@ -428,6 +468,7 @@ class Model:
         self.h = create_model(grid)
 
     def set_model(self, data, kind=VELOCITY, stream=None):
+        _need(data, self.grid.npts, "the medium")
         set_model(self.h, data, kind, stream)
 
     def forward_shot(self, shot, **kw):

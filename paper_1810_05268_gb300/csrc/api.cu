@@ -2610,8 +2610,12 @@ extern "C" int ckfwi_codec_decompress(const uint32_t* in, long long nwords, int 
     if (nwords < 16) return CKFWI_CORRUPT;
     CK_TRY(cudaMemcpyAsync(hv, in, sizeof(hv), cudaMemcpyDeviceToHost, st));
     CK_TRY(cudaStreamSynchronize(st));
-    if ((hv[1] >> 8) == 2u) CK_TRY(codec_rate_decompress_dev(in, sc, nwords, v, (int)hv[8], x, err, st));
-    else CK_TRY(codec_decompress_dev(in, sc, nwords, v, x, err, st));
+    if ((hv[1] >> 8) == 2u) {
+        if (hv[8] < 1u || hv[8] > 32u) return CKFWI_CORRUPT;   // the rate word of a fixed-rate stream
+        CK_TRY(codec_rate_decompress_dev(in, sc, nwords, v, (int)hv[8], x, err, st));
+    } else {
+        CK_TRY(codec_decompress_dev(in, sc, nwords, v, x, err, st));
+    }
     int e = 0;
     CK_TRY(cudaMemcpyAsync(&e, err, sizeof(int), cudaMemcpyDeviceToHost, st));
     CK_TRY(cudaStreamSynchronize(st));

@@ -449,8 +449,8 @@ def codec_compress_rate(x, rate, stream=None):
 
 def codec_decompress(stream_words, shape, stream=None):
     import torch
-    if not _is_torch_cuda(stream_words) or not stream_words.is_contiguous():
-        raise ValueError("codec_decompress needs a contiguous CUDA tensor of stream words")
+    if not _is_torch_cuda(stream_words) or not stream_words.is_contiguous() or stream_words.element_size() != 4:
+        raise ValueError("codec_decompress needs a contiguous CUDA tensor of 32-bit stream words")
     dims = len(shape)
     nz, ny, nx = _shape3(tuple(shape))
     out = torch.zeros(tuple(shape), dtype=torch.float32, device=stream_words.device)

@@ -91,6 +91,39 @@ def traffic_per_point(kernel, tile):
         return None
 
 
+def roofline_block(H, nt, npts, peak, peak_kind):
+    """The bench line's `roofline`: the kernel class with the largest device
+    time in the headline mode H (one mode's profiled stats), its algorithmic
+    bytes per launch over its average launch time, against `peak`."""
+    F = max(1.0, H["ratio_mean"] or 1.0)
+    # a step that writes an FP32 or 16-bit checkpoint writes 4 more B/pt
+    # (u^{n-1} in FP32, or both levels in 16 bits), W of the launches
+    ck_bytes = 4.0 if H["store_mode"] in ("fp32", "fp16", "bf16") and H["ckpt_slots"] < nt else 0.0
+    fwd_b = (FWD_BYTES + ck_bytes * H["W"] / max(1, H["fwd_launches"])) * npts
+    classes = {
+        "fwd": (H["fwd_ms"], H["fwd_launches"], fwd_b),
+        "adj": (H["adj_ms"], H["adj_launches"], ADJ_BYTES * npts),
+        "comp": (H["comp_ms"], H["comp_calls"], (4.0 + 4.0 / F) * npts),
+        "decomp": (H["decomp_ms"], H["decomp_calls"], (4.0 / F + 4.0) * npts),
+    }
+    gbs = {k: (b * n / (ms / 1e3) / 1e9 if ms > 0 and n > 0 else 0.0) for k, (ms, n, b) in classes.items()}
+    dom = max(classes, key=lambda k: classes[k][0])
+    _, n_d, b_d = classes[dom]
+    if dom in ("fwd", "adj"):
+        ver = H[dom + "_kernel"][0]
+        kname = KERNEL_NAMES.get(ver, ("?", "?"))[0 if dom == "fwd" else 1]
+        tpp = traffic_per_point(kname, H[dom + "_kernel"])
+    else:
+        kname = "codec compression (enc+compact)" if dom == "comp" else "dec_kernel"
+        tpp = None
+    return {"bound": "hbm", "kernel": kname, "class": dom, "achieved": gbs[dom], "peak": peak,
+            "unit": "GB/s", "frac": gbs[dom] / peak, "peak_kind": peak_kind,
+            "frac_of_nominal": gbs[dom] / NOMINAL_HBM_GBS,
+            "algorithmic_bytes_per_launch": b_d, "launches": n_d,
+            "traffic": (tpp * npts) if tpp is not None else None,
+            "class_gbs": gbs}
+
+
 class Clocks:
     """nvidia-smi sampling during the timed region."""
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -602,30 +635,6 @@ def main():
 
     if rk == 0:
         H = results[headline]
-        peak, peak_kind = peaks()
-        # the kernel class with the largest device-time share in the headline
-        # mode, its algorithmic bytes per launch over its average launch time
-        F = max(1.0, H["ratio_mean"] or 1.0)
-        # a step that writes an FP32 or 16-bit checkpoint writes 4 more B/pt
-        # (u^{n-1} in FP32, or both levels in 16 bits), W of the launches
-        ck_bytes = 4.0 if H["store_mode"] in ("fp32", "fp16", "bf16") and H["ckpt_slots"] < nt else 0.0
-        fwd_b = (FWD_BYTES + ck_bytes * H["W"] / max(1, H["fwd_launches"])) * npts
-        classes = {
-            "fwd": (H["fwd_ms"], H["fwd_launches"], fwd_b),
-            "adj": (H["adj_ms"], H["adj_launches"], ADJ_BYTES * npts),
-            "comp": (H["comp_ms"], H["comp_calls"], (4.0 + 4.0 / F) * npts),
-            "decomp": (H["decomp_ms"], H["decomp_calls"], (4.0 / F + 4.0) * npts),
-        }
-        gbs = {k: (b * n / (ms / 1e3) / 1e9 if ms > 0 and n > 0 else 0.0) for k, (ms, n, b) in classes.items()}
-        dom = max(classes, key=lambda k: classes[k][0])
-        ms_d, n_d, b_d = classes[dom]
-        if dom in ("fwd", "adj"):
-            ver = H[dom + "_kernel"][0]
-            kname = KERNEL_NAMES.get(ver, ("?", "?"))[0 if dom == "fwd" else 1]
-            tpp = traffic_per_point(kname, H[dom + "_kernel"])
-        else:
-            kname = "codec compression (enc+compact)" if dom == "comp" else "dec_kernel"
-            tpp = None
         line = {
             "metric": "gradient point-updates per second (useful 2*N*npts/t)",
             "value": H["gpts"], "unit": "Gpt/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
@@ -638,12 +647,7 @@ def main():
                            ", codec abs tol %g" % TOL if H["store_mode"] == "codec" else ""),
                        "ckpt_slots": H["ckpt_slots"], "l2": "working set (checkpoints + fields) > L2",
                        "parallelism": "shots" if ws > 1 else "single"},
-            "roofline": {"bound": "hbm", "kernel": kname, "class": dom, "achieved": gbs[dom], "peak": peak,
-                         "unit": "GB/s", "frac": gbs[dom] / peak, "peak_kind": peak_kind,
-                         "frac_of_nominal": gbs[dom] / NOMINAL_HBM_GBS,
-                         "algorithmic_bytes_per_launch": b_d, "launches": n_d,
-                         "traffic": (tpp * npts) if tpp is not None else None,
-                         "class_gbs": gbs},
+            "roofline": roofline_block(H, nt, npts, *peaks()),
             "e2e": {"value": 2.0 * nt * npts / e2e_s / 1e9, "unit": "Gpt/s",
                     "h2d_bytes_per_step": int(dh.numel() * 4), "d2h_bytes_per_step": int(gh.numel() * 4 + 8)},
             "gpu_launches": int(H["kernel_launches"] * args.steps),

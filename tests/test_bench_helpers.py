@@ -1,7 +1,7 @@
 """Host-side logic of bench.py (no GPU): the traffic lookup, the fixed-rate
-slot count at a budget, and the time model fitted to a set of measured
-modes (unit costs from store-all, FP32 and FP16 runs; choices at both
-budgets)."""
+slot count at a budget, the time model fitted to a set of measured modes
+(unit costs from store-all, FP32 and FP16 runs; choices at both budgets),
+and the bench line's roofline block."""
 import json
 import os
 import sys
@@ -74,3 +74,42 @@ def test_time_model_fit_recovers_its_own_costs():
     assert u["t_d16"] == pytest.approx(td16)
     for k, m in out["modes"].items():
         assert m["predicted_ms"] == pytest.approx(m["measured_ms"], rel=1e-9), k
+
+
+def _headline(**kw):
+    H = {"ratio_mean": 0.0, "store_mode": "fp16", "ckpt_slots": 39, "W": 909, "fwd_launches": 2140,
+         "fwd_ms": 2140 * 0.0433, "adj_launches": 1000, "adj_ms": 1000 * 0.0801, "comp_ms": 0.0, "comp_calls": 0,
+         "decomp_ms": 30.0, "decomp_calls": 960, "fwd_kernel": [4, 32, 16, 4, 21, 1],
+         "adj_kernel": [3, 32, 16, 4, 21]}
+    H.update(kw)
+    return H
+
+
+def test_roofline_block_of_a_stencil_dominated_mode():
+    npts, nt = 208 ** 3, 1000
+    H = _headline()
+    r = bench.roofline_block(H, nt, npts, 6686.1, "measured")
+    assert r["class"] == "fwd" and r["kernel"] == "fwd4_kernel" and r["unit"] == "GB/s"
+    # every forward launch moves 16 B/pt; the W launches that write a 16-bit
+    # checkpoint pair move 4 more
+    total = (16.0 * H["fwd_launches"] + 4.0 * H["W"]) * npts
+    want = total / (H["fwd_ms"] * 1e-3) / 1e9
+    assert r["achieved"] == pytest.approx(want)
+    assert r["frac"] == pytest.approx(want / 6686.1)
+    assert r["frac_of_nominal"] == pytest.approx(want / bench.NOMINAL_HBM_GBS)
+    assert r["launches"] == H["fwd_launches"]
+    assert r["algorithmic_bytes_per_launch"] * r["launches"] == pytest.approx(total)
+    tpp = bench.traffic_per_point("fwd4_kernel", H["fwd_kernel"])
+    assert tpp is not None and r["traffic"] == pytest.approx(tpp * npts)
+    assert set(r["class_gbs"]) == {"fwd", "adj", "comp", "decomp"}
+    json.dumps(r)
+
+
+def test_roofline_block_of_a_codec_dominated_mode():
+    npts, nt = 208 ** 3, 1000
+    H = _headline(store_mode="codec", ckpt_slots=232, ratio_mean=25.0, comp_ms=500.0, comp_calls=1692)
+    r = bench.roofline_block(H, nt, npts, 6686.1, "measured")
+    assert r["class"] == "comp" and r["traffic"] is None
+    assert r["algorithmic_bytes_per_launch"] == pytest.approx((4.0 + 4.0 / 25.0) * npts)
+    # no checkpoint bytes in the forward class of a codec mode
+    assert r["class_gbs"]["fwd"] == pytest.approx(16.0 * npts * H["fwd_launches"] / (H["fwd_ms"] * 1e-3) / 1e9)

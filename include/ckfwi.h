@@ -163,7 +163,12 @@ typedef struct ckfwi_stats {
     double pool_bytes_peak;  /* device bytes of checkpoint storage in use, peak */
     double ratio_min;        /* CODEC: smallest and mean compression ratio */
     double ratio_mean;
-    double u_absmax;         /* reserved (0) */
+    double u_absmax;         /* max |u^N| over the total grid, from a device
+                                reduction at the end of the first sweep: the
+                                wavefield's scale, against which an absolute
+                                codec tolerance (Sec. 2.2) can be read as
+                                tol / max|u|.  Batches: the largest over the
+                                lanes of the last batch. */
     /* with opts->profile: device time [ms] and launches per kernel class */
     double fwd_ms, adj_ms, comp_ms, decomp_ms, other_ms;
     long long fwd_launches, adj_launches, comp_calls, decomp_calls;

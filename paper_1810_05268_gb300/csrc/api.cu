@@ -925,6 +925,20 @@ int sample_last(Ctx& cx, const Role& uN)
     return CKFWI_OK;
 }
 
+// max |u^N| of every lane (the wavefield's scale, reported beside a codec
+// tolerance); the second word of the lane's phi buffer, zeroed at the start
+// of the gradient
+int field_absmax(Ctx& cx, const Role& uN)
+{
+    if (!cx.issue) return CKFWI_OK;
+    for (int l = 0; l < cx.nl(); ++l) {
+        ckfwi_model* m = cx.lane(l);
+        CK_TRY(launch_absmax(cx.fptr(l, uN), m->fg, reinterpret_cast<unsigned*>(m->phi.as<double>() + 1), cx.st));
+        ++cx.launches;
+    }
+    return CKFWI_OK;
+}
+
 // residual r = d - d_obs and the FP64 misfit of every lane
 int residual(Ctx& cx)
 {
@@ -1259,6 +1273,7 @@ int run_body(Ctx& cx, const RunCfg& rc, const std::vector<Action>& acts, long lo
             for (int i = 0; i < 3; ++i) CK_TRY(cudaMemsetAsync(m->lam[i].p, 0, m->lam[i].bytes, cx.st));
             CK_TRY(cudaMemsetAsync(m->gacc.p, 0, m->gacc.bytes, cx.st));
             CK_TRY(cudaMemsetAsync(m->shot.dsim.p, 0, m->shot.dsim.bytes, cx.st));
+            CK_TRY(cudaMemsetAsync(m->phi.as<double>() + 1, 0, sizeof(double), cx.st));
         }
     }
     int li = 0;   // lam rotation: lam[li] = lam^{j}, lam[(li+1)%3] = lam^{j+1}
@@ -1277,6 +1292,7 @@ int run_body(Ctx& cx, const RunCfg& rc, const std::vector<Action>& acts, long lo
             ++fsteps;
         }
         ST_TRY(sample_last(cx, UN_R));
+        ST_TRY(field_absmax(cx, UN_R));
         ST_TRY(residual(cx));
         for (int s = N - 1; s >= 0; --s) ST_TRY(reverse(s, s == 0 ? ZERO_R : traj_r(s), U_FP32));
         counters[0] = fsteps;
@@ -1429,6 +1445,7 @@ int run_body(Ctx& cx, const RunCfg& rc, const std::vector<Action>& acts, long lo
                 ST_TRY(fwd_step(cx, st.cur, st.prev, UN_R, N - 1, true, CK_NONE, NONE_R, NONE_R));
                 ++fsteps;
                 ST_TRY(sample_last(cx, UN_R));
+                ST_TRY(field_absmax(cx, UN_R));
                 ST_TRY(residual(cx));
                 first_sweep = false;
             }
@@ -1568,6 +1585,16 @@ void trim_graphs(Map& g, std::vector<typename Map::key_type>& order, size_t cap)
 }
 
 // Fill stats from the per-class timings and the schedule counts.
+// the float max |u| that field_absmax left in the low word of a double slot
+double absmax_of(double slot)
+{
+    uint32_t b = 0;
+    std::memcpy(&b, &slot, sizeof(b));
+    float f = 0.0f;
+    std::memcpy(&f, &b, sizeof(f));
+    return (double)f;
+}
+
 void fill_stats(ckfwi_stats* stats, Ctx& cx, const RunCfg& rc, const long long* cnt, const long long* counters,
                 const FieldGeom& f)
 {
@@ -1706,10 +1733,11 @@ int gradient_one(ckfwi_model* m, const ckfwi_shot* s, const float* d_obs, int me
     } else {
         ST_TRY(run_body(cx, rc, acts, counters));
     }
-    double phi = 0.0;
-    CK_TRY(cudaMemcpyAsync(&phi, m->phi.p, sizeof(double), cudaMemcpyDeviceToHost, st));
+    double phi2[2] = {0.0, 0.0};
+    CK_TRY(cudaMemcpyAsync(phi2, m->phi.p, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
     int fl = 0;
     ST_TRY(read_flags(m, st, &fl));
+    const double phi = phi2[0];
     if (misfit) *misfit = phi;
     m->last_words.clear();
     if (counters[1] > 0) {
@@ -1718,6 +1746,7 @@ int gradient_one(ckfwi_model* m, const ckfwi_shot* s, const float* d_obs, int me
     }
     if (stats) {
         fill_stats(stats, cx, rc, cnt, counters, f);
+        stats->u_absmax = absmax_of(phi2[1]);
         const long long ncomp = counters[1];
         if (ncomp > 0) {
             double mn, sum, peak;
@@ -2053,14 +2082,19 @@ int gradient_batch(const std::vector<ckfwi_model*>& lanes, const ckfwi_shot* sho
         }
     }
     int fl = 0;
+    double umax = 0.0;
     for (int l = 0; l < NL; ++l) {
-        CK_TRY(cudaMemcpyAsync(phis + l, lanes[l]->phi.p, sizeof(double), cudaMemcpyDeviceToHost, st));
+        double p2[2] = {0.0, 0.0};
+        CK_TRY(cudaMemcpyAsync(p2, lanes[l]->phi.p, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
         int f1 = 0;
         ST_TRY(read_flags(lanes[l], st, &f1));
+        phis[l] = p2[0];
+        umax = std::max(umax, absmax_of(p2[1]));
         if (fl == CKFWI_OK) fl = f1;
     }
     if (stats) {
         fill_stats(stats, cx, rc, cnt, counters, m0->fg);
+        stats->u_absmax = umax;
         const long long ncomp = counters[1];
         if (ncomp > 0) {
             double mn = 1e300, sum = 0, peak = 0;

@@ -202,6 +202,8 @@ cudaError_t launch_adj_tma(const AdjArgs& a, const CUtensorMap& tml, const CUten
 
 // aux.cu
 cudaError_t launch_sample(const float* u, const Sample& smp, cudaStream_t s);
+// *out = max(*out, bits of max |u|) over the total grid (out must start at 0)
+cudaError_t launch_absmax(const float* u_origin, const FieldGeom& g, unsigned* out, cudaStream_t s);
 cudaError_t launch_residual(const float* d, const float* dobs, float* r, int rows, int nrec,
                             double* partials, int nparts, double* phi, cudaStream_t s);
 cudaError_t launch_to_padded_w(const float* dense, int kind, float dt, const FieldGeom& g,

@@ -113,3 +113,38 @@ def test_roofline_block_of_a_codec_dominated_mode():
     assert r["algorithmic_bytes_per_launch"] == pytest.approx((4.0 + 4.0 / 25.0) * npts)
     # no checkpoint bytes in the forward class of a codec mode
     assert r["class_gbs"]["fwd"] == pytest.approx(16.0 * npts * H["fwd_launches"] / (H["fwd_ms"] * 1e-3) / 1e9)
+
+
+def test_bench_line_is_short_and_complete():
+    """The driver keeps about 1.5 KB of stdout: a full-sized line (every key
+    filled, long names) stays below that and keeps its required keys."""
+    line = {
+        "metric": "gradient point-updates per second (useful 2*N*npts/t)", "value": 102.512345678,
+        "unit": "Gpt/s", "n_gpus": 1, "steps": 20, "warmup": 5, "ms_per_step": 175.61234567,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "3d-128cube-so8", "grid": [208, 208, 208], "nt": 1000, "space_order": 8,
+                   "mode": "codec Revolve at the memory of 20 fp32 checkpoints, abs tol 0.0001",
+                   "ckpt_slots": 232, "l2": "inputs > L2 (fields + checkpoints)", "parallelism": "single"},
+        "roofline": {"bound": "hbm", "kernel": "codec compression (enc+compact)", "class": "comp",
+                     "achieved": 3591.2, "peak": 6679.2, "unit": "GB/s", "frac": 0.5377, "peak_kind": "measured",
+                     "algorithmic_bytes_per_launch": 159312345.123456, "traffic": 146312345.123456},
+        "cpu_baseline": {"value": 0.4291965276, "unit": "Gpt/s", "cores": 16, "kind": "oracle",
+                         "sample": "one FP64 oracle gradient of the whole workload (1000 steps, 123.4 s)"},
+        "e2e": {"value": 99.123456789, "unit": "Gpt/s", "h2d_bytes_per_step": 16400000,
+                "d2h_bytes_per_step": 35995656},
+        "gpu_launches": 123456,
+        "clocks": {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": ["sw_power_cap"]},
+        "recompute_ratio": 2.1401, "gradients_per_hour": 20500.3,
+        "oracle": {"grad_rel_err": 0.00331234567, "tol": 0.01},
+    }
+    out = bench.compact_line(dict(line))
+    assert len(out) < 1500
+    d = json.loads(out)
+    for k in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "roofline", "cpu_baseline",
+              "e2e", "gpu_launches", "config"):
+        assert k in d
+    assert out == json.dumps(line)          # nothing had to be dropped
+    # an over-long line drops optional keys, never the required ones
+    line["config"]["mode"] = "x" * 1200
+    d = json.loads(bench.compact_line(dict(line)))
+    assert "value" in d and "roofline" in d and "oracle" not in d

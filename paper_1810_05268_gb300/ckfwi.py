@@ -396,9 +396,10 @@ def codec_compress(x, tol, stream=None):
     out = torch.zeros(cap, dtype=torch.int32, device=x.device)
     used = ctypes.c_longlong(0)
     flags = ctypes.c_int(0)
-    _check(lib().ckfwi_codec_compress(ctypes.c_void_p(x.data_ptr()), dims, nz, ny, nx, float(tol),
-                                      ctypes.c_void_p(out.data_ptr()), cap, ctypes.byref(used), ctypes.byref(flags),
-                                      _stream(stream)), "ckfwi_codec_compress")
+    with torch.cuda.device(x.device):
+        _check(lib().ckfwi_codec_compress(ctypes.c_void_p(x.data_ptr()), dims, nz, ny, nx, float(tol),
+                                          ctypes.c_void_p(out.data_ptr()), cap, ctypes.byref(used),
+                                          ctypes.byref(flags), _stream(stream)), "ckfwi_codec_compress")
     return out[:used.value].clone(), bool(flags.value & 1)
 
 
@@ -412,13 +413,18 @@ def codec_compress_noalloc(x, out, tol, stream=None):
         raise ValueError("codec_compress_noalloc needs a contiguous float32 CUDA tensor")
     if not _is_torch_cuda(out) or not out.is_contiguous() or out.element_size() != 4:
         raise ValueError("codec_compress_noalloc needs a contiguous CUDA output tensor of 32-bit words")
+    if out.device != x.device:
+        raise ValueError("codec_compress_noalloc: x and out must be on the same device")
     dims = x.dim()
     nz, ny, nx = _shape3(tuple(x.shape))
     used = ctypes.c_longlong(0)
     flags = ctypes.c_int(0)
-    _check(lib().ckfwi_codec_compress_noalloc(ctypes.c_void_p(x.data_ptr()), dims, nz, ny, nx, float(tol),
-                                              ctypes.c_void_p(out.data_ptr()), out.numel(), ctypes.byref(used),
-                                              ctypes.byref(flags), _stream(stream)), "ckfwi_codec_compress_noalloc")
+    # the library launches on, and takes its scratch of, the current device
+    with torch.cuda.device(x.device):
+        _check(lib().ckfwi_codec_compress_noalloc(ctypes.c_void_p(x.data_ptr()), dims, nz, ny, nx, float(tol),
+                                                  ctypes.c_void_p(out.data_ptr()), out.numel(), ctypes.byref(used),
+                                                  ctypes.byref(flags), _stream(stream)),
+               "ckfwi_codec_compress_noalloc")
     return used.value, bool(flags.value & 1)
 
 
@@ -454,9 +460,10 @@ def codec_decompress(stream_words, shape, stream=None):
     dims = len(shape)
     nz, ny, nx = _shape3(tuple(shape))
     out = torch.zeros(tuple(shape), dtype=torch.float32, device=stream_words.device)
-    _check(lib().ckfwi_codec_decompress(ctypes.c_void_p(stream_words.data_ptr()), stream_words.numel(), dims, nz,
-                                        ny, nx, ctypes.c_void_p(out.data_ptr()), _stream(stream)),
-           "ckfwi_codec_decompress")
+    with torch.cuda.device(stream_words.device):
+        _check(lib().ckfwi_codec_decompress(ctypes.c_void_p(stream_words.data_ptr()), stream_words.numel(), dims,
+                                            nz, ny, nx, ctypes.c_void_p(out.data_ptr()), _stream(stream)),
+               "ckfwi_codec_decompress")
     return out
 
 

@@ -1531,7 +1531,9 @@ int prepare_storage(ckfwi_model* m, const RunCfg& rc, const ckfwi_grad_opts* o)
         CK_TRY(m->pool.alloc(bytes, false));
         m->cap_words = (long long)(bytes / 4);
         CK_TRY(m->slotbase.alloc(sizeof(long long) * (2 * (size_t)rc.M + 4)));
-        if (!rc.rate) CK_TRY(m->scratch.alloc((size_t)codec_scratch_bytes(f.dims, f.nz, f.ny, f.nx), false));
+        // a fresh scratch is zeroed (its counter and group sums start at zero;
+        // every compression of this model's fields leaves them zero)
+        if (!rc.rate) CK_TRY(m->scratch.alloc((size_t)codec_scratch_bytes(f.dims, f.nz, f.ny, f.nx), true));
         CK_TRY(m->statw.alloc(sizeof(unsigned long long) * (size_t)(4 * rc.N + 8)));
     }
     return CKFWI_OK;
@@ -2560,6 +2562,9 @@ extern "C" int ckfwi_codec_compress(const float* x, int dims, int nz, int ny, in
     if (scr.bytes < need) CK_TRY(scr.alloc(need, false));
     CK_TRY(scal.alloc(64, true));
     CK_TRY(cudaMemsetAsync(scal.p, 0, 64, st));
+    // the scratch serves fields of any size here: its counter and group sums
+    // are cleared for this one's layout
+    CK_TRY(cudaMemsetAsync(scr.p, 0, (size_t)codec_scratch_zero_bytes(dims, nz, ny, nx), st));
     CodecView v{};
     v.dims = dims; v.nz = nz; v.ny = ny; v.nx = nx;
     v.py = nx;
@@ -2574,6 +2579,7 @@ extern "C" int ckfwi_codec_compress(const float* x, int dims, int nz, int ny, in
     const int e = (int)(h[4] & 0xffffffff);
     if (flags) *flags = (e & 1) ? 1 : 0;
     if (e & 2) return CKFWI_POOL_OVERFLOW;
+    if (e & 4) return CKFWI_CORRUPT;          // a chunk the compaction refused: the stream is incomplete
     if (used_words) *used_words = h[1];
     return CKFWI_OK;
 }

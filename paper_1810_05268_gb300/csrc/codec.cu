@@ -33,14 +33,21 @@
 //
 // GPU layout of the work: one thread encodes / decodes one block; a warp
 // owns one chunk, so block bit offsets inside a chunk come from a warp scan
-// of the size table.  Compression runs in two launches: encode every block
-// into a fixed-size scratch slot and write its size (and each chunk's word
-// count), then compact each chunk's bits through shared memory into the
-// payload, every CTA summing the counts before its chunks for their offsets
-// (CTA 0 writes the header).  The pool position of a stream is
-// read from and written to device memory, so a schedule of compressions and
-// decompressions runs without host synchronisation; running out of pool
-// raises an error bit and the stream is not written.
+// of the size table.  Compression runs in two launches:
+//  1. encode: every thread codes its block into its own shared-memory
+//     column; the warp assembles its chunk's bits contiguously in shared
+//     memory and writes them to the chunk's staging slot in scratch, with the
+//     chunk's word count, which it also adds to the sums of its group of 32
+//     and of 1024 chunks;
+//  2. compact: each warp copies one chunk from staging to the payload at an
+//     offset its CTA forms from at most (chunks / 1024) + 62 sums and counts
+//     (linear total work); CTA 0 writes the header, the last CTA resets the
+//     group sums.
+// The pool position of a stream is read from and written to device memory,
+// so a schedule of compressions and decompressions runs without host
+// synchronisation; running out of pool raises an error bit and the stream
+// is not written.  The scratch's counter and group sums must be zero before
+// the first compression; every compression leaves them zero.
 #include <cstdint>
 
 #include "codec_common.cuh"
@@ -56,22 +63,30 @@ constexpr int DEC_THREADS = 128;
 
 
 
-// bit writer into a per-block scratch slot of `cap` words; bits past the
-// slot are counted but not stored (such a stream is replaced by the raw form)
+// Bit writer into this thread's shared column (stride ENC_THREADS): words
+// 0 .. V-1 in the column, word V (the last of a raw-size stream) in a
+// register; bits past that are counted but not stored (such a stream is
+// replaced by the raw form).
+template <int DIMS>
 struct BitW {
+    static constexpr int V = Cfg<DIMS>::V;
     uint32_t* w;
     unsigned long long acc;
     int nacc;
     int nw;
-    int cap;
+    uint32_t last;
+    __device__ __forceinline__ void store(uint32_t v)
+    {
+        if (nw < V) w[nw * ENC_THREADS] = v;
+        else if (nw == V) last = v;
+        ++nw;
+    }
     __device__ __forceinline__ void put(uint32_t v, int n)   // n <= 32, v < 2^n
     {
-        if (n == 0) return;
         acc |= (unsigned long long)v << nacc;
         nacc += n;
         if (nacc >= 32) {
-            if (nw < cap) w[nw] = (uint32_t)acc;
-            ++nw;
+            store((uint32_t)acc);
             acc >>= 32;
             nacc -= 32;
         }
@@ -81,7 +96,7 @@ struct BitW {
         if (n > 32) {
             put((uint32_t)v, 32);
             put((uint32_t)(v >> 32), n - 32);
-        } else {
+        } else if (n > 0) {
             put((uint32_t)v, n);
         }
     }
@@ -89,10 +104,7 @@ struct BitW {
     __device__ __forceinline__ int flush()
     {
         const int b = bits();
-        if (nacc > 0) {
-            if (nw < cap) w[nw] = (uint32_t)acc;
-            ++nw;
-        }
+        if (nacc > 0) store((uint32_t)acc);
         return b;
     }
 };
@@ -105,11 +117,11 @@ __device__ __forceinline__ unsigned long long low_mask(int n)
 // Raw form of a block: bits 1, 1, then the V float bit patterns, 32 bits
 // each, LSB first; value i occupies bits 2 + 32 i .. 33 + 32 i, so word k
 // holds the top two bits of value k-1 and the low 30 bits of value k.
+// Words 0 .. V-1 go to the thread's column, word V is returned.
 template <int DIMS>
-__device__ __forceinline__ int raw_block(const float* __restrict__ x, const CodecView& v, const BlockPos& bp,
-                                         uint32_t* __restrict__ w)
+__device__ __forceinline__ uint32_t raw_block(const float* __restrict__ x, const CodecView& v, const BlockPos& bp,
+                                              uint32_t* __restrict__ col)
 {
-    constexpr int V = Cfg<DIMS>::V;
     constexpr int ROWS = DIMS == 3 ? 16 : 4;
     const int xs = 4 * bp.bx;
     uint32_t prev = 3u;      // the two header bits (as the "top bits" of value -1: 3 >> 30 would drop them)
@@ -125,13 +137,12 @@ __device__ __forceinline__ int raw_block(const float* __restrict__ x, const Code
         for (int c = 0; c < 4; ++c) {
             const uint32_t g = __float_as_uint(__ldg(row + min(xs + c, v.nx - 1)));
             const int k = 4 * r + c;
-            w[k] = (first ? prev : (prev >> 30)) | (g << 2);
+            col[k * ENC_THREADS] = (first ? prev : (prev >> 30)) | (g << 2);
             first = false;
             prev = g;
         }
     }
-    w[V] = prev >> 30;
-    return 2 + 32 * V;
+    return prev >> 30;
 }
 
 
@@ -140,27 +151,28 @@ __constant__ Perm c_perm3 = make_perm(3);
 __constant__ Perm c_perm2 = make_perm(2);
 template <int DIMS> __device__ __forceinline__ int perm_of(int r) { return DIMS == 3 ? c_perm3.p[r] : c_perm2.p[r]; }
 
-// Encode block b into its scratch slot; returns its bit count.  The block
-// is processed in four z slices (2D: four rows) so that only one slice's
-// values are held in registers outside the closed-loop search, which keeps
-// the code small and the register count low.  siv and col are this
-// thread's two columns of shared memory (stride ENC_THREADS): col holds the
-// slice values, then the transformed coefficients (natural order, as
-// negabinary); siv the integers before the transform, then the bit-plane
-// words (plane p of the first 32 coefficients in sequency order at row p,
-// of the next 32 at row 32 + p).
+// Encode block b; returns its bit count, with the stream's words 0 .. V-1 in
+// this thread's col column and word V in *last.  The block is processed in
+// four z slices (2D: four rows) so that only one slice's values are held in
+// registers outside the closed-loop search, which keeps the code small and
+// the register count low.  siv and col are this thread's two columns of
+// shared memory (stride ENC_THREADS): col holds the slice values, then the
+// transformed coefficients (natural order, as negabinary), then the coded
+// stream; siv the integers before the transform, then the bit-plane words
+// (plane p of the first 32 coefficients in sequency order at row p, of the
+// next 32 at row 32 + p).
 template <int DIMS>
 __device__ __forceinline__ int encode_block(const float* __restrict__ x, const CodecView& v, const Geo& G,
-                                            float tol_f, uint32_t* __restrict__ scratch, long long b,
-                                            int32_t* siv, uint32_t* col, int* err)
+                                            float tol_f, long long b, int32_t* siv, uint32_t* col, uint32_t* last,
+                                            int* err)
 {
     constexpr int V = Cfg<DIMS>::V;
     constexpr int SL = V / 4;                 // values per slice
     constexpr int S = ENC_THREADS;
     const BlockPos bp = block_pos(G, b);
-    BitW bw{scratch + b * Cfg<DIMS>::MAXW, 0ull, 0, 0, Cfg<DIMS>::MAXW};
     const int xs = 4 * bp.bx;
     const bool vec = v.aligned && xs + 3 < v.nx;
+    *last = 0u;
     // 1. gather, finiteness and max |x|
     float amax = 0.0f;
     bool bad = false;
@@ -189,8 +201,8 @@ __device__ __forceinline__ int encode_block(const float* __restrict__ x, const C
     }
     if (bad) atomicOr(err, 1);
     if (bad || amax <= tol_f) {
-        bw.put(0u, 1);
-        return bw.flush();
+        col[0] = 0u;                          // the single 0 bit
+        return 1;
     }
     // block exponent: that of the largest magnitude (float order is exponent order)
     const int emax = max((int)(__float_as_uint(amax) >> 23), 1) - 127;
@@ -277,11 +289,10 @@ __device__ __forceinline__ int encode_block(const float* __restrict__ x, const C
 #pragma unroll
             for (int q = 0; q < 32; ++q) siv[(32 * h + q) * S] = (int32_t)m[q];
         }
-        bw.put(1u, 1);
-        bw.put(0u, 1);
-        bw.put((uint32_t)(emax + 127), 8);
-        bw.put((uint32_t)ptop, 5);
-        bw.put((uint32_t)pbot, 5);
+        // 6. the stream, into the col column (the coefficients are no longer needed)
+        asm volatile("" ::: "memory");
+        BitW<DIMS> bw{col, 0ull, 0, 0, 0u};
+        bw.put(1u | ((uint32_t)(emax + 127) << 2) | ((uint32_t)ptop << 10) | ((uint32_t)pbot << 15), 20);
         int s = 0;
 #pragma unroll 1
         for (int p = ptop; p >= pbot; --p) {
@@ -289,26 +300,39 @@ __device__ __forceinline__ int encode_block(const float* __restrict__ x, const C
             if (V > 32) W |= (unsigned long long)(uint32_t)siv[(32 + p) * S] << 32;
             bw.put64(W & low_mask(s), s);
             while (s < V) {
-                const unsigned long long rest = W >> s;
+                const unsigned long long rest = s < 64 ? W >> s : 0ull;
                 if (rest == 0ull) {
                     bw.put(0u, 1);
                     break;
                 }
                 const int z = __ffsll((long long)rest) - 1;
-                bw.put(1u, 1);
-                bw.put64(1ull << z, z + 1);     // z zeros, then the set bit
+                // a group test (1), z zeros, the set bit (1)
+                if (z <= 29) {
+                    bw.put(1u | (2u << z), z + 2);
+                } else {
+                    bw.put(1u, 1);
+                    bw.put64(1ull << z, z + 1);
+                }
                 s += z + 1;
             }
+            if (bw.nw > V) break;             // longer than raw already
         }
-        if (bw.bits() <= Cfg<DIMS>::MAXBITS) return bw.flush();
+        if (bw.bits() <= Cfg<DIMS>::MAXBITS) {
+            const int nb = bw.flush();
+            *last = bw.last;
+            return nb;
+        }
         // longer than raw: the raw form replaces it
     }
-    return raw_block<DIMS>(x, v, bp, scratch + b * Cfg<DIMS>::MAXW);
+    *last = raw_block<DIMS>(x, v, bp, col);
+    return Cfg<DIMS>::MAXBITS;
 }
 
-// One thread per block; each warp owns one 32-block chunk and stores the
-// chunk's word count after the block slots of the scratch (the compaction
-// turns counts into offsets).
+// One thread per block; each warp owns one 32-block chunk.  After its
+// blocks are coded, the warp assembles the chunk's bits contiguously in its
+// part of the siv array (plus two words of xtra), writes them to the chunk's
+// staging slot and its word count, and adds the count to the sums of its
+// groups of 32 and of 1024 chunks (the compaction's offsets).
 template <int DIMS>
 __global__ void __launch_bounds__(ENC_THREADS, 7) enc_kernel(const float* __restrict__ x, CodecView v,
                                                           Geo G, float tol_f, uint32_t* __restrict__ scratch,
@@ -317,76 +341,133 @@ __global__ void __launch_bounds__(ENC_THREADS, 7) enc_kernel(const float* __rest
 {
     constexpr int V = Cfg<DIMS>::V;
     constexpr int CWD = V > 32 ? V : 32;       // plane words need 32 rows even in 2D
+    constexpr int S = ENC_THREADS;
     __shared__ int32_t siv[CWD * ENC_THREADS];
     __shared__ uint32_t colw[V * ENC_THREADS];
+    __shared__ uint32_t xtra[ENC_THREADS / 32][4];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const long long b = (long long)blockIdx.x * ENC_THREADS + threadIdx.x;
     const long long base = *base_word;
     if (base + G.table_words > cap_words) {
         if (b == 0) atomicOr(err, 2);
         return;
     }
+    const ScratchLayout L = scratch_layout(G);
     uint16_t* sizes = reinterpret_cast<uint16_t*>(out + base + HDR + G.nchunks);
     if (b == 0 && (G.nblocks & 1)) sizes[G.nblocks] = 0;
     int nbits = 0;
+    uint32_t last = 0u;
     if (b < G.nblocks) {
-        nbits = encode_block<DIMS>(x, v, G, tol_f, scratch, b, siv + threadIdx.x, colw + threadIdx.x, err);
+        nbits = encode_block<DIMS>(x, v, G, tol_f, b, siv + threadIdx.x, colw + threadIdx.x, &last, err);
         sizes[b] = (uint16_t)nbits;
     }
-    int tot = nbits;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) tot += __shfl_xor_sync(0xffffffffu, tot, o);
     const long long c = b / CHUNK;
-    uint32_t* counts = scratch + (G.nblocks + CHUNK) * Cfg<DIMS>::MAXW;   // words of each chunk
-    if ((threadIdx.x & 31) == 0 && c < G.nchunks) counts[c] = (uint32_t)((tot + 31) / 32);
+    if (c >= G.nchunks) return;                // whole warp
+    __syncwarp();
+    int incl = nbits;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += t;
+    }
+    const int totb = __shfl_sync(0xffffffffu, incl, 31);
+    const int off = incl - nbits;
+    const int words = (totb + 31) / 32;
+    // word j of the chunk: row j / 32, this warp's column j % 32 of siv (32 CWD
+    // words), then xtra
+    uint32_t* sv = reinterpret_cast<uint32_t*>(siv) + 32 * wid;
+    auto bufw = [&](int j) -> uint32_t* { return j < 32 * CWD ? sv + (j >> 5) * S + (j & 31) : &xtra[wid][j - 32 * CWD]; };
+    for (int k = lane; k < words; k += 32) *bufw(k) = 0u;
+    __syncwarp();
+    const int sw = (nbits + 31) / 32;
+    const uint32_t* cw = colw + threadIdx.x;
+    for (int k = 0; k < sw; ++k) {
+        uint32_t val = k < V ? cw[k * S] : last;
+        const int rem = nbits - 32 * k;
+        if (rem < 32) val &= (1u << rem) - 1u;
+        const int pos = off + 32 * k;
+        const int sh = pos & 31, idx = pos >> 5;
+        atomicOr(bufw(idx), val << sh);
+        if (sh) atomicOr(bufw(idx + 1), val >> (32 - sh));
+    }
+    __syncwarp();
+    uint32_t* stage = scratch + L.stage + c * L.cw;
+    for (int k = lane; k < words; k += 32) stage[k] = *bufw(k);
+    if (lane == 0) {
+        scratch[L.counts + c] = (uint32_t)words;
+        atomicAdd(scratch + L.g1 + (c >> 5), (uint32_t)words);
+        atomicAdd(scratch + L.g2 + (c >> 10), (uint32_t)words);
+    }
 }
 
-// Compaction of each chunk's blocks from their scratch slots into the
-// payload.  A CTA handles CMP_WARPS consecutive chunks (a warp each) and
-// finds their payload offsets itself: it sums the word counts of all chunks
-// before its first one, and of all chunks for the stream's total, so no
-// separate scan launch is needed (every CTA reads the 4-byte counts, a few
-// KB from L2).  The total decides the overflow (nothing is written) and,
-// in CTA 0, the header, the pool's next word and the statistics.
+// Compaction: each warp copies one chunk's assembled words from its staging
+// slot to the payload.  A CTA finds the payload offset of its first chunk in
+// linear total work: the sums of the whole groups of 1024 chunks before it,
+// of the whole groups of 32 chunks before it inside its group of 1024, and
+// of the chunks before it inside its group of 32 (at most 31 + 31 values
+// beyond the group-of-1024 sums, which also give the stream's total).  The
+// total decides the overflow (nothing is written) and, in CTA 0, the header,
+// the pool's next word and the statistics.  The last CTA to finish reading
+// the sums (a counter, no waiting) sets them back to zero for the next
+// compression.
 template <int DIMS>
 __global__ void __launch_bounds__(CMP_WARPS * 32) compact_kernel(uint32_t* __restrict__ out, const long long* base_word,
                                                                  long long cap_words, long long* next_word, Geo G,
-                                                                 float tol_f, const uint32_t* __restrict__ scratch,
+                                                                 float tol_f, uint32_t* __restrict__ scratch,
                                                                  int* err, unsigned long long* stat_words)
 {
-    constexpr int CW = (CHUNK * Cfg<DIMS>::MAXBITS + 31) / 32 + 1;
-    __shared__ uint32_t buf[CMP_WARPS][CW];
+    constexpr int NT = CMP_WARPS * 32;
     __shared__ long long red[2][CMP_WARPS];
+    __shared__ int s_last;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const long long base = *base_word;
     if (base + G.table_words > cap_words) {            // the encoder raised the error
         if (blockIdx.x == 0 && threadIdx.x == 0) *next_word = base;
         return;
     }
-    const uint32_t* counts = scratch + (G.nblocks + CHUNK) * Cfg<DIMS>::MAXW;
+    const ScratchLayout L = scratch_layout(G);
+    const long long ng1 = (G.nchunks + 31) / 32, ng2 = (G.nchunks + 1023) / 1024;
+    const uint32_t* counts = scratch + L.counts;
+    uint32_t* g1 = scratch + L.g1;
+    uint32_t* g2 = scratch + L.g2;
     const long long c0 = (long long)blockIdx.x * CMP_WARPS;
-    long long before = 0, after = 0;
-    for (long long i = threadIdx.x; i < G.nchunks; i += CMP_WARPS * 32) {
-        const uint32_t w = __ldg(counts + i);
-        if (i < c0) before += w;
-        else after += w;
+    long long before = 0, total = 0;
+    for (long long i = threadIdx.x; i < ng2; i += NT) {
+        const uint32_t w = g2[i];
+        total += w;
+        if (i < (c0 >> 10)) before += w;
     }
+    for (long long g = ((c0 >> 10) << 5) + threadIdx.x; g < (c0 >> 5); g += NT) before += g1[g];
+    for (long long k = ((c0 >> 5) << 5) + threadIdx.x; k < c0; k += NT) before += counts[k];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         before += __shfl_xor_sync(0xffffffffu, before, o);
-        after += __shfl_xor_sync(0xffffffffu, after, o);
+        total += __shfl_xor_sync(0xffffffffu, total, o);
     }
     if (lane == 0) {
         red[0][wid] = before;
-        red[1][wid] = after;
+        red[1][wid] = total;
     }
     __syncthreads();
-    long long prefix = 0, total = 0;
+    long long prefix = 0;
+    total = 0;
 #pragma unroll
     for (int k = 0; k < CMP_WARPS; ++k) {
         prefix += red[0][k];
         total += red[1][k];
     }
-    total += prefix;
+    // every thread of this CTA has read the sums; the last CTA resets them
+    if (threadIdx.x == 0) {
+        __threadfence();
+        s_last = atomicAdd(scratch, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (s_last) {
+        __threadfence();
+        for (long long i = threadIdx.x; i < ng1; i += NT) g1[i] = 0u;
+        for (long long i = threadIdx.x; i < ng2; i += NT) g2[i] = 0u;
+        if (threadIdx.x == 0) scratch[0] = 0u;
+    }
     const long long end = base + G.table_words + total;
     uint32_t* hdr = out + base;
     if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -413,56 +494,63 @@ __global__ void __launch_bounds__(CMP_WARPS * 32) compact_kernel(uint32_t* __res
     const long long c = c0 + wid;
     if (c >= G.nchunks) return;
     long long off_c = prefix;                          // payload word offset of this warp's chunk
-    for (long long k = c0; k < c; ++k) off_c += __ldg(counts + k);
-    const uint16_t* sizes = reinterpret_cast<const uint16_t*>(hdr + HDR + G.nchunks);
-    const long long b = c * CHUNK + lane;
-    const int nbits = b < G.nblocks ? sizes[b] : 0;
-    int incl = nbits;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const int t = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= o) incl += t;
-    }
-    const int totb = __shfl_sync(0xffffffffu, incl, 31);
-    const int off = incl - nbits;
-    const int words = (totb + 31) / 32;
-    // every block is at most MAXBITS long by construction; a chunk that is
-    // not would overrun the shared buffer, so it is refused outright
-    if (__any_sync(0xffffffffu, nbits > Cfg<DIMS>::MAXBITS) || words > CW) {
+    for (long long k = c0; k < c; ++k) off_c += counts[k];
+    const uint32_t words = counts[c];
+    if (words > (uint32_t)L.cw) {                      // not a count the encoder can write
         if (lane == 0) atomicOr(err, 4);
         return;
     }
     if (lane == 0) hdr[HDR + c] = (uint32_t)off_c;
-    for (int k = lane; k < words; k += 32) buf[wid][k] = 0u;
-    __syncwarp();
-    const uint32_t* src = scratch + b * Cfg<DIMS>::MAXW;
-    const int sw = (nbits + 31) / 32;
-    for (int k = 0; k < sw; ++k) {
-        uint32_t val = src[k];
-        const int rem = nbits - 32 * k;
-        if (rem < 32) val &= (1u << rem) - 1u;
-        const int pos = off + 32 * k;
-        const int sh = pos & 31, idx = pos >> 5;
-        atomicOr(&buf[wid][idx], val << sh);
-        if (sh) atomicOr(&buf[wid][idx + 1], val >> (32 - sh));
-    }
-    __syncwarp();
+    const uint32_t* src = scratch + L.stage + c * L.cw;
     uint32_t* payload = out + base + G.table_words + off_c;
-    for (int k = lane; k < words; k += 32) payload[k] = buf[wid][k];
+    for (uint32_t k = lane; k < words; k += 32) payload[k] = src[k];
 }
 
-// 64 stream bits starting at bit `pos` of the payload (zeros past `limit` words)
-__device__ __forceinline__ unsigned long long peek64(const uint32_t* __restrict__ p, long long pos, long long limit)
-{
-    const long long w = pos >> 5;
-    const int sh = (int)(pos & 31);
-    const unsigned long long w0 = w < limit ? p[w] : 0u;
-    const unsigned long long w1 = w + 1 < limit ? p[w + 1] : 0u;
-    const unsigned long long w2 = w + 2 < limit ? p[w + 2] : 0u;
-    unsigned long long v = (w0 | (w1 << 32)) >> sh;
-    if (sh) v |= w2 << (64 - sh);
-    return v;
-}
+// Streaming reader of the payload's bits (LSB first): a 64-bit window
+// holding at least 33 valid bits after each refill, one 32-bit load per 32
+// bits consumed; words past `limit` read as zero.
+struct BitR {
+    const uint32_t* __restrict__ p;
+    long long limit, wpos, pos;
+    unsigned long long buf;
+    int nb;
+    __device__ __forceinline__ void fill()
+    {
+        while (nb <= 32) {
+            const unsigned long long w = wpos < limit ? p[wpos] : 0u;
+            buf |= w << nb;
+            nb += 32;
+            ++wpos;
+        }
+    }
+    __device__ __forceinline__ void init(const uint32_t* __restrict__ q, long long lim, long long start)
+    {
+        p = q;
+        limit = lim;
+        wpos = start >> 5;
+        pos = start;
+        buf = 0ull;
+        nb = 0;
+        fill();
+        const int sh = (int)(start & 31);
+        buf >>= sh;
+        nb -= sh;
+    }
+    __device__ __forceinline__ unsigned long long peek() { fill(); return buf; }
+    __device__ __forceinline__ void skip(int n)        // n <= valid bits
+    {
+        buf = n >= 64 ? 0ull : buf >> n;
+        nb -= n;
+        pos += n;
+    }
+    __device__ __forceinline__ uint32_t get(int n)     // n <= 32
+    {
+        fill();
+        const uint32_t v = (uint32_t)(buf & ((n >= 32) ? 0xffffffffull : ((1ull << n) - 1ull)));
+        skip(n);
+        return v;
+    }
+};
 
 template <int DIMS>
 __global__ void __launch_bounds__(DEC_THREADS) dec_kernel(const uint32_t* __restrict__ in, const long long* base_word,
@@ -507,26 +595,24 @@ __global__ void __launch_bounds__(DEC_THREADS) dec_kernel(const uint32_t* __rest
         atomicOr(err, 4);
         return;
     }
-    long long pos = start;
+    BitR rd;
+    rd.init(payload, pw, start);
     bool corrupt = false;
     float f[V];
-    const unsigned long long h0 = peek64(payload, pos, pw);
+    const unsigned long long h0 = rd.peek();
     if (!(h0 & 1ull)) {
-        pos += 1;
+        rd.skip(1);
 #pragma unroll
         for (int i = 0; i < V; ++i) f[i] = 0.0f;
     } else if (h0 & 2ull) {
-        pos += 2;
+        rd.skip(2);
 #pragma unroll
-        for (int i = 0; i < V; ++i) {
-            f[i] = __uint_as_float((uint32_t)peek64(payload, pos, pw));
-            pos += 32;
-        }
+        for (int i = 0; i < V; ++i) f[i] = __uint_as_float(rd.get(32));
     } else {
         const int emax = (int)((h0 >> 2) & 0xFFu) - 127;
         const int ptop = (int)((h0 >> 10) & 31u);
         const int pbot = (int)((h0 >> 15) & 31u);
-        pos += 20;
+        rd.skip(20);
         if (emax < -126 || emax > 127 || pbot > ptop) corrupt = true;
         // plane words into this thread's shared column (rows p and 32 + p),
         // then one bit-matrix transpose gives the coefficient words
@@ -540,23 +626,34 @@ __global__ void __launch_bounds__(DEC_THREADS) dec_kernel(const uint32_t* __rest
 #pragma unroll 1
         for (int p = ptop; p >= pbot && !corrupt; --p) {
             unsigned long long W = 0;
-            if (s > 0) {
-                W = peek64(payload, pos, pw) & low_mask(s);
-                pos += s;
+            if (s > 32) {
+                W = rd.get(32);
+                W |= (unsigned long long)rd.get(s - 32) << 32;
+            } else if (s > 0) {
+                W = rd.get(s);
             }
             while (s < V) {
-                const unsigned long long t = peek64(payload, pos, pw);
-                pos += 1;
-                if (!(t & 1ull)) break;
-                const unsigned long long look = peek64(payload, pos, pw);
-                if (look == 0ull) { corrupt = true; break; }
-                const int z = __ffsll((long long)look) - 1;
+                if (!rd.get(1)) break;
+                // z zeros, then the newly significant coefficient's set bit
+                int z = 0;
+                for (;;) {
+                    const unsigned long long look = rd.peek();
+                    if (look == 0ull) {
+                        z += rd.nb;
+                        rd.skip(rd.nb);
+                        if (s + z >= V || rd.pos > end) break;
+                        continue;
+                    }
+                    const int q = __ffsll((long long)look) - 1;
+                    z += q;
+                    rd.skip(q + 1);
+                    break;
+                }
                 if (s + z >= V) { corrupt = true; break; }
                 W |= 1ull << (s + z);
-                pos += z + 1;
                 s += z + 1;
             }
-            if (pos > end) corrupt = true;
+            if (rd.pos > end) corrupt = true;
             col[p * S] = (uint32_t)W;
             if (V > 32) col[(32 + p) * S] = (uint32_t)(W >> 32);
         }
@@ -578,6 +675,7 @@ __global__ void __launch_bounds__(DEC_THREADS) dec_kernel(const uint32_t* __rest
 #pragma unroll
         for (int i = 0; i < V; ++i) f[i] = __fmul_rn(__int2float_rn(t[i]), sc);
     }
+    const long long pos = rd.pos;
     if (corrupt || pos != end) {
         atomicOr(err, 4);
         return;
@@ -614,9 +712,12 @@ long long codec_bound_words(int dims, int nz, int ny, int nx)
 
 long long codec_scratch_bytes(int dims, int nz, int ny, int nx)
 {
-    const Geo G = make_geo(dims, nz, ny, nx);
-    const long long w = dims == 3 ? Cfg<3>::MAXW : Cfg<2>::MAXW;
-    return ((G.nblocks + CHUNK) * w + G.nchunks) * 4;   // block slots, then each chunk's word count
+    return scratch_layout(make_geo(dims, nz, ny, nx)).words * 4;
+}
+
+long long codec_scratch_zero_bytes(int dims, int nz, int ny, int nx)
+{
+    return scratch_zero_words(make_geo(dims, nz, ny, nx)) * 4;
 }
 
 cudaError_t codec_compress_dev(const float* x, const CodecView& v, float tol_f, uint32_t* out,

@@ -38,6 +38,33 @@ __host__ __device__ inline Geo make_geo(int dims, int nz, int ny, int nx)
     return G;
 }
 
+// Scratch of one fixed-accuracy compression, in 32-bit words: a counter of
+// finished compaction CTAs, the payload words of every group of 1024 chunks
+// and of every group of 32 chunks (accumulated by the encoder, read and
+// reset to zero by the compaction), each chunk's word count, and each
+// chunk's bits assembled contiguously (at most CW words a chunk).
+struct ScratchLayout {
+    long long g2, g1, counts, stage, words;
+    int cw;
+};
+constexpr ScratchLayout scratch_layout_for(int dims, long long nchunks)
+{
+    ScratchLayout L{};
+    const long long ng1 = (nchunks + 31) / 32, ng2 = (nchunks + 1023) / 1024;
+    const int maxbits = dims == 3 ? Cfg<3>::MAXBITS : Cfg<2>::MAXBITS;
+    L.cw = (CHUNK * maxbits + 31) / 32;
+    L.g2 = 32;
+    L.g1 = L.g2 + ng2;
+    L.counts = (L.g1 + ng1 + 31) / 32 * 32;
+    L.stage = (L.counts + nchunks + 63) / 64 * 64;
+    L.words = L.stage + nchunks * L.cw;
+    return L;
+}
+__host__ __device__ inline ScratchLayout scratch_layout(const Geo& G) { return scratch_layout_for(G.dims, G.nchunks); }
+// words of the scratch that must hold zero before a compression (the
+// counter and both group sums); a compression leaves them zero again
+__host__ __device__ inline long long scratch_zero_words(const Geo& G) { return scratch_layout(G).counts; }
+
 // sequency order, built at compile time from its definition
 struct Perm { int p[64]; };
 constexpr Perm make_perm(int dims)
@@ -160,12 +187,27 @@ __device__ __forceinline__ BlockPos block_pos(const Geo& G, long long b)
 }
 
 // In-place transpose of a 32 x 32 bit matrix: on return a[p] bit r is the
-// input a[r] bit p (five stages of block swaps: j = 16, 8, 4, 2, 1).
+// input a[r] bit p (five stages of block swaps: j = 16, 8, 4, 2, 1).  The
+// half-word and byte swaps of the first two stages are byte permutes (two
+// per pair of words); the last three use masks.
 __device__ __forceinline__ void transpose32(uint32_t (&a)[32])
 {
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {          // j = 16: swap a[k] bits 16..31 with a[k+16] bits 0..15
+        const uint32_t x = a[k], y = a[k + 16];
+        a[k] = __byte_perm(x, y, 0x5410);
+        a[k + 16] = __byte_perm(x, y, 0x7632);
+    }
+#pragma unroll
+    for (int k = 0; k < 32; ++k) {          // j = 8: swap the odd bytes of a[k] with the even bytes of a[k+8]
+        if (k & 8) continue;
+        const uint32_t x = a[k], y = a[k + 8];
+        a[k] = __byte_perm(x, y, 0x6240);
+        a[k + 8] = __byte_perm(x, y, 0x7351);
+    }
     constexpr uint32_t M[5] = {0x0000FFFFu, 0x00FF00FFu, 0x0F0F0F0Fu, 0x33333333u, 0x55555555u};
 #pragma unroll
-    for (int st = 0; st < 5; ++st) {
+    for (int st = 2; st < 5; ++st) {
         const int j = 16 >> st;
 #pragma unroll
         for (int k = 0; k < 32; ++k) {

@@ -229,6 +229,9 @@ struct CodecView {       // a float field to (de)compress, origin based
 };
 long long codec_bound_words(int dims, int nz, int ny, int nx);
 long long codec_scratch_bytes(int dims, int nz, int ny, int nx);
+// leading bytes of that scratch that must be zero before a compression
+// (a compression leaves them zero again)
+long long codec_scratch_zero_bytes(int dims, int nz, int ny, int nx);
 // Compress into `out` at word offset read from *base_word (device), checking
 // against cap_words; writes *next_word = base + stream length (device) and
 // raises err bits: 1 NONFINITE, 2 OVERFLOW.

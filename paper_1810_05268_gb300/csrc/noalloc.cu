@@ -1,7 +1,8 @@
 // Allocation-free variant of the standalone codec compression.
 //
-// ckfwi_codec_compress needs scratch memory (one fixed-size slot per 4^d
-// block for the encoded bits, plus a few device scalars) and allocates it
+// ckfwi_codec_compress needs scratch memory (a staging slot per 32-block
+// chunk for the encoded bits, the chunks' word counts and group sums, plus
+// a few device scalars) and allocates it
 // with cudaMalloc on first use.  Some callers cannot allow that: code that
 // must not trigger cudaMalloc's implicit device synchronisation (a latency-
 // critical path), processes whose device memory is entirely owned by
@@ -11,8 +12,9 @@
 // statically sized __device__ array, so a call allocates nothing; the
 // caller still passes the input field and the output buffer.
 //
-// The array holds NOALLOC_MAX_BLOCKS blocks of scratch (about 17 MB on
-// every device that loads the library, kept until the process exits).
+// The array holds the scratch of a field of NOALLOC_MAX_BLOCKS blocks (about
+// 17 MB on every device that loads the library, kept until the process
+// exits).
 // Every call on a device shares it and it keeps the last call's contents,
 // so two calls whose work overlaps on the GPU (different streams, or
 // different host threads) race and corrupt each other's output; calls must
@@ -22,16 +24,19 @@
 #include <mutex>
 
 #include "../../include/ckfwi.h"
-#include "internal.h"
+#include "codec_common.cuh"
 
 using namespace ckfwi;
 
 namespace {
 
 constexpr long long NOALLOC_MAX_BLOCKS = 65536;            // 4^d blocks per field
-constexpr long long NOALLOC_WORDS_PER_BLOCK = 65;           // 2 + 32 * 64 bits, rounded up to words
-// block slots, then one word count per 32-block chunk
-constexpr long long NOALLOC_SCRATCH_WORDS = (NOALLOC_MAX_BLOCKS + 32) * NOALLOC_WORDS_PER_BLOCK + NOALLOC_MAX_BLOCKS / 32;
+// the compression scratch of the largest field accepted: its layout for the
+// most chunks, in 3D (a 2D chunk needs fewer staging words)
+constexpr long long NOALLOC_MAX_CHUNKS = (NOALLOC_MAX_BLOCKS + CHUNK - 1) / CHUNK;
+constexpr long long NOALLOC_SCRATCH_WORDS = scratch_layout_for(3, NOALLOC_MAX_CHUNKS).words;
+static_assert(scratch_layout_for(2, NOALLOC_MAX_CHUNKS).words <= NOALLOC_SCRATCH_WORDS,
+              "a 2D field of the largest size must fit the static scratch");
 
 // Device-side scratch.  In host code these names are host-side stand-ins,
 // not device addresses: the address is looked up once per device below.
@@ -80,9 +85,14 @@ extern "C" int ckfwi_codec_compress_noalloc(const float* x, int dims, int nz, in
     const int rs = resolve(dev, &scratch, &sc);
     if (rs != CKFWI_OK) return rs;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    // the stream's start word, end word and error bits start at zero; the
-    // per-block scratch slots are written before they are read
+    if (codec_scratch_bytes(dims, nz, ny, nx) > (long long)sizeof(uint32_t) * NOALLOC_SCRATCH_WORDS)
+        return CKFWI_EINVAL;
+    // the stream's start word, end word and error bits start at zero, and
+    // so do the scratch's counter and group sums for this field's layout
+    // (every other scratch word is written before it is read)
     if (cudaMemsetAsync(sc, 0, sizeof(long long) * 8, st) != cudaSuccess) return CKFWI_ECUDA;
+    if (cudaMemsetAsync(scratch, 0, (size_t)codec_scratch_zero_bytes(dims, nz, ny, nx), st) != cudaSuccess)
+        return CKFWI_ECUDA;
     CodecView v{};
     v.dims = dims; v.nz = nz; v.ny = ny; v.nx = nx;
     v.py = nx;
@@ -99,6 +109,7 @@ extern "C" int ckfwi_codec_compress_noalloc(const float* x, int dims, int nz, in
     const int e = (int)(h[4] & 0xffffffff);
     if (flags) *flags = (e & 1) ? 1 : 0;
     if (e & 2) return CKFWI_POOL_OVERFLOW;
+    if (e & 4) return CKFWI_CORRUPT;          // a chunk the compaction refused: the stream is incomplete
     if (used_words) *used_words = h[1];
     return CKFWI_OK;
 }

@@ -171,6 +171,20 @@ def test_codec_streams_bitwise_vs_oracle(dims, shape, rel):
     assert np.all(np.abs(y.astype(np.float64) - x) <= tol)
 
 
+@pytest.mark.parametrize("dims,shape", [(3, (131, 133, 139)), (2, (700, 903))])
+def test_codec_streams_bitwise_vs_oracle_many_chunks(dims, shape):
+    """More than 1024 chunks of 32 blocks (two levels of group sums in the
+    compaction's offsets), twice in a row on the same scratch."""
+    for rel, seed in ((1e-4, 3), (1e-3, 4)):
+        x = _field(dims, shape, seed=seed)
+        tol = rel * float(np.abs(x).max())
+        ref, _ = OC.compress(x, tol)
+        words, _ = C.codec_compress(torch.from_numpy(x).cuda(), tol)
+        assert np.array_equal(words.cpu().numpy().view(np.uint32), ref)
+        y = C.codec_decompress(words, shape).cpu().numpy()
+        assert np.array_equal(y.view(np.uint32), OC.decompress(ref, shape).view(np.uint32))
+
+
 def test_codec_overlong_blocks_fall_back_to_raw_bitwise():
     rng = np.random.default_rng(12)
     z, y, x = np.meshgrid(*[np.arange(12)] * 3, indexing="ij")

@@ -30,7 +30,10 @@ def _field(shape, seed):
     return torch.from_numpy((f * 1e-2).astype(np.float32)).cuda()
 
 
-@pytest.mark.parametrize("shape,tol", [((33, 41, 58), 1e-5), ((64, 48, 80), 1e-7), ((37, 130), 1e-6)])
+# the last case is exactly the largest field the static scratch accepts
+# (16 x 64 x 64 = 65536 blocks)
+@pytest.mark.parametrize("shape,tol", [((33, 41, 58), 1e-5), ((64, 48, 80), 1e-7), ((37, 130), 1e-6),
+                                       ((64, 256, 256), 1e-5)])
 def test_noalloc_matches_allocating_entry_point_twice(C, shape, tol):
     for call in range(2):
         x = _field(shape, seed=call + len(shape))

@@ -823,7 +823,9 @@ int fwd_step(Ctx& cx, const Role& u, const Role& up, const Role& out, int n, boo
             continue;
         }
         const int tok = cx.begin(PC_FWD);
-        if (m->tf.ver >= 5) {
+        if (m->tf.ver == 7) {
+            CK_TRY(launch_fwd5(a, m->tf, m->K, ck, cx.st));
+        } else if (m->tf.ver >= 5) {
             ST_TRY(ot4_fwd_step(m, a, m->tf, ck, cx.st));
             ++cx.launches;
         } else if (m->tf.ver == 2 && in_host(m, u)) {
@@ -878,7 +880,9 @@ int adj_step(Ctx& cx, const Role& l1, const Role& l2, const Role& l0, const Role
             continue;
         }
         const int tok = cx.begin(PC_ADJ);
-        if (m->ta.ver >= 5) {
+        if (m->ta.ver == 7) {
+            CK_TRY(launch_adj5(a, m->ta, m->K, utype, cx.st));
+        } else if (m->ta.ver >= 5) {
             ST_TRY(ot4_adj_step(m, a, m->ta, utype, j, cx.st));
             cx.launches += 2;
         } else if (m->ta.ver == 2 && in_host(m, u)) {
@@ -1055,6 +1059,12 @@ int autotune(ckfwi_model* m, cudaStream_t st)
                 if (v4_supported(f.dims, m->K, t4)) cands.push_back(t4);
                 t4.pf = 1;                       // one plane of prefetch, six CTAs per SM
                 if (v4_supported(f.dims, m->K, t4)) cands.push_back(t4);
+                Tile t7 = v3_tile_at(i, z);     // the lean generation, one or two planes per step
+                t7.ver = 7;
+                for (int np : {1, 2}) {
+                    t7.pf = np;
+                    if (v5_supported(f.dims, m->K, t7)) cands.push_back(t7);
+                }
             }
         }
     }
@@ -1094,7 +1104,10 @@ int autotune(ckfwi_model* m, cudaStream_t st)
     const int reps = 3;
     CUtensorMap tm_u, tm_l;
     auto go = [&](const Tile& t, int pass) -> int {
-        if (t.ver >= 5) {
+        if (t.ver == 7) {
+            if (pass == 0) CK_TRY(launch_fwd5(a, t, m->K, CK_NONE, st));
+            else CK_TRY(launch_adj5(b, t, m->K, U_FP32, st));
+        } else if (t.ver >= 5) {
             if (pass == 0) ST_TRY(ot4_fwd_step(m, a, t, CK_NONE, st));
             else ST_TRY(ot4_adj_step(m, b, t, U_FP32, m->g.nt, st));
         } else if (t.ver == 4) {
@@ -1124,8 +1137,9 @@ int autotune(ckfwi_model* m, cudaStream_t st)
         if (nf < 4 || u.zlen < 1) return false;
         if (nf < 5) u.vec = 1;
         if (nf < 6) u.pf = 0;
-        if ((u.ver >= 5) != (m->ot == 4)) return false;
-        const bool okv = u.ver == 6   ? ot4v_supported(f.dims, m->K, u, reverse) && v3_fits(f, m->K)
+        if ((u.ver == 5 || u.ver == 6) != (m->ot == 4)) return false;
+        const bool okv = u.ver == 7   ? v5_supported(f.dims, m->K, u) && v3_fits(f, m->K)
+                         : u.ver == 6 ? ot4v_supported(f.dims, m->K, u, reverse) && v3_fits(f, m->K)
                          : u.ver == 5 ? ot4_supported(f.dims, m->K, u)
                          : u.ver == 4 ? v4_supported(f.dims, m->K, u) && v3_fits(f, m->K)
                          : u.ver == 3 ? v3_supported(f.dims, m->K, u) && v3_fits(f, m->K)

@@ -39,10 +39,10 @@
 //     memory and writes them to the chunk's staging slot in scratch, with the
 //     chunk's word count, which it also adds to the sums of its group of 32
 //     and of 1024 chunks;
-//  2. compact: each warp copies one chunk from staging to the payload at an
-//     offset its CTA forms from at most (chunks / 1024) + 62 sums and counts
-//     (linear total work); CTA 0 writes the header, the last CTA resets the
-//     group sums.
+//  2. compact: a CTA per group of 32 chunks copies them from staging to the
+//     payload at offsets formed from at most (chunks / 1024) + 31 group sums
+//     and a warp scan of the group's counts (linear total work); CTA 0 writes
+//     the header, the last CTA resets the group sums.
 // The pool position of a stream is read from and written to device memory,
 // so a schedule of compressions and decompressions runs without host
 // synchronisation; running out of pool raises an error bit and the stream
@@ -58,7 +58,6 @@ namespace {
 constexpr uint32_t VERSION = 1u;
 constexpr int GUARD = 1;
 constexpr int ENC_THREADS = 64;
-constexpr int CMP_WARPS = 4;
 constexpr int DEC_THREADS = 128;
 
 
@@ -400,24 +399,26 @@ __global__ void __launch_bounds__(ENC_THREADS, 7) enc_kernel(const float* __rest
     }
 }
 
-// Compaction: each warp copies one chunk's assembled words from its staging
-// slot to the payload.  A CTA finds the payload offset of its first chunk in
-// linear total work: the sums of the whole groups of 1024 chunks before it,
-// of the whole groups of 32 chunks before it inside its group of 1024, and
-// of the chunks before it inside its group of 32 (at most 31 + 31 values
-// beyond the group-of-1024 sums, which also give the stream's total).  The
-// total decides the overflow (nothing is written) and, in CTA 0, the header,
-// the pool's next word and the statistics.  The last CTA to finish reading
-// the sums (a counter, no waiting) sets them back to zero for the next
-// compression.
+// Compaction: a CTA moves one group of 32 chunks from their staging slots
+// to the payload.  Its payload offset is the sum of the whole groups of 1024
+// chunks before it and of the groups of 32 before it inside its group of
+// 1024 (at most chunks / 1024 + 31 values, linear total work); the chunks'
+// offsets inside the group come from a warp scan of their counts.  The sums
+// of the groups of 1024 also give the stream's total, which decides the
+// overflow (nothing is written) and, in CTA 0, the header, the pool's next
+// word and the statistics.  The last CTA to finish reading the sums (a
+// counter, no waiting) sets them back to zero for the next compression.
+constexpr int CMP_THREADS = 256;
+
 template <int DIMS>
-__global__ void __launch_bounds__(CMP_WARPS * 32) compact_kernel(uint32_t* __restrict__ out, const long long* base_word,
-                                                                 long long cap_words, long long* next_word, Geo G,
-                                                                 float tol_f, uint32_t* __restrict__ scratch,
-                                                                 int* err, unsigned long long* stat_words)
+__global__ void __launch_bounds__(CMP_THREADS) compact_kernel(uint32_t* __restrict__ out, const long long* base_word,
+                                                              long long cap_words, long long* next_word, Geo G,
+                                                              float tol_f, uint32_t* __restrict__ scratch,
+                                                              int* err, unsigned long long* stat_words)
 {
-    constexpr int NT = CMP_WARPS * 32;
-    __shared__ long long red[2][CMP_WARPS];
+    constexpr int NW = CMP_THREADS / 32;
+    __shared__ long long red[2][NW];
+    __shared__ uint32_t offs[CHUNK + 1];
     __shared__ int s_last;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const long long base = *base_word;
@@ -430,15 +431,25 @@ __global__ void __launch_bounds__(CMP_WARPS * 32) compact_kernel(uint32_t* __res
     const uint32_t* counts = scratch + L.counts;
     uint32_t* g1 = scratch + L.g1;
     uint32_t* g2 = scratch + L.g2;
-    const long long c0 = (long long)blockIdx.x * CMP_WARPS;
+    const long long grp = blockIdx.x, c0 = grp * CHUNK;
     long long before = 0, total = 0;
-    for (long long i = threadIdx.x; i < ng2; i += NT) {
+    for (long long i = threadIdx.x; i < ng2; i += CMP_THREADS) {
         const uint32_t w = g2[i];
         total += w;
-        if (i < (c0 >> 10)) before += w;
+        if (i < (grp >> 5)) before += w;
     }
-    for (long long g = ((c0 >> 10) << 5) + threadIdx.x; g < (c0 >> 5); g += NT) before += g1[g];
-    for (long long k = ((c0 >> 5) << 5) + threadIdx.x; k < c0; k += NT) before += counts[k];
+    for (long long g = ((grp >> 5) << 5) + threadIdx.x; g < grp; g += CMP_THREADS) before += g1[g];
+    if (wid == 0) {                                    // offsets of the group's chunks
+        const uint32_t w = c0 + lane < G.nchunks ? counts[c0 + lane] : 0u;
+        uint32_t incl = w;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += t;
+        }
+        offs[lane] = incl - w;
+        if (lane == 31) offs[CHUNK] = incl;
+    }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         before += __shfl_xor_sync(0xffffffffu, before, o);
@@ -452,7 +463,7 @@ __global__ void __launch_bounds__(CMP_WARPS * 32) compact_kernel(uint32_t* __res
     long long prefix = 0;
     total = 0;
 #pragma unroll
-    for (int k = 0; k < CMP_WARPS; ++k) {
+    for (int k = 0; k < NW; ++k) {
         prefix += red[0][k];
         total += red[1][k];
     }
@@ -464,8 +475,8 @@ __global__ void __launch_bounds__(CMP_WARPS * 32) compact_kernel(uint32_t* __res
     __syncthreads();
     if (s_last) {
         __threadfence();
-        for (long long i = threadIdx.x; i < ng1; i += NT) g1[i] = 0u;
-        for (long long i = threadIdx.x; i < ng2; i += NT) g2[i] = 0u;
+        for (long long i = threadIdx.x; i < ng1; i += CMP_THREADS) g1[i] = 0u;
+        for (long long i = threadIdx.x; i < ng2; i += CMP_THREADS) g2[i] = 0u;
         if (threadIdx.x == 0) scratch[0] = 0u;
     }
     const long long end = base + G.table_words + total;
@@ -491,36 +502,39 @@ __global__ void __launch_bounds__(CMP_WARPS * 32) compact_kernel(uint32_t* __res
         if (stat_words) atomicAdd(stat_words, (unsigned long long)(G.table_words + total));
     }
     if (end > cap_words) return;                       // overflow: nothing is written
-    const long long c = c0 + wid;
-    if (c >= G.nchunks) return;
-    long long off_c = prefix;                          // payload word offset of this warp's chunk
-    for (long long k = c0; k < c; ++k) off_c += counts[k];
-    const uint32_t words = counts[c];
-    if (words > (uint32_t)L.cw) {                      // not a count the encoder can write
-        if (lane == 0) atomicOr(err, 4);
-        return;
+    for (int k = wid; k < CHUNK; k += NW) {
+        const long long c = c0 + k;
+        if (c >= G.nchunks) break;
+        const uint32_t words = offs[k + 1] - offs[k];
+        if (words > (uint32_t)L.cw) {                  // not a count the encoder can write
+            if (lane == 0) atomicOr(err, 4);
+            continue;
+        }
+        const long long off_c = prefix + offs[k];
+        if (lane == 0) hdr[HDR + c] = (uint32_t)off_c;
+        const uint32_t* src = scratch + L.stage + c * L.cw;
+        uint32_t* payload = out + base + G.table_words + off_c;
+        for (uint32_t w = lane; w < words; w += 32) payload[w] = src[w];
     }
-    if (lane == 0) hdr[HDR + c] = (uint32_t)off_c;
-    const uint32_t* src = scratch + L.stage + c * L.cw;
-    uint32_t* payload = out + base + G.table_words + off_c;
-    for (uint32_t k = lane; k < words; k += 32) payload[k] = src[k];
 }
 
 // Streaming reader of the payload's bits (LSB first): a 64-bit window
 // holding at least 33 valid bits after each refill, one 32-bit load per 32
-// bits consumed; words past `limit` read as zero.
+// bits consumed, issued one refill ahead (the next word is already in a
+// register when the window needs it); words past `limit` read as zero.
 struct BitR {
     const uint32_t* __restrict__ p;
     long long limit, wpos, pos;
     unsigned long long buf;
+    uint32_t nextw;
     int nb;
+    __device__ __forceinline__ uint32_t word(long long k) const { return k < limit ? p[k] : 0u; }
     __device__ __forceinline__ void fill()
     {
         while (nb <= 32) {
-            const unsigned long long w = wpos < limit ? p[wpos] : 0u;
-            buf |= w << nb;
+            buf |= (unsigned long long)nextw << nb;
             nb += 32;
-            ++wpos;
+            nextw = word(++wpos);
         }
     }
     __device__ __forceinline__ void init(const uint32_t* __restrict__ q, long long lim, long long start)
@@ -529,12 +543,12 @@ struct BitR {
         limit = lim;
         wpos = start >> 5;
         pos = start;
-        buf = 0ull;
-        nb = 0;
-        fill();
+        const unsigned long long w0 = word(wpos), w1 = word(wpos + 1);
+        nextw = word(wpos + 2);
+        wpos += 2;
         const int sh = (int)(start & 31);
-        buf >>= sh;
-        nb -= sh;
+        buf = (w0 | (w1 << 32)) >> sh;
+        nb = 64 - sh;
     }
     __device__ __forceinline__ unsigned long long peek() { fill(); return buf; }
     __device__ __forceinline__ void skip(int n)        // n <= valid bits
@@ -727,14 +741,14 @@ cudaError_t codec_compress_dev(const float* x, const CodecView& v, float tol_f, 
     const Geo G = make_geo(v.dims, v.nz, v.ny, v.nx);
     uint32_t* sc = static_cast<uint32_t*>(scratch);
     const unsigned eb = (unsigned)((G.nblocks + ENC_THREADS - 1) / ENC_THREADS);
-    const unsigned cb = (unsigned)((G.nchunks + CMP_WARPS - 1) / CMP_WARPS);
+    const unsigned cb = (unsigned)((G.nchunks + CHUNK - 1) / CHUNK);
     if (v.dims == 3) {
         enc_kernel<3><<<eb, ENC_THREADS, 0, s>>>(x, v, G, tol_f, sc, out, base_word, cap_words, err);
-        compact_kernel<3><<<cb, CMP_WARPS * 32, 0, s>>>(out, base_word, cap_words, next_word, G, tol_f, sc, err,
+        compact_kernel<3><<<cb, CMP_THREADS, 0, s>>>(out, base_word, cap_words, next_word, G, tol_f, sc, err,
                                                          stat_words);
     } else {
         enc_kernel<2><<<eb, ENC_THREADS, 0, s>>>(x, v, G, tol_f, sc, out, base_word, cap_words, err);
-        compact_kernel<2><<<cb, CMP_WARPS * 32, 0, s>>>(out, base_word, cap_words, next_word, G, tol_f, sc, err,
+        compact_kernel<2><<<cb, CMP_THREADS, 0, s>>>(out, base_word, cap_words, next_word, G, tol_f, sc, err,
                                                          stat_words);
     }
     return cudaGetLastError();

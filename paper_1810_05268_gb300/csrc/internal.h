@@ -134,9 +134,10 @@ struct Tile {
     int ver = 1;          // 1: register-queue kernels, 2: TMA-fed kernels (3D, orders 2-8),
                           // 3: vector-blocked kernels (3D), 4: vector-blocked forward step fed
                           // by asynchronous copies (3D), 5: the two-pass OT4 kernels,
-                          // 6: the same vector-blocked (3D)
+                          // 6: the same vector-blocked (3D), 7: the lean async-copy
+                          // OT2 kernels (3D, one or two planes per step)
     int vec = 1;          // ver 3, 4: x points per thread (2 or 4)
-    int pf = 0;           // ver 4: planes of prefetch (0 = the default, 2)
+    int pf = 0;           // ver 4: planes of prefetch (0 = the default, 2); ver 7: planes per step (1, 2)
 };
 
 // One batched step over several lanes (shots): lane l's arguments are
@@ -172,6 +173,10 @@ cudaError_t launch_adj3(const AdjArgs& a, const Tile& t, int K, int ut, cudaStre
 bool v4_supported(int dims, int K, const Tile& t);
 cudaError_t launch_fwd4(const FwdArgs& a, const Tile& t, int K, int ck, cudaStream_t s);
 cudaError_t launch_adj4(const AdjArgs& a, const Tile& t, int K, int ut, cudaStream_t s);
+// stencil_v5.cu: the lean async-copy generation (Tile.ver 7; geometry must pass v3_fits)
+bool v5_supported(int dims, int K, const Tile& t);
+cudaError_t launch_fwd5(const FwdArgs& a, const Tile& t, int K, int ck, cudaStream_t s);
+cudaError_t launch_adj5(const AdjArgs& a, const Tile& t, int K, int ut, cudaStream_t s);
 // batch_v3.cu (every lane's geometry must pass v3_fits)
 cudaError_t launch_fwd3_batch(const BatchLaunch<FwdArgs>& b, const Tile& t, int K, int ck, cudaStream_t s);
 cudaError_t launch_adj3_batch(const BatchLaunch<AdjArgs>& b, const Tile& t, int K, int ut, cudaStream_t s);

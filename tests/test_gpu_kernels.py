@@ -124,3 +124,28 @@ def test_async_copy_forward_bitwise_equal_register_queue(so, shape, vec, mode):
         assert np.array_equal(got[0], ref[0])
         assert got[1] == ref[1]
         assert np.array_equal(got[2], ref[2])
+
+
+@pytest.mark.parametrize("so,shape", [(2, (30, 37, 70)), (4, (33, 41, 131)), (8, (35, 43, 70)), (8, (26, 29, 200)),
+                                      (16, (36, 41, 77)), (4, (21, 19, 13))])
+@pytest.mark.parametrize("np_", [1, 2])
+@pytest.mark.parametrize("mode", ["fp32", "fp16"])
+def test_lean_kernels_bitwise_equal_register_queue(so, shape, np_, mode):
+    """The lean async-copy generation (Tile.ver 7) with one or two planes per
+    step: forward and reverse steps, alone and mixed with other generations,
+    with z runs of odd and even length (a two-plane step that ends with one
+    plane) and a run covering the whole column."""
+    case = make_case(3, so, shape, nbl=6, nt=70, seed=so + 5 * np_)
+    rng = np.random.default_rng(so + 1)
+    dobs = torch.from_numpy((rng.standard_normal((71, case.rec.shape[0])) * 1e-3).astype(np.float32)).cuda()
+    k = so // 2
+    by1 = max(8, k)
+    ref = _run(case, "1,32,%d,9" % by1, "1,32,%d,9" % by1, dobs, 5, mode)
+    tiles = [("7,32,16,%d,4,%d" % (z, np_), "7,32,16,%d,4,%d" % (z, np_)) for z in (7, 8, 64)]
+    tiles.append(("7,32,16,9,4,%d" % np_, "3,32,16,9,4"))
+    tiles.append(("4,32,16,9,4", "7,32,16,5,4,%d" % np_))
+    for tf, ta in tiles:
+        got = _run(case, tf, ta, dobs, 5, mode)
+        assert np.array_equal(got[0], ref[0]), (tf, ta)
+        assert got[1] == ref[1], (tf, ta)
+        assert np.array_equal(got[2], ref[2]), (tf, ta)

@@ -193,9 +193,22 @@ def perf_model(results, nt, fmin):
     # cost of a step that writes a checkpoint, and of a reverse step reading a
     # 16-bit one, from the FP32 / FP16 runs and their event counts
     sa = named("storeall")
-    c_f = sa["fwd_ms"] / sa["fwd_launches"] if sa else unit("fwd", "fwd_launches")
-    c_r = sa["adj_ms"] / sa["adj_launches"] if sa else (unit("adj", "adj_launches", ("fp32", "codec", "rate"))
-                                                        or unit("adj", "adj_launches"))
+    # the profiled gradients time every kernel-class call between two events;
+    # the store-all gradient gives that overhead per call: its profiled class
+    # times minus its un-profiled (graph replay) time, over its calls
+    delta = 0.0
+    if sa:
+        calls = sa["fwd_launches"] + sa["adj_launches"]
+        prof = sa["fwd_ms"] + sa["adj_ms"] + sa.get("other_ms", 0.0)
+        delta = max(0.0, (prof - sa["ms"]) / calls) if calls else 0.0
+    raw_unit = unit
+
+    def unit(cls, n, modes=None):
+        u = raw_unit(cls, n, modes)
+        return None if u is None else max(0.0, u - delta)
+    c_f = sa["fwd_ms"] / sa["fwd_launches"] - delta if sa else unit("fwd", "fwd_launches")
+    c_r = sa["adj_ms"] / sa["adj_launches"] - delta if sa else (unit("adj", "adj_launches", ("fp32", "codec", "rate"))
+                                                                or unit("adj", "adj_launches"))
     t_ck = {}
     c_r16 = t_d16 = None
     for key, mode in (("fp32", "fp32"), ("fp16", "fp16")):
@@ -203,18 +216,18 @@ def perf_model(results, nt, fmin):
         if r and r["fwd_launches"] > 0 and c_f is not None:
             ev = P.events(nt, r["ckpt_slots"], mode)
             if ev["takeshots"]:
-                t_ck[mode] = max(0.0, (r["fwd_ms"] - ev["fwd"] * c_f) / ev["takeshots"])
+                t_ck[mode] = max(0.0, (r["fwd_ms"] - ev["fwd"] * (c_f + delta)) / ev["takeshots"])
             if mode == "fp16":
-                c_r16 = r["adj_ms"] / r["adj_launches"]
+                c_r16 = r["adj_ms"] / r["adj_launches"] - delta
                 if ev["decomp"]:
-                    t_d16 = r["decomp_ms"] / ev["decomp"]
+                    t_d16 = max(0.0, r["decomp_ms"] / ev["decomp"] - delta)
     costs = P.Costs(c_f=c_f, c_r=c_r, c_r16=c_r16, t_c=unit("comp", "comp_calls", ("codec",)),
                     t_d=unit("decomp", "decomp_calls", ("codec",)), f_min=fmin,
                     t_c_rate=unit("comp", "comp_calls", ("rate",)), t_d_rate=unit("decomp", "decomp_calls", ("rate",)),
                     t_d16=t_d16,
                     t_ck32=t_ck.get("fp32", 0.0), t_ck16=t_ck.get("fp16", 0.0), rate=RATE,
                     grad_err={r["store_mode"]: r.get("grad_rel_err_vs_storeall", 0.0) for r in results.values()})
-    out = {"unit_ms": {"C_F": costs.c_f, "C_R": costs.c_r, "C_R16": costs.c_r16, "t_c": costs.t_c,
+    out = {"event_overhead_ms_per_call": delta, "unit_ms": {"C_F": costs.c_f, "C_R": costs.c_r, "C_R16": costs.c_r16, "t_c": costs.t_c,
                        "t_d": costs.t_d, "t_c_rate": costs.t_c_rate, "t_d_rate": costs.t_d_rate,
                        "t_d16": costs.t_d16, "t_ck32": costs.t_ck32, "t_ck16": costs.t_ck16, "F_min": fmin},
            "modes": {}}
@@ -318,7 +331,8 @@ def time_modes(C, torch, model, shot, d_obs, modes, nt, npts, args, ws, lr, full
             "fwd_launches": st["fwd_launches"], "adj_launches": st["adj_launches"],
             "comp_calls": st["comp_calls"], "decomp_calls": st["decomp_calls"],
             "fwd_ms": avg("fwd_ms"), "adj_ms": avg("adj_ms"), "comp_ms": avg("comp_ms"),
-            "decomp_ms": avg("decomp_ms"), "kernel_launches": st_plain["kernel_launches"], "misfit": phi,
+            "decomp_ms": avg("decomp_ms"), "other_ms": avg("other_ms"),
+            "kernel_launches": st_plain["kernel_launches"], "misfit": phi,
             "ratio_mean": st["ratio_mean"], "ratio_min": st["ratio_min"],
             "pool_bytes_peak": st["pool_bytes_peak"],
             "fwd_kernel": [st["fwd_ver"], st["fwd_bx"], st["fwd_by"], st["fwd_vec"], st["fwd_zlen"], st["fwd_pf"]],

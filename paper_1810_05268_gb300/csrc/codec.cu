@@ -403,12 +403,13 @@ __global__ void __launch_bounds__(ENC_THREADS, 7) enc_kernel(const float* __rest
 // to the payload.  Its payload offset is the sum of the whole groups of 1024
 // chunks before it and of the groups of 32 before it inside its group of
 // 1024 (at most chunks / 1024 + 31 values, linear total work); the chunks'
-// offsets inside the group come from a warp scan of their counts.  The sums
+// offsets inside the group come from a warp scan of their counts, and the
+// group's words are copied by all threads at once.  The sums
 // of the groups of 1024 also give the stream's total, which decides the
 // overflow (nothing is written) and, in CTA 0, the header, the pool's next
 // word and the statistics.  The last CTA to finish reading the sums (a
 // counter, no waiting) sets them back to zero for the next compression.
-constexpr int CMP_THREADS = 256;
+constexpr int CMP_THREADS = 512;
 
 template <int DIMS>
 __global__ void __launch_bounds__(CMP_THREADS) compact_kernel(uint32_t* __restrict__ out, const long long* base_word,
@@ -502,69 +503,38 @@ __global__ void __launch_bounds__(CMP_THREADS) compact_kernel(uint32_t* __restri
         if (stat_words) atomicAdd(stat_words, (unsigned long long)(G.table_words + total));
     }
     if (end > cap_words) return;                       // overflow: nothing is written
-    for (int k = wid; k < CHUNK; k += NW) {
-        const long long c = c0 + k;
-        if (c >= G.nchunks) break;
-        const uint32_t words = offs[k + 1] - offs[k];
-        if (words > (uint32_t)L.cw) {                  // not a count the encoder can write
-            if (lane == 0) atomicOr(err, 4);
-            continue;
-        }
-        const long long off_c = prefix + offs[k];
-        if (lane == 0) hdr[HDR + c] = (uint32_t)off_c;
-        const uint32_t* src = scratch + L.stage + c * L.cw;
-        uint32_t* payload = out + base + G.table_words + off_c;
-        for (uint32_t w = lane; w < words; w += 32) payload[w] = src[w];
+    if (threadIdx.x < CHUNK && c0 + threadIdx.x < G.nchunks) {
+        const int k = threadIdx.x;
+        if (offs[k + 1] - offs[k] > (uint32_t)L.cw) atomicOr(err, 4);   // not a count the encoder can write
+        hdr[HDR + c0 + k] = (uint32_t)(prefix + offs[k]);
+    }
+    // the group's chunks are contiguous in the payload: every thread copies
+    // words of it, finding each word's chunk by a binary search of the
+    // offsets (all loads independent, so their latencies overlap)
+    const uint32_t gw = offs[CHUNK];
+    uint32_t* payload = out + base + G.table_words + prefix;
+    const uint32_t* stage = scratch + L.stage + c0 * L.cw;
+    for (uint32_t w = threadIdx.x; w < gw; w += CMP_THREADS) {
+        int lo = 0;
+#pragma unroll
+        for (int st = CHUNK / 2; st > 0; st >>= 1)
+            if (offs[lo + st] <= w) lo += st;
+        payload[w] = stage[(long long)lo * L.cw + (w - offs[lo])];
     }
 }
 
-// Streaming reader of the payload's bits (LSB first): a 64-bit window
-// holding at least 33 valid bits after each refill, one 32-bit load per 32
-// bits consumed, issued one refill ahead (the next word is already in a
-// register when the window needs it); words past `limit` read as zero.
-struct BitR {
-    const uint32_t* __restrict__ p;
-    long long limit, wpos, pos;
-    unsigned long long buf;
-    uint32_t nextw;
-    int nb;
-    __device__ __forceinline__ uint32_t word(long long k) const { return k < limit ? p[k] : 0u; }
-    __device__ __forceinline__ void fill()
-    {
-        while (nb <= 32) {
-            buf |= (unsigned long long)nextw << nb;
-            nb += 32;
-            nextw = word(++wpos);
-        }
-    }
-    __device__ __forceinline__ void init(const uint32_t* __restrict__ q, long long lim, long long start)
-    {
-        p = q;
-        limit = lim;
-        wpos = start >> 5;
-        pos = start;
-        const unsigned long long w0 = word(wpos), w1 = word(wpos + 1);
-        nextw = word(wpos + 2);
-        wpos += 2;
-        const int sh = (int)(start & 31);
-        buf = (w0 | (w1 << 32)) >> sh;
-        nb = 64 - sh;
-    }
-    __device__ __forceinline__ unsigned long long peek() { fill(); return buf; }
-    __device__ __forceinline__ void skip(int n)        // n <= valid bits
-    {
-        buf = n >= 64 ? 0ull : buf >> n;
-        nb -= n;
-        pos += n;
-    }
-    __device__ __forceinline__ uint32_t get(int n)     // n <= 32
-    {
-        fill();
-        const uint32_t v = (uint32_t)(buf & ((n >= 32) ? 0xffffffffull : ((1ull << n) - 1ull)));
-        skip(n);
-        return v;
-    }
-};
+// 64 stream bits starting at bit `pos` of the payload (zeros past `limit` words)
+__device__ __forceinline__ unsigned long long peek64(const uint32_t* __restrict__ p, long long pos, long long limit)
+{
+    const long long w = pos >> 5;
+    const int sh = (int)(pos & 31);
+    const unsigned long long w0 = w < limit ? p[w] : 0u;
+    const unsigned long long w1 = w + 1 < limit ? p[w + 1] : 0u;
+    const unsigned long long w2 = w + 2 < limit ? p[w + 2] : 0u;
+    unsigned long long v = (w0 | (w1 << 32)) >> sh;
+    if (sh) v |= w2 << (64 - sh);
+    return v;
+}
 
 template <int DIMS>
 __global__ void __launch_bounds__(DEC_THREADS) dec_kernel(const uint32_t* __restrict__ in, const long long* base_word,
@@ -609,24 +579,26 @@ __global__ void __launch_bounds__(DEC_THREADS) dec_kernel(const uint32_t* __rest
         atomicOr(err, 4);
         return;
     }
-    BitR rd;
-    rd.init(payload, pw, start);
+    long long pos = start;
     bool corrupt = false;
     float f[V];
-    const unsigned long long h0 = rd.peek();
+    const unsigned long long h0 = peek64(payload, pos, pw);
     if (!(h0 & 1ull)) {
-        rd.skip(1);
+        pos += 1;
 #pragma unroll
         for (int i = 0; i < V; ++i) f[i] = 0.0f;
     } else if (h0 & 2ull) {
-        rd.skip(2);
+        pos += 2;
 #pragma unroll
-        for (int i = 0; i < V; ++i) f[i] = __uint_as_float(rd.get(32));
+        for (int i = 0; i < V; ++i) {
+            f[i] = __uint_as_float((uint32_t)peek64(payload, pos, pw));
+            pos += 32;
+        }
     } else {
         const int emax = (int)((h0 >> 2) & 0xFFu) - 127;
         const int ptop = (int)((h0 >> 10) & 31u);
         const int pbot = (int)((h0 >> 15) & 31u);
-        rd.skip(20);
+        pos += 20;
         if (emax < -126 || emax > 127 || pbot > ptop) corrupt = true;
         // plane words into this thread's shared column (rows p and 32 + p),
         // then one bit-matrix transpose gives the coefficient words
@@ -640,34 +612,23 @@ __global__ void __launch_bounds__(DEC_THREADS) dec_kernel(const uint32_t* __rest
 #pragma unroll 1
         for (int p = ptop; p >= pbot && !corrupt; --p) {
             unsigned long long W = 0;
-            if (s > 32) {
-                W = rd.get(32);
-                W |= (unsigned long long)rd.get(s - 32) << 32;
-            } else if (s > 0) {
-                W = rd.get(s);
+            if (s > 0) {
+                W = peek64(payload, pos, pw) & low_mask(s);
+                pos += s;
             }
             while (s < V) {
-                if (!rd.get(1)) break;
-                // z zeros, then the newly significant coefficient's set bit
-                int z = 0;
-                for (;;) {
-                    const unsigned long long look = rd.peek();
-                    if (look == 0ull) {
-                        z += rd.nb;
-                        rd.skip(rd.nb);
-                        if (s + z >= V || rd.pos > end) break;
-                        continue;
-                    }
-                    const int q = __ffsll((long long)look) - 1;
-                    z += q;
-                    rd.skip(q + 1);
-                    break;
-                }
+                const unsigned long long t = peek64(payload, pos, pw);
+                pos += 1;
+                if (!(t & 1ull)) break;
+                const unsigned long long look = peek64(payload, pos, pw);
+                if (look == 0ull) { corrupt = true; break; }
+                const int z = __ffsll((long long)look) - 1;
                 if (s + z >= V) { corrupt = true; break; }
                 W |= 1ull << (s + z);
+                pos += z + 1;
                 s += z + 1;
             }
-            if (rd.pos > end) corrupt = true;
+            if (pos > end) corrupt = true;
             col[p * S] = (uint32_t)W;
             if (V > 32) col[(32 + p) * S] = (uint32_t)(W >> 32);
         }
@@ -689,7 +650,6 @@ __global__ void __launch_bounds__(DEC_THREADS) dec_kernel(const uint32_t* __rest
 #pragma unroll
         for (int i = 0; i < V; ++i) f[i] = __fmul_rn(__int2float_rn(t[i]), sc);
     }
-    const long long pos = rd.pos;
     if (corrupt || pos != end) {
         atomicOr(err, 4);
         return;

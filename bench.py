@@ -96,10 +96,13 @@ def traffic_per_point(kernel, tile):
         return None
 
 
-def roofline_block(H, nt, npts, peak, peak_kind):
+def roofline_block(H, nt, npts, peak, peak_kind, delta=0.0):
     """The bench line's `roofline`: the kernel class with the largest device
     time in the headline mode H (one mode's profiled stats), its algorithmic
-    bytes per launch over its average launch time, against `peak`."""
+    bytes per launch over its average launch time, against `peak`.  A
+    profiled gradient brackets every kernel-class call with two events; the
+    per-call overhead `delta` [ms] that adds (measured on the store-all
+    gradient against its graph replay) is taken off each call's time."""
     F = max(1.0, H["ratio_mean"] or 1.0)
     # a step that writes an FP32 or 16-bit checkpoint writes 4 more B/pt
     # (u^{n-1} in FP32, or both levels in 16 bits), W of the launches
@@ -111,7 +114,8 @@ def roofline_block(H, nt, npts, peak, peak_kind):
         "comp": (H["comp_ms"], H["comp_calls"], (4.0 + 4.0 / F) * npts),
         "decomp": (H["decomp_ms"], H["decomp_calls"], (4.0 / F + 4.0) * npts),
     }
-    gbs = {k: (b * n / (ms / 1e3) / 1e9 if ms > 0 and n > 0 else 0.0) for k, (ms, n, b) in classes.items()}
+    per = {k: (max(1e-9, ms / n - delta) if ms > 0 and n > 0 else 0.0) for k, (ms, n, b) in classes.items()}
+    gbs = {k: (b / (per[k] / 1e3) / 1e9 if per[k] > 0 else 0.0) for k, (ms, n, b) in classes.items()}
     dom = max(classes, key=lambda k: classes[k][0])
     _, n_d, b_d = classes[dom]
     if dom in ("fwd", "adj"):
@@ -124,7 +128,8 @@ def roofline_block(H, nt, npts, peak, peak_kind):
     return {"bound": "hbm", "kernel": kname, "class": dom, "achieved": gbs[dom], "peak": peak,
             "unit": "GB/s", "frac": gbs[dom] / peak, "peak_kind": peak_kind,
             "frac_of_nominal": gbs[dom] / NOMINAL_HBM_GBS,
-            "algorithmic_bytes_per_launch": b_d, "launches": n_d,
+            "algorithmic_bytes_per_launch": b_d, "launches": n_d, "launch_us": 1e3 * per[dom],
+            "event_overhead_us_per_call": 1e3 * delta,
             "traffic": (tpp * npts) if tpp is not None else None,
             "class_gbs": gbs}
 
@@ -602,6 +607,260 @@ def error_table(C, torch, model, shot, dobs_o, g_ref, nt, npts, state_bytes, sha
             "plateau": (codec[-1]["rel_err"] / fp32) if codec and fp32 else None}
 
 
+def _timed(torch, fn):
+    """(seconds, result) of fn() bracketed by device synchronisations and CUDA events."""
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    out = fn()
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / 1e3, out
+
+
+def _rel(torch, g, ref):
+    d = float(torch.linalg.vector_norm(g.double() - ref))
+    return d, d / float(torch.linalg.vector_norm(ref))
+
+
+def sweep_c3(C, torch, synth, args):
+    """The 300 x 600 x 600 workload (order 16, 3000 steps of 1.5 ms, 25 m,
+    layered model with faults): store-all would need 1.3 TB, so the gradient
+    runs at checkpoint budgets of M uncompressed states (M S bytes, S = 864
+    MB) with FP32, BF16, FP16 and codec storage in the same bytes.  Each
+    configuration runs once (un-profiled, CUDA events); the error is stated
+    against the FP32 Revolve gradient, which every FP32 schedule gives bit
+    for bit.  The FP64 oracle's rate on this grid is extrapolated from its
+    first ORACLE_STEPS steps."""
+    w = synth.workload("3d-300x600x600-so16", nt=args.nt)
+    nt = w.nt
+    npts = int(np.prod(w.shape))
+    S = 2 * npts * 4
+    grid = C.GridSpec(3, w.shape, w.nbl, w.h, w.so, w.dt, nt, w.vmax)
+    model = C.Model(grid)
+    shot = C.ShotSpec(src=w.src, rec=w.rec, f0=w.f0)
+    model.set_model(torch.from_numpy(w.true.astype(np.float32)).cuda())
+    d_obs = model.forward_shot(shot).clone()
+    model.set_model(torch.from_numpy(w.start.astype(np.float32)).cuda())
+    budgets = [int(b) for b in args.budgets.split(",")]
+    tols = (1e-3, 1e-4, 1e-5)
+    out = {"workload": "3d-300x600x600-so16", "grid": list(w.shape), "nt": nt, "space_order": w.so,
+           "state_bytes": S, "rows": []}
+
+    def grad(kw, profile=False):
+        return model.adjoint_gradient(shot, d_obs, profile=profile, **kw)
+    t, (phi, g_ref, st) = _timed(torch, lambda: grad(dict(ckpt_slots=32, store_mode="fp32")))
+    g_ref = g_ref.double()
+    _, (_, _, stp) = _timed(torch, lambda: grad(dict(ckpt_slots=32, store_mode="fp32"), True))
+    out["kernels"] = {"fwd_us": 1e3 * stp["fwd_ms"] / stp["fwd_launches"], "adj_us": 1e3 * stp["adj_ms"] / stp["adj_launches"],
+                      "fwd_kernel": [stp["fwd_ver"], stp["fwd_bx"], stp["fwd_by"], stp["fwd_vec"], stp["fwd_zlen"], stp["fwd_pf"]],
+                      "adj_kernel": [stp["adj_ver"], stp["adj_bx"], stp["adj_by"], stp["adj_vec"], stp["adj_zlen"], stp["adj_pf"]]}
+    out["kernels"]["fwd_gbs"] = FWD_BYTES * npts / (out["kernels"]["fwd_us"] * 1e-6) / 1e9
+    out["kernels"]["adj_gbs"] = ADJ_BYTES * npts / (out["kernels"]["adj_us"] * 1e-6) / 1e9
+    out["u_absmax"] = st["u_absmax"]
+    # worst compression ratio per tolerance, from a pilot at the smallest budget
+    fmin = {}
+    for tol in tols:
+        slots, pool = min(nt, 3 * budgets[0]), budgets[0] * S
+        for _ in range(6):
+            try:
+                stc = grad(dict(ckpt_slots=slots, store_mode="codec", tol=tol, pool_bytes=pool))[2]
+                fmin[tol] = max(1.0, stc["ratio_min"])
+                break
+            except C.CkfwiError as e:
+                if e.status != C.POOL_OVERFLOW:
+                    raise
+                slots = max(2, slots // 2)
+    out["F_min"] = {str(k): v for k, v in fmin.items()}
+    for M in budgets:
+        modes = [("fp32", dict(ckpt_slots=min(nt, M), store_mode="fp32")),
+                 ("bf16", dict(ckpt_slots=min(nt, 2 * (M - 1) + 1), store_mode="bf16")),
+                 ("fp16", dict(ckpt_slots=min(nt, 2 * (M - 1) + 1), store_mode="fp16"))]
+        for tol in tols:
+            if tol in fmin:
+                modes.append(("codec %g" % tol, dict(ckpt_slots=int(min(nt, max(2, M * fmin[tol] / 1.1))),
+                                                     store_mode="codec", tol=tol, pool_bytes=M * S)))
+        for name, kw in modes:
+            row = {"budget_fp32_states": M, "storage": name}
+            try:
+                for _ in range(4):
+                    try:
+                        t, (phi, g, st) = _timed(torch, lambda: grad(kw))
+                        break
+                    except C.CkfwiError as e:
+                        if e.status != C.POOL_OVERFLOW or kw["store_mode"] != "codec":
+                            raise
+                        kw["ckpt_slots"] = max(2, int(kw["ckpt_slots"] * 0.8))
+                ea, er = _rel(torch, g, g_ref)
+                row.update(slots=kw["ckpt_slots"], seconds=t, gpts=2.0 * nt * npts / t / 1e9,
+                           recompute_ratio=st["fwd_steps"] / nt, p=st["p"], W=st["takeshots"], R=st["restores"],
+                           abs_err=ea, rel_err=er)
+                if kw["store_mode"] == "codec":
+                    row.update(F_mean=st["ratio_mean"], F_min=st["ratio_min"],
+                               tol_over_max_u=kw["tol"] / st["u_absmax"] if st["u_absmax"] else None)
+            except C.CkfwiError as e:
+                row["skipped"] = str(e)
+            out["rows"].append(row)
+            print("c3", json.dumps(row), file=sys.stderr, flush=True)
+    model.close()
+    if not args.no_cpu:
+        r, secs = cpu_sample(w, ORACLE_STEPS)
+        out["oracle"] = {"gpts_extrapolated": r, "steps": ORACLE_STEPS, "seconds": secs, "cores": os.cpu_count(),
+                         "gradient_seconds_extrapolated": 2.0 * nt * npts / (r * 1e9),
+                         "note": "the oracle's rate over its first %d steps; its 3000-step gradient is not run" %
+                                 ORACLE_STEPS}
+    return out
+
+
+ORACLE_STEPS = 50
+
+
+def sweep_c4(C, torch, synth, args):
+    """32 shots with uneven 3D apertures (128^3 to 256 x 320 x 320 windows of
+    one survey model, order 8, 15 m, 1500 steps of 1 ms), every stencil step
+    of a batch one launch over all its shots, recorded as a CUDA graph, at
+    M = 32 checkpoints per shot with BF16, FP16 and codec (1e-4) storage; the
+    FP16 batch against the same shots one at a time."""
+    nt = args.nt or 1500
+    vel, wins = synth.batched_apertures()
+    nbl, h, so, dt = 40, 15.0, 8, 1.0
+    models, shots, dobs, offs = [], [], [], []
+    npts = 0
+    for wn in wins:
+        g = C.GridSpec(3, wn.shape, nbl, h, so, dt, nt, 4.5)
+        m = C.Model(g)
+        ext = [(n - 2 * nbl - 1) * h for n in wn.shape]
+        rec = synth.receiver_grid(30.0, np.linspace(0, ext[1], 32), np.linspace(0, ext[2], 32))
+        sh = C.ShotSpec(src=(30.0, ext[1] / 2, ext[2] / 2), rec=rec, f0=0.008)
+        # observed data of a 3% faster medium, the gradient at the window's own
+        m.set_model(torch.from_numpy((wn.vel * 1.03).astype(np.float32)).cuda())
+        dobs.append(m.forward_shot(sh).clone())
+        m.set_model(torch.from_numpy(wn.vel.astype(np.float32)).cuda())
+        models.append(m)
+        shots.append(sh)
+        offs.append(wn.offset)
+        npts += int(np.prod(wn.shape))
+    out = {"shots": len(wins), "nt": nt, "space_order": so, "slots": 32, "points_all_shots": npts,
+           "window_shapes": [list(wn.shape) for wn in wins], "survey": list(vel.shape), "modes": {}}
+    M = 32
+    for name, kw in (("bf16", dict(store_mode="bf16")), ("fp16", dict(store_mode="fp16")),
+                     ("codec 1e-4", dict(store_mode="codec", tol=1e-4, pool_bytes=0))):
+        run = lambda prof=False: C.batch_gradient_models(models, shots, dobs, offs, vel.shape, M, use_graph=not prof,
+                                                         profile=prof, **kw)
+        try:
+            run()
+            t, (phi, gs, st) = _timed(torch, run)
+            _, (_, _, sp) = _timed(torch, lambda: run(True))
+        except C.CkfwiError as e:
+            out["modes"][name] = {"skipped": str(e)}
+            continue
+        row = {"seconds": t, "gpts": 2.0 * nt * npts / t / 1e9, "misfit": phi,
+               "fwd_launches": sp["fwd_launches"], "adj_launches": sp["adj_launches"],
+               "recompute_ratio": st["fwd_steps"] / nt}
+        # the batched kernels' aggregate algorithmic bandwidth: every lane's
+        # forward steps move 16 B a point, reverse steps 28 B
+        if sp["fwd_ms"] > 0:
+            row["fwd_gbs"] = FWD_BYTES * npts * (st["fwd_steps"]) / (sp["fwd_ms"] / 1e3) / 1e9
+        if sp["adj_ms"] > 0:
+            row["adj_gbs"] = ADJ_BYTES * npts * nt / (sp["adj_ms"] / 1e3) / 1e9
+        row["fwd_kernel"] = [sp["fwd_ver"], sp["fwd_bx"], sp["fwd_by"], sp["fwd_vec"], sp["fwd_zlen"]]
+        if kw["store_mode"] == "codec":
+            row.update(F_mean=st["ratio_mean"], F_min=st["ratio_min"])
+        out["modes"][name] = row
+        print("c4", name, json.dumps(row), file=sys.stderr, flush=True)
+    # the same FP16 gradients one shot at a time
+    def singles():
+        for m, sh, d in zip(models, shots, dobs):
+            m.adjoint_gradient(sh, d, M, store_mode="fp16", use_graph=True)
+    singles()
+    t1, _ = _timed(torch, singles)
+    out["fp16_one_shot_at_a_time_seconds"] = t1
+    if "fp16" in out["modes"] and "seconds" in out["modes"]["fp16"]:
+        out["fp16_batch_speedup"] = t1 / out["modes"]["fp16"]["seconds"]
+    for m in models:
+        m.close()
+    return out
+
+
+def sweep_c5(C, torch, synth, args):
+    """The FWI loop on the 2D 1104 x 464 workload (order 8, 2000 steps): 64
+    shots evenly on the surface, observed data of the layered true model from
+    the FP64 oracle, steepest descent from the smoothed start model through
+    the torch.autograd wrapper (backward = the batched checkpointed adjoint
+    with codec checkpoints, M = 16), for ITERATIONS iterations.  At the
+    first and the last iteration the misfit and gradient of four of the shots
+    are compared with the oracle's (with FP32 and with codec checkpoints), and
+    at the first the gradient's directional derivative with central
+    differences of the misfit."""
+    from oracle import propagator as O
+    from paper_1810_05268_gb300 import autograd as A
+    w = synth.workload("2d-1024x384-so8", nt=args.nt)
+    nt = w.nt
+    og = O.Grid(2, tuple(w.shape), w.nbl, w.h, w.so, w.dt, nt, w.vmax)
+    grid = C.GridSpec(2, w.shape, w.nbl, w.h, w.so, w.dt, nt, w.vmax)
+    ext = (w.shape[1] - 2 * w.nbl - 1) * w.h
+    srcs = [(20.0, 0.0, float(x)) for x in np.linspace(0.0, ext, 64)]
+    ser = O.ricker(nt, w.dt, w.f0)
+    true = w.true.astype(np.float32).astype(np.float64)
+    t0 = time.perf_counter()
+    dobs_np = [O.forward(og, true, [s], ser, w.rec).astype(np.float32) for s in srcs]
+    oracle_data_s = time.perf_counter() - t0
+    shots = [C.ShotSpec(src=s, rec=w.rec, f0=w.f0) for s in srcs]
+    dobs = [torch.from_numpy(d).cuda() for d in dobs_np]
+    model = C.Model(grid)
+    m0 = torch.from_numpy((1.0 / w.start.astype(np.float64) ** 2).astype(np.float32)).cuda()
+    # codec tolerance: 1e-3 of the wavefield's scale (max |u^N| of a first gradient)
+    model.set_model(m0, kind=C.SLOWNESS2)
+    _, _, st0 = model.batch_gradient(shots[:1], dobs[:1], 16)
+    tol = 1e-3 * st0["u_absmax"]
+    S = 2 * int(np.prod(w.shape)) * 4
+    opts = dict(store_mode="codec", tol=tol, pool_bytes=16 * S)
+    check_idx = [0, 21, 42, 63]
+
+    def oracle_check(m):
+        vel = 1.0 / np.sqrt(m.detach().cpu().numpy().astype(np.float64))
+        phi_o, g_o = 0.0, np.zeros(w.shape)
+        for i in check_idx:
+            p, g, _ = O.gradient(og, vel, [srcs[i]], ser, w.rec, dobs_np[i].astype(np.float64))
+            phi_o += p
+            g_o += g
+        res = {}
+        model.set_model(m.detach(), kind=C.SLOWNESS2)
+        for name, kw in (("fp32", dict(store_mode="fp32")), ("codec", opts)):
+            phi, gs, _ = model.batch_gradient([shots[i] for i in check_idx], [dobs[i] for i in check_idx], 16, **kw)
+            gg = gs.cpu().numpy()
+            res[name] = {"misfit": phi, "misfit_oracle": phi_o, "misfit_rel_diff": abs(phi - phi_o) / phi_o,
+                         "grad_rel_err": float(np.linalg.norm(gg - g_o) / np.linalg.norm(g_o))}
+        return res
+
+    out = {"workload": "2d-1024x384-so8", "grid": list(w.shape), "nt": nt, "shots": 64, "slots": 16,
+           "codec_tol": tol, "iterations": ITERATIONS, "oracle_data_seconds": oracle_data_s,
+           "checked_shots": check_idx}
+    out["check_first"] = oracle_check(m0)
+    # directional derivative at the start: central differences of the misfit
+    dm = torch.from_numpy(synth.smooth_perturbation(tuple(w.shape), 10.0, 7).astype(np.float32)).cuda()
+    eps = 1e-3 * float(m0.abs().max())
+    x = m0.clone().requires_grad_(True)
+    phi = A.misfit(x, model, shots, dobs, 16, **opts)
+    (g,) = torch.autograd.grad(phi, x)
+    pp = float(A.misfit(m0 + eps * dm, model, shots, dobs, 16, **opts))
+    pm = float(A.misfit(m0 - eps * dm, model, shots, dobs, 16, **opts))
+    fd = (pp - pm) / (2 * eps)
+    ad = float((g.double() * dm.double()).sum())
+    out["fd_check"] = {"fd": fd, "adjoint": ad, "rel_diff": abs(fd - ad) / abs(fd), "eps": eps}
+    t, (m_fin, hist) = _timed(torch, lambda: A.steepest_descent(m0, model, shots, dobs, ITERATIONS, 16,
+                                                               m_min=1.0 / 4.5 ** 2, m_max=1.0 / 1.5 ** 2,
+                                                               **opts))
+    out["misfit_history"] = hist
+    out["loop_seconds"] = t
+    out["check_last"] = oracle_check(m_fin)
+    model.close()
+    return out
+
+
+ITERATIONS = 20
+
+
 def run_reference(args):
     ws, rk, _ = dist_env()
     if rk != 0:
@@ -700,6 +959,10 @@ def main():
                     default="storeall,codec,codec_sched,rate,fp32,fp16,bf16,codec_low,rate_low,"
                             "fp32_low,fp16_low,fp32_host,ot4,batch2d")
     ap.add_argument("--oracle-sample", default=None, help=argparse.SUPPRESS)
+    ap.add_argument("--sweep", default=None, choices=["c3", "c4", "c5"],
+                    help="instead of the headline: the 300x600x600 budget sweep, the batched apertures, or the "
+                         "FWI loop, into the side file")
+    ap.add_argument("--budgets", default="8,16,32,64,128,256", help="c3: checkpoint budgets (uncompressed states)")
     args = ap.parse_args()
     if args.oracle_sample:
         from paper_1810_05268_gb300 import synth
@@ -719,6 +982,14 @@ def main():
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     torch.cuda.set_device(lr)
     build.build()
+    if args.sweep:
+        fn = {"c3": sweep_c3, "c4": sweep_c4, "c5": sweep_c5}[args.sweep]
+        res = fn(C, torch, synth, args)
+        os.makedirs(os.path.dirname(os.path.abspath(args.detail)), exist_ok=True)
+        with open(args.detail, "w") as f:
+            json.dump({"sweep": args.sweep, "result": res}, f, indent=1)
+        print("bench: %s sweep in %s" % (args.sweep, os.path.abspath(args.detail)), file=sys.stderr, flush=True)
+        return 0
 
     w = synth.workload(WORKLOAD, nt=args.nt)
     nt = w.nt
@@ -829,7 +1100,7 @@ def main():
         batch = batch_compare(C, torch, synth)
 
     if rk == 0:
-        roof = roofline_block(H, nt, npts, *peaks())
+        roof = roofline_block(H, nt, npts, *peaks(), delta=model_block.get("event_overhead_ms_per_call", 0.0))
         clk = clocks.get(headline) or {}
         line = {
             "metric": "gradient point-updates per second (useful 2*N*npts/t)",
@@ -845,7 +1116,7 @@ def main():
                          "achieved": round(roof["achieved"], 1), "peak": roof["peak"], "unit": "GB/s",
                          "frac": round(roof["frac"], 4), "peak_kind": roof["peak_kind"],
                          "algorithmic_bytes_per_launch": roof["algorithmic_bytes_per_launch"],
-                         "traffic": roof["traffic"]},
+                         "launch_us": round(roof["launch_us"], 2), "traffic": roof["traffic"]},
             "cpu_baseline": cpu,
             "e2e": {"value": 2.0 * nt * npts / e2e_s / 1e9, "unit": "Gpt/s",
                     "h2d_bytes_per_step": int(dh.numel() * 4), "d2h_bytes_per_step": int(gh.numel() * 4 + 8)},

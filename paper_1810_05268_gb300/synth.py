@@ -175,3 +175,33 @@ def workload(name, nt=None):
                         receiver_line(20.0, np.arange(0.0, 1024 * h - 1e-9, 2 * h)), true,
                         smooth_start(true, 15.0))
     raise KeyError(name)
+
+
+@dataclass
+class Window:
+    shape: tuple         # total grid of the window (incl. its damping layer)
+    offset: tuple        # (z, y, x) of its first point in the survey grid
+    vel: np.ndarray      # velocity [km/s] of the window
+
+
+def batched_apertures(nshots=32, seed=1813, survey=(256, 448, 448), small=(128, 128, 128),
+                      large=(256, 320, 320)):
+    """Shots with uneven 3D apertures cut from one survey model: a Gaussian
+    random field (sigma 8 cells, 1.5-4.5 km/s) on the survey grid, and
+    `nshots` windows whose sizes ramp from `small` to `large` (rounded to
+    multiples of 8, order shuffled by the seed), each at a seeded offset that
+    keeps it inside the survey.  Returns (survey velocity, windows)."""
+    r = rng(seed)
+    vel = grf(survey, 8.0, seed, 1.5, 4.5)
+    sizes = []
+    for i in range(nshots):
+        t = i / max(1, nshots - 1)
+        sizes.append(tuple(int(round((a + t * (b - a)) / 8.0)) * 8 for a, b in zip(small, large)))
+    order = r.permutation(nshots)
+    wins = []
+    for i in order:
+        s = sizes[i]
+        off = tuple(int(r.integers(0, n - w + 1)) for n, w in zip(survey, s))
+        sl = tuple(slice(o, o + w) for o, w in zip(off, s))
+        wins.append(Window(s, off, np.ascontiguousarray(vel[sl])))
+    return vel, wins

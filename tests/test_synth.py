@@ -77,3 +77,19 @@ def test_workloads_have_the_stated_sizes(name, shape, so, dims):
     for a in lat:
         assert rec[:, a].min() >= 0.0 and rec[:, a].max() <= ext[a] + 1e-6
         assert 0.0 <= w.src[a] <= ext[a]
+
+
+def test_batched_apertures_shapes_and_placement():
+    from paper_1810_05268_gb300 import synth
+    vel, wins = synth.batched_apertures(nshots=6, survey=(64, 80, 80), small=(32, 32, 32), large=(48, 56, 64))
+    assert len(wins) == 6
+    sizes = sorted(w.shape for w in wins)
+    assert sizes[0] == (32, 32, 32) and sizes[-1] == (48, 56, 64)
+    for w in wins:
+        assert all(s % 8 == 0 for s in w.shape)
+        assert all(o >= 0 and o + s <= n for o, s, n in zip(w.offset, w.shape, vel.shape))
+        sl = tuple(slice(o, o + s) for o, s in zip(w.offset, w.shape))
+        assert np.array_equal(w.vel, vel[sl])
+    assert 1.5 <= vel.min() and vel.max() <= 4.5
+    vel2, wins2 = synth.batched_apertures(nshots=6, survey=(64, 80, 80), small=(32, 32, 32), large=(48, 56, 64))
+    assert np.array_equal(vel, vel2) and [w.offset for w in wins] == [w.offset for w in wins2]

@@ -339,6 +339,7 @@ struct ckfwi_model {
     DevMem pool;                    // checkpoint pool
     HostMem hpool;                  // checkpoint slots in host memory (second level)
     int host_slots = 0;             // slots 1 .. host_slots live in hpool
+    long long wait_limit = 1LL << 22;   // TMA kernels: back-off rounds of a plane's wait
     size_t pool_cap_bytes = 0;
     int pool_tag = -1;              // storage mode whose layout the pool holds
     DevMem slotbase;                // codec: device word offsets of slots
@@ -667,6 +668,7 @@ FwdArgs fwd_args(ckfwi_model* m)
     a.hdt = m->hdt;
     std::memcpy(a.c, m->c, sizeof(a.c));
     a.err = m->flags.as<int>();
+    a.wait_limit = m->wait_limit;
     return a;
 }
 
@@ -680,6 +682,7 @@ AdjArgs adj_args(ckfwi_model* m)
     a.hdt = m->hdt;
     std::memcpy(a.c, m->c, sizeof(a.c));
     a.err = m->flags.as<int>();
+    a.wait_limit = m->wait_limit;
     return a;
 }
 
@@ -1101,6 +1104,7 @@ int autotune(ckfwi_model* m, cudaStream_t st)
     b.hdt = m->hdt;
     std::memcpy(b.c, m->c, sizeof(b.c));
     b.err = m->flags.as<int>();
+    b.wait_limit = m->wait_limit;
     const int reps = 3;
     CUtensorMap tm_u, tm_l;
     auto go = [&](const Tile& t, int pass) -> int {
@@ -2192,6 +2196,10 @@ int ckfwi_create_model(const ckfwi_grid* g, ckfwi_model** out)
     if (g->dims == 2) m->g.n[1] = 1;
     m->K = g->space_order / 2;
     m->fg = make_geom(g->dims, g->n[0], m->g.n[1], g->n[2], m->K);
+    // CKFWI_TMA_WAIT_LIMIT < 0 makes the TMA kernels' waits run out at once
+    // (the test of the CKFWI_TIMEOUT path; the copies in flight are still
+    // waited for before a CTA leaves)
+    if (const char* wl = std::getenv("CKFWI_TMA_WAIT_LIMIT")) m->wait_limit = std::atoll(wl);
     double c[MAXK + 1];
     fd_weights(m->K, c);
     const double ih2 = 1.0 / (g->h * g->h);

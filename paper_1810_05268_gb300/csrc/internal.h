@@ -66,6 +66,7 @@ struct FwdArgs {
     void* ck_u;           // fused takeshot outputs (see CkMode)
     void* ck_up;
     int* err;             // error flags (bit 0: FP16 overflow, bit 3: a bounded wait ran out)
+    long long wait_limit; // TMA kernels: back-off rounds of a plane's bounded wait (< 0: give up at once)
 };
 
 // Fused reverse step:
@@ -86,6 +87,7 @@ struct AdjArgs {
     Inj adj;              // -P^T r^j  (weights carry the minus sign)
     Inj src;              // Q^T s^{j-1}
     int* err;             // error flags (bit 3: a bounded wait ran out)
+    long long wait_limit; // TMA kernels: back-off rounds of a plane's bounded wait (< 0: give up at once)
 };
 
 // OT4 kernel (Sec. 6): a forward step is two passes, Z = w lap f and then the

@@ -81,12 +81,14 @@ __device__ __forceinline__ bool mbar_try(uint64_t* bar, unsigned parity)
 }
 
 // bounded wait with a short back-off, so that waiting warps yield their
-// issue slots instead of spinning
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity)
+// issue slots instead of spinning; `rounds` < 0 gives up without looking
+// (how a test makes a wait run out without delaying any copy)
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity, long long rounds = WAIT_ROUNDS)
 {
+    if (rounds < 0) return false;
     for (int i = 0; i < 8; ++i)
         if (mbar_try(bar, parity)) return true;
-    for (long long i = 0; i < WAIT_ROUNDS; ++i) {
+    for (long long i = 0; i < rounds; ++i) {
         __nanosleep(32);
         if (mbar_try(bar, parity)) return true;
     }
@@ -341,11 +343,12 @@ __device__ __forceinline__ void ring_prologue(Ring<K, TY, T, PF>& R, const CUten
 }
 
 template <int K, int TY, class T, int PF>
-__device__ __forceinline__ bool ring_wait(const Ring<K, TY, T, PF>& R, int zz, int zb, int kb)
+__device__ __forceinline__ bool ring_wait(const Ring<K, TY, T, PF>& R, int zz, int zb, int kb,
+                                          long long rounds = WAIT_ROUNDS)
 {
     constexpr int NS = Ring<K, TY, T, PF>::NS;
     const int k = kb + (zz - zb);
-    return mbar_wait(&R.bar[k % NS], (unsigned)((k / NS) & 1));
+    return mbar_wait(&R.bar[k % NS], (unsigned)((k / NS) & 1), rounds);
 }
 
 // After the CTA barrier of plane z: the slot of plane z-K takes plane z-K+NS.
@@ -358,9 +361,9 @@ __device__ __forceinline__ void ring_refill(Ring<K, TY, T, PF>& R, const CUtenso
     if (zn <= zlast) ring_issue(R, tm, x0, y0, zn, zb, kb, H);
 }
 
-// On an aborted run: wait (bounded) for every plane still held or in
-// flight (planes max(zb, z-K) .. the last one issued), so that no copy
-// lands in shared memory after the CTA has left.
+// On an aborted run: wait (bounded, always the full WAIT_ROUNDS) for every
+// plane still held or in flight (planes max(zb, z-K) .. the last one
+// issued), so that no copy lands in shared memory after the CTA has left.
 template <int K, int TY, class T, int PF>
 __device__ __forceinline__ void ring_drain(const Ring<K, TY, T, PF>& R, int z, int zb, int zlast, int kb)
 {
@@ -470,7 +473,7 @@ __global__ void __launch_bounds__(NTX * TY) fwd_tma_kernel(const FwdArgs a, cons
         }
         const Inj4 ic = inj4(a.src, y, x, nx, row);
         const int r = ty + K, c = RingCfg<K, PF_FWD>::HX + 4 * tx;
-        for (int zz = zb; zz < za + K; ++zz) ok &= ring_wait(R, zz, zb, kb);
+        for (int zz = zb; zz < za + K; ++zz) ok &= ring_wait(R, zz, zb, kb, a.wait_limit);
         Window<K, TY, float, PF_FWD> W;
         W.init(kb, r, c);
         const long long colo = (long long)y * px + x;
@@ -486,7 +489,7 @@ __global__ void __launch_bounds__(NTX * TY) fwd_tma_kernel(const FwdArgs a, cons
         }
         int z = za;
         for (; z < zc; ++z) {
-            ok &= ring_wait(R, z + K, zb, kb);
+            ok &= ring_wait(R, z + K, zb, kb, a.wait_limit);
             const float4 upv = up0, wv = w0;
             up0 = up1;
             w0 = w1;
@@ -590,8 +593,8 @@ __global__ void __launch_bounds__(NTX * TY) adj_tma_kernel(const AdjArgs a, cons
         const Inj4 is = inj4(a.src, y, x, nx, row);
         const int r = ty + K, c = RingCfg<K, PF_ADJ>::HX + 4 * tx;
         for (int zz = zb; zz < za + K; ++zz) {
-            ok &= ring_wait(L, zz, zb, kb);
-            ok &= ring_wait(U, zz, zb, kb);
+            ok &= ring_wait(L, zz, zb, kb, a.wait_limit);
+            ok &= ring_wait(U, zz, zb, kb, a.wait_limit);
         }
         Window<K, TY, float, PF_ADJ> WL;
         Window<K, TY, UT, PF_ADJ> WU;
@@ -613,8 +616,8 @@ __global__ void __launch_bounds__(NTX * TY) adj_tma_kernel(const AdjArgs a, cons
         }
         int z = za;
         for (; z < zc; ++z) {
-            ok &= ring_wait(L, z + K, zb, kb);
-            ok &= ring_wait(U, z + K, zb, kb);
+            ok &= ring_wait(L, z + K, zb, kb, a.wait_limit);
+            ok &= ring_wait(U, z + K, zb, kb, a.wait_limit);
             const float4 l2v = l20, wv = w0, gv = g0v;
             l20 = l21;
             w0 = w1;

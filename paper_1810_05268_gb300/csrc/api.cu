@@ -851,7 +851,9 @@ int fwd_step(Ctx& cx, const Role& u, const Role& up, const Role& out, int n, boo
         if (cx.issue) {
             const int tok = cx.begin(PC_FWD);
             BatchLaunch<FwdArgs> b{cx.ftab_d + cx.fi, cx.fstart_d, NL, cx.m->fg.dims, cx.fblocks};
-            if (cx.bf.ver == 3) CK_TRY(launch_fwd3_batch(b, cx.bf, cx.m->K, ck, cx.st));
+            if (cx.bf.ver == 7) CK_TRY(launch_fwd5_batch(b, cx.bf, cx.m->K, ck, cx.st));
+            else if (cx.bf.ver == 4) CK_TRY(launch_fwd4_batch(b, cx.bf, cx.m->K, ck, cx.st));
+            else if (cx.bf.ver == 3) CK_TRY(launch_fwd3_batch(b, cx.bf, cx.m->K, ck, cx.st));
             else CK_TRY(launch_fwd_batch(b, cx.bf, cx.m->K, ck, cx.st));
             cx.end(tok);
             ++cx.launches;
@@ -910,7 +912,8 @@ int adj_step(Ctx& cx, const Role& l1, const Role& l2, const Role& l0, const Role
         if (cx.issue) {
             const int tok = cx.begin(PC_ADJ);
             BatchLaunch<AdjArgs> b{cx.atab_d + cx.ai, cx.astart_d, NL, cx.m->fg.dims, cx.ablocks};
-            if (cx.ba.ver == 3) CK_TRY(launch_adj3_batch(b, cx.ba, cx.m->K, utype, cx.st));
+            if (cx.ba.ver == 7) CK_TRY(launch_adj5_batch(b, cx.ba, cx.m->K, utype, cx.st));
+            else if (cx.ba.ver == 3) CK_TRY(launch_adj3_batch(b, cx.ba, cx.m->K, utype, cx.st));
             else CK_TRY(launch_adj_batch(b, cx.ba, cx.m->K, utype, cx.st));
             cx.end(tok);
             ++cx.launches;
@@ -1844,6 +1847,25 @@ int batch_tune(const std::vector<ckfwi_model*>& lanes, cudaStream_t st, const Ba
     for (int i = 0; fits3 && i < v3_shape_count(); ++i) {
         const Tile t = v3_tile_at(i, 1);
         if (v3_supported(dims, K, t)) shapes.push_back(t);
+        if (t.vec != 4) continue;
+        Tile t4 = t;                     // fed by asynchronous copies (forward step only)
+        t4.ver = 4;
+        t4.pf = 1;
+        if (v4_supported(dims, K, t4)) shapes.push_back(t4);
+        Tile t7 = t;                     // the lean generation, one or two planes per step
+        t7.ver = 7;
+        for (int np : {1, 2}) {
+            t7.pf = np;
+            if (v5_supported(dims, K, t7)) shapes.push_back(t7);
+        }
+    }
+    // CKFWI_BATCH_VER restricts the candidates to one generation (tests)
+    if (const char* bv = std::getenv("CKFWI_BATCH_VER")) {
+        const int want = std::atoi(bv);
+        std::vector<Tile> keep;
+        for (const Tile& t : shapes)
+            if (t.ver == want) keep.push_back(t);
+        if (!keep.empty()) shapes = keep;
     }
     for (const Tile& t : shapes) {
         long long cols = 0;
@@ -1914,9 +1936,14 @@ int batch_tune(const std::vector<ckfwi_model*>& lanes, cudaStream_t st, const Ba
             break;
         }
         for (int pass = 0; pass < 2 && rs == CKFWI_OK; ++pass) {
+            if (pass == 1 && c.t.ver == 4) continue;    // generation 4 has no batched reverse step
             auto go = [&]() {
                 const BatchLaunch<FwdArgs> bf{ftab, dst.as<int>(), NL, dims, total};
                 const BatchLaunch<AdjArgs> ba{atab, dst.as<int>(), NL, dims, total};
+                if (c.t.ver == 7)
+                    return pass == 0 ? launch_fwd5_batch(bf, c.t, K, CK_NONE, st)
+                                     : launch_adj5_batch(ba, c.t, K, U_FP32, st);
+                if (c.t.ver == 4) return launch_fwd4_batch(bf, c.t, K, CK_NONE, st);
                 if (c.t.ver == 3)
                     return pass == 0 ? launch_fwd3_batch(bf, c.t, K, CK_NONE, st)
                                      : launch_adj3_batch(ba, c.t, K, U_FP32, st);

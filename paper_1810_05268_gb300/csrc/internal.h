@@ -179,6 +179,10 @@ cudaError_t launch_adj4(const AdjArgs& a, const Tile& t, int K, int ut, cudaStre
 bool v5_supported(int dims, int K, const Tile& t);
 cudaError_t launch_fwd5(const FwdArgs& a, const Tile& t, int K, int ck, cudaStream_t s);
 cudaError_t launch_adj5(const AdjArgs& a, const Tile& t, int K, int ut, cudaStream_t s);
+// batched forms of generations 4 and 7 (every lane's geometry must pass v3_fits)
+cudaError_t launch_fwd4_batch(const BatchLaunch<FwdArgs>& b, const Tile& t, int K, int ck, cudaStream_t s);
+cudaError_t launch_fwd5_batch(const BatchLaunch<FwdArgs>& b, const Tile& t, int K, int ck, cudaStream_t s);
+cudaError_t launch_adj5_batch(const BatchLaunch<AdjArgs>& b, const Tile& t, int K, int ut, cudaStream_t s);
 // batch_v3.cu (every lane's geometry must pass v3_fits)
 cudaError_t launch_fwd3_batch(const BatchLaunch<FwdArgs>& b, const Tile& t, int K, int ck, cudaStream_t s);
 cudaError_t launch_adj3_batch(const BatchLaunch<AdjArgs>& b, const Tile& t, int K, int ut, cudaStream_t s);

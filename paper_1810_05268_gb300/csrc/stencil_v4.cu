@@ -495,7 +495,69 @@ cudaError_t adj4_k(const AdjArgs& a, const Tile& t, cudaStream_t s)
     return cudaErrorInvalidValue;
 }
 
+// Batched forward step: one launch advances every lane of a batch, lane l's
+// CTAs laid out like its own single-lane grid, its arguments staged from a
+// device table; the single-lane body, so the values are bitwise a
+// single-shot run's.
+template <int K, int V, int TX, int TY, int PF, int CK>
+__global__ void __launch_bounds__(TX * TY, fwd4_min_blocks<K, V, PF>())
+    fwd4_batch_kernel(const FwdArgs* __restrict__ tab, const int* __restrict__ start, int nl)
+{
+    using G = G3<K, V, TX, TY>;
+    extern __shared__ __align__(16) float smem4[];
+    __shared__ __align__(16) FwdArgs a;
+    const int b = stage_args(a, tab, start, nl);
+    const int gx = (a.g.nx + G::BXP - 1) / G::BXP;
+    const int gy = (a.g.ny + TY - 1) / TY;
+    fwd4_body<K, V, TX, TY, PF, CK>(a, smem4, b % gx, (b / gx) % gy, b / (gx * gy), gx, gy);
+}
+
+template <int K, int V, int TX, int TY, int PF, int CK>
+cudaError_t fwd4b_ck(const BatchLaunch<FwdArgs>& b, cudaStream_t s)
+{
+    const size_t sh = G4<K, V, TX, TY, PF>::FLOATS * sizeof(float);
+    cudaError_t e = cudaFuncSetAttribute(fwd4_batch_kernel<K, V, TX, TY, PF, CK>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh);
+    if (e != cudaSuccess) return e;
+    fwd4_batch_kernel<K, V, TX, TY, PF, CK><<<dim3((unsigned)b.blocks), dim3(TX, TY), sh, s>>>(b.tab, b.start,
+                                                                                               b.lanes);
+    return cudaGetLastError();
+}
+
+template <int K, int V, int TX, int TY, int PF>
+cudaError_t fwd4b_go(const BatchLaunch<FwdArgs>& b, int ck, cudaStream_t s)
+{
+    switch (ck) {
+    case CK_NONE: return fwd4b_ck<K, V, TX, TY, PF, CK_NONE>(b, s);
+    case CK_FP32: return fwd4b_ck<K, V, TX, TY, PF, CK_FP32>(b, s);
+    case CK_BF16: return fwd4b_ck<K, V, TX, TY, PF, CK_BF16>(b, s);
+    case CK_FP16: return fwd4b_ck<K, V, TX, TY, PF, CK_FP16>(b, s);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+template <int K>
+cudaError_t fwd4b_k(const BatchLaunch<FwdArgs>& b, const Tile& t, int ck, cudaStream_t s)
+{
+    if (t.vec == 4 && t.bx == 32 && t.by == 16 && t.pf == 1) return fwd4b_go<K, 4, 8, 16, 1>(b, ck, s);
+    if (t.vec == 4 && t.bx == 32 && t.by == 16) return fwd4b_go<K, 4, 8, 16, 2>(b, ck, s);
+    return cudaErrorInvalidValue;
+}
+
 }  // namespace
+
+cudaError_t launch_fwd4_batch(const BatchLaunch<FwdArgs>& b, const Tile& t, int K, int ck, cudaStream_t s)
+{
+    if (b.dims != 3 || b.lanes < 1 || b.blocks < 1 || b.blocks > 0x7fffffffLL || !v4_supported(3, K, t) || t.vec != 4)
+        return cudaErrorInvalidValue;
+    switch (K) {
+    case 1: return fwd4b_k<1>(b, t, ck, s);
+    case 2: return fwd4b_k<2>(b, t, ck, s);
+    case 4: return fwd4b_k<4>(b, t, ck, s);
+    case 8: return fwd4b_k<8>(b, t, ck, s);
+    default: return cudaErrorInvalidValue;
+    }
+}
 
 bool v4_supported(int dims, int K, const Tile& t)
 {

@@ -237,13 +237,12 @@ __device__ __forceinline__ void fwd5_plane(const FwdArgs& a, const float (&q)[NQ
 }
 
 template <int K, int NP, int CK>
-__device__ __forceinline__ void fwd5_body(const FwdArgs& a, float* smem)
+__device__ __forceinline__ void fwd5_body(const FwdArgs& a, float* smem, int bxi, int byi, int bzi, int gxn, int gyn)
 {
     using H = G5<K, NP>;
     using G = typename H::G;
     constexpr int NQ = 2 * K + NP;
     const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TX5 + tx;
-    const int bxi = blockIdx.x, byi = blockIdx.y, bzi = blockIdx.z;
     const int nz = a.g.nz, ny = a.g.ny, nx = a.g.nx;
     const int px = (int)a.g.px;
     const long long pxy = a.g.pxy;
@@ -252,7 +251,7 @@ __device__ __forceinline__ void fwd5_body(const FwdArgs& a, float* smem)
     const int y = yb + ty;
 
     if (a.smp.n > 0) {   // receiver sampling of u^n by the first threads of the grid
-        const int gt = ((bzi * gridDim.y + byi) * gridDim.x + bxi) * H::NT + tid;
+        const int gt = ((bzi * gyn + byi) * gxn + bxi) * H::NT + tid;
         if (gt < a.smp.n) {
             float acc = 0.0f;
             for (int i = 0; i < a.smp.nst; ++i)
@@ -368,7 +367,7 @@ template <int K, int NP, int CK>
 __global__ void __launch_bounds__(TX5 * TY5, fwd5_min_blocks<K, NP>()) fwd5_kernel(const FwdArgs a)
 {
     extern __shared__ __align__(16) float smem5[];
-    fwd5_body<K, NP, CK>(a, smem5);
+    fwd5_body<K, NP, CK>(a, smem5, blockIdx.x, blockIdx.y, blockIdx.z, gridDim.x, gridDim.y);
 }
 
 template <int K, int NP>
@@ -463,7 +462,7 @@ __device__ __forceinline__ void adj5_plane(const AdjArgs& a, const float (&ql)[N
 }
 
 template <int K, int NP>
-__device__ __forceinline__ void adj5_body(const AdjArgs& a, float* smem)
+__device__ __forceinline__ void adj5_body(const AdjArgs& a, float* smem, int bxi, int byi, int bzi)
 {
     using H = G5<K, NP>;
     using G = typename H::G;
@@ -472,10 +471,10 @@ __device__ __forceinline__ void adj5_body(const AdjArgs& a, float* smem)
     const int nz = a.g.nz, ny = a.g.ny, nx = a.g.nx;
     const int px = (int)a.g.px;
     const long long pxy = a.g.pxy;
-    const int xb = blockIdx.x * G::BXP, yb = blockIdx.y * TY5;
+    const int xb = bxi * G::BXP, yb = byi * TY5;
     const int x0 = xb + V5 * tx;
     const int y = yb + ty;
-    const int z0 = blockIdx.z * a.zlen;
+    const int z0 = bzi * a.zlen;
     if (z0 >= nz) return;
     const int z1 = min(z0 + a.zlen, nz);
     const bool rowact = y < ny;
@@ -604,7 +603,7 @@ template <int K, int NP>
 __global__ void __launch_bounds__(TX5 * TY5, adj5_min_blocks<K, NP>()) adj5_kernel(const AdjArgs a)
 {
     extern __shared__ __align__(16) float smem5[];
-    adj5_body<K, NP>(a, smem5);
+    adj5_body<K, NP>(a, smem5, blockIdx.x, blockIdx.y, blockIdx.z);
 }
 
 template <int K, int NP>
@@ -628,6 +627,71 @@ cudaError_t adj5_k(const AdjArgs& a, const Tile& t, cudaStream_t s)
 {
     if (t.pf == 2) return adj5_go<K, 2>(a, s);
     return adj5_go<K, 1>(a, s);
+}
+
+// ------------------------------------------------------------- batches
+// One launch advances every lane of a batch: lane l's CTAs are laid out
+// like its own single-lane grid (x fastest, then y, then z runs) and its
+// arguments are staged from a device table (the single-lane bodies above,
+// so every lane's values are bitwise a single-shot run's).
+template <int K, int NP>
+__global__ void __launch_bounds__(TX5 * TY5, adj5_min_blocks<K, NP>())
+    adj5_batch_kernel(const AdjArgs* __restrict__ tab, const int* __restrict__ start, int nl)
+{
+    using G = typename G5<K, NP>::G;
+    extern __shared__ __align__(16) float smem5[];
+    __shared__ __align__(16) AdjArgs a;
+    const int b = stage_args(a, tab, start, nl);
+    const int gx = (a.g.nx + G::BXP - 1) / G::BXP;
+    const int gy = (a.g.ny + TY5 - 1) / TY5;
+    adj5_body<K, NP>(a, smem5, b % gx, (b / gx) % gy, b / (gx * gy));
+}
+
+template <int K, int NP, int CK>
+__global__ void __launch_bounds__(TX5 * TY5, fwd5_min_blocks<K, NP>())
+    fwd5_batch_kernel(const FwdArgs* __restrict__ tab, const int* __restrict__ start, int nl)
+{
+    using G = typename G5<K, NP>::G;
+    extern __shared__ __align__(16) float smem5[];
+    __shared__ __align__(16) FwdArgs a;
+    const int b = stage_args(a, tab, start, nl);
+    const int gx = (a.g.nx + G::BXP - 1) / G::BXP;
+    const int gy = (a.g.ny + TY5 - 1) / TY5;
+    fwd5_body<K, NP, CK>(a, smem5, b % gx, (b / gx) % gy, b / (gx * gy), gx, gy);
+}
+
+template <int K, int NP>
+cudaError_t adj5b_go(const BatchLaunch<AdjArgs>& b, cudaStream_t s)
+{
+    const size_t sh = adj5_smem<K, NP>();
+    cudaError_t e = cudaFuncSetAttribute(adj5_batch_kernel<K, NP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)sh);
+    if (e != cudaSuccess) return e;
+    adj5_batch_kernel<K, NP><<<dim3((unsigned)b.blocks), dim3(TX5, TY5), sh, s>>>(b.tab, b.start, b.lanes);
+    return cudaGetLastError();
+}
+
+template <int K, int NP, int CK>
+cudaError_t fwd5b_ck(const BatchLaunch<FwdArgs>& b, cudaStream_t s)
+{
+    const size_t sh = fwd5_smem<K, NP>();
+    cudaError_t e = cudaFuncSetAttribute(fwd5_batch_kernel<K, NP, CK>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)sh);
+    if (e != cudaSuccess) return e;
+    fwd5_batch_kernel<K, NP, CK><<<dim3((unsigned)b.blocks), dim3(TX5, TY5), sh, s>>>(b.tab, b.start, b.lanes);
+    return cudaGetLastError();
+}
+
+template <int K, int NP>
+cudaError_t fwd5b_go(const BatchLaunch<FwdArgs>& b, int ck, cudaStream_t s)
+{
+    switch (ck) {
+    case CK_NONE: return fwd5b_ck<K, NP, CK_NONE>(b, s);
+    case CK_FP32: return fwd5b_ck<K, NP, CK_FP32>(b, s);
+    case CK_BF16: return fwd5b_ck<K, NP, CK_BF16>(b, s);
+    case CK_FP16: return fwd5b_ck<K, NP, CK_FP16>(b, s);
+    default: return cudaErrorInvalidValue;
+    }
 }
 
 }  // namespace
@@ -675,6 +739,45 @@ cudaError_t launch_adj5(const AdjArgs& a, const Tile& t, int K, int ut, cudaStre
     case 2: return adj5_k<2>(b, t, s);
     case 4: return adj5_k<4>(b, t, s);
     case 8: return adj5_k<8>(b, t, s);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace ckfwi
+
+namespace ckfwi {
+
+cudaError_t launch_fwd5_batch(const BatchLaunch<FwdArgs>& b, const Tile& t, int K, int ck, cudaStream_t s)
+{
+    if (b.dims != 3 || b.lanes < 1 || b.blocks < 1 || b.blocks > 0x7fffffffLL || !v5_supported(3, K, t))
+        return cudaErrorInvalidValue;
+    const bool two = t.pf == 2;
+    switch (K) {
+    case 1: return two ? fwd5b_go<1, 2>(b, ck, s) : fwd5b_go<1, 1>(b, ck, s);
+    case 2: return two ? fwd5b_go<2, 2>(b, ck, s) : fwd5b_go<2, 1>(b, ck, s);
+    case 4: return two ? fwd5b_go<4, 2>(b, ck, s) : fwd5b_go<4, 1>(b, ck, s);
+    case 8: return two ? fwd5b_go<8, 2>(b, ck, s) : fwd5b_go<8, 1>(b, ck, s);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+// FP32 u^{j-1} only (16-bit batches read through the vector-blocked kernel)
+cudaError_t launch_adj5_batch(const BatchLaunch<AdjArgs>& b, const Tile& t, int K, int ut, cudaStream_t s)
+{
+    if (b.dims != 3 || b.lanes < 1 || b.blocks < 1 || b.blocks > 0x7fffffffLL || !v5_supported(3, K, t))
+        return cudaErrorInvalidValue;
+    if (ut != U_FP32) {
+        Tile t3 = t;
+        t3.ver = 3;
+        t3.pf = 0;
+        return launch_adj3_batch(b, t3, K, ut, s);
+    }
+    const bool two = t.pf == 2;
+    switch (K) {
+    case 1: return two ? adj5b_go<1, 2>(b, s) : adj5b_go<1, 1>(b, s);
+    case 2: return two ? adj5b_go<2, 2>(b, s) : adj5b_go<2, 1>(b, s);
+    case 4: return two ? adj5b_go<4, 2>(b, s) : adj5b_go<4, 1>(b, s);
+    case 8: return two ? adj5b_go<8, 2>(b, s) : adj5b_go<8, 1>(b, s);
     default: return cudaErrorInvalidValue;
     }
 }

@@ -112,6 +112,30 @@ def test_batch_equals_single_shots(monkeypatch, dims, so, shape, nbl, nt, nshots
     assert np.array_equal(g2.cpu().numpy(), got) and phi2 == phi_b
 
 
+@pytest.mark.parametrize("ver", [4, 7])
+@pytest.mark.parametrize("dims,so,shape,nbl,nt,nshots,lanes,M,mode",
+                         [c for c in BATCH_CASES if c[0] == 3] + [(3, 8, (29, 35, 38), 6, 60, 3, 64, 5, "fp16")])
+def test_batch_async_copy_generations_equal_single_shots(monkeypatch, ver, dims, so, shape, nbl, nt, nshots, lanes,
+                                                         M, mode):
+    """The batched async-copy forward step (generation 4) and the batched lean
+    forward and reverse steps (generation 7), forced by CKFWI_BATCH_VER."""
+    monkeypatch.setenv("CKFWI_MAX_LANES", str(lanes))
+    monkeypatch.setenv("CKFWI_BATCH_VER", str(ver))
+    case = make_case(dims, so, shape, nbl, nt, seed=7 * dims + so + ver)
+    m = C.Model(case.pg)
+    m.set_model(torch.from_numpy(case.vel).cuda())
+    shots = _shots(case, nshots, seed=so)
+    d_obs = _observed(m, shots)
+    tol = 1e-5 if mode == "codec" else 0.0
+    grads, phis = _singles(m, shots, d_obs, M, mode, tol)
+    phi_b, gsum, st = m.batch_gradient(shots, d_obs, M, store_mode=mode, tol=tol, use_graph=True, profile=False)
+    _, _, sp = m.batch_gradient(shots, d_obs, M, store_mode=mode, tol=tol, profile=True)
+    assert sp["fwd_ver"] == ver
+    ref = _neumaier(grads)
+    assert np.array_equal(gsum.cpu().numpy(), ref)
+    assert phi_b == _misfit_sum(phis)
+
+
 def test_batch_launch_count(monkeypatch):
     """All lanes of a batch share each stencil launch."""
     monkeypatch.setenv("CKFWI_MAX_LANES", "4")

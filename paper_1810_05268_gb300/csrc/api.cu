@@ -1859,14 +1859,11 @@ int batch_tune(const std::vector<ckfwi_model*>& lanes, cudaStream_t st, const Ba
             if (v5_supported(dims, K, t7)) shapes.push_back(t7);
         }
     }
-    // CKFWI_BATCH_VER restricts the candidates to one generation (tests)
-    if (const char* bv = std::getenv("CKFWI_BATCH_VER")) {
-        const int want = std::atoi(bv);
-        std::vector<Tile> keep;
-        for (const Tile& t : shapes)
-            if (t.ver == want) keep.push_back(t);
-        if (!keep.empty()) shapes = keep;
-    }
+    // CKFWI_BATCH_VER restricts the timed candidates to one generation
+    // (tests); generation 4 has no batched reverse step, which then takes
+    // the vector-blocked kernels
+    const char* bv = std::getenv("CKFWI_BATCH_VER");
+    const int want = bv ? std::atoi(bv) : 0;
     for (const Tile& t : shapes) {
         long long cols = 0;
         int nzmax = 1;
@@ -1937,6 +1934,7 @@ int batch_tune(const std::vector<ckfwi_model*>& lanes, cudaStream_t st, const Ba
         }
         for (int pass = 0; pass < 2 && rs == CKFWI_OK; ++pass) {
             if (pass == 1 && c.t.ver == 4) continue;    // generation 4 has no batched reverse step
+            if (want && c.t.ver != want && !(want == 4 && pass == 1 && c.t.ver == 3)) continue;
             auto go = [&]() {
                 const BatchLaunch<FwdArgs> bf{ftab, dst.as<int>(), NL, dims, total};
                 const BatchLaunch<AdjArgs> ba{atab, dst.as<int>(), NL, dims, total};

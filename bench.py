@@ -754,16 +754,19 @@ def sweep_c4(C, torch, synth, args):
         except C.CkfwiError as e:
             out["modes"][name] = {"skipped": str(e)}
             continue
+        nsh = len(shots)
+        steps = st["fwd_steps"] / nsh            # the stats count every lane's steps
         row = {"seconds": t, "gpts": 2.0 * nt * npts / t / 1e9, "misfit": phi,
                "fwd_launches": sp["fwd_launches"], "adj_launches": sp["adj_launches"],
-               "recompute_ratio": st["fwd_steps"] / nt}
+               "recompute_ratio": steps / nt, "u_absmax": st["u_absmax"]}
         # the batched kernels' aggregate algorithmic bandwidth: every lane's
         # forward steps move 16 B a point, reverse steps 28 B
         if sp["fwd_ms"] > 0:
-            row["fwd_gbs"] = FWD_BYTES * npts * (st["fwd_steps"]) / (sp["fwd_ms"] / 1e3) / 1e9
+            row["fwd_gbs"] = FWD_BYTES * npts * steps / (sp["fwd_ms"] / 1e3) / 1e9
         if sp["adj_ms"] > 0:
             row["adj_gbs"] = ADJ_BYTES * npts * nt / (sp["adj_ms"] / 1e3) / 1e9
-        row["fwd_kernel"] = [sp["fwd_ver"], sp["fwd_bx"], sp["fwd_by"], sp["fwd_vec"], sp["fwd_zlen"]]
+        row["fwd_kernel"] = [sp["fwd_ver"], sp["fwd_bx"], sp["fwd_by"], sp["fwd_vec"], sp["fwd_zlen"], sp["fwd_pf"]]
+        row["adj_kernel"] = [sp["adj_ver"], sp["adj_bx"], sp["adj_by"], sp["adj_vec"], sp["adj_zlen"], sp["adj_pf"]]
         if kw["store_mode"] == "codec":
             row.update(F_mean=st["ratio_mean"], F_min=st["ratio_min"])
         out["modes"][name] = row

@@ -167,8 +167,8 @@ typedef struct ckfwi_stats {
                                 reduction at the end of the first sweep: the
                                 wavefield's scale, against which an absolute
                                 codec tolerance (Sec. 2.2) can be read as
-                                tol / max|u|.  Batches: the largest over the
-                                lanes of the last batch. */
+                                tol / max|u|.  Batches: the largest over all
+                                shots. */
     /* with opts->profile: device time [ms] and launches per kernel class */
     double fwd_ms, adj_ms, comp_ms, decomp_ms, other_ms;
     long long fwd_launches, adj_launches, comp_calls, decomp_calls;

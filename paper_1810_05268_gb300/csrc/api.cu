@@ -826,7 +826,9 @@ int fwd_step(Ctx& cx, const Role& u, const Role& up, const Role& out, int n, boo
             continue;
         }
         const int tok = cx.begin(PC_FWD);
-        if (m->tf.ver == 7) {
+        if (m->tf.ver == 8) {
+            CK_TRY(launch_fwd6(a, m->tf, m->K, ck, cx.st));
+        } else if (m->tf.ver == 7) {
             CK_TRY(launch_fwd5(a, m->tf, m->K, ck, cx.st));
         } else if (m->tf.ver >= 5) {
             ST_TRY(ot4_fwd_step(m, a, m->tf, ck, cx.st));
@@ -1065,6 +1067,9 @@ int autotune(ckfwi_model* m, cudaStream_t st)
                 if (v4_supported(f.dims, m->K, t4)) cands.push_back(t4);
                 t4.pf = 1;                       // one plane of prefetch, six CTAs per SM
                 if (v4_supported(f.dims, m->K, t4)) cands.push_back(t4);
+                Tile t8 = v3_tile_at(i, z);     // the compile-time queue and ring (forward step only)
+                t8.ver = 8;
+                if (v6_supported(f.dims, m->K, t8)) cands.push_back(t8);
                 Tile t7 = v3_tile_at(i, z);     // the lean generation, one or two planes per step
                 t7.ver = 7;
                 for (int np : {1, 2}) {
@@ -1111,7 +1116,10 @@ int autotune(ckfwi_model* m, cudaStream_t st)
     const int reps = 3;
     CUtensorMap tm_u, tm_l;
     auto go = [&](const Tile& t, int pass) -> int {
-        if (t.ver == 7) {
+        if (t.ver == 8) {
+            if (pass == 0) CK_TRY(launch_fwd6(a, t, m->K, CK_NONE, st));
+            else return CKFWI_EINVAL;
+        } else if (t.ver == 7) {
             if (pass == 0) CK_TRY(launch_fwd5(a, t, m->K, CK_NONE, st));
             else CK_TRY(launch_adj5(b, t, m->K, U_FP32, st));
         } else if (t.ver >= 5) {
@@ -1145,7 +1153,8 @@ int autotune(ckfwi_model* m, cudaStream_t st)
         if (nf < 5) u.vec = 1;
         if (nf < 6) u.pf = 0;
         if ((u.ver == 5 || u.ver == 6) != (m->ot == 4)) return false;
-        const bool okv = u.ver == 7   ? v5_supported(f.dims, m->K, u) && v3_fits(f, m->K)
+        const bool okv = u.ver == 8   ? !reverse && v6_supported(f.dims, m->K, u) && v3_fits(f, m->K)
+                         : u.ver == 7 ? v5_supported(f.dims, m->K, u) && v3_fits(f, m->K)
                          : u.ver == 6 ? ot4v_supported(f.dims, m->K, u, reverse) && v3_fits(f, m->K)
                          : u.ver == 5 ? ot4_supported(f.dims, m->K, u)
                          : u.ver == 4 ? v4_supported(f.dims, m->K, u) && v3_fits(f, m->K)
@@ -1187,6 +1196,7 @@ int autotune(ckfwi_model* m, cudaStream_t st)
         for (size_t i = 0; i < cands.size(); ++i) {
             // vector-blocked OT4 reverse steps come in one vector width only
             if (cands[i].ver == 6 && !ot4v_supported(f.dims, m->K, cands[i], pass == 1)) continue;
+            if (cands[i].ver == 8 && pass == 1) continue;      // forward step only
             ST_TRY(go(cands[i], pass));
             float ms = 0;
             ST_TRY(time_of(cands[i], pass, 3, &ms));
@@ -2425,6 +2435,7 @@ int ckfwi_batch_gradient(ckfwi_model* m, const ckfwi_shot* shots, int nshots, co
         acc.decomp_ms += one.decomp_ms;
         acc.other_ms += one.other_ms;
         acc.pool_bytes_peak = std::max(acc.pool_bytes_peak, one.pool_bytes_peak * nb);
+        acc.u_absmax = std::max(acc.u_absmax, one.u_absmax);
         acc.fwd_ver = one.fwd_ver;
         acc.fwd_bx = one.fwd_bx;
         acc.fwd_by = one.fwd_by;

@@ -119,7 +119,7 @@ def test_batch_async_copy_generations_equal_single_shots(monkeypatch, ver, dims,
                                                          M, mode):
     """The batched async-copy forward step (generation 4) and the batched lean
     forward and reverse steps (generation 7), forced by CKFWI_BATCH_VER."""
-    monkeypatch.setenv("CKFWI_MAX_LANES", str(lanes))
+    monkeypatch.setenv("CKFWI_MAX_LANES", "64")          # one batch: its tiles are the stats'
     monkeypatch.setenv("CKFWI_BATCH_VER", str(ver))
     case = make_case(dims, so, shape, nbl, nt, seed=7 * dims + so + ver)
     m = C.Model(case.pg)
@@ -130,7 +130,8 @@ def test_batch_async_copy_generations_equal_single_shots(monkeypatch, ver, dims,
     grads, phis = _singles(m, shots, d_obs, M, mode, tol)
     phi_b, gsum, st = m.batch_gradient(shots, d_obs, M, store_mode=mode, tol=tol, use_graph=True, profile=False)
     _, _, sp = m.batch_gradient(shots, d_obs, M, store_mode=mode, tol=tol, profile=True)
-    assert sp["fwd_ver"] == ver
+    assert sp["fwd_ver"] == ver and sp["adj_ver"] == (7 if ver == 7 else 3)
+    assert sp["u_absmax"] > 0
     ref = _neumaier(grads)
     assert np.array_equal(gsum.cpu().numpy(), ref)
     assert phi_b == _misfit_sum(phis)

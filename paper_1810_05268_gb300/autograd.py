@@ -48,12 +48,14 @@ def misfit(m, model, shots, d_obs_list, ckpt_slots, **opts):
 
 
 def steepest_descent(m0, model, shots, d_obs_list, iterations, ckpt_slots, step=0.05, m_min=None, m_max=None,
-                     backtrack=6, **opts):
+                     backtrack=6, stop_on_stall=False, **opts):
     """Steepest descent m <- clip(m - alpha g / max|g|), starting from
     alpha = step * max|m| and halving alpha until the misfit decreases
     (the paper names steepest descent, Sec. 6; the step rule is this
-    driver's).  Each trial costs one forward-only misfit.  Returns
-    (m, misfit history)."""
+    driver's).  Each trial costs one forward-only misfit.  With
+    stop_on_stall, the iterations end when no trial lowers the misfit (the
+    next iteration would repeat the same search).  Returns (m, misfit
+    history)."""
     m = m0.detach().clone()
     hist = []
     phi_m = None
@@ -76,5 +78,8 @@ def steepest_descent(m0, model, shots, d_obs_list, iterations, ckpt_slots, step=
                     phi_m = phi_t
                     break
                 alpha *= 0.5
+            else:
+                if stop_on_stall:
+                    break
     hist.append(phi_m if phi_m is not None else float(misfit(m, model, shots, d_obs_list, ckpt_slots, **opts)))
     return m, hist

@@ -826,9 +826,7 @@ int fwd_step(Ctx& cx, const Role& u, const Role& up, const Role& out, int n, boo
             continue;
         }
         const int tok = cx.begin(PC_FWD);
-        if (m->tf.ver == 8) {
-            CK_TRY(launch_fwd6(a, m->tf, m->K, ck, cx.st));
-        } else if (m->tf.ver == 7) {
+        if (m->tf.ver == 7) {
             CK_TRY(launch_fwd5(a, m->tf, m->K, ck, cx.st));
         } else if (m->tf.ver >= 5) {
             ST_TRY(ot4_fwd_step(m, a, m->tf, ck, cx.st));
@@ -1067,9 +1065,6 @@ int autotune(ckfwi_model* m, cudaStream_t st)
                 if (v4_supported(f.dims, m->K, t4)) cands.push_back(t4);
                 t4.pf = 1;                       // one plane of prefetch, six CTAs per SM
                 if (v4_supported(f.dims, m->K, t4)) cands.push_back(t4);
-                Tile t8 = v3_tile_at(i, z);     // the compile-time queue and ring (forward step only)
-                t8.ver = 8;
-                if (v6_supported(f.dims, m->K, t8)) cands.push_back(t8);
                 Tile t7 = v3_tile_at(i, z);     // the lean generation, one or two planes per step
                 t7.ver = 7;
                 for (int np : {1, 2}) {
@@ -1116,10 +1111,7 @@ int autotune(ckfwi_model* m, cudaStream_t st)
     const int reps = 3;
     CUtensorMap tm_u, tm_l;
     auto go = [&](const Tile& t, int pass) -> int {
-        if (t.ver == 8) {
-            if (pass == 0) CK_TRY(launch_fwd6(a, t, m->K, CK_NONE, st));
-            else return CKFWI_EINVAL;
-        } else if (t.ver == 7) {
+        if (t.ver == 7) {
             if (pass == 0) CK_TRY(launch_fwd5(a, t, m->K, CK_NONE, st));
             else CK_TRY(launch_adj5(b, t, m->K, U_FP32, st));
         } else if (t.ver >= 5) {
@@ -1153,8 +1145,7 @@ int autotune(ckfwi_model* m, cudaStream_t st)
         if (nf < 5) u.vec = 1;
         if (nf < 6) u.pf = 0;
         if ((u.ver == 5 || u.ver == 6) != (m->ot == 4)) return false;
-        const bool okv = u.ver == 8   ? !reverse && v6_supported(f.dims, m->K, u) && v3_fits(f, m->K)
-                         : u.ver == 7 ? v5_supported(f.dims, m->K, u) && v3_fits(f, m->K)
+        const bool okv = u.ver == 7   ? v5_supported(f.dims, m->K, u) && v3_fits(f, m->K)
                          : u.ver == 6 ? ot4v_supported(f.dims, m->K, u, reverse) && v3_fits(f, m->K)
                          : u.ver == 5 ? ot4_supported(f.dims, m->K, u)
                          : u.ver == 4 ? v4_supported(f.dims, m->K, u) && v3_fits(f, m->K)
@@ -1196,7 +1187,6 @@ int autotune(ckfwi_model* m, cudaStream_t st)
         for (size_t i = 0; i < cands.size(); ++i) {
             // vector-blocked OT4 reverse steps come in one vector width only
             if (cands[i].ver == 6 && !ot4v_supported(f.dims, m->K, cands[i], pass == 1)) continue;
-            if (cands[i].ver == 8 && pass == 1) continue;      // forward step only
             ST_TRY(go(cands[i], pass));
             float ms = 0;
             ST_TRY(time_of(cands[i], pass, 3, &ms));
@@ -1860,7 +1850,7 @@ int batch_tune(const std::vector<ckfwi_model*>& lanes, cudaStream_t st, const Ba
         if (t.vec != 4) continue;
         Tile t4 = t;                     // fed by asynchronous copies (forward step only)
         t4.ver = 4;
-        t4.pf = 1;
+        t4.pf = K <= 4 ? 1 : 2;
         if (v4_supported(dims, K, t4)) shapes.push_back(t4);
         Tile t7 = t;                     // the lean generation, one or two planes per step
         t7.ver = 7;

@@ -137,8 +137,7 @@ struct Tile {
                           // 3: vector-blocked kernels (3D), 4: vector-blocked forward step fed
                           // by asynchronous copies (3D), 5: the two-pass OT4 kernels,
                           // 6: the same vector-blocked (3D), 7: the lean async-copy
-                          // OT2 kernels (3D, one or two planes per step), 8: the OT2
-                          // forward step with a compile-time z queue and ring (3D)
+                          // OT2 kernels (3D, one or two planes per step)
     int vec = 1;          // ver 3, 4: x points per thread (2 or 4)
     int pf = 0;           // ver 4: planes of prefetch (0 = the default, 2); ver 7: planes per step (1, 2)
 };
@@ -180,9 +179,6 @@ cudaError_t launch_adj4(const AdjArgs& a, const Tile& t, int K, int ut, cudaStre
 bool v5_supported(int dims, int K, const Tile& t);
 cudaError_t launch_fwd5(const FwdArgs& a, const Tile& t, int K, int ck, cudaStream_t s);
 cudaError_t launch_adj5(const AdjArgs& a, const Tile& t, int K, int ut, cudaStream_t s);
-// stencil_v6.cu: the forward step with a compile-time queue and ring (Tile.ver 8, orders 2-8)
-bool v6_supported(int dims, int K, const Tile& t);
-cudaError_t launch_fwd6(const FwdArgs& a, const Tile& t, int K, int ck, cudaStream_t s);
 // batched forms of generations 4 and 7 (every lane's geometry must pass v3_fits)
 cudaError_t launch_fwd4_batch(const BatchLaunch<FwdArgs>& b, const Tile& t, int K, int ck, cudaStream_t s);
 cudaError_t launch_fwd5_batch(const BatchLaunch<FwdArgs>& b, const Tile& t, int K, int ck, cudaStream_t s);

@@ -172,24 +172,3 @@ def test_tma_wait_that_runs_out_reports_timeout():
     ref = _run(case, "1,32,8,9", "1,32,8,9", torch.zeros((41, case.rec.shape[0]), device="cuda"), 5)
     got = _run(case, "2,64,16,2", "2,64,16,2", torch.zeros((41, case.rec.shape[0]), device="cuda"), 5)
     assert np.array_equal(got[0], ref[0])
-
-
-@pytest.mark.parametrize("so,shape", [(2, (30, 37, 70)), (4, (33, 41, 131)), (8, (35, 43, 70)), (8, (26, 29, 200)),
-                                      (4, (21, 19, 13)), (8, (50, 44, 64))])
-@pytest.mark.parametrize("mode", ["fp32", "fp16", "bf16"])
-def test_compile_time_ring_forward_bitwise_equal_register_queue(so, shape, mode):
-    """The forward step with a compile-time z queue and ring (Tile.ver 8):
-    z runs shorter than, equal to, longer than and not a multiple of the
-    unrolled round of 2K+1 planes, and a run covering the whole column."""
-    case = make_case(3, so, shape, nbl=6, nt=70, seed=so + 11)
-    rng = np.random.default_rng(so + 2)
-    dobs = torch.from_numpy((rng.standard_normal((71, case.rec.shape[0])) * 1e-3).astype(np.float32)).cuda()
-    k = so // 2
-    by1 = max(8, k)
-    ref = _run(case, "1,32,%d,9" % by1, "1,32,%d,9" % by1, dobs, 5, mode)
-    nq = 2 * k + 1
-    for z in sorted({3, nq, nq + 4, 2 * nq, 64}):
-        got = _run(case, "8,32,16,%d,4" % z, "7,32,16,%d,4,1" % z, dobs, 5, mode)
-        assert np.array_equal(got[0], ref[0]), z
-        assert got[1] == ref[1], z
-        assert np.array_equal(got[2], ref[2]), z

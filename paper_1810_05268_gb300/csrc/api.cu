@@ -372,10 +372,22 @@ struct ckfwi_model {
     std::vector<BatchKey> bgraph_order;
     DevMem btabs;                   // batch argument tables of an unrecorded run
     DevMem hostgrad;                // device staging of a gradient returned to host memory
+    // FP32 slots in host memory, staged: a checkpoint goes to one of three
+    // device staging pairs (hstage, used in turn, so the pair a step writes is
+    // never one the step reads) in the step that makes it and is copied to
+    // its host slot on the copy stream `side`, overlapped with the next
+    // steps; a restore copies the slot into a device pair (hrest)
+    DevMem hstage[3][2], hrest[2];
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_done[3] = {nullptr, nullptr, nullptr};
     ~ckfwi_model()
     {
         graphs.clear();
         bgraphs.clear();
+        if (side) cudaStreamDestroy(side);
+        if (ev_fork) cudaEventDestroy(ev_fork);
+        for (cudaEvent_t e : ev_done)
+            if (e) cudaEventDestroy(e);
         if (cap) cudaStreamDestroy(cap);
         if (ev) cudaEventDestroy(ev);
         for (cudaEvent_t e : evpool) cudaEventDestroy(e);
@@ -578,7 +590,7 @@ struct Prof {
 // The buffers a schedule step reads and writes.  Every lane (shot) of a
 // batch runs the same schedule, so a step names roles, and each lane
 // resolves them to its own buffers.
-enum RoleKind { R_NONE, R_ZERO, R_WORK, R_LAM, R_UN, R_TRAJ, R_SLOT };
+enum RoleKind { R_NONE, R_ZERO, R_WORK, R_LAM, R_UN, R_TRAJ, R_SLOT, R_HSTAGE, R_HREST };
 struct Role {
     int kind = R_NONE;
     int idx = 0;      // work / lam index, trajectory level, or slot (>= 1)
@@ -593,6 +605,8 @@ Role work_r(int i) { return Role{R_WORK, i, 0}; }
 Role lam_r(int i) { return Role{R_LAM, i, 0}; }
 Role traj_r(int n) { return Role{R_TRAJ, n, 0}; }
 Role slot_r(int s, int w) { return Role{R_SLOT, s, w}; }
+Role hstage_r(int k, int w) { return Role{R_HSTAGE, k, w}; }
+Role hrest_r(int w) { return Role{R_HREST, 0, w}; }
 
 void* rptr(ckfwi_model* m, int mode, const Role& r)
 {
@@ -603,6 +617,8 @@ void* rptr(ckfwi_model* m, int mode, const Role& r)
     case R_LAM: return org(m->lam[r.idx], f);
     case R_UN: return org(m->uN, f);
     case R_TRAJ: return m->traj.as<float>() + (size_t)r.idx * f.alloc + f.origin;
+    case R_HSTAGE: return org(m->hstage[r.idx][r.which], f);
+    case R_HREST: return org(m->hrest[r.which], f);
     case R_SLOT: {
         // uncompressed slots: two padded fields per slot, FP32 or 16-bit;
         // slots 1 .. host_slots in host memory, the rest in device memory
@@ -623,6 +639,9 @@ struct Ctx {
     Prof prof;
     long long count[PC_N] = {0, 0, 0, 0, 0};
     int mode = CKFWI_STORE_FP32;    // storage mode R_SLOT roles resolve for
+    bool stage = false;             // FP32 host slots go through the device staging pairs
+    bool pend[3] = {false, false, false};  // a copy from staging pair k to a host slot is in flight
+    int sk = 0;                     // the staging pair the next host checkpoint takes
     // batch: every stencil step is one launch over all lanes
     std::vector<ckfwi_model*> lanes;   // empty: the model alone
     bool batch = false;
@@ -1347,9 +1366,19 @@ int run_body(Ctx& cx, const RunCfg& rc, const std::vector<Action>& acts, long lo
                 int ck = CK_NONE;
                 Role cku = NONE_R, ckup = NONE_R;
                 Role out = pick_free(st);
+                int staged = -1;             // staging pair of a host-slot checkpoint
                 if (last && next_take && !rc.codec) {
                     const int slot = acts[ai + 1].b;
-                    if (rc.mode == CKFWI_STORE_FP32) {
+                    if (rc.mode == CKFWI_STORE_FP32 && cx.stage && slot <= cx.m->host_slots) {
+                        // into a device staging pair, copied to the host slot below
+                        staged = cx.sk;
+                        cx.sk = (cx.sk + 1) % 3;
+                        if (cx.pend[staged]) CK_TRY(cudaStreamWaitEvent(cx.st, cx.m->ev_done[staged], 0));
+                        cx.pend[staged] = false;
+                        out = hstage_r(staged, 0);
+                        ck = CK_FP32;
+                        ckup = hstage_r(staged, 1);
+                    } else if (rc.mode == CKFWI_STORE_FP32) {
                         out = slot_r(slot, 0);   // u^{n+1} straight into the slot
                         ck = CK_FP32;
                         ckup = slot_r(slot, 1);
@@ -1361,6 +1390,18 @@ int run_body(Ctx& cx, const RunCfg& rc, const std::vector<Action>& acts, long lo
                 }
                 ST_TRY(fwd_step(cx, st.cur, st.prev, out, n, first_sweep, ck, cku, ckup));
                 ++fsteps;
+                if (staged >= 0) {
+                    // the pair to its host slot on the copy stream, overlapped with the next steps
+                    ckfwi_model* m = cx.m;
+                    const size_t fb = field_bytes(m->fg);
+                    char* hs = static_cast<char*>(m->hpool.p) + (size_t)(acts[ai + 1].b - 1) * 2 * fb;
+                    CK_TRY(cudaEventRecord(m->ev_fork, cx.st));
+                    CK_TRY(cudaStreamWaitEvent(m->side, m->ev_fork, 0));
+                    for (int w = 0; w < 2; ++w)
+                        CK_TRY(cudaMemcpyAsync(hs + w * fb, m->hstage[staged][w].p, fb, cudaMemcpyDefault, m->side));
+                    CK_TRY(cudaEventRecord(m->ev_done[staged], m->side));
+                    cx.pend[staged] = true;
+                }
                 st.prev = st.cur;
                 st.tprev = st.tcur;
                 st.cur = out;
@@ -1399,6 +1440,21 @@ int run_body(Ctx& cx, const RunCfg& rc, const std::vector<Action>& acts, long lo
         } else if (A.op == ACT_RESTORE) {
             if (A.b == 0) {
                 st = State{ZERO_R, ZERO_R, U_FP32, U_FP32};
+            } else if (rc.mode == CKFWI_STORE_FP32 && cx.stage && A.b <= cx.m->host_slots) {
+                // a host slot: its copy finished (every pending one is waited
+                // for), then copied into the restore pair (u^s only before a
+                // reverse step)
+                ckfwi_model* m = cx.m;
+                for (int k = 0; k < 3; ++k)
+                    if (cx.pend[k]) {
+                        CK_TRY(cudaStreamWaitEvent(cx.st, m->ev_done[k], 0));
+                        cx.pend[k] = false;
+                    }
+                const size_t fb = field_bytes(m->fg);
+                const char* hs = static_cast<const char*>(m->hpool.p) + (size_t)(A.b - 1) * 2 * fb;
+                for (int w = 0; w < (next_turn ? 1 : 2); ++w)
+                    CK_TRY(cudaMemcpyAsync(m->hrest[w].p, hs + w * fb, fb, cudaMemcpyDefault, cx.st));
+                st = State{hrest_r(0), hrest_r(1), U_FP32, U_FP32};
             } else if (rc.mode == CKFWI_STORE_FP32) {
                 st = State{slot_r(A.b, 0), slot_r(A.b, 1), U_FP32, U_FP32};   // the slot is the state
             } else if (rc.codec) {
@@ -1473,6 +1529,12 @@ int run_body(Ctx& cx, const RunCfg& rc, const std::vector<Action>& acts, long lo
             ST_TRY(reverse(A.a, st.cur, st.tcur));
         }
     }
+    // join the copy stream: no checkpoint copy outlives the gradient
+    for (int k = 0; k < 3; ++k)
+        if (cx.pend[k]) {
+            CK_TRY(cudaStreamWaitEvent(cx.st, cx.m->ev_done[k], 0));
+            cx.pend[k] = false;
+        }
     counters[0] = fsteps;
     counters[1] = ncomp;
     return CKFWI_OK;
@@ -1539,6 +1601,16 @@ int prepare_storage(ckfwi_model* m, const RunCfg& rc, const ckfwi_grad_opts* o)
         }
         m->host_slots = hs;
         m->pool_tag = tag;
+        if (hs > 0 && tag == 4) {
+            // the staging pairs and the copy stream of FP32 host slots
+            for (int k = 0; k < 3; ++k)
+                for (int w = 0; w < 2; ++w) CK_TRY(m->hstage[k][w].alloc(field_bytes(f)));
+            for (int w = 0; w < 2; ++w) CK_TRY(m->hrest[w].alloc(field_bytes(f)));
+            if (!m->side) CK_TRY(cudaStreamCreateWithFlags(&m->side, cudaStreamNonBlocking));
+            if (!m->ev_fork) CK_TRY(cudaEventCreateWithFlags(&m->ev_fork, cudaEventDisableTiming));
+            for (int k = 0; k < 3; ++k)
+                if (!m->ev_done[k]) CK_TRY(cudaEventCreateWithFlags(&m->ev_done[k], cudaEventDisableTiming));
+        }
     } else {
         m->pool_tag = 0;
         size_t bytes = o->pool_bytes ? o->pool_bytes : (size_t)(rc.M - 1) * 2 * f.npts * 4;
@@ -1708,6 +1780,7 @@ int gradient_one(ckfwi_model* m, const ckfwi_shot* s, const float* d_obs, int me
     if (!rc.store_all) revolve_schedule(rc.N, rc.M, acts, cnt);
     Ctx cx{m, st, 0};
     cx.mode = rc.mode;
+    cx.stage = rc.mode == CKFWI_STORE_FP32 && !rc.codec && !rc.store_all && m->host_slots > 0 && m->side;
     long long counters[2] = {0, 0};
     const bool graph = o->use_graph != 0 && !o->profile;
     if (o->profile) {

@@ -971,7 +971,7 @@ def main():
                     help="side file for everything but the headline")
     ap.add_argument("--modes",
                     default="storeall,codec,codec_sched,rate,fp32,fp16,bf16,codec_low,rate_low,"
-                            "fp32_low,fp16_low,fp32_host,ot4,batch2d")
+                            "fp32_low,fp16_low,fp32_host,fp32_eq,ot4,batch2d")
     ap.add_argument("--oracle-sample", default=None, help=argparse.SUPPRESS)
     ap.add_argument("--sweep", default=None, choices=["c3", "c4", "c5"],
                     help="instead of the headline: the 300x600x600 budget sweep, the batched apertures, or the "
@@ -1056,6 +1056,9 @@ def main():
     # a second storage level: the device budget plus HOST_SLOTS slots in pinned host memory
     if "fp32_host" in want:
         modes["fp32_host"] = dict(ckpt_slots=BUDGET_SLOTS + HOST_SLOTS, store_mode="fp32", host_slots=HOST_SLOTS)
+    # the same slot count all in device memory: what the second level costs
+    if "fp32_eq" in want:
+        modes["fp32_eq"] = dict(ckpt_slots=BUDGET_SLOTS + HOST_SLOTS, store_mode="fp32")
 
     # the headline's candidates are timed over K replays, the rest over min(K, 5)
     cands = ("codec", "rate", "fp32", "fp16", "bf16")

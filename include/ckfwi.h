@@ -200,14 +200,16 @@ CKFWI_API int ckfwi_create_model(const ckfwi_grid* g, ckfwi_model** out);
 CKFWI_API int ckfwi_set_model(ckfwi_model* m, const float* data, int kind, int mem, void* stream);
 
 /* Forward modelling of one shot (Sec. 6, the forward problem): writes
- * d_sim [nt+1][nrec] float32 (row 0 = P u^0 = 0).  EINVAL for a source or
- * receiver outside the grid or nrec < 1. */
+ * d_sim [nt+1][nrec] float32 (row 0 = P u^0 = 0).  Synchronous: it reads
+ * the kernels' error flags at the end (TIMEOUT when a TMA kernel's bounded
+ * wait ran out).  EINVAL for a source or receiver outside the grid or
+ * nrec < 1. */
 CKFWI_API int ckfwi_forward_shot(ckfwi_model* m, const ckfwi_shot* s, float* d_sim, int mem, void* stream);
 
 /* Misfit of one shot without its gradient (Sec. 6): forward modelling, the
  * residual and phi = 1/2 sum_{n=1..N} ||d^n - d_obs^n||^2 in FP64 on the
  * device; *misfit (host) receives phi, d_sim (optional, same `mem`) the
- * simulated data.  Synchronous. */
+ * simulated data.  Synchronous; TIMEOUT as for ckfwi_forward_shot. */
 CKFWI_API int ckfwi_misfit(ckfwi_model* m, const ckfwi_shot* s, const float* d_obs, int mem, double* misfit,
                            float* d_sim, void* stream);
 

@@ -2364,6 +2364,7 @@ int ckfwi_forward_shot(ckfwi_model* m, const ckfwi_shot* s, float* d_sim, int me
     cudaStream_t st = S(stream);
     ST_TRY(set_shot(m, s));
     ST_TRY(autotune(m, st));
+    ST_TRY(reset_flags(m, st));
     Ctx cx{m, st, 0};
     CK_TRY(cudaMemsetAsync(m->shot.dsim.p, 0, m->shot.dsim.bytes, st));
     State sv{ZERO_R, ZERO_R, U_FP32, U_FP32};
@@ -2377,8 +2378,10 @@ int ckfwi_forward_shot(ckfwi_model* m, const ckfwi_shot* s, float* d_sim, int me
     const size_t nd = (size_t)(m->g.nt + 1) * m->shot.nrec;
     CK_TRY(cudaMemcpyAsync(d_sim, m->shot.dsim.p, nd * sizeof(float),
                            mem == CKFWI_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, st));
-    if (mem == CKFWI_HOST) CK_TRY(cudaStreamSynchronize(st));
-    return CKFWI_OK;
+    // the kernels' error flags (a bounded wait that ran out); synchronises
+    int fl = 0;
+    ST_TRY(read_flags(m, st, &fl));
+    return fl;
 }
 
 int ckfwi_misfit(ckfwi_model* m, const ckfwi_shot* s, const float* d_obs, int mem, double* misfit, float* d_sim,
@@ -2388,6 +2391,7 @@ int ckfwi_misfit(ckfwi_model* m, const ckfwi_shot* s, const float* d_obs, int me
     cudaStream_t st = S(stream);
     ST_TRY(set_shot(m, s));
     ST_TRY(autotune(m, st));
+    ST_TRY(reset_flags(m, st));
     Ctx cx{m, st, 0};
     const size_t nd = (size_t)(m->g.nt + 1) * m->shot.nrec;
     CK_TRY(cudaMemcpyAsync(m->shot.dobs.p, d_obs, nd * sizeof(float),
@@ -2407,9 +2411,10 @@ int ckfwi_misfit(ckfwi_model* m, const ckfwi_shot* s, const float* d_obs, int me
                                mem == CKFWI_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, st));
     double phi = 0.0;
     CK_TRY(cudaMemcpyAsync(&phi, m->phi.p, sizeof(double), cudaMemcpyDeviceToHost, st));
-    CK_TRY(cudaStreamSynchronize(st));
+    int fl = 0;
+    ST_TRY(read_flags(m, st, &fl));
     *misfit = phi;
-    return CKFWI_OK;
+    return fl;
 }
 
 int ckfwi_adjoint_gradient(ckfwi_model* m, const ckfwi_shot* s, const float* d_obs, int mem,

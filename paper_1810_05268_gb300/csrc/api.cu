@@ -376,17 +376,24 @@ struct ckfwi_model {
     // device staging pairs (hstage, used in turn, so the pair a step writes is
     // never one the step reads) in the step that makes it and is copied to
     // its host slot on the copy stream `side`, overlapped with the next
-    // steps; a restore copies the slot into a device pair (hrest)
-    DevMem hstage[3][2], hrest[2];
+    // steps; a restore reads one of two device pairs (hrest), filled by a
+    // copy on the copy stream as soon as the previous host restore has
+    // happened (the schedule is known), or on the main stream if it could
+    // not be prefetched
+    DevMem hstage[3][2], hrest[2][2];
     cudaStream_t side = nullptr;
-    cudaEvent_t ev_fork = nullptr, ev_done[3] = {nullptr, nullptr, nullptr};
+    cudaEvent_t ev_fork = nullptr, ev_done[3] = {nullptr, nullptr, nullptr}, ev_pf[2] = {nullptr, nullptr},
+                ev_join = nullptr;
     ~ckfwi_model()
     {
         graphs.clear();
         bgraphs.clear();
         if (side) cudaStreamDestroy(side);
         if (ev_fork) cudaEventDestroy(ev_fork);
+        if (ev_join) cudaEventDestroy(ev_join);
         for (cudaEvent_t e : ev_done)
+            if (e) cudaEventDestroy(e);
+        for (cudaEvent_t e : ev_pf)
             if (e) cudaEventDestroy(e);
         if (cap) cudaStreamDestroy(cap);
         if (ev) cudaEventDestroy(ev);
@@ -606,7 +613,7 @@ Role lam_r(int i) { return Role{R_LAM, i, 0}; }
 Role traj_r(int n) { return Role{R_TRAJ, n, 0}; }
 Role slot_r(int s, int w) { return Role{R_SLOT, s, w}; }
 Role hstage_r(int k, int w) { return Role{R_HSTAGE, k, w}; }
-Role hrest_r(int w) { return Role{R_HREST, 0, w}; }
+Role hrest_r(int r, int w) { return Role{R_HREST, r, w}; }
 
 void* rptr(ckfwi_model* m, int mode, const Role& r)
 {
@@ -618,7 +625,7 @@ void* rptr(ckfwi_model* m, int mode, const Role& r)
     case R_UN: return org(m->uN, f);
     case R_TRAJ: return m->traj.as<float>() + (size_t)r.idx * f.alloc + f.origin;
     case R_HSTAGE: return org(m->hstage[r.idx][r.which], f);
-    case R_HREST: return org(m->hrest[r.which], f);
+    case R_HREST: return org(m->hrest[r.idx][r.which], f);
     case R_SLOT: {
         // uncompressed slots: two padded fields per slot, FP32 or 16-bit;
         // slots 1 .. host_slots in host memory, the rest in device memory
@@ -642,6 +649,9 @@ struct Ctx {
     bool stage = false;             // FP32 host slots go through the device staging pairs
     bool pend[3] = {false, false, false};  // a copy from staging pair k to a host slot is in flight
     int sk = 0;                     // the staging pair the next host checkpoint takes
+    int pf_slot[2] = {0, 0};        // host slot prefetched into restore pair r (0: none)
+    int pf_fields[2] = {0, 0};      // and how many of its fields
+    int rk = 0;                     // the restore pair the next unprefetched restore takes
     // batch: every stencil step is one launch over all lanes
     std::vector<ckfwi_model*> lanes;   // empty: the model alone
     bool batch = false;
@@ -1441,20 +1451,51 @@ int run_body(Ctx& cx, const RunCfg& rc, const std::vector<Action>& acts, long lo
             if (A.b == 0) {
                 st = State{ZERO_R, ZERO_R, U_FP32, U_FP32};
             } else if (rc.mode == CKFWI_STORE_FP32 && cx.stage && A.b <= cx.m->host_slots) {
-                // a host slot: its copy finished (every pending one is waited
-                // for), then copied into the restore pair (u^s only before a
-                // reverse step)
+                // a host slot: from its prefetched restore pair, or copied now
                 ckfwi_model* m = cx.m;
-                for (int k = 0; k < 3; ++k)
-                    if (cx.pend[k]) {
-                        CK_TRY(cudaStreamWaitEvent(cx.st, m->ev_done[k], 0));
-                        cx.pend[k] = false;
-                    }
                 const size_t fb = field_bytes(m->fg);
-                const char* hs = static_cast<const char*>(m->hpool.p) + (size_t)(A.b - 1) * 2 * fb;
-                for (int w = 0; w < (next_turn ? 1 : 2); ++w)
-                    CK_TRY(cudaMemcpyAsync(m->hrest[w].p, hs + w * fb, fb, cudaMemcpyDefault, cx.st));
-                st = State{hrest_r(0), hrest_r(1), U_FP32, U_FP32};
+                const int need = next_turn ? 1 : 2;   // a reverse step needs u^s only
+                int r = -1;
+                for (int q = 0; q < 2; ++q)
+                    if (cx.pf_slot[q] == A.b && cx.pf_fields[q] >= need) r = q;
+                if (r >= 0) {
+                    CK_TRY(cudaStreamWaitEvent(cx.st, m->ev_pf[r], 0));
+                } else {
+                    r = cx.rk;
+                    // the slot's own copy to the host, if still in flight
+                    for (int k = 0; k < 3; ++k)
+                        if (cx.pend[k]) CK_TRY(cudaStreamWaitEvent(cx.st, m->ev_done[k], 0));
+                    const char* hs = static_cast<const char*>(m->hpool.p) + (size_t)(A.b - 1) * 2 * fb;
+                    for (int w = 0; w < need; ++w)
+                        CK_TRY(cudaMemcpyAsync(m->hrest[r][w].p, hs + w * fb, fb, cudaMemcpyDefault, cx.st));
+                }
+                cx.pf_slot[0] = cx.pf_slot[1] = 0;
+                st = State{hrest_r(r, 0), hrest_r(r, 1), U_FP32, U_FP32};
+                // prefetch the next host restore into the other pair, unless a
+                // checkpoint is written into its slot before it
+                const int o = r ^ 1;
+                cx.rk = o;
+                for (size_t aj = ai + 1; aj < acts.size(); ++aj) {
+                    const Action& B = acts[aj];
+                    if (B.op != ACT_RESTORE || B.b == 0 || B.b > m->host_slots) continue;
+                    bool written = false;
+                    for (size_t ak = ai + 1; ak < aj && !written; ++ak)
+                        written = acts[ak].op == ACT_TAKESHOT && acts[ak].b == B.b;
+                    if (!written) {
+                        const int nb = aj + 1 < acts.size() && acts[aj + 1].op == ACT_YOUTURN ? 1 : 2;
+                        const char* hs = static_cast<const char*>(m->hpool.p) + (size_t)(B.b - 1) * 2 * fb;
+                        // after every step issued so far (the pair may still be read by them);
+                        // the copy stream has the slot's own copy to the host before it
+                        CK_TRY(cudaEventRecord(m->ev_fork, cx.st));
+                        CK_TRY(cudaStreamWaitEvent(m->side, m->ev_fork, 0));
+                        for (int w = 0; w < nb; ++w)
+                            CK_TRY(cudaMemcpyAsync(m->hrest[o][w].p, hs + w * fb, fb, cudaMemcpyDefault, m->side));
+                        CK_TRY(cudaEventRecord(m->ev_pf[o], m->side));
+                        cx.pf_slot[o] = B.b;
+                        cx.pf_fields[o] = nb;
+                    }
+                    break;
+                }
             } else if (rc.mode == CKFWI_STORE_FP32) {
                 st = State{slot_r(A.b, 0), slot_r(A.b, 1), U_FP32, U_FP32};   // the slot is the state
             } else if (rc.codec) {
@@ -1529,12 +1570,12 @@ int run_body(Ctx& cx, const RunCfg& rc, const std::vector<Action>& acts, long lo
             ST_TRY(reverse(A.a, st.cur, st.tcur));
         }
     }
-    // join the copy stream: no checkpoint copy outlives the gradient
-    for (int k = 0; k < 3; ++k)
-        if (cx.pend[k]) {
-            CK_TRY(cudaStreamWaitEvent(cx.st, cx.m->ev_done[k], 0));
-            cx.pend[k] = false;
-        }
+    // join the copy stream: no checkpoint copy or prefetch outlives the gradient
+    if (cx.stage) {
+        CK_TRY(cudaEventRecord(cx.m->ev_join, cx.m->side));
+        CK_TRY(cudaStreamWaitEvent(cx.st, cx.m->ev_join, 0));
+        for (int k = 0; k < 3; ++k) cx.pend[k] = false;
+    }
     counters[0] = fsteps;
     counters[1] = ncomp;
     return CKFWI_OK;
@@ -1605,11 +1646,15 @@ int prepare_storage(ckfwi_model* m, const RunCfg& rc, const ckfwi_grad_opts* o)
             // the staging pairs and the copy stream of FP32 host slots
             for (int k = 0; k < 3; ++k)
                 for (int w = 0; w < 2; ++w) CK_TRY(m->hstage[k][w].alloc(field_bytes(f)));
-            for (int w = 0; w < 2; ++w) CK_TRY(m->hrest[w].alloc(field_bytes(f)));
+            for (int r = 0; r < 2; ++r)
+                for (int w = 0; w < 2; ++w) CK_TRY(m->hrest[r][w].alloc(field_bytes(f)));
             if (!m->side) CK_TRY(cudaStreamCreateWithFlags(&m->side, cudaStreamNonBlocking));
             if (!m->ev_fork) CK_TRY(cudaEventCreateWithFlags(&m->ev_fork, cudaEventDisableTiming));
             for (int k = 0; k < 3; ++k)
                 if (!m->ev_done[k]) CK_TRY(cudaEventCreateWithFlags(&m->ev_done[k], cudaEventDisableTiming));
+            for (int r = 0; r < 2; ++r)
+                if (!m->ev_pf[r]) CK_TRY(cudaEventCreateWithFlags(&m->ev_pf[r], cudaEventDisableTiming));
+            if (!m->ev_join) CK_TRY(cudaEventCreateWithFlags(&m->ev_join, cudaEventDisableTiming));
         }
     } else {
         m->pool_tag = 0;

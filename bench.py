@@ -55,7 +55,9 @@ CPU_STEPS = 300            # time steps of the oracle sample (about 10-30 s on 1
 GRAD_TOL = 1e-2            # gradient accuracy a storage mode must keep to be the headline
 KERNEL_NAMES = {1: ("fwd_kernel", "adj_kernel"), 2: ("fwd_tma_kernel", "adj_tma_kernel"),
                 3: ("fwd3_kernel", "adj3_kernel"), 4: ("fwd4_kernel", "adj4_kernel"),
-                5: ("ot4_lap_kernel+ot4_fwd_kernel", "ot4_lap_kernel+ot4_adj_kernel")}
+                5: ("ot4_lap_kernel+ot4_fwd_kernel", "ot4_lap_kernel+ot4_adj_kernel"),
+                6: ("ot4v_lap_kernel+ot4v_fwd_kernel", "ot4v_lap_kernel+ot4v_fwd_kernel+ot4v_grad_kernel"),
+                7: ("fwd5_kernel", "adj5_kernel")}
 # OT4 forward step (two passes): reads u^n, w and writes Z = w lap u^n, then
 # reads Z, u^n, u^{n-1}, w and writes u^{n+1}.  Reverse step (three passes):
 # reads lam^j, u^{j-1}, w, the previous Z_u and g, writes Z_l, Z_u, g; reads

@@ -180,18 +180,17 @@ __global__ void f64_to_f32_kernel(const double* __restrict__ a, float* __restric
 }
 
 // max |u| over the total grid of a padded field (the wavefield's scale, for
-// stating a codec tolerance relative to it): the magnitudes' bit patterns
-// order like the values, so one unsigned atomicMax per warp.
+// stating a codec tolerance relative to it): a CTA per group of rows (z, y),
+// its threads along x; the magnitudes' bit patterns order like the values,
+// so one unsigned atomicMax per warp.
 __global__ void absmax_kernel(const float* __restrict__ u, FieldGeom g, unsigned* __restrict__ out)
 {
     unsigned m = 0u;
-    const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < g.npts; p += stride) {
-        const long long x = p % g.nx;
-        const long long t = p / g.nx;
-        const long long y = t % g.ny;
-        const long long z = t / g.ny;
-        m = max(m, __float_as_uint(fabsf(__ldg(u + z * g.pxy + y * g.px + x))));
+    const long long rows = (long long)g.nz * g.ny;
+    for (long long r = blockIdx.x; r < rows; r += gridDim.x) {
+        const long long z = r / g.ny, y = r % g.ny;
+        const float* row = u + z * g.pxy + y * g.px;
+        for (int x = threadIdx.x; x < g.nx; x += blockDim.x) m = max(m, __float_as_uint(fabsf(__ldg(row + x))));
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
@@ -211,8 +210,8 @@ cudaError_t launch_sample(const float* u, const Sample& smp, cudaStream_t s)
 
 cudaError_t launch_absmax(const float* u_origin, const FieldGeom& g, unsigned* out, cudaStream_t s)
 {
-    // a grid-stride loop over at most 8 CTAs per SM of a 152-SM GPU
-    const unsigned nb = (unsigned)std::min<long long>((g.npts + 255) / 256, 8LL * 152);
+    // at most 8 CTAs per SM of a 152-SM GPU, each taking rows in turn
+    const unsigned nb = (unsigned)std::min<long long>((long long)g.nz * g.ny, 8LL * 152);
     absmax_kernel<<<nb, 256, 0, s>>>(u_origin, g, out);
     return cudaGetLastError();
 }

@@ -143,11 +143,17 @@ typedef struct ckfwi_grad_opts {
                             sum rounded once) instead of float64 */
     int host_slots;      /* FP32 / BF16 / FP16 Revolve: how many of the M - 1
                             checkpoint slots live in pinned host memory (the
-                            second storage level, read and written by the step
-                            kernels over the host link); the lowest-numbered
-                            slots, which Revolve writes and reads least, go
-                            there.  0: every slot in device memory.  Values are
-                            unchanged by the placement. */
+                            second storage level).  FP32: the gradient follows
+                            ckfwi_multistage_schedule (host checkpoints written
+                            once, in the first sweep); a host checkpoint goes
+                            through a device staging pair and a copy stream,
+                            overlapped with the steps, and a host restore is
+                            copied ahead of use.  BF16 / FP16: the Revolve
+                            schedule, its lowest-numbered slots (written and
+                            read least) on the host, read and written by the
+                            step kernels over the host link.  0: every slot in
+                            device memory.  Values are unchanged by the
+                            placement (FP32 checkpoints are exact). */
     int rate;            /* CODEC_RATE: bits per value, 1..32.  The pool holds
                             exactly (M - 1) * 2 fixed-size streams; a non-zero
                             pool_bytes below that is EINVAL. */
@@ -290,6 +296,21 @@ CKFWI_API int ckfwi_stream_words(const ckfwi_model* m, long long* words, long lo
  * receives {p, W, R}.  EINVAL if cap is too small (n_triples still set). */
 CKFWI_API int ckfwi_revolve_schedule(int nt, int slots, int32_t* actions, long long cap,
                            long long* n_triples, long long* counts);
+
+/* The schedule of a gradient whose FP32 checkpoints use two storage levels
+ * (multi-level checkpointing, a future-work item of Sec. 8, in the
+ * multistage form of Stumm and Walther that Sec. 3's model builds on):
+ * slots 1 .. host_slots are in host memory, host_slots + 1 .. slots - 1 on
+ * the device.  Host checkpoints are taken once each, in the first forward
+ * sweep, at the starts of segments; each segment is reversed, last first,
+ * by Revolve from its start with the device slots.  The segments give the
+ * fewest forward steps within that family (the first sweep's segments are
+ * of equal length, since p(n, m) is convex in n; the last one, which the
+ * first sweep does not cross, may be longer), ties going to fewer host
+ * checkpoints.  host_slots = 0 is ckfwi_revolve_schedule.  Same output
+ * convention; EINVAL unless 0 <= host_slots <= slots - 1.  Host only. */
+CKFWI_API int ckfwi_multistage_schedule(int nt, int slots, int host_slots, int32_t* actions, long long cap,
+                                        long long* n_triples, long long* counts);
 
 /* Fixed-accuracy block codec on dense device fields (Sec. 2.2: ZFP's
  * fixed-tolerance mode is the lossy compressor the paper uses; this codec

@@ -138,6 +138,31 @@ def simulate(acts, N, M):
     return adv
 
 
+def multistage_p(N, M, H):
+    """Fewest forward steps to reverse N steps when slots 1..H are a second
+    storage level written only in the first forward sweep (multistage
+    checkpointing, Stumm and Walther, on which Sec. 3's model builds): the
+    first sweep stores the starts of segments there, and each segment is
+    reversed from its start by Revolve with the M - H remaining slots (its
+    start included).  By the recursion over the first segment's length l,
+
+        C(n, 0) = p(n, M - H)
+        C(n, h) = min( C(n, h-1),  min over 1 <= l <= n-1 of
+                       l + C(n - l, h - 1) + p(l, M - H) ),
+
+    C(N, H) is returned (every segmentation is tried)."""
+    md = M - H
+    tab = p_table(N, md)[md]
+    C = tab.copy()
+    for h in range(1, H + 1):
+        nxt = C.copy()
+        for n in range(2, N + 1):
+            l = np.arange(1, n)
+            nxt[n] = min(nxt[n], int(np.min(l + C[n - l] + tab[l])))
+        C = nxt
+    return int(C[N])
+
+
 @lru_cache(maxsize=None)
 def counts(N, M):
     return schedule(N, M)[1]

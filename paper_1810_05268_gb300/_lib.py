@@ -55,7 +55,7 @@ class Stats(ctypes.Structure):
 
 EXPORTS = ["ckfwi_create_model", "ckfwi_set_model", "ckfwi_forward_shot", "ckfwi_misfit", "ckfwi_adjoint_gradient",
            "ckfwi_batch_gradient", "ckfwi_batch_gradient_models", "ckfwi_free", "ckfwi_error_string", "ckfwi_revolve_schedule",
-           "ckfwi_codec_bound_words", "ckfwi_codec_compress", "ckfwi_codec_decompress",
+           "ckfwi_multistage_schedule", "ckfwi_codec_bound_words", "ckfwi_codec_compress", "ckfwi_codec_decompress",
            "ckfwi_codec_compress_noalloc", "ckfwi_codec_rate_words", "ckfwi_codec_compress_rate", "ckfwi_stream_words"]
 
 
@@ -82,6 +82,7 @@ def lib():
         L.ckfwi_error_string.argtypes = [I]
         L.ckfwi_error_string.restype = ctypes.c_char_p
         L.ckfwi_revolve_schedule.argtypes = [I, I, P, LL, P, P]
+        L.ckfwi_multistage_schedule.argtypes = [I, I, I, P, LL, P, P]
         L.ckfwi_codec_bound_words.argtypes = [I, I, I, I]
         L.ckfwi_codec_bound_words.restype = LL
         L.ckfwi_codec_compress.argtypes = [P, I, I, I, I, D, P, LL, P, P, P]
@@ -93,8 +94,8 @@ def lib():
         L.ckfwi_codec_compress_rate.argtypes = [P, I, I, I, I, I, P, LL, P, P, P]
         for name in ("ckfwi_create_model", "ckfwi_set_model", "ckfwi_forward_shot", "ckfwi_misfit",
                      "ckfwi_adjoint_gradient",
-                     "ckfwi_batch_gradient", "ckfwi_batch_gradient_models", "ckfwi_revolve_schedule", "ckfwi_codec_compress",
-                     "ckfwi_codec_decompress", "ckfwi_codec_compress_noalloc"):
+                     "ckfwi_batch_gradient", "ckfwi_batch_gradient_models", "ckfwi_revolve_schedule", "ckfwi_multistage_schedule",
+                     "ckfwi_codec_compress", "ckfwi_codec_decompress", "ckfwi_codec_compress_noalloc"):
             getattr(L, name).restype = I
         _lib = L
         return _lib

@@ -362,6 +362,19 @@ def revolve_schedule(nt, slots):
     return acts, (cnt[0], cnt[1], cnt[2])
 
 
+def multistage_schedule(nt, slots, host_slots):
+    """(actions int32 [n][3], (p, W, R)) of the schedule of a gradient with
+    FP32 checkpoints in two storage levels (slots 1 .. host_slots on the host)."""
+    n = ctypes.c_longlong(0)
+    cnt = (ctypes.c_longlong * 3)()
+    args = (int(nt), int(slots), int(host_slots))
+    _check(lib().ckfwi_multistage_schedule(*args, None, 0, ctypes.byref(n), cnt), "ckfwi_multistage_schedule")
+    acts = np.zeros((n.value, 3), dtype=np.int32)
+    _check(lib().ckfwi_multistage_schedule(*args, acts.ctypes.data, n.value, ctypes.byref(n), cnt),
+           "ckfwi_multistage_schedule")
+    return acts, (cnt[0], cnt[1], cnt[2])
+
+
 def stream_words(model):
     """Words of every compression of the model's last compressed-checkpoint
     gradient, in schedule order (u^s, u^{s-1} per takeshot)."""

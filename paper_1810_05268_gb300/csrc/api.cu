@@ -18,6 +18,9 @@
 // device.  Nothing synchronises with the host until the gradient is done.
 // With M >= N every state is kept instead (store-all): the forward sweep
 // writes u^{n+1} straight into the trajectory.
+// Every action is an NVTX range named after it ("ckfwi advance" and so on,
+// the state as payload) inside a "ckfwi gradient" range; with use_graph the
+// ranges mark the recording call only.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
@@ -34,6 +37,8 @@
 #include <set>
 #include <tuple>
 #include <vector>
+
+#include <nvtx3/nvToolsExt.h>
 
 #include "../../include/ckfwi.h"
 #include "internal.h"
@@ -649,8 +654,10 @@ struct Ctx {
     bool stage = false;             // FP32 host slots go through the device staging pairs
     bool pend[3] = {false, false, false};  // a copy from staging pair k to a host slot is in flight
     int sk = 0;                     // the staging pair the next host checkpoint takes
-    int pf_slot[2] = {0, 0};        // host slot prefetched into restore pair r (0: none)
-    int pf_fields[2] = {0, 0};      // and how many of its fields
+    int stage_slot[3] = {0, 0, 0};  // host slot whose checkpoint staging pair k still holds (0: none)
+    int rest_slot[2] = {0, 0};      // host slot copied into restore pair r (0: none)
+    int rest_fields[2] = {0, 0};    // and how many of its fields
+    bool rest_pf[2] = {false, false};   // that copy is a prefetch on the copy stream (event ev_pf[r])
     int rk = 0;                     // the restore pair the next unprefetched restore takes
     // batch: every stencil step is one launch over all lanes
     std::vector<ckfwi_model*> lanes;   // empty: the model alone
@@ -1281,6 +1288,12 @@ struct State {
     int tcur, tprev;    // U_FP32 / U_BF16 / U_FP16
 };
 
+// the state reads device pair idx of this kind (a staging or a restore pair)
+bool reads_pair(const State& st, int kind, int idx)
+{
+    return (st.cur.kind == kind && st.cur.idx == idx) || (st.prev.kind == kind && st.prev.idx == idx);
+}
+
 struct RunCfg {
     int N, M, mode;
     float tol_f;          // CODEC: the bound; CODEC_RATE: the rate (a graph key)
@@ -1313,8 +1326,29 @@ Role pick_free(const State& s)
 // The recorded part of a gradient: everything between "inputs staged" and
 // "outputs ready" (this is what a CUDA graph captures).  Runs every lane of
 // the context through the same schedule.
+// An NVTX range for the lifetime of the object (a no-op without a tool
+// attached), with an integer payload
+struct NvtxRange {
+    NvtxRange(const char* name, long long payload)
+    {
+        nvtxEventAttributes_t a{};
+        a.version = NVTX_VERSION;
+        a.size = NVTX_EVENT_ATTRIB_STRUCT_SIZE;
+        a.messageType = NVTX_MESSAGE_TYPE_ASCII;
+        a.message.ascii = name;
+        a.payloadType = NVTX_PAYLOAD_TYPE_INT64;
+        a.payload.llValue = payload;
+        nvtxRangePushEx(&a);
+    }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
+const char* const kActionRange[4] = {"ckfwi advance", "ckfwi takeshot", "ckfwi restore", "ckfwi youturn"};
+
 int run_body(Ctx& cx, const RunCfg& rc, const std::vector<Action>& acts, long long* counters)
 {
+    NvtxRange whole("ckfwi gradient", (long long)cx.nl());
     const int NL = cx.nl();
     const int N = rc.N;
     if (cx.issue) {
@@ -1334,16 +1368,20 @@ int run_body(Ctx& cx, const RunCfg& rc, const std::vector<Action>& acts, long lo
     };
     long long fsteps = 0;
     if (rc.store_all) {
-        for (int n = 0; n < N; ++n) {
-            const Role u = n == 0 ? ZERO_R : traj_r(n);
-            const Role up = n <= 1 ? ZERO_R : traj_r(n - 1);
-            const Role out = (n + 1 < N) ? traj_r(n + 1) : UN_R;
-            ST_TRY(fwd_step(cx, u, up, out, n, true, CK_NONE, NONE_R, NONE_R));
-            ++fsteps;
+        {
+            NvtxRange range(kActionRange[ACT_ADVANCE], 0);
+            for (int n = 0; n < N; ++n) {
+                const Role u = n == 0 ? ZERO_R : traj_r(n);
+                const Role up = n <= 1 ? ZERO_R : traj_r(n - 1);
+                const Role out = (n + 1 < N) ? traj_r(n + 1) : UN_R;
+                ST_TRY(fwd_step(cx, u, up, out, n, true, CK_NONE, NONE_R, NONE_R));
+                ++fsteps;
+            }
+            ST_TRY(sample_last(cx, UN_R));
+            ST_TRY(field_absmax(cx, UN_R));
+            ST_TRY(residual(cx));
         }
-        ST_TRY(sample_last(cx, UN_R));
-        ST_TRY(field_absmax(cx, UN_R));
-        ST_TRY(residual(cx));
+        NvtxRange range(kActionRange[ACT_YOUTURN], N - 1);
         for (int s = N - 1; s >= 0; --s) ST_TRY(reverse(s, s == 0 ? ZERO_R : traj_r(s), U_FP32));
         counters[0] = fsteps;
         return CKFWI_OK;
@@ -1367,6 +1405,7 @@ int run_body(Ctx& cx, const RunCfg& rc, const std::vector<Action>& acts, long lo
     bool first_sweep = true;
     for (size_t ai = 0; ai < acts.size(); ++ai) {
         const Action& A = acts[ai];
+        NvtxRange range(kActionRange[A.op & 3], A.a);
         const bool next_take = ai + 1 < acts.size() && acts[ai + 1].op == ACT_TAKESHOT;
         const bool next_turn = ai + 1 < acts.size() && acts[ai + 1].op == ACT_YOUTURN;
         if (A.op == ACT_ADVANCE) {
@@ -1380,11 +1419,18 @@ int run_body(Ctx& cx, const RunCfg& rc, const std::vector<Action>& acts, long lo
                 if (last && next_take && !rc.codec) {
                     const int slot = acts[ai + 1].b;
                     if (rc.mode == CKFWI_STORE_FP32 && cx.stage && slot <= cx.m->host_slots) {
-                        // into a device staging pair, copied to the host slot below
+                        // into a device staging pair (not one the step reads), copied to the host slot below
                         staged = cx.sk;
-                        cx.sk = (cx.sk + 1) % 3;
+                        for (int t = 0; t < 3 && reads_pair(st, R_HSTAGE, staged); ++t) staged = (staged + 1) % 3;
+                        cx.sk = (staged + 1) % 3;
                         if (cx.pend[staged]) CK_TRY(cudaStreamWaitEvent(cx.st, cx.m->ev_done[staged], 0));
                         cx.pend[staged] = false;
+                        // the slot's older copies on the device are stale from here on
+                        for (int k = 0; k < 3; ++k)
+                            if (cx.stage_slot[k] == slot) cx.stage_slot[k] = 0;
+                        for (int r = 0; r < 2; ++r)
+                            if (cx.rest_slot[r] == slot) cx.rest_slot[r] = 0;
+                        cx.stage_slot[staged] = slot;
                         out = hstage_r(staged, 0);
                         ck = CK_FP32;
                         ckup = hstage_r(staged, 1);
@@ -1451,49 +1497,71 @@ int run_body(Ctx& cx, const RunCfg& rc, const std::vector<Action>& acts, long lo
             if (A.b == 0) {
                 st = State{ZERO_R, ZERO_R, U_FP32, U_FP32};
             } else if (rc.mode == CKFWI_STORE_FP32 && cx.stage && A.b <= cx.m->host_slots) {
-                // a host slot: from its prefetched restore pair, or copied now
+                // a host slot: from the staging pair that still holds its
+                // checkpoint, from a restore pair it was copied into, or
+                // copied now
                 ckfwi_model* m = cx.m;
                 const size_t fb = field_bytes(m->fg);
                 const int need = next_turn ? 1 : 2;   // a reverse step needs u^s only
-                int r = -1;
-                for (int q = 0; q < 2; ++q)
-                    if (cx.pf_slot[q] == A.b && cx.pf_fields[q] >= need) r = q;
-                if (r >= 0) {
-                    CK_TRY(cudaStreamWaitEvent(cx.st, m->ev_pf[r], 0));
+                int k = -1, r = -1;
+                for (int q = 0; q < 3; ++q)
+                    if (cx.stage_slot[q] == A.b) k = q;
+                for (int q = 0; q < 2 && k < 0; ++q)
+                    if (cx.rest_slot[q] == A.b && cx.rest_fields[q] >= need) r = q;
+                if (k >= 0) {
+                    st = State{hstage_r(k, 0), hstage_r(k, 1), U_FP32, U_FP32};
                 } else {
-                    r = cx.rk;
-                    // the slot's own copy to the host, if still in flight
-                    for (int k = 0; k < 3; ++k)
-                        if (cx.pend[k]) CK_TRY(cudaStreamWaitEvent(cx.st, m->ev_done[k], 0));
-                    const char* hs = static_cast<const char*>(m->hpool.p) + (size_t)(A.b - 1) * 2 * fb;
-                    for (int w = 0; w < need; ++w)
-                        CK_TRY(cudaMemcpyAsync(m->hrest[r][w].p, hs + w * fb, fb, cudaMemcpyDefault, cx.st));
-                }
-                cx.pf_slot[0] = cx.pf_slot[1] = 0;
-                st = State{hrest_r(r, 0), hrest_r(r, 1), U_FP32, U_FP32};
-                // prefetch the next host restore into the other pair, unless a
-                // checkpoint is written into its slot before it
-                const int o = r ^ 1;
-                cx.rk = o;
-                for (size_t aj = ai + 1; aj < acts.size(); ++aj) {
-                    const Action& B = acts[aj];
-                    if (B.op != ACT_RESTORE || B.b == 0 || B.b > m->host_slots) continue;
-                    bool written = false;
-                    for (size_t ak = ai + 1; ak < aj && !written; ++ak)
-                        written = acts[ak].op == ACT_TAKESHOT && acts[ak].b == B.b;
-                    if (!written) {
-                        const int nb = aj + 1 < acts.size() && acts[aj + 1].op == ACT_YOUTURN ? 1 : 2;
-                        const char* hs = static_cast<const char*>(m->hpool.p) + (size_t)(B.b - 1) * 2 * fb;
-                        // after every step issued so far (the pair may still be read by them);
-                        // the copy stream has the slot's own copy to the host before it
-                        CK_TRY(cudaEventRecord(m->ev_fork, cx.st));
-                        CK_TRY(cudaStreamWaitEvent(m->side, m->ev_fork, 0));
-                        for (int w = 0; w < nb; ++w)
-                            CK_TRY(cudaMemcpyAsync(m->hrest[o][w].p, hs + w * fb, fb, cudaMemcpyDefault, m->side));
-                        CK_TRY(cudaEventRecord(m->ev_pf[o], m->side));
-                        cx.pf_slot[o] = B.b;
-                        cx.pf_fields[o] = nb;
+                    if (r >= 0) {
+                        if (cx.rest_pf[r]) CK_TRY(cudaStreamWaitEvent(cx.st, m->ev_pf[r], 0));
+                    } else {
+                        // a pair with no prefetch in flight, else the next in turn
+                        r = !cx.rest_pf[cx.rk] ? cx.rk : (!cx.rest_pf[cx.rk ^ 1] ? cx.rk ^ 1 : cx.rk);
+                        cx.rk = r ^ 1;
+                        if (cx.rest_pf[r]) CK_TRY(cudaStreamWaitEvent(cx.st, m->ev_pf[r], 0));
+                        // copies to the host still in flight (none of this slot's: it would be staged)
+                        for (int q = 0; q < 3; ++q)
+                            if (cx.pend[q]) CK_TRY(cudaStreamWaitEvent(cx.st, m->ev_done[q], 0));
+                        const char* hs = static_cast<const char*>(m->hpool.p) + (size_t)(A.b - 1) * 2 * fb;
+                        for (int w = 0; w < need; ++w)
+                            CK_TRY(cudaMemcpyAsync(m->hrest[r][w].p, hs + w * fb, fb, cudaMemcpyDefault, cx.st));
+                        cx.rest_slot[r] = A.b;
+                        cx.rest_fields[r] = need;
                     }
+                    cx.rest_pf[r] = false;
+                    st = State{hrest_r(r, 0), hrest_r(r, 1), U_FP32, U_FP32};
+                }
+                // Prefetch the next host restore whose slot no device pair
+                // holds and that no checkpoint rewrites first, into a restore
+                // pair the state does not use, unless that pair's slot is
+                // restored before it.
+                int o = -1;
+                if (!reads_pair(st, R_HREST, 0)) o = 0;
+                if (!reads_pair(st, R_HREST, 1) && (o < 0 || cx.rest_slot[o] != 0)) o = 1;
+                std::vector<int> taken;
+                for (size_t aj = ai + 1; o >= 0 && aj < acts.size(); ++aj) {
+                    const Action& B = acts[aj];
+                    if (B.op == ACT_TAKESHOT && B.b <= m->host_slots) taken.push_back(B.b);
+                    if (B.op != ACT_RESTORE || B.b == 0 || B.b > m->host_slots) continue;
+                    if (std::find(taken.begin(), taken.end(), B.b) != taken.end()) continue;
+                    const int nb = aj + 1 < acts.size() && acts[aj + 1].op == ACT_YOUTURN ? 1 : 2;
+                    bool held = false;
+                    for (int q = 0; q < 3; ++q) held |= cx.stage_slot[q] == B.b;
+                    for (int q = 0; q < 2; ++q) held |= cx.rest_slot[q] == B.b && cx.rest_fields[q] >= nb;
+                    if (held) {
+                        if (cx.rest_slot[o] == B.b) break;   // the target pair is needed first
+                        continue;
+                    }
+                    const char* hs = static_cast<const char*>(m->hpool.p) + (size_t)(B.b - 1) * 2 * fb;
+                    // after every step issued so far (the pair may still be read by them);
+                    // the copy stream has every copy to the host before it
+                    CK_TRY(cudaEventRecord(m->ev_fork, cx.st));
+                    CK_TRY(cudaStreamWaitEvent(m->side, m->ev_fork, 0));
+                    for (int w = 0; w < nb; ++w)
+                        CK_TRY(cudaMemcpyAsync(m->hrest[o][w].p, hs + w * fb, fb, cudaMemcpyDefault, m->side));
+                    CK_TRY(cudaEventRecord(m->ev_pf[o], m->side));
+                    cx.rest_slot[o] = B.b;
+                    cx.rest_fields[o] = nb;
+                    cx.rest_pf[o] = true;
                     break;
                 }
             } else if (rc.mode == CKFWI_STORE_FP32) {
@@ -1617,7 +1685,6 @@ int prepare_storage(ckfwi_model* m, const RunCfg& rc, const ckfwi_grad_opts* o)
         return CKFWI_OK;
     }
     if (rc.M <= 1) return CKFWI_OK;
-    const size_t nslot = (size_t)(rc.M - 1) * 2;
     // Uncompressed slots are read with their halo cells, which must hold 0;
     // a pool last used with another layout is cleared before reuse.
     const int tag = rc.mode == CKFWI_STORE_FP32 ? 4 : (rc.codec ? 0 : 2);
@@ -1805,6 +1872,17 @@ void codec_stats(const std::vector<long long>& words, const std::vector<Action>&
     *peak_bytes = (double)peak * 4;
 }
 
+// The action list: Revolve, or with FP32 slots in host memory the two-level
+// (multistage) schedule, which writes each host slot once
+void make_schedule(const ckfwi_model* m, const RunCfg& rc, std::vector<Action>& acts, long long cnt[3])
+{
+    if (rc.store_all) return;
+    if (rc.mode == CKFWI_STORE_FP32 && !rc.codec && m->host_slots > 0)
+        multistage_schedule(rc.N, rc.M, m->host_slots, acts, cnt);
+    else
+        revolve_schedule(rc.N, rc.M, acts, cnt);
+}
+
 int gradient_one(ckfwi_model* m, const ckfwi_shot* s, const float* d_obs, int mem,
                  const ckfwi_grad_opts* o, double* misfit, ckfwi_stats* stats, cudaStream_t st)
 {
@@ -1822,7 +1900,7 @@ int gradient_one(ckfwi_model* m, const ckfwi_shot* s, const float* d_obs, int me
     ST_TRY(reset_flags(m, st));
     std::vector<Action> acts;
     long long cnt[3] = {rc.N - 1, 0, 0};
-    if (!rc.store_all) revolve_schedule(rc.N, rc.M, acts, cnt);
+    make_schedule(m, rc, acts, cnt);
     Ctx cx{m, st, 0};
     cx.mode = rc.mode;
     cx.stage = rc.mode == CKFWI_STORE_FP32 && !rc.codec && !rc.store_all && m->host_slots > 0 && m->side;
@@ -2151,7 +2229,7 @@ int gradient_batch(const std::vector<ckfwi_model*>& lanes, const ckfwi_shot* sho
     }
     std::vector<Action> acts;
     long long cnt[3] = {rc.N - 1, 0, 0};
-    if (!rc.store_all) revolve_schedule(rc.N, rc.M, acts, cnt);
+    make_schedule(m0, rc, acts, cnt);
     Ctx cx{m0, st, 0};
     cx.mode = rc.mode;
     cx.lanes = lanes;
@@ -2680,10 +2758,18 @@ const char* ckfwi_error_string(int status)
 int ckfwi_revolve_schedule(int nt, int slots, int32_t* actions, long long cap, long long* n_triples,
                            long long* counts)
 {
-    if (nt < 1 || slots < 1) return CKFWI_EINVAL;
+    return ckfwi_multistage_schedule(nt, slots, 0, actions, cap, n_triples, counts);
+}
+
+int ckfwi_multistage_schedule(int nt, int slots, int host_slots, int32_t* actions, long long cap,
+                              long long* n_triples, long long* counts)
+{
+    if (nt < 1 || slots < 1 || host_slots < 0 || host_slots > slots - 1) return CKFWI_EINVAL;
     std::vector<Action> acts;
     long long cnt[3];
-    if (revolve_schedule(nt, slots, acts, cnt) != 0) return CKFWI_EINVAL;
+    const int rc = host_slots > 0 ? multistage_schedule(nt, slots, host_slots, acts, cnt)
+                                  : revolve_schedule(nt, slots, acts, cnt);
+    if (rc != 0) return CKFWI_EINVAL;
     if (n_triples) *n_triples = (long long)acts.size();
     if (counts) {
         counts[0] = cnt[0];

@@ -21,6 +21,7 @@ long long revolve_p(long long n, long long m)
 {
     if (n <= 1) return 0;
     if (m >= n) return n - 1;
+    if (m == 1) return n * (n - 1) / 2;
     // beta = C(m + r, m), grown until it reaches n
     long long r = 0, beta = 1;
     while (beta < n) {
@@ -38,11 +39,15 @@ struct Builder {
     std::vector<std::vector<long long>> tab;   // tab[m][n] = p(n, m)
     std::vector<Action>* out;
     long long p = 0, W = 0, R = 0;
+    // slot numbers as emitted: the range's own start slot 0 is `start`,
+    // slot i >= 1 is dev0 + i
+    long long start = 0, dev0 = 0;
 
     long long P(long long n, long long m) const { return tab[m][n]; }
 
     void emit(int op, long long a, long long b)
     {
+        if (op == ACT_TAKESHOT || op == ACT_RESTORE) b = b == 0 ? start : dev0 + b;
         out->push_back(Action{op, (int)a, (int)b});
         if (op == ACT_ADVANCE) p += b;
         if (op == ACT_TAKESHOT) ++W;
@@ -103,6 +108,73 @@ int revolve_schedule(int N, int M, std::vector<Action>& acts, long long counts[3
         for (long long n = 0; n <= N; ++n) B.tab[m][n] = revolve_p(n, m);
     acts.clear();
     B.rev(0, N, mm, 0);
+    if (counts) {
+        counts[0] = B.p;
+        counts[1] = B.W;
+        counts[2] = B.R;
+    }
+    return 0;
+}
+
+int multistage_schedule(int N, int M, int H, std::vector<Action>& acts, long long counts[3])
+{
+    if (N < 1 || M < 1 || H < 0 || H > M - 1) return -1;
+    const long long md = M - H;                        // a segment's start plus the device slots
+    std::vector<long long> pd(N + 1);
+    for (long long n = 0; n <= N; ++n) pd[n] = revolve_p(n, md);
+    // k segments of the first sweep (equal lengths: p is convex in n, so an
+    // even split minimises their sum) and a last segment of L steps, which
+    // the first sweep does not cross
+    auto cost = [&](long long k, long long L) {
+        long long c = (N - L) + pd[L];
+        if (k > 0) {
+            const long long q = (N - L) / k, rem = (N - L) % k;
+            c += rem * pd[q + 1] + (k - rem) * pd[q];
+        }
+        return c;
+    };
+    long long bk = 0, bL = N, best = pd[N];
+    for (long long k = 1; k <= std::min<long long>(H, N - 1); ++k)
+        for (long long L = 1; L <= N - k; ++L) {
+            const long long c = cost(k, L);
+            if (c < best) {
+                best = c;
+                bk = k;
+                bL = L;
+            }
+        }
+    std::vector<long long> b0(bk + 2, 0), len(bk + 1, 0);
+    if (bk > 0) {
+        const long long q = (N - bL) / bk, rem = (N - bL) % bk;
+        for (long long j = 0; j < bk; ++j) len[j] = q + (j < rem ? 1 : 0);
+    }
+    len[bk] = bL;
+    for (long long j = 0; j <= bk; ++j) b0[j + 1] = b0[j] + len[j];
+    Builder B;
+    B.out = &acts;
+    const long long mm = std::min<long long>(md, N);
+    B.tab.assign(mm + 1, std::vector<long long>(N + 1, 0));
+    for (long long m = 1; m <= mm; ++m)
+        for (long long n = 0; n <= N; ++n) B.tab[m][n] = revolve_p(n, m);
+    acts.clear();
+    B.dev0 = H;
+    // first sweep: host slot j holds the start of segment j (j = 1 .. k)
+    for (long long j = 1; j <= bk; ++j) {
+        B.start = 0;
+        B.out->push_back(Action{ACT_ADVANCE, (int)b0[j - 1], (int)len[j - 1]});
+        B.p += len[j - 1];
+        B.out->push_back(Action{ACT_TAKESHOT, (int)b0[j], (int)j});
+        ++B.W;
+    }
+    // reversal, last segment first; its start slot is the segment's host slot
+    for (long long j = bk; j >= 0; --j) {
+        B.start = j;
+        if (j < bk) {
+            B.out->push_back(Action{ACT_RESTORE, (int)b0[j], (int)j});
+            ++B.R;
+        }
+        B.rev(b0[j], len[j], std::min(md, len[j]), 0);
+    }
     if (counts) {
         counts[0] = B.p;
         counts[1] = B.W;

@@ -53,8 +53,9 @@ def main():
     fb, ab = (32, 72) if args.time_order == 4 else (16, 28)
     out["fwd_gbs"] = fb * npts / (out["fwd_us"] * 1e-6) / 1e9
     out["adj_gbs"] = ab * npts / (out["adj_us"] * 1e-6) / 1e9
-    out["fwd_kernel"] = [st["fwd_ver"], st["fwd_bx"], st["fwd_by"], st["fwd_zlen"]]
-    out["adj_kernel"] = [st["adj_ver"], st["adj_bx"], st["adj_by"], st["adj_zlen"]]
+    # ver, bx, by, zlen, vec, pf: the CKFWI_TILE_FWD / CKFWI_TILE_ADJ form
+    out["fwd_kernel"] = [st["fwd_ver"], st["fwd_bx"], st["fwd_by"], st["fwd_zlen"], st["fwd_vec"], st["fwd_pf"]]
+    out["adj_kernel"] = [st["adj_ver"], st["adj_bx"], st["adj_by"], st["adj_zlen"], st["adj_vec"], st["adj_pf"]]
     # codec on a wavefield-like field: the last forward state of the shot
     x = torch.from_numpy((vel - vel.mean()) * 1e-2).cuda()
     for _ in range(args.reps):

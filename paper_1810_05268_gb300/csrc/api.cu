@@ -644,6 +644,76 @@ void* rptr(ckfwi_model* m, int mode, const Role& r)
     }
 }
 
+// CKFWI_DEBUG=1 (read at the start of every gradient call): before every
+// step launch the executor checks on the host that each field the step reads
+// or writes lies inside the allocation its role names, and that the fields it
+// writes are none of those it reads; a violation is CKFWI_EINVAL with a
+// message on stderr, and nothing is launched.
+bool debug_env()
+{
+    const char* v = std::getenv("CKFWI_DEBUG");
+    return v && *v && std::strcmp(v, "0") != 0;
+}
+
+// The allocation that holds role r (base, bytes) and its element size;
+// false for a role index outside its kind's range.
+bool role_extent(const ckfwi_model* m, int mode, const Role& r, const char** base, size_t* bytes, size_t* es)
+{
+    *es = 4;
+    const DevMem* d = nullptr;
+    switch (r.kind) {
+    case R_ZERO: d = &m->zero; break;
+    case R_WORK: if (r.idx < 0 || r.idx >= 3) return false; d = &m->work[r.idx]; break;
+    case R_LAM: if (r.idx < 0 || r.idx >= 3) return false; d = &m->lam[r.idx]; break;
+    case R_UN: d = &m->uN; break;
+    case R_TRAJ: if (r.idx < 0) return false; d = &m->traj; break;
+    case R_HSTAGE: if (r.idx < 0 || r.idx >= 3 || r.which < 0 || r.which > 1) return false;
+        d = &m->hstage[r.idx][r.which]; break;
+    case R_HREST: if (r.idx < 0 || r.idx >= 2 || r.which < 0 || r.which > 1) return false;
+        d = &m->hrest[r.idx][r.which]; break;
+    case R_SLOT:
+        if (r.idx < 1 || r.which < 0 || r.which > 1) return false;
+        *es = mode == CKFWI_STORE_FP32 ? 4 : 2;
+        if (r.idx <= m->host_slots) {
+            *base = static_cast<const char*>(m->hpool.d);
+            *bytes = m->hpool.bytes;
+            return *base != nullptr;
+        }
+        d = &m->pool;
+        break;
+    default: return false;
+    }
+    *base = static_cast<const char*>(d->p);
+    *bytes = d->bytes;
+    return *base != nullptr;
+}
+
+// CKFWI_OK when the padded field of role r, whose element (0,0,0) is at p,
+// lies inside r's allocation; else CKFWI_EINVAL and a message
+int check_field(const ckfwi_model* m, int mode, const Role& r, const void* p, const char* what)
+{
+    const char* base = nullptr;
+    size_t bytes = 0, es = 4;
+    bool ok = role_extent(m, mode, r, &base, &bytes, &es);
+    if (ok) {
+        const char* start = static_cast<const char*>(p) - (size_t)m->fg.origin * es;
+        ok = start >= base && start + field_bytes(m->fg, es) <= base + bytes;
+    }
+    if (!ok)
+        std::fprintf(stderr, "ckfwi debug: %s (role %d, index %d, field %d) is outside its allocation\n", what,
+                     r.kind, r.idx, r.which);
+    return ok ? CKFWI_OK : CKFWI_EINVAL;
+}
+
+// CKFWI_EINVAL and a message when the written role w is the read role r
+int check_distinct(const Role& w, const Role& r, const char* what)
+{
+    if (w.kind == R_NONE || w != r) return CKFWI_OK;
+    std::fprintf(stderr, "ckfwi debug: %s (role %d, index %d, field %d) is both read and written\n", what, w.kind,
+                 w.idx, w.which);
+    return CKFWI_EINVAL;
+}
+
 struct Ctx {
     ckfwi_model* m;                 // the model (lane 0 of a batch)
     cudaStream_t st;
@@ -659,6 +729,7 @@ struct Ctx {
     int rest_fields[2] = {0, 0};    // and how many of its fields
     bool rest_pf[2] = {false, false};   // that copy is a prefetch on the copy stream (event ev_pf[r])
     int rk = 0;                     // the restore pair the next unprefetched restore takes
+    bool debug = debug_env();       // host checks of every step's fields (CKFWI_DEBUG)
     // batch: every stencil step is one launch over all lanes
     std::vector<ckfwi_model*> lanes;   // empty: the model alone
     bool batch = false;
@@ -844,6 +915,21 @@ int fwd_step(Ctx& cx, const Role& u, const Role& up, const Role& out, int n, boo
         a.src.series = m->shot.wavelet.as<float>() + n;
         a.ck_u = cx.ptr(l, ck_u);
         a.ck_up = cx.ptr(l, ck_up);
+        if (cx.debug) {
+            ST_TRY(check_field(m, CKFWI_STORE_FP32, u, a.u, "forward step: u^n"));
+            ST_TRY(check_field(m, CKFWI_STORE_FP32, up, a.up, "forward step: u^{n-1}"));
+            ST_TRY(check_field(m, CKFWI_STORE_FP32, out, a.out, "forward step: u^{n+1}"));
+            for (const Role* r : {&u, &up}) {
+                ST_TRY(check_distinct(out, *r, "forward step: u^{n+1}"));
+                ST_TRY(check_distinct(ck_u, *r, "forward step: checkpoint u^s"));
+                ST_TRY(check_distinct(ck_up, *r, "forward step: checkpoint u^{s-1}"));
+            }
+            if (ck != CK_NONE) {
+                const int cm = ck == CK_FP32 ? CKFWI_STORE_FP32 : CKFWI_STORE_FP16;
+                if (ck != CK_FP32) ST_TRY(check_field(m, cm, ck_u, a.ck_u, "forward step: checkpoint u^s"));
+                ST_TRY(check_field(m, cm, ck_up, a.ck_up, "forward step: checkpoint u^{s-1}"));
+            }
+        }
         const Tile& t = cx.batch ? cx.bf : m->tf;
         const int zlen = cx.batch ? cx.zf[l] : m->tf.zlen;
         bool sep = false;
@@ -911,6 +997,15 @@ int adj_step(Ctx& cx, const Role& l1, const Role& l2, const Role& l0, const Role
         a.l2 = cx.fptr(l, l2);
         a.l0 = cx.fptr(l, l0);
         a.u = cx.ptr(l, u);
+        if (cx.debug) {
+            ST_TRY(check_field(m, CKFWI_STORE_FP32, l1, a.l1, "reverse step: lambda^j"));
+            ST_TRY(check_field(m, CKFWI_STORE_FP32, l2, a.l2, "reverse step: lambda^{j+1}"));
+            ST_TRY(check_field(m, CKFWI_STORE_FP32, l0, a.l0, "reverse step: lambda^{j-1}"));
+            ST_TRY(check_field(m, utype == U_FP32 ? CKFWI_STORE_FP32 : CKFWI_STORE_FP16, u, a.u,
+                               "reverse step: u^{j-1}"));
+            ST_TRY(check_distinct(l0, l1, "reverse step: lambda^{j-1}"));
+            ST_TRY(check_distinct(l0, l2, "reverse step: lambda^{j-1}"));
+        }
         a.adj = m->shot.adj.view;
         a.adj.series = m->shot.resid.as<float>() + (size_t)j * m->shot.nrec;
         a.src = m->shot.src.view;

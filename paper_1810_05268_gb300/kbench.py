@@ -1,8 +1,11 @@
 """Kernel-level driver: forward modelling, a store-all gradient and a codec
-round trip on one synthetic 3D model, through the C-ABI.  Used for timing
-and ncu captures of single kernels on a chosen grid.
+round trip on one synthetic 3D model, through the C-ABI; optionally a
+gradient with FP16 checkpoints (the up-cast kernel) and a batched gradient
+over several shots (the batched step kernels).  Used for timing and ncu
+captures of single kernels on a chosen grid.
 
   python -m paper_1810_05268_gb300.kbench --shape 256,256,256 --so 8 --nt 12
+  python -m paper_1810_05268_gb300.kbench --shape 128,128,128 --nt 12 --fp16 --batch 4
 """
 import argparse
 import json
@@ -24,6 +27,8 @@ def main():
     ap.add_argument("--tol", type=float, default=1e-4)
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--time-order", type=int, default=2, help="2: OT2 kernel, 4: OT4 kernel")
+    ap.add_argument("--fp16", action="store_true", help="also a gradient with FP16 checkpoints (4 slots)")
+    ap.add_argument("--batch", type=int, default=0, help="also a batched gradient over this many shots")
     args = ap.parse_args()
     build.build()
     shape = tuple(int(v) for v in args.shape.split(","))
@@ -56,6 +61,21 @@ def main():
     # ver, bx, by, zlen, vec, pf: the CKFWI_TILE_FWD / CKFWI_TILE_ADJ form
     out["fwd_kernel"] = [st["fwd_ver"], st["fwd_bx"], st["fwd_by"], st["fwd_zlen"], st["fwd_vec"], st["fwd_pf"]]
     out["adj_kernel"] = [st["adj_ver"], st["adj_bx"], st["adj_by"], st["adj_zlen"], st["adj_vec"], st["adj_pf"]]
+    if args.fp16:
+        # Revolve with FP16 checkpoints: every restore up-casts u^s (and u^{s-1})
+        _, _, st16 = m.adjoint_gradient(shot, dobs, ckpt_slots=min(4, args.nt), store_mode=C.STORE_FP16,
+                                        profile=True)
+        out["fp16_upcast_us"] = st16["decomp_ms"] * 1e3 / max(1, st16["decomp_calls"])
+    if args.batch > 0:
+        # shots along y; one launch per stencil step over all lanes
+        shots = [C.ShotSpec(src=(2 * args.h, float(y), ext[2] / 2), rec=rec, f0=0.02, t0=25.0)
+                 for y in np.linspace(0.2 * ext[1], 0.8 * ext[1], args.batch)]
+        dl = [m.forward_shot(s) * 1.01 for s in shots]
+        for _ in range(args.reps):
+            _, _, stb = m.batch_gradient(shots, dl, min(4, args.nt), store_mode=C.STORE_FP16, profile=True)
+        out["batch_fwd_us"] = stb["fwd_ms"] * 1e3 / stb["fwd_launches"]
+        out["batch_adj_us"] = stb["adj_ms"] * 1e3 / stb["adj_launches"]
+        out["batch_kernels"] = [stb["fwd_ver"], stb["adj_ver"]]
     # codec on a wavefield-like field: the last forward state of the shot
     x = torch.from_numpy((vel - vel.mean()) * 1e-2).cuda()
     for _ in range(args.reps):

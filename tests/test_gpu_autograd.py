@@ -75,7 +75,8 @@ def test_gradient_directional_derivative_by_finite_differences():
             fm = float(A.misfit(m0 - eps * dm, m, shots, dd, ckpt_slots=260))
         rel[eps] = abs((fp - fm) / (2 * eps) - an) / abs(an)
     print("central differences against the adjoint: relative difference %s" % rel)
-    assert rel[0.5] <= 2e-2 and rel[0.2] <= 2e-2, rel
+    # measured on a GB300: 2.2e-4 and 2.9e-4
+    assert rel[0.5] <= 1e-3 and rel[0.2] <= 1e-3, rel
 
 
 def test_backward_scales_with_grad_output():

@@ -138,7 +138,10 @@ def test_half_precision_checkpoints(mode):
     e32 = rel_l2(g32.cpu().numpy(), g_ref)
     eh = rel_l2(gh.cpu().numpy(), g_ref)
     print("%s checkpoints: gradient rel-L2 vs oracle %.3e (fp32 %.3e)" % (mode, eh, e32))
-    assert eh < 5e-2
+    # measured on a GB300: 3.34e-2 (bfloat16, 8 significant bits) and 4.09e-3
+    # (binary16, 11 bits), against 1.1e-6 with FP32 checkpoints
+    assert eh < {"bf16": 4e-2, "fp16": 6e-3}[mode]
+    assert e32 < 1e-5
     assert st["p"] > 0
 
 

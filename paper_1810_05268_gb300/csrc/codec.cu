@@ -34,21 +34,22 @@
 // GPU layout of the work: one thread encodes / decodes one block; a warp
 // owns one chunk, so block bit offsets inside a chunk come from a warp scan
 // of the size table.  Compression runs in two launches:
-//  1. encode: every thread codes its block into its own shared-memory
-//     column; the warp assembles its chunk's bits contiguously in shared
-//     memory and writes them to the chunk's staging slot in scratch, with the
-//     chunk's word count, which it also adds to the sums of its group of 32
-//     and of 1024 chunks;
-//  2. compact: a CTA per group of 32 chunks copies them from staging to the
-//     payload at offsets formed from at most (chunks / 1024) + 31 group sums
-//     and a warp scan of the group's counts (linear total work); CTA 0 writes
-//     the header, the last CTA resets the group sums.
+//  1. encode: every thread codes its block through its own shared-memory
+//     column into its own area of the chunk's staging slot in scratch; the
+//     warp assembles its chunk's bits contiguously in shared memory and
+//     writes them back over the slot, with the chunk's word count, which it
+//     also adds to the sums of its group of 32 and of 1024 chunks;
+//  2. compact: a small CTA per 4 chunks copies them from staging to the
+//     payload at offsets formed from at most (chunks / 1024) + 62 group sums
+//     and chunk counts (linear total work); CTA 0 writes the header, the
+//     last CTA resets the group sums.
 // The pool position of a stream is read from and written to device memory,
 // so a schedule of compressions and decompressions runs without host
 // synchronisation; running out of pool raises an error bit and the stream
 // is not written.  The scratch's counter and group sums must be zero before
 // the first compression; every compression leaves them zero.
 #include <cstdint>
+#include <utility>
 
 #include "codec_common.cuh"
 
@@ -62,22 +63,19 @@ constexpr int DEC_THREADS = 128;
 
 
 
-// Bit writer into this thread's shared column (stride ENC_THREADS): words
-// 0 .. V-1 in the column, word V (the last of a raw-size stream) in a
-// register; bits past that are counted but not stored (such a stream is
-// replaced by the raw form).
+// Bit writer into a block's stream area in global memory (MAXW contiguous
+// words, in the chunk's staging slot); words past MAXW are counted but not
+// stored (such a stream is replaced by the raw form).
 template <int DIMS>
 struct BitW {
-    static constexpr int V = Cfg<DIMS>::V;
+    static constexpr int MW = Cfg<DIMS>::MAXW;
     uint32_t* w;
     unsigned long long acc;
     int nacc;
     int nw;
-    uint32_t last;
     __device__ __forceinline__ void store(uint32_t v)
     {
-        if (nw < V) w[nw * ENC_THREADS] = v;
-        else if (nw == V) last = v;
+        if (nw < MW) w[nw] = v;
         ++nw;
     }
     __device__ __forceinline__ void put(uint32_t v, int n)   // n <= 32, v < 2^n
@@ -113,65 +111,102 @@ __device__ __forceinline__ unsigned long long low_mask(int n)
     return n >= 64 ? ~0ull : ((1ull << n) - 1ull);
 }
 
+// Row (lz, ly) of block bp (2D: row lz), the partial block's clamped samples
+template <int DIMS>
+__device__ __forceinline__ void load_row(const float* __restrict__ x, const CodecView& v, const BlockPos& bp,
+                                         bool vec, int lz, int ly, float (&f)[4])
+{
+    const int xs = 4 * bp.bx;
+    const int z = min(4 * bp.bz + lz, v.nz - 1);
+    const int y = DIMS == 3 ? min(4 * bp.by + ly, v.ny - 1) : 0;
+    const float* row = x + (long long)z * v.pz + (long long)y * v.py;
+    if (vec) {
+        const float4 q = __ldg(reinterpret_cast<const float4*>(row + xs));
+        f[0] = q.x; f[1] = q.y; f[2] = q.z; f[3] = q.w;
+    } else {
+#pragma unroll
+        for (int c = 0; c < 4; ++c) f[c] = __ldg(row + min(xs + c, v.nx - 1));
+    }
+}
+
 // Raw form of a block: bits 1, 1, then the V float bit patterns, 32 bits
 // each, LSB first; value i occupies bits 2 + 32 i .. 33 + 32 i, so word k
 // holds the top two bits of value k-1 and the low 30 bits of value k.
-// Words 0 .. V-1 go to the thread's column, word V is returned.
+// Words 0 .. V go to the block's stream area.
 template <int DIMS>
-__device__ __forceinline__ uint32_t raw_block(const float* __restrict__ x, const CodecView& v, const BlockPos& bp,
-                                              uint32_t* __restrict__ col)
+__device__ __forceinline__ void raw_block(const float* __restrict__ x, const CodecView& v, const BlockPos& bp,
+                                          uint32_t* __restrict__ gs)
 {
     constexpr int ROWS = DIMS == 3 ? 16 : 4;
-    const int xs = 4 * bp.bx;
     uint32_t prev = 3u;      // the two header bits (as the "top bits" of value -1: 3 >> 30 would drop them)
     bool first = true;
 #pragma unroll 1
     for (int r = 0; r < ROWS; ++r) {
-        const int lz = DIMS == 3 ? r / 4 : r;
-        const int ly = DIMS == 3 ? r % 4 : 0;
-        const int z = min(4 * bp.bz + lz, v.nz - 1);
-        const int y = DIMS == 3 ? min(4 * bp.by + ly, v.ny - 1) : 0;
-        const float* row = x + (long long)z * v.pz + (long long)y * v.py;
+        float f[4];
+        load_row<DIMS>(x, v, bp, false, DIMS == 3 ? r / 4 : r, DIMS == 3 ? r % 4 : 0, f);
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
-            const uint32_t g = __float_as_uint(__ldg(row + min(xs + c, v.nx - 1)));
-            const int k = 4 * r + c;
-            col[k * ENC_THREADS] = (first ? prev : (prev >> 30)) | (g << 2);
+            const uint32_t g = __float_as_uint(f[c]);
+            gs[4 * r + c] = (first ? prev : (prev >> 30)) | (g << 2);
             first = false;
             prev = g;
         }
     }
-    return prev >> 30;
+    gs[Cfg<DIMS>::V] = prev >> 30;
 }
 
+// Shared-column offset of the coefficient of sequency rank R (a
+// compile-time constant; ranks past V read row 0, never used)
+template <int DIMS, int R>
+__device__ __forceinline__ uint32_t at_rank(const uint32_t* col)
+{
+    constexpr int i = R < Cfg<DIMS>::V ? make_perm(DIMS).p[R < 64 ? R : 0] : 0;
+    return R < Cfg<DIMS>::V ? col[i * ENC_THREADS] : 0u;
+}
+template <int DIMS, int H, int... R>
+__device__ __forceinline__ void gather_ranks(uint32_t (&m)[32], const uint32_t* col, std::integer_sequence<int, R...>)
+{
+    ((m[R] = at_rank<DIMS, 32 * H + R>(col)), ...);
+}
 
-// sequency order: coefficient index of rank r
+// Row of plane p of half h (see step 5 of encode_block)
 __constant__ Perm c_perm3 = make_perm(3);
-__constant__ Perm c_perm2 = make_perm(2);
-template <int DIMS> __device__ __forceinline__ int perm_of(int r) { return DIMS == 3 ? c_perm3.p[r] : c_perm2.p[r]; }
+template <int DIMS> __device__ __forceinline__ int plane_row(int h, int p)
+{
+    return DIMS == 3 ? c_perm3.p[32 * h + p] : p;
+}
+template <int DIMS, int H, int R>
+__device__ __forceinline__ void put_plane(uint32_t v, uint32_t* col)
+{
+    constexpr int row = DIMS == 3 ? make_perm(3).p[32 * H + R] : R;
+    col[row * ENC_THREADS] = v;
+}
+template <int DIMS, int H, int... R>
+__device__ __forceinline__ void scatter_planes(const uint32_t (&m)[32], uint32_t* col, std::integer_sequence<int, R...>)
+{
+    (put_plane<DIMS, H, R>(m[R], col), ...);
+}
 
-// Encode block b; returns its bit count, with the stream's words 0 .. V-1 in
-// this thread's col column and word V in *last.  The block is processed in
+// Encode block b; returns its bit count, with the stream in gs (the block's
+// area of the chunk's staging slot, 16-byte aligned).  The block is processed in
 // four z slices (2D: four rows) so that only one slice's values are held in
 // registers outside the closed-loop search, which keeps the code small and
-// the register count low.  siv and col are this thread's two columns of
-// shared memory (stride ENC_THREADS): col holds the slice values, then the
-// transformed coefficients (natural order, as negabinary), then the coded
-// stream; siv the integers before the transform, then the bit-plane words
-// (plane p of the first 32 coefficients in sequency order at row p, of the
-// next 32 at row 32 + p).
+// the register count low.  col is this thread's one column of shared memory
+// (stride ENC_THREADS): the slice values, then the transformed coefficients
+// (natural order, as negabinary), then the bit-plane words (step 5).  The
+// closed loop's reference integers wait in gs until the stream overwrites
+// them, so one shared column a thread suffices (half the shared memory of
+// keeping them there too, twice the warps an SM holds).
 template <int DIMS>
 __device__ __forceinline__ int encode_block(const float* __restrict__ x, const CodecView& v, const Geo& G,
-                                            float tol_f, long long b, int32_t* siv, uint32_t* col, uint32_t* last,
+                                            float tol_f, long long b, uint32_t* col, uint32_t* __restrict__ gs,
                                             int* err)
 {
     constexpr int V = Cfg<DIMS>::V;
     constexpr int SL = V / 4;                 // values per slice
     constexpr int S = ENC_THREADS;
     const BlockPos bp = block_pos(G, b);
-    const int xs = 4 * bp.bx;
-    const bool vec = v.aligned && xs + 3 < v.nx;
-    *last = 0u;
+    const bool vec = v.aligned && 4 * bp.bx + 3 < v.nx;
     // 1. gather, finiteness and max |x|
     float amax = 0.0f;
     bool bad = false;
@@ -179,17 +214,8 @@ __device__ __forceinline__ int encode_block(const float* __restrict__ x, const C
     for (int sl = 0; sl < 4; ++sl) {
 #pragma unroll
         for (int ly = 0; ly < SL / 4; ++ly) {
-            const int z = min(4 * bp.bz + sl, v.nz - 1);
-            const int y = DIMS == 3 ? min(4 * bp.by + ly, v.ny - 1) : 0;
-            const float* row = x + (long long)z * v.pz + (long long)y * v.py;
             float f[4];
-            if (vec) {
-                const float4 q = __ldg(reinterpret_cast<const float4*>(row + xs));
-                f[0] = q.x; f[1] = q.y; f[2] = q.z; f[3] = q.w;
-            } else {
-#pragma unroll
-                for (int c = 0; c < 4; ++c) f[c] = __ldg(row + min(xs + c, v.nx - 1));
-            }
+            load_row<DIMS>(x, v, bp, vec, sl, ly, f);
 #pragma unroll
             for (int c = 0; c < 4; ++c) {
                 bad |= !isfinite(f[c]);
@@ -200,7 +226,7 @@ __device__ __forceinline__ int encode_block(const float* __restrict__ x, const C
     }
     if (bad) atomicOr(err, 1);
     if (bad || amax <= tol_f) {
-        col[0] = 0u;                          // the single 0 bit
+        gs[0] = 0u;                           // the single 0 bit
         return 1;
     }
     // block exponent: that of the largest magnitude (float order is exponent order)
@@ -212,7 +238,7 @@ __device__ __forceinline__ int encode_block(const float* __restrict__ x, const C
     const int sc = 23 - emax;
     const int sa = min(sc, 127);
     const float s1 = pow2f(sa), s2 = pow2f(sc - sa);
-    // 2. integers (kept in siv for the closed loop), lifts along x and y
+    // 2. integers (kept in the block's stream area for the closed loop), lifts along x and y
 #pragma unroll 1
     for (int sl = 0; sl < 4; ++sl) {
         int32_t c[SL];
@@ -220,8 +246,10 @@ __device__ __forceinline__ int encode_block(const float* __restrict__ x, const C
         for (int k = 0; k < SL; ++k) {
             const float f = __uint_as_float(col[(SL * sl + k) * S]);
             c[k] = __float2int_rz(__fmul_rn(__fmul_rn(f, s1), s2));
-            siv[(SL * sl + k) * S] = c[k];
         }
+#pragma unroll
+        for (int k = 0; k < SL; k += 4)        // the closed loop's reference
+            *reinterpret_cast<int4*>(gs + SL * sl + k) = make_int4(c[k], c[k + 1], c[k + 2], c[k + 3]);
 #pragma unroll
         for (int r = 0; r < SL / 4; ++r) lift_fwd(c[4 * r], c[4 * r + 1], c[4 * r + 2], c[4 * r + 3]);
         if constexpr (DIMS == 3) {
@@ -260,16 +288,44 @@ __device__ __forceinline__ int encode_block(const float* __restrict__ x, const C
             int32_t t[V];
 #pragma unroll
             for (int i = 0; i < V; ++i) t[i] = unnega(col[i * S] & mask);
-            xform_inv<DIMS>(t);
-            // keep the comparison's shared loads after the transform: hoisted
-            // above it they would hold 64 more registers
-            asm volatile("" ::: "memory");
+            // the inverse transform's lifts along z first (they mix the
+            // slices), then slice by slice the lifts within it and the
+            // comparison, leaving at the first slice that fails (the lifts
+            // are those of xform_inv, in an order that changes no result)
+            if constexpr (DIMS == 3) {
+#pragma unroll
+                for (int r = 0; r < 16; ++r) lift_inv(t[r], t[16 + r], t[32 + r], t[48 + r]);
+            } else {
+#pragma unroll
+                for (int xx = 0; xx < 4; ++xx) lift_inv(t[xx], t[4 + xx], t[8 + xx], t[12 + xx]);
+            }
             // |i - t| <= T - 2 as one unsigned comparison (|i|, |t| < 2^26,
             // T <= 2^24 because max|x| > tol)
             const uint32_t lim = (uint32_t)(T - 2);
             bool ok = true;
 #pragma unroll
-            for (int i = 0; i < V; ++i) ok &= (uint32_t)(siv[i * S] - t[i]) + lim <= 2u * lim;
+            for (int sl = 0; sl < 4; ++sl) {
+                int32_t* u = t + SL * sl;
+                if constexpr (DIMS == 3) {
+#pragma unroll
+                    for (int xx = 0; xx < 4; ++xx) lift_inv(u[xx], u[4 + xx], u[8 + xx], u[12 + xx]);
+#pragma unroll
+                    for (int r = 0; r < 4; ++r) lift_inv(u[4 * r], u[4 * r + 1], u[4 * r + 2], u[4 * r + 3]);
+                } else {
+                    lift_inv(u[0], u[1], u[2], u[3]);
+                }
+                // the reference loads of one slice at a time, after its lifts
+                asm volatile("" ::: "memory");
+#pragma unroll
+                for (int k = 0; k < SL; k += 4) {
+                    const int4 r = *reinterpret_cast<const int4*>(gs + SL * sl + k);
+                    ok &= (uint32_t)(r.x - u[k]) + lim <= 2u * lim;
+                    ok &= (uint32_t)(r.y - u[k + 1]) + lim <= 2u * lim;
+                    ok &= (uint32_t)(r.z - u[k + 2]) + lim <= 2u * lim;
+                    ok &= (uint32_t)(r.w - u[k + 3]) + lim <= 2u * lim;
+                }
+                if (!ok) break;
+            }
             if (ok) {
                 pbot = p;
                 break;
@@ -277,26 +333,32 @@ __device__ __forceinline__ int encode_block(const float* __restrict__ x, const C
         }
     }
     if (pbot >= 0) {
-        // 5. bit-plane words: sequency-ordered coefficients, transposed 32 at a time
+        // 5. bit-plane words: sequency-ordered coefficients, transposed 32 at
+        // a time.  3D: plane p of half h goes to the row of the coefficient
+        // of rank 32 h + p (free once its half has been read, and never an
+        // input of the other half); 2D: the one half's plane p to row p.
         asm volatile("" ::: "memory");
-#pragma unroll 1
-        for (int h = 0; h < (V + 31) / 32; ++h) {
+        {
             uint32_t m[32];
-#pragma unroll
-            for (int r = 0; r < 32; ++r) m[r] = (32 * h + r < V) ? col[perm_of<DIMS>(32 * h + r) * S] : 0u;
+            gather_ranks<DIMS, 0>(m, col, std::make_integer_sequence<int, 32>{});
             transpose32(m);
-#pragma unroll
-            for (int q = 0; q < 32; ++q) siv[(32 * h + q) * S] = (int32_t)m[q];
+            scatter_planes<DIMS, 0>(m, col, std::make_integer_sequence<int, 32>{});
         }
-        // 6. the stream, into the col column (the coefficients are no longer needed)
+        if constexpr (V > 32) {
+            uint32_t m[32];
+            gather_ranks<DIMS, 1>(m, col, std::make_integer_sequence<int, 32>{});
+            transpose32(m);
+            scatter_planes<DIMS, 1>(m, col, std::make_integer_sequence<int, 32>{});
+        }
+        // 6. the stream, into the block's area of the staging slot
         asm volatile("" ::: "memory");
-        BitW<DIMS> bw{col, 0ull, 0, 0, 0u};
+        BitW<DIMS> bw{gs, 0ull, 0, 0};
         bw.put(1u | ((uint32_t)(emax + 127) << 2) | ((uint32_t)ptop << 10) | ((uint32_t)pbot << 15), 20);
         int s = 0;
 #pragma unroll 1
         for (int p = ptop; p >= pbot; --p) {
-            unsigned long long W = (uint32_t)siv[p * S];
-            if (V > 32) W |= (unsigned long long)(uint32_t)siv[(32 + p) * S] << 32;
+            unsigned long long W = col[plane_row<DIMS>(0, p) * S];
+            if (V > 32) W |= (unsigned long long)col[plane_row<DIMS>(1, p) * S] << 32;
             bw.put64(W & low_mask(s), s);
             while (s < V) {
                 const unsigned long long rest = s < 64 ? W >> s : 0ull;
@@ -316,24 +378,22 @@ __device__ __forceinline__ int encode_block(const float* __restrict__ x, const C
             }
             if (bw.nw > V) break;             // longer than raw already
         }
-        if (bw.bits() <= Cfg<DIMS>::MAXBITS) {
-            const int nb = bw.flush();
-            *last = bw.last;
-            return nb;
-        }
+        if (bw.bits() <= Cfg<DIMS>::MAXBITS) return bw.flush();
         // longer than raw: the raw form replaces it
     }
-    *last = raw_block<DIMS>(x, v, bp, col);
+    raw_block<DIMS>(x, v, bp, gs);
     return Cfg<DIMS>::MAXBITS;
 }
 
 // One thread per block; each warp owns one 32-block chunk.  After its
-// blocks are coded, the warp assembles the chunk's bits contiguously in its
-// part of the siv array (plus two words of xtra), writes them to the chunk's
-// staging slot and its word count, and adds the count to the sums of its
-// groups of 32 and of 1024 chunks (the compaction's offsets).
+// blocks are coded (each into its own area of the chunk's staging slot),
+// the warp assembles the chunk's bits contiguously in its part of the
+// shared columns (plus two words of xtra), writes them back over the
+// staging slot, writes its word count, and adds the count to the sums of
+// its groups of 32 and of 1024 chunks (the compaction's offsets).
+constexpr int ENC_MIN_CTAS = 10;
 template <int DIMS>
-__global__ void __launch_bounds__(ENC_THREADS, 7) enc_kernel(const float* __restrict__ x, CodecView v,
+__global__ void __launch_bounds__(ENC_THREADS, ENC_MIN_CTAS) enc_kernel(const float* __restrict__ x, CodecView v,
                                                           Geo G, float tol_f, uint32_t* __restrict__ scratch,
                                                           uint32_t* __restrict__ out, const long long* base_word,
                                                           long long cap_words, int* err)
@@ -341,8 +401,8 @@ __global__ void __launch_bounds__(ENC_THREADS, 7) enc_kernel(const float* __rest
     constexpr int V = Cfg<DIMS>::V;
     constexpr int CWD = V > 32 ? V : 32;       // plane words need 32 rows even in 2D
     constexpr int S = ENC_THREADS;
-    __shared__ int32_t siv[CWD * ENC_THREADS];
-    __shared__ uint32_t colw[V * ENC_THREADS];
+    constexpr int MW = Cfg<DIMS>::AREA;
+    __shared__ uint32_t colw[CWD * ENC_THREADS];
     __shared__ uint32_t xtra[ENC_THREADS / 32][4];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const long long b = (long long)blockIdx.x * ENC_THREADS + threadIdx.x;
@@ -354,13 +414,14 @@ __global__ void __launch_bounds__(ENC_THREADS, 7) enc_kernel(const float* __rest
     const ScratchLayout L = scratch_layout(G);
     uint16_t* sizes = reinterpret_cast<uint16_t*>(out + base + HDR + G.nchunks);
     if (b == 0 && (G.nblocks & 1)) sizes[G.nblocks] = 0;
+    const long long c = b / CHUNK;
+    uint32_t* stage = scratch + L.stage + c * L.cw;          // dereferenced only for c < nchunks
+    uint32_t* gs = stage + (b % CHUNK) * MW;
     int nbits = 0;
-    uint32_t last = 0u;
     if (b < G.nblocks) {
-        nbits = encode_block<DIMS>(x, v, G, tol_f, b, siv + threadIdx.x, colw + threadIdx.x, &last, err);
+        nbits = encode_block<DIMS>(x, v, G, tol_f, b, colw + threadIdx.x, gs, err);
         sizes[b] = (uint16_t)nbits;
     }
-    const long long c = b / CHUNK;
     if (c >= G.nchunks) return;                // whole warp
     __syncwarp();
     int incl = nbits;
@@ -372,16 +433,15 @@ __global__ void __launch_bounds__(ENC_THREADS, 7) enc_kernel(const float* __rest
     const int totb = __shfl_sync(0xffffffffu, incl, 31);
     const int off = incl - nbits;
     const int words = (totb + 31) / 32;
-    // word j of the chunk: row j / 32, this warp's column j % 32 of siv (32 CWD
-    // words), then xtra
-    uint32_t* sv = reinterpret_cast<uint32_t*>(siv) + 32 * wid;
+    // word j of the chunk: row j / 32, this warp's column j % 32 of the
+    // shared columns (32 CWD words), then xtra
+    uint32_t* sv = colw + 32 * wid;
     auto bufw = [&](int j) -> uint32_t* { return j < 32 * CWD ? sv + (j >> 5) * S + (j & 31) : &xtra[wid][j - 32 * CWD]; };
     for (int k = lane; k < words; k += 32) *bufw(k) = 0u;
     __syncwarp();
     const int sw = (nbits + 31) / 32;
-    const uint32_t* cw = colw + threadIdx.x;
     for (int k = 0; k < sw; ++k) {
-        uint32_t val = k < V ? cw[k * S] : last;
+        uint32_t val = gs[k];
         const int rem = nbits - 32 * k;
         if (rem < 32) val &= (1u << rem) - 1u;
         const int pos = off + 32 * k;
@@ -389,8 +449,8 @@ __global__ void __launch_bounds__(ENC_THREADS, 7) enc_kernel(const float* __rest
         atomicOr(bufw(idx), val << sh);
         if (sh) atomicOr(bufw(idx + 1), val >> (32 - sh));
     }
+    // every block's stream has been read: the slot takes the assembled chunk
     __syncwarp();
-    uint32_t* stage = scratch + L.stage + c * L.cw;
     for (int k = lane; k < words; k += 32) stage[k] = *bufw(k);
     if (lane == 0) {
         scratch[L.counts + c] = (uint32_t)words;
@@ -399,17 +459,18 @@ __global__ void __launch_bounds__(ENC_THREADS, 7) enc_kernel(const float* __rest
     }
 }
 
-// Compaction: a CTA moves one group of 32 chunks from their staging slots
-// to the payload.  Its payload offset is the sum of the whole groups of 1024
-// chunks before it and of the groups of 32 before it inside its group of
-// 1024 (at most chunks / 1024 + 31 values, linear total work); the chunks'
-// offsets inside the group come from a warp scan of their counts, and the
-// group's words are copied by all threads at once.  The sums
-// of the groups of 1024 also give the stream's total, which decides the
+// Compaction: a 128-thread CTA moves CPB consecutive chunks from their
+// staging slots to the payload.  Its payload offset is the sum of the whole
+// groups of 1024 chunks before it, of the groups of 32 before it inside its
+// group of 1024, and of the chunks before it inside its group of 32 (at most
+// chunks / 1024 + 62 values, all loaded at once; linear total work).  The
+// sums of the groups of 1024 also give the stream's total, which decides the
 // overflow (nothing is written) and, in CTA 0, the header, the pool's next
 // word and the statistics.  The last CTA to finish reading the sums (a
 // counter, no waiting) sets them back to zero for the next compression.
-constexpr int CMP_THREADS = 512;
+// Small CTAs spread the copy over every SM.
+constexpr int CMP_THREADS = 128;
+constexpr int CPB = 4;
 
 template <int DIMS>
 __global__ void __launch_bounds__(CMP_THREADS) compact_kernel(uint32_t* __restrict__ out, const long long* base_word,
@@ -419,7 +480,7 @@ __global__ void __launch_bounds__(CMP_THREADS) compact_kernel(uint32_t* __restri
 {
     constexpr int NW = CMP_THREADS / 32;
     __shared__ long long red[2][NW];
-    __shared__ uint32_t offs[CHUNK + 1];
+    __shared__ uint32_t offs[CPB + 1];
     __shared__ int s_last;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const long long base = *base_word;
@@ -432,24 +493,23 @@ __global__ void __launch_bounds__(CMP_THREADS) compact_kernel(uint32_t* __restri
     const uint32_t* counts = scratch + L.counts;
     uint32_t* g1 = scratch + L.g1;
     uint32_t* g2 = scratch + L.g2;
-    const long long grp = blockIdx.x, c0 = grp * CHUNK;
+    const long long c0 = (long long)blockIdx.x * CPB;
+    const long long q2 = c0 >> 10, q1 = c0 >> 5;
     long long before = 0, total = 0;
     for (long long i = threadIdx.x; i < ng2; i += CMP_THREADS) {
         const uint32_t w = g2[i];
         total += w;
-        if (i < (grp >> 5)) before += w;
+        if (i < q2) before += w;
     }
-    for (long long g = ((grp >> 5) << 5) + threadIdx.x; g < grp; g += CMP_THREADS) before += g1[g];
-    if (wid == 0) {                                    // offsets of the group's chunks
-        const uint32_t w = c0 + lane < G.nchunks ? counts[c0 + lane] : 0u;
-        uint32_t incl = w;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
-            if (lane >= o) incl += t;
+    for (long long g = (q2 << 5) + threadIdx.x; g < q1; g += CMP_THREADS) before += g1[g];
+    for (long long k = (q1 << 5) + threadIdx.x; k < c0; k += CMP_THREADS) before += counts[k];
+    if (threadIdx.x == 0) {                            // offsets of this CTA's chunks
+        uint32_t o = 0;
+        for (int k = 0; k < CPB; ++k) {
+            offs[k] = o;
+            if (c0 + k < G.nchunks) o += counts[c0 + k];
         }
-        offs[lane] = incl - w;
-        if (lane == 31) offs[CHUNK] = incl;
+        offs[CPB] = o;
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -503,22 +563,21 @@ __global__ void __launch_bounds__(CMP_THREADS) compact_kernel(uint32_t* __restri
         if (stat_words) atomicAdd(stat_words, (unsigned long long)(G.table_words + total));
     }
     if (end > cap_words) return;                       // overflow: nothing is written
-    if (threadIdx.x < CHUNK && c0 + threadIdx.x < G.nchunks) {
+    if (threadIdx.x < CPB && c0 + threadIdx.x < G.nchunks) {
         const int k = threadIdx.x;
         if (offs[k + 1] - offs[k] > (uint32_t)L.cw) atomicOr(err, 4);   // not a count the encoder can write
         hdr[HDR + c0 + k] = (uint32_t)(prefix + offs[k]);
     }
-    // the group's chunks are contiguous in the payload: every thread copies
-    // words of it, finding each word's chunk by a binary search of the
-    // offsets (all loads independent, so their latencies overlap)
-    const uint32_t gw = offs[CHUNK];
+    // the CTA's chunks are contiguous in the payload: every thread copies
+    // words of them (all loads independent, so their latencies overlap)
+    const uint32_t gw = offs[CPB];
     uint32_t* payload = out + base + G.table_words + prefix;
     const uint32_t* stage = scratch + L.stage + c0 * L.cw;
     for (uint32_t w = threadIdx.x; w < gw; w += CMP_THREADS) {
         int lo = 0;
 #pragma unroll
-        for (int st = CHUNK / 2; st > 0; st >>= 1)
-            if (offs[lo + st] <= w) lo += st;
+        for (int k = 1; k < CPB; ++k)
+            if (offs[k] <= w) lo = k;
         payload[w] = stage[(long long)lo * L.cw + (w - offs[lo])];
     }
 }
@@ -537,7 +596,7 @@ __device__ __forceinline__ unsigned long long peek64(const uint32_t* __restrict_
 }
 
 template <int DIMS>
-__global__ void __launch_bounds__(DEC_THREADS) dec_kernel(const uint32_t* __restrict__ in, const long long* base_word,
+__global__ void __launch_bounds__(DEC_THREADS, 5) dec_kernel(const uint32_t* __restrict__ in, const long long* base_word,
                                                           long long cap_words, Geo G, CodecView v,
                                                           float* __restrict__ x, int* err)
 {
@@ -617,15 +676,25 @@ __global__ void __launch_bounds__(DEC_THREADS) dec_kernel(const uint32_t* __rest
                 pos += s;
             }
             while (s < V) {
+                // one look at the group test and the run after it; a run
+                // longer than the 63 bits past the test takes a second look
                 const unsigned long long t = peek64(payload, pos, pw);
-                pos += 1;
-                if (!(t & 1ull)) break;
-                const unsigned long long look = peek64(payload, pos, pw);
-                if (look == 0ull) { corrupt = true; break; }
-                const int z = __ffsll((long long)look) - 1;
+                if (!(t & 1ull)) {
+                    pos += 1;
+                    break;
+                }
+                unsigned long long look = t >> 1;
+                int z;
+                if (look != 0ull) {
+                    z = __ffsll((long long)look) - 1;
+                } else {
+                    look = peek64(payload, pos + 1, pw);
+                    if (look == 0ull) { corrupt = true; break; }
+                    z = __ffsll((long long)look) - 1;
+                }
                 if (s + z >= V) { corrupt = true; break; }
                 W |= 1ull << (s + z);
-                pos += z + 1;
+                pos += z + 2;
                 s += z + 1;
             }
             if (pos > end) corrupt = true;
@@ -701,7 +770,7 @@ cudaError_t codec_compress_dev(const float* x, const CodecView& v, float tol_f, 
     const Geo G = make_geo(v.dims, v.nz, v.ny, v.nx);
     uint32_t* sc = static_cast<uint32_t*>(scratch);
     const unsigned eb = (unsigned)((G.nblocks + ENC_THREADS - 1) / ENC_THREADS);
-    const unsigned cb = (unsigned)((G.nchunks + CHUNK - 1) / CHUNK);
+    const unsigned cb = (unsigned)((G.nchunks + CPB - 1) / CPB);
     if (v.dims == 3) {
         enc_kernel<3><<<eb, ENC_THREADS, 0, s>>>(x, v, G, tol_f, sc, out, base_word, cap_words, err);
         compact_kernel<3><<<cb, CMP_THREADS, 0, s>>>(out, base_word, cap_words, next_word, G, tol_f, sc, err,

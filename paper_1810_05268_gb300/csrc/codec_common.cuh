@@ -17,7 +17,8 @@ constexpr int CHUNK = 32;
 template <int DIMS> struct Cfg {
     static constexpr int V = DIMS == 3 ? 64 : 16;
     static constexpr int MAXBITS = 2 + 32 * V;
-    static constexpr int MAXW = (MAXBITS + 31) / 32;       // scratch words per block
+    static constexpr int MAXW = (MAXBITS + 31) / 32;       // words of the longest block stream
+    static constexpr int AREA = (MAXW + 3) / 4 * 4;        // a block's staging area (16-byte multiple)
 };
 
 struct Geo {
@@ -42,7 +43,8 @@ __host__ __device__ inline Geo make_geo(int dims, int nz, int ny, int nx)
 // finished compaction CTAs, the payload words of every group of 1024 chunks
 // and of every group of 32 chunks (accumulated by the encoder, read and
 // reset to zero by the compaction), each chunk's word count, and each
-// chunk's bits assembled contiguously (at most CW words a chunk).
+// chunk's staging slot of CW = 32 AREA words (first the blocks' own streams,
+// AREA words apart, then the chunk's bits assembled contiguously).
 struct ScratchLayout {
     long long g2, g1, counts, stage, words;
     int cw;
@@ -51,8 +53,7 @@ constexpr ScratchLayout scratch_layout_for(int dims, long long nchunks)
 {
     ScratchLayout L{};
     const long long ng1 = (nchunks + 31) / 32, ng2 = (nchunks + 1023) / 1024;
-    const int maxbits = dims == 3 ? Cfg<3>::MAXBITS : Cfg<2>::MAXBITS;
-    L.cw = (CHUNK * maxbits + 31) / 32;
+    L.cw = CHUNK * (dims == 3 ? Cfg<3>::AREA : Cfg<2>::AREA);
     L.g2 = 32;
     L.g1 = L.g2 + ng2;
     L.counts = (L.g1 + ng1 + 31) / 32 * 32;

@@ -79,7 +79,7 @@ extern "C" {
 #define CKFWI_POOL_OVERFLOW -3  /* compressed checkpoints exceeded the pool */
 #define CKFWI_NONFINITE -4      /* NaN/Inf met, or FP16 checkpoint overflow */
 #define CKFWI_CORRUPT -5        /* compressed stream failed its checks */
-#define CKFWI_TIMEOUT -6        /* reserved: a bounded device wait gave up */
+#define CKFWI_TIMEOUT -6        /* a bounded device wait gave up */
 #define CKFWI_ECUDA -7          /* a CUDA runtime call failed */
 
 #define CKFWI_HOST 0
@@ -227,7 +227,8 @@ CKFWI_API int ckfwi_misfit(ckfwi_model* m, const ckfwi_shot* s, const float* d_o
  * host) receives the counters.  Synchronises the stream before returning
  * (the misfit and error flags are read back).  POOL_OVERFLOW if compressed
  * checkpoints outgrow pool_bytes; NONFINITE for NaN/Inf in a checkpoint;
- * CORRUPT if a stored stream fails its checks. */
+ * CORRUPT if a stored stream fails its checks; TIMEOUT if a TMA kernel's
+ * bounded plane wait gave up. */
 CKFWI_API int ckfwi_adjoint_gradient(ckfwi_model* m, const ckfwi_shot* s, const float* d_obs, int mem,
                            const ckfwi_grad_opts* opts, double* misfit, float* grad,
                            ckfwi_stats* stats, void* stream);
@@ -319,7 +320,8 @@ CKFWI_API int ckfwi_multistage_schedule(int nt, int slots, int host_slots, int32
  * ckfwi_codec_compress: x (device, float32 dense [nz][ny][nx]) -> out
  *   (device uint32, cap words); *used_words (host) receives the stream
  *   length; *flags (host) bit0 = NONFINITE.  Synchronous.  Uses scratch
- *   memory the library allocates and keeps per device.
+ *   memory the library allocates and keeps per device.  POOL_OVERFLOW if
+ *   cap is too small.
  * ckfwi_codec_decompress: stream (device) -> x (device).  Synchronous;
  *   CORRUPT if a check fails. */
 CKFWI_API long long ckfwi_codec_bound_words(int dims, int nz, int ny, int nx);

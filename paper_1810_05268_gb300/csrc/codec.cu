@@ -207,21 +207,18 @@ __device__ __forceinline__ int encode_block(const float* __restrict__ x, const C
     constexpr int S = ENC_THREADS;
     const BlockPos bp = block_pos(G, b);
     const bool vec = v.aligned && 4 * bp.bx + 3 < v.nx;
-    // 1. gather, finiteness and max |x|
+    // 1. finiteness and max |x| over the block's rows (the values are read
+    // again, from the caches, in step 2)
     float amax = 0.0f;
     bool bad = false;
-#pragma unroll 1
-    for (int sl = 0; sl < 4; ++sl) {
 #pragma unroll
-        for (int ly = 0; ly < SL / 4; ++ly) {
-            float f[4];
-            load_row<DIMS>(x, v, bp, vec, sl, ly, f);
+    for (int r = 0; r < V / 4; ++r) {
+        float f[4];
+        load_row<DIMS>(x, v, bp, vec, DIMS == 3 ? r / 4 : r, DIMS == 3 ? r % 4 : 0, f);
 #pragma unroll
-            for (int c = 0; c < 4; ++c) {
-                bad |= !isfinite(f[c]);
-                amax = fmaxf(amax, fabsf(f[c]));
-                col[(SL * sl + 4 * ly + c) * S] = __float_as_uint(f[c]);
-            }
+        for (int c = 0; c < 4; ++c) {
+            bad |= !isfinite(f[c]);
+            amax = fmaxf(amax, fabsf(f[c]));
         }
     }
     if (bad) atomicOr(err, 1);
@@ -243,9 +240,11 @@ __device__ __forceinline__ int encode_block(const float* __restrict__ x, const C
     for (int sl = 0; sl < 4; ++sl) {
         int32_t c[SL];
 #pragma unroll
-        for (int k = 0; k < SL; ++k) {
-            const float f = __uint_as_float(col[(SL * sl + k) * S]);
-            c[k] = __float2int_rz(__fmul_rn(__fmul_rn(f, s1), s2));
+        for (int ly = 0; ly < SL / 4; ++ly) {
+            float f[4];
+            load_row<DIMS>(x, v, bp, vec, sl, ly, f);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) c[4 * ly + q] = __float2int_rz(__fmul_rn(__fmul_rn(f[q], s1), s2));
         }
 #pragma unroll
         for (int k = 0; k < SL; k += 4)        // the closed loop's reference
@@ -290,8 +289,9 @@ __device__ __forceinline__ int encode_block(const float* __restrict__ x, const C
             for (int i = 0; i < V; ++i) t[i] = unnega(col[i * S] & mask);
             // the inverse transform's lifts along z first (they mix the
             // slices), then slice by slice the lifts within it and the
-            // comparison, leaving at the first slice that fails (the lifts
-            // are those of xform_inv, in an order that changes no result)
+            // comparison (the lifts are those of xform_inv, in an order that
+            // changes no result; leaving at the first failing slice was
+            // slower: the branch costs spills)
             if constexpr (DIMS == 3) {
 #pragma unroll
                 for (int r = 0; r < 16; ++r) lift_inv(t[r], t[16 + r], t[32 + r], t[48 + r]);
@@ -324,7 +324,6 @@ __device__ __forceinline__ int encode_block(const float* __restrict__ x, const C
                     ok &= (uint32_t)(r.z - u[k + 2]) + lim <= 2u * lim;
                     ok &= (uint32_t)(r.w - u[k + 3]) + lim <= 2u * lim;
                 }
-                if (!ok) break;
             }
             if (ok) {
                 pbot = p;

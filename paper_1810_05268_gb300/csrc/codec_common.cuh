@@ -180,6 +180,15 @@ struct BlockPos { int bz, by, bx; };
 __device__ __forceinline__ BlockPos block_pos(const Geo& G, long long b)
 {
     BlockPos p;
+    if (G.nblocks <= 0xFFFFFFFFll) {
+        // 32-bit division (a 64-bit one costs several times as many instructions)
+        const unsigned ub = (unsigned)b, nbx = (unsigned)G.nbx, nby = (unsigned)G.nby;
+        const unsigned t = ub / nbx, bz = t / nby;
+        p.bx = (int)(ub - t * nbx);
+        p.by = (int)(t - bz * nby);
+        p.bz = (int)bz;
+        return p;
+    }
     p.bx = (int)(b % G.nbx);
     const long long t = b / G.nbx;
     p.by = (int)(t % G.nby);

@@ -13,7 +13,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libckfwi.so")
-SOURCES = ["kernels.cu", "batch.cu", "stencil_tma.cu", "stencil_v3.cu", "batch_v3.cu", "stencil_v4.cu", "stencil_v5.cu", "ot4.cu", "ot4_v3.cu", "codec.cu", "codec_rate.cu", "aux.cu", "api.cu", "revolve.cpp", "noalloc.cu"]
+SOURCES = ["kernels.cu", "batch.cu", "stencil_tma.cu", "stencil_v3.cu", "batch_v3.cu", "stencil_v4.cu", "stencil_v5.cu", "stencil_tq.cu", "ot4.cu", "ot4_v3.cu", "codec.cu", "codec_rate.cu", "aux.cu", "api.cu", "revolve.cpp", "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "--expt-relaxed-constexpr", "-Xcompiler", "-fPIC",
          "-Xcompiler", "-fvisibility=hidden", "-I", os.path.join(HERE, "..", "include")]

@@ -948,7 +948,21 @@ int fwd_step(Ctx& cx, const Role& u, const Role& up, const Role& out, int n, boo
             continue;
         }
         const int tok = cx.begin(PC_FWD);
-        if (m->tf.ver == 7) {
+        if (m->tf.ver == 8) {
+            if (in_host(m, u) || in_host(m, up)) {
+                // tensor maps cover device memory only: the async-copy kernel of the same tile
+                Tile t4 = m->tf;
+                t4.ver = 4;
+                t4.pf = m->K <= 4 ? 1 : 0;
+                CK_TRY(launch_fwd4(a, t4, m->K, ck, cx.st));
+            } else {
+                CUtensorMap tu, tp, tw;
+                ST_TRY(tensor_map(m, a.u, U_FP32, tq_box_x(m->K), tq_box_y(m->K), &tu));
+                ST_TRY(tensor_map(m, a.up, U_FP32, 32, 16, &tp));
+                ST_TRY(tensor_map(m, a.w, U_FP32, 32, 16, &tw));
+                CK_TRY(launch_fwdq(a, tu, tp, tw, m->tf, m->K, ck, cx.st));
+            }
+        } else if (m->tf.ver == 7) {
             CK_TRY(launch_fwd5(a, m->tf, m->K, ck, cx.st));
         } else if (m->tf.ver >= 5) {
             ST_TRY(ot4_fwd_step(m, a, m->tf, ck, cx.st));
@@ -1202,6 +1216,10 @@ int autotune(ckfwi_model* m, cudaStream_t st)
                     t7.pf = np;
                     if (v5_supported(f.dims, m->K, t7)) cands.push_back(t7);
                 }
+                Tile t8 = v3_tile_at(i, z);     // the forward step fed by tensor copies
+                t8.ver = 8;
+                t8.pf = 1;
+                if (encode_fn() && tq_supported(f.dims, m->K, t8)) cands.push_back(t8);
             }
         }
     }
@@ -1242,7 +1260,14 @@ int autotune(ckfwi_model* m, cudaStream_t st)
     const int reps = 3;
     CUtensorMap tm_u, tm_l;
     auto go = [&](const Tile& t, int pass) -> int {
-        if (t.ver == 7) {
+        if (t.ver == 8) {
+            if (pass != 0) return CKFWI_EINVAL;     // a forward step only
+            CUtensorMap tu, tp, tw;
+            ST_TRY(tensor_map(m, a.u, U_FP32, tq_box_x(m->K), tq_box_y(m->K), &tu));
+            ST_TRY(tensor_map(m, a.up, U_FP32, 32, 16, &tp));
+            ST_TRY(tensor_map(m, a.w, U_FP32, 32, 16, &tw));
+            CK_TRY(launch_fwdq(a, tu, tp, tw, t, m->K, CK_NONE, st));
+        } else if (t.ver == 7) {
             if (pass == 0) CK_TRY(launch_fwd5(a, t, m->K, CK_NONE, st));
             else CK_TRY(launch_adj5(b, t, m->K, U_FP32, st));
         } else if (t.ver >= 5) {
@@ -1276,7 +1301,8 @@ int autotune(ckfwi_model* m, cudaStream_t st)
         if (nf < 5) u.vec = 1;
         if (nf < 6) u.pf = 0;
         if ((u.ver == 5 || u.ver == 6) != (m->ot == 4)) return false;
-        const bool okv = u.ver == 7   ? v5_supported(f.dims, m->K, u) && v3_fits(f, m->K)
+        const bool okv = u.ver == 8   ? !reverse && tma_ok && tq_supported(f.dims, m->K, u) && v3_fits(f, m->K)
+                         : u.ver == 7 ? v5_supported(f.dims, m->K, u) && v3_fits(f, m->K)
                          : u.ver == 6 ? ot4v_supported(f.dims, m->K, u, reverse) && v3_fits(f, m->K)
                          : u.ver == 5 ? ot4_supported(f.dims, m->K, u)
                          : u.ver == 4 ? v4_supported(f.dims, m->K, u) && v3_fits(f, m->K)
@@ -1316,8 +1342,10 @@ int autotune(ckfwi_model* m, cudaStream_t st)
         // more rounds (single timings of ~100 us launches vary by several %)
         std::vector<std::pair<float, size_t>> t1;
         for (size_t i = 0; i < cands.size(); ++i) {
-            // vector-blocked OT4 reverse steps come in one vector width only
+            // vector-blocked OT4 reverse steps come in one vector width only;
+            // the tensor-copy generation has a forward step only
             if (cands[i].ver == 6 && !ot4v_supported(f.dims, m->K, cands[i], pass == 1)) continue;
+            if (cands[i].ver == 8 && pass == 1) continue;
             ST_TRY(go(cands[i], pass));
             float ms = 0;
             ST_TRY(time_of(cands[i], pass, 3, &ms));

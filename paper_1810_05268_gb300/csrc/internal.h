@@ -137,7 +137,8 @@ struct Tile {
                           // 3: vector-blocked kernels (3D), 4: vector-blocked forward step fed
                           // by asynchronous copies (3D), 5: the two-pass OT4 kernels,
                           // 6: the same vector-blocked (3D), 7: the lean async-copy
-                          // OT2 kernels (3D, one or two planes per step)
+                          // OT2 kernels (3D, one or two planes per step), 8: the
+                          // forward step fed by tensor copies (3D)
     int vec = 1;          // ver 3, 4: x points per thread (2 or 4)
     int pf = 0;           // ver 4: planes of prefetch (0 = the default, 2); ver 7: planes per step (1, 2)
 };
@@ -210,6 +211,14 @@ bool tma_supported(int dims, int K, int ty);
 cudaError_t launch_fwd_tma(const FwdArgs& a, const CUtensorMap& tmu, const Tile& t, int K, int ck, cudaStream_t s);
 cudaError_t launch_adj_tma(const AdjArgs& a, const CUtensorMap& tml, const CUtensorMap& tmu, const Tile& t, int K,
                            int ut, cudaStream_t s);
+// stencil_tq.cu: the forward step fed by tensor copies (Tile.ver 8; geometry
+// must pass v3_fits; tu: box tq_box_x x tq_box_y of u, tp / tw: 32 x 16 of
+// u^{n-1} / w, maps of the padded device allocations)
+bool tq_supported(int dims, int K, const Tile& t);
+int tq_box_x(int K);
+int tq_box_y(int K);
+cudaError_t launch_fwdq(const FwdArgs& a, const CUtensorMap& tu, const CUtensorMap& tp, const CUtensorMap& tw,
+                        const Tile& t, int K, int ck, cudaStream_t s);
 
 // aux.cu
 cudaError_t launch_sample(const float* u, const Sample& smp, cudaStream_t s);

@@ -1,4 +1,4 @@
-"""The three generations of 3D stencil kernels agree bit for bit.
+"""The generations of 3D stencil kernels agree bit for bit.
 
 The TMA-fed kernels (stencil_tma.cu) and the vector-blocked kernels
 (stencil_v3.cu) perform the same FP32 operations in the same order as the
@@ -32,8 +32,8 @@ def _run(case, fwd_tile, adj_tile, dobs, slots, mode="fp32"):
         m = C.Model(case.pg)
         m.set_model(torch.from_numpy(case.vel).cuda())
         d = m.forward_shot(case.shot()).cpu().numpy()
-        phi, g, _ = m.adjoint_gradient(case.shot(), dobs, ckpt_slots=slots, store_mode=mode)
-        out = (d, phi, g.cpu().numpy())
+        phi, g, st = m.adjoint_gradient(case.shot(), dobs, ckpt_slots=slots, store_mode=mode)
+        out = (d, phi, g.cpu().numpy(), st)
         m.close()
         return out
     finally:
@@ -124,6 +124,29 @@ def test_async_copy_forward_bitwise_equal_register_queue(so, shape, vec, mode):
         assert np.array_equal(got[0], ref[0])
         assert got[1] == ref[1]
         assert np.array_equal(got[2], ref[2])
+
+
+@pytest.mark.parametrize("so,shape", [(2, (30, 37, 70)), (4, (33, 41, 131)), (8, (35, 43, 70)), (8, (26, 29, 200)),
+                                      (16, (36, 41, 77)), (4, (21, 19, 13))])
+@pytest.mark.parametrize("mode", ["fp32", "fp16"])
+def test_tensor_copy_forward_bitwise_equal_register_queue(so, shape, mode):
+    """The forward step fed by tensor copies (generation 8) with z runs of
+    one plane, several planes and the whole column, paired with reverse
+    steps of other generations; the forced tile must be the one that ran."""
+    case = make_case(3, so, shape, nbl=6, nt=70, seed=so + 11)
+    rng = np.random.default_rng(so + 2)
+    dobs = torch.from_numpy((rng.standard_normal((71, case.rec.shape[0])) * 1e-3).astype(np.float32)).cuda()
+    k = so // 2
+    by1 = max(8, k)
+    ref = _run(case, "1,32,%d,9" % by1, "1,32,%d,9" % by1, dobs, 5, mode)
+    tiles = [("8,32,16,%d,4" % z, "3,32,16,9,4") for z in (1, 7, 64)]
+    tiles.append(("8,32,16,9,4", "7,32,16,9,4,1"))
+    for tf, ta in tiles:
+        got = _run(case, tf, ta, dobs, 5, mode)
+        assert got[3]["fwd_ver"] == 8, (tf, ta)
+        assert np.array_equal(got[0], ref[0]), (tf, ta)
+        assert got[1] == ref[1], (tf, ta)
+        assert np.array_equal(got[2], ref[2]), (tf, ta)
 
 
 @pytest.mark.parametrize("so,shape", [(2, (30, 37, 70)), (4, (33, 41, 131)), (8, (35, 43, 70)), (8, (26, 29, 200)),

@@ -1218,8 +1218,10 @@ int autotune(ckfwi_model* m, cudaStream_t st)
                 }
                 Tile t8 = v3_tile_at(i, z);     // the forward step fed by tensor copies
                 t8.ver = 8;
-                t8.pf = 1;
-                if (encode_fn() && tq_supported(f.dims, m->K, t8)) cands.push_back(t8);
+                for (int pf : {1, 2}) {
+                    t8.pf = pf;
+                    if (encode_fn() && tq_supported(f.dims, m->K, t8)) cands.push_back(t8);
+                }
             }
         }
     }

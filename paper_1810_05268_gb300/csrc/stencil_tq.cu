@@ -5,12 +5,13 @@
 // vectors of u^{n-1} and w, each with an address, a predicate and a
 // zero-fill size, and keeps those copy descriptors in registers.  Here one
 // thread issues three tensor copies a plane instead (cp.async.bulk.tensor):
-// the halo'd u tile of plane z + K + 1 and the point tiles of u^{n-1} and w
-// of plane z + 1, all completing on the mbarrier of their ring slot.  The
+// the halo'd u tile of plane z + K + D and the point tiles of u^{n-1} and w
+// of plane z + D (D = 1 or 2 planes of prefetch, Tile.pf; 0 reads as 1),
+// all completing on the mbarrier of their ring slot.  The
 // other threads only wait on that barrier.  Everything else is the
 // async-copy generation's: a 32 x 16 tile, four x points a thread, the
-// queue of 2K + 1 planes in registers fed from the ring, one plane of
-// prefetch, and the same arithmetic in the same order (lap3, leap2v), so
+// queue of 2K + 1 planes in registers fed from the ring, and the same
+// arithmetic in the same order (lap3, leap2v), so
 // the results are bitwise those of every other generation.
 //
 // The tensor maps cover the padded allocations (x from 0 to px, y and z
@@ -76,9 +77,9 @@ __device__ __forceinline__ void tile3(void* dst, const CUtensorMap* tm, int x, i
         : "memory");
 }
 
-template <int K>
+template <int K, int PF>
 struct TQ {
-    static constexpr int V = 4, TX = 8, TY = 16, D = 1;
+    static constexpr int V = 4, TX = 8, TY = 16, D = PF;
     using G = G3<K, V, TX, TY>;
     static constexpr int RU = K + D + 1;                       // u tiles in the ring
     static constexpr int RP = D + 1;                           // point tiles of each point field
@@ -96,16 +97,16 @@ __device__ __forceinline__ unsigned char* align128(unsigned char* p)
     return p + ((128u - (a & 127u)) & 127u);
 }
 
-// CTAs an SM: six at order <= 8 for the two-plane ring (as the async-copy
-// kernel), set by the register cap
-template <int K> constexpr int tq_min_blocks() { return K <= 4 ? 6 : 1; }
+// CTAs an SM at order <= 8, set by the register cap: six with one plane of
+// prefetch (31 KB of shared memory), five with two (39 KB)
+template <int K, int PF> constexpr int tq_min_blocks() { return K <= 4 ? (PF == 1 ? 6 : 5) : 1; }
 
-template <int K, int CK>
-__global__ void __launch_bounds__(128, tq_min_blocks<K>())
+template <int K, int PF, int CK>
+__global__ void __launch_bounds__(128, tq_min_blocks<K, PF>())
     fwdq_kernel(const FwdArgs a, const __grid_constant__ CUtensorMap tmu, const __grid_constant__ CUtensorMap tmp,
                 const __grid_constant__ CUtensorMap tmw)
 {
-    using Q = TQ<K>;
+    using Q = TQ<K, PF>;
     using G = typename Q::G;
     constexpr int V = Q::V, TX = Q::TX, TY = Q::TY, D = Q::D, RU = Q::RU, RP = Q::RP;
     extern __shared__ unsigned char smq_raw[];
@@ -260,31 +261,38 @@ __global__ void __launch_bounds__(128, tq_min_blocks<K>())
     }
 }
 
-template <int K, int CK>
+template <int K, int PF, int CK>
 cudaError_t fwdq_go(const FwdArgs& a, const CUtensorMap& tu, const CUtensorMap& tp, const CUtensorMap& tw,
                     cudaStream_t s)
 {
-    using Q = TQ<K>;
+    using Q = TQ<K, PF>;
     using G = typename Q::G;
     const dim3 blk(Q::TX, Q::TY, 1);
     const dim3 grd((a.g.nx + G::BXP - 1) / G::BXP, (a.g.ny + Q::TY - 1) / Q::TY, (a.g.nz + a.zlen - 1) / a.zlen);
-    cudaError_t e = cudaFuncSetAttribute(fwdq_kernel<K, CK>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Q::SMEM);
+    cudaError_t e = cudaFuncSetAttribute(fwdq_kernel<K, PF, CK>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Q::SMEM);
     if (e != cudaSuccess) return e;
-    fwdq_kernel<K, CK><<<grd, blk, Q::SMEM, s>>>(a, tu, tp, tw);
+    fwdq_kernel<K, PF, CK><<<grd, blk, Q::SMEM, s>>>(a, tu, tp, tw);
     return cudaGetLastError();
 }
 
-template <int K>
+template <int K, int PF>
 cudaError_t fwdq_k(const FwdArgs& a, const CUtensorMap& tu, const CUtensorMap& tp, const CUtensorMap& tw, int ck,
                    cudaStream_t s)
 {
     switch (ck) {
-    case CK_NONE: return fwdq_go<K, CK_NONE>(a, tu, tp, tw, s);
-    case CK_FP32: return fwdq_go<K, CK_FP32>(a, tu, tp, tw, s);
-    case CK_BF16: return fwdq_go<K, CK_BF16>(a, tu, tp, tw, s);
-    case CK_FP16: return fwdq_go<K, CK_FP16>(a, tu, tp, tw, s);
+    case CK_NONE: return fwdq_go<K, PF, CK_NONE>(a, tu, tp, tw, s);
+    case CK_FP32: return fwdq_go<K, PF, CK_FP32>(a, tu, tp, tw, s);
+    case CK_BF16: return fwdq_go<K, PF, CK_BF16>(a, tu, tp, tw, s);
+    case CK_FP16: return fwdq_go<K, PF, CK_FP16>(a, tu, tp, tw, s);
     default: return cudaErrorInvalidValue;
     }
+}
+
+template <int K>
+cudaError_t fwdq_p(const FwdArgs& a, const CUtensorMap& tu, const CUtensorMap& tp, const CUtensorMap& tw, int pf,
+                   int ck, cudaStream_t s)
+{
+    return pf == 2 ? fwdq_k<K, 2>(a, tu, tp, tw, ck, s) : fwdq_k<K, 1>(a, tu, tp, tw, ck, s);
 }
 
 }  // namespace
@@ -292,7 +300,7 @@ cudaError_t fwdq_k(const FwdArgs& a, const CUtensorMap& tu, const CUtensorMap& t
 bool tq_supported(int dims, int K, const Tile& t)
 {
     return dims == 3 && t.ver == 8 && (K == 1 || K == 2 || K == 4 || K == 8) && t.bx == 32 && t.by == 16 &&
-           t.vec == 4 && t.zlen >= 1;
+           t.vec == 4 && t.zlen >= 1 && t.pf >= 0 && t.pf <= 2;
 }
 
 int tq_box_x(int K) { return 32 + 2 * (K <= 4 ? 4 : 8); }
@@ -307,10 +315,10 @@ cudaError_t launch_fwdq(const FwdArgs& a, const CUtensorMap& tu, const CUtensorM
     FwdArgs b = a;
     b.zlen = t.zlen;
     switch (K) {
-    case 1: return fwdq_k<1>(b, tu, tp, tw, ck, s);
-    case 2: return fwdq_k<2>(b, tu, tp, tw, ck, s);
-    case 4: return fwdq_k<4>(b, tu, tp, tw, ck, s);
-    case 8: return fwdq_k<8>(b, tu, tp, tw, ck, s);
+    case 1: return fwdq_p<1>(b, tu, tp, tw, t.pf, ck, s);
+    case 2: return fwdq_p<2>(b, tu, tp, tw, t.pf, ck, s);
+    case 4: return fwdq_p<4>(b, tu, tp, tw, t.pf, ck, s);
+    case 8: return fwdq_p<8>(b, tu, tp, tw, t.pf, ck, s);
     default: return cudaErrorInvalidValue;
     }
 }

@@ -130,9 +130,10 @@ def test_async_copy_forward_bitwise_equal_register_queue(so, shape, vec, mode):
                                       (16, (36, 41, 77)), (4, (21, 19, 13))])
 @pytest.mark.parametrize("mode", ["fp32", "fp16"])
 def test_tensor_copy_forward_bitwise_equal_register_queue(so, shape, mode):
-    """The forward step fed by tensor copies (generation 8) with z runs of
-    one plane, several planes and the whole column, paired with reverse
-    steps of other generations; the forced tile must be the one that ran."""
+    """The forward step fed by tensor copies (generation 8), one or two
+    planes of prefetch, with z runs of one plane, several planes and the
+    whole column, paired with reverse steps of other generations; the
+    forced tile must be the one that ran."""
     case = make_case(3, so, shape, nbl=6, nt=70, seed=so + 11)
     rng = np.random.default_rng(so + 2)
     dobs = torch.from_numpy((rng.standard_normal((71, case.rec.shape[0])) * 1e-3).astype(np.float32)).cuda()
@@ -141,6 +142,7 @@ def test_tensor_copy_forward_bitwise_equal_register_queue(so, shape, mode):
     ref = _run(case, "1,32,%d,9" % by1, "1,32,%d,9" % by1, dobs, 5, mode)
     tiles = [("8,32,16,%d,4" % z, "3,32,16,9,4") for z in (1, 7, 64)]
     tiles.append(("8,32,16,9,4", "7,32,16,9,4,1"))
+    tiles += [("8,32,16,%d,4,2" % z, "3,32,16,9,4") for z in (1, 2, 9)]   # two planes of prefetch
     for tf, ta in tiles:
         got = _run(case, tf, ta, dobs, 5, mode)
         assert got[3]["fwd_ver"] == 8, (tf, ta)

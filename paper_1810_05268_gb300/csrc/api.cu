@@ -1448,9 +1448,6 @@ Role pick_free(const State& s)
     return NONE_R;
 }
 
-// The recorded part of a gradient: everything between "inputs staged" and
-// "outputs ready" (this is what a CUDA graph captures).  Runs every lane of
-// the context through the same schedule.
 // An NVTX range for the lifetime of the object (a no-op without a tool
 // attached), with an integer payload
 struct NvtxRange {
@@ -1471,6 +1468,9 @@ struct NvtxRange {
 };
 const char* const kActionRange[4] = {"ckfwi advance", "ckfwi takeshot", "ckfwi restore", "ckfwi youturn"};
 
+// The recorded part of a gradient: everything between "inputs staged" and
+// "outputs ready" (this is what a CUDA graph captures).  Runs every lane of
+// the context through the same schedule.
 int run_body(Ctx& cx, const RunCfg& rc, const std::vector<Action>& acts, long long* counters)
 {
     NvtxRange whole("ckfwi gradient", (long long)cx.nl());

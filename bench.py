@@ -57,7 +57,7 @@ KERNEL_NAMES = {1: ("fwd_kernel", "adj_kernel"), 2: ("fwd_tma_kernel", "adj_tma_
                 3: ("fwd3_kernel", "adj3_kernel"), 4: ("fwd4_kernel", "adj4_kernel"),
                 5: ("ot4_lap_kernel+ot4_fwd_kernel", "ot4_lap_kernel+ot4_adj_kernel"),
                 6: ("ot4v_lap_kernel+ot4v_fwd_kernel", "ot4v_lap_kernel+ot4v_fwd_kernel+ot4v_grad_kernel"),
-                7: ("fwd5_kernel", "adj5_kernel"), 8: ("fwdq_kernel", "(no reverse step)")}
+                7: ("fwd5_kernel", "adj5_kernel"), 8: ("fwdq_kernel", "fwdq_kernel+gradq_kernel")}
 # OT4 forward step (two passes): reads u^n, w and writes Z = w lap u^n, then
 # reads Z, u^n, u^{n-1}, w and writes u^{n+1}.  Reverse step (three passes):
 # reads lam^j, u^{j-1}, w, the previous Z_u and g, writes Z_l, Z_u, g; reads

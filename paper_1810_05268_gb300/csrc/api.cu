@@ -901,6 +901,21 @@ int ot4_adj_step(ckfwi_model* m, const AdjArgs& a, const Tile& t, int utype, int
 
 // One forward step n of every lane: u -> out, optionally sampling d^n and
 // writing a fused takeshot (ck, ck_u, ck_up).
+// The six tensor maps of a split reverse step (launch_adjq): lam^j with the
+// u box, lam^{j+1} and w with point boxes, u^{j-1} with the u box, lam^{j-1}
+// and g with point boxes
+int adjq_maps(ckfwi_model* m, const AdjArgs& a, CUtensorMap* mp)
+{
+    const int bx = tq_box_x(m->K), by = tq_box_y(m->K);
+    ST_TRY(tensor_map(m, a.l1, U_FP32, bx, by, &mp[0]));
+    ST_TRY(tensor_map(m, a.l2, U_FP32, 32, 16, &mp[1]));
+    ST_TRY(tensor_map(m, a.w, U_FP32, 32, 16, &mp[2]));
+    ST_TRY(tensor_map(m, a.u, U_FP32, bx, by, &mp[3]));
+    ST_TRY(tensor_map(m, a.l0, U_FP32, 32, 16, &mp[4]));
+    ST_TRY(tensor_map(m, a.gacc, U_FP32, 32, 16, &mp[5]));
+    return CKFWI_OK;
+}
+
 int fwd_step(Ctx& cx, const Role& u, const Role& up, const Role& out, int n, bool record, int ck,
              const Role& ck_u, const Role& ck_up)
 {
@@ -1030,7 +1045,18 @@ int adj_step(Ctx& cx, const Role& l1, const Role& l2, const Role& l0, const Role
             continue;
         }
         const int tok = cx.begin(PC_ADJ);
-        if (m->ta.ver == 7) {
+        if (m->ta.ver == 8 && (utype != U_FP32 || in_host(m, u))) {
+            // tensor maps cover FP32 device fields only: the lean kernel of the same tile
+            Tile t7 = m->ta;
+            t7.ver = 7;
+            t7.pf = 1;
+            CK_TRY(launch_adj5(a, t7, m->K, utype, cx.st));
+        } else if (m->ta.ver == 8) {
+            CUtensorMap mp[6];
+            ST_TRY(adjq_maps(m, a, mp));
+            CK_TRY(launch_adjq(a, mp, m->ta, m->K, cx.st));
+            ++cx.launches;
+        } else if (m->ta.ver == 7) {
             CK_TRY(launch_adj5(a, m->ta, m->K, utype, cx.st));
         } else if (m->ta.ver >= 5) {
             ST_TRY(ot4_adj_step(m, a, m->ta, utype, j, cx.st));
@@ -1262,8 +1288,11 @@ int autotune(ckfwi_model* m, cudaStream_t st)
     const int reps = 3;
     CUtensorMap tm_u, tm_l;
     auto go = [&](const Tile& t, int pass) -> int {
-        if (t.ver == 8) {
-            if (pass != 0) return CKFWI_EINVAL;     // a forward step only
+        if (t.ver == 8 && pass == 1) {
+            CUtensorMap mp[6];
+            ST_TRY(adjq_maps(m, b, mp));
+            CK_TRY(launch_adjq(b, mp, t, m->K, st));
+        } else if (t.ver == 8) {
             CUtensorMap tu, tp, tw;
             ST_TRY(tensor_map(m, a.u, U_FP32, tq_box_x(m->K), tq_box_y(m->K), &tu));
             ST_TRY(tensor_map(m, a.up, U_FP32, 32, 16, &tp));
@@ -1303,7 +1332,7 @@ int autotune(ckfwi_model* m, cudaStream_t st)
         if (nf < 5) u.vec = 1;
         if (nf < 6) u.pf = 0;
         if ((u.ver == 5 || u.ver == 6) != (m->ot == 4)) return false;
-        const bool okv = u.ver == 8   ? !reverse && tma_ok && tq_supported(f.dims, m->K, u) && v3_fits(f, m->K)
+        const bool okv = u.ver == 8   ? tma_ok && tq_supported(f.dims, m->K, u) && v3_fits(f, m->K)
                          : u.ver == 7 ? v5_supported(f.dims, m->K, u) && v3_fits(f, m->K)
                          : u.ver == 6 ? ot4v_supported(f.dims, m->K, u, reverse) && v3_fits(f, m->K)
                          : u.ver == 5 ? ot4_supported(f.dims, m->K, u)
@@ -1344,10 +1373,8 @@ int autotune(ckfwi_model* m, cudaStream_t st)
         // more rounds (single timings of ~100 us launches vary by several %)
         std::vector<std::pair<float, size_t>> t1;
         for (size_t i = 0; i < cands.size(); ++i) {
-            // vector-blocked OT4 reverse steps come in one vector width only;
-            // the tensor-copy generation has a forward step only
+            // vector-blocked OT4 reverse steps come in one vector width only
             if (cands[i].ver == 6 && !ot4v_supported(f.dims, m->K, cands[i], pass == 1)) continue;
-            if (cands[i].ver == 8 && pass == 1) continue;
             ST_TRY(go(cands[i], pass));
             float ms = 0;
             ST_TRY(time_of(cands[i], pass, 3, &ms));

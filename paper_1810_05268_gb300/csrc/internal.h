@@ -219,6 +219,11 @@ int tq_box_x(int K);
 int tq_box_y(int K);
 cudaError_t launch_fwdq(const FwdArgs& a, const CUtensorMap& tu, const CUtensorMap& tp, const CUtensorMap& tw,
                         const Tile& t, int K, int ck, cudaStream_t s);
+// the reverse step split in two launches: the lam half by fwdq_kernel (maps
+// 0-2: lam^j with the u box, lam^{j+1} and w with point boxes), then the
+// gradient half (maps 3-5: u^{j-1} with the u box, lam^{j-1} and g with
+// point boxes); FP32 u^{j-1} only
+cudaError_t launch_adjq(const AdjArgs& a, const CUtensorMap* maps, const Tile& t, int K, cudaStream_t s);
 
 // aux.cu
 cudaError_t launch_sample(const float* u, const Sample& smp, cudaStream_t s);

@@ -295,6 +295,154 @@ cudaError_t fwdq_p(const FwdArgs& a, const CUtensorMap& tu, const CUtensorMap& t
     return pf == 2 ? fwdq_k<K, 2>(a, tu, tp, tw, ck, s) : fwdq_k<K, 1>(a, tu, tp, tw, ck, s);
 }
 
+// The reverse step's gradient half: g += lam^{j-1} (lap u^{j-1} + Q^T s^{j-1}),
+// with the same ring and queue of u^{j-1} as the forward step and point
+// tiles of lam^{j-1} and g.  (The lam half, lam^{j-1} from lam^j and
+// lam^{j+1}, is the forward step's arithmetic with the adjoint injection, so
+// fwdq_kernel computes it.)  The arithmetic is the fused reverse kernels':
+// the same Laplacian and injection order and one packed FMA, so g is
+// bitwise theirs.
+template <int K, int PF>
+__global__ void __launch_bounds__(128, tq_min_blocks<K, PF>())
+    gradq_kernel(const AdjArgs a, const __grid_constant__ CUtensorMap tmu, const __grid_constant__ CUtensorMap tml,
+                 const __grid_constant__ CUtensorMap tmg)
+{
+    using Q = TQ<K, PF>;
+    using G = typename Q::G;
+    constexpr int V = Q::V, TX = Q::TX, TY = Q::TY, D = Q::D, RU = Q::RU, RP = Q::RP;
+    extern __shared__ unsigned char smq_raw[];
+    __shared__ int abort_s;
+    unsigned char* sm0 = align128(smq_raw);
+    float* ring = reinterpret_cast<float*>(sm0);
+    float* lr = ring + RU * Q::US;
+    float* gr = lr + RP * Q::PT;
+    uint64_t* bar = reinterpret_cast<uint64_t*>(gr + RP * Q::PT);
+
+    const int bxi = blockIdx.x, byi = blockIdx.y, bzi = blockIdx.z;
+    const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TX + tx;
+    const int nz = a.g.nz, ny = a.g.ny, nx = a.g.nx;
+    const int px = (int)a.g.px, pxy = (int)a.g.pxy;
+    const int xb = bxi * G::BXP, yb = byi * TY;
+    const int x0 = xb + V * tx;
+    const int y = yb + ty;
+    const int z0 = bzi * a.zlen;
+    if (z0 >= nz) return;
+    const int z1 = min(z0 + a.zlen, nz);
+    const int nstep = z1 - z0;
+    const bool rowact = y < ny;
+    const bool cload = rowact && x0 < nx;
+    const bool full = rowact && x0 + V <= nx;
+    const int col = y * px + x0;
+    const int cs = (ty + K) * G::RX + G::PX + V * tx;
+    const int ps = ty * G::BXP + V * tx;
+    Inj3<V> is;
+    is.init(a.src, y, x0, nx, rowact);
+    const int zqmax = nz + K - 1;
+    const long long rounds = a.wait_limit;
+    const float* u = static_cast<const float*>(a.u);
+
+    auto issue = [&](int g) {
+        uint64_t* b = bar + g % RU;
+        const bool pts = g >= K;
+        bar_expect(b, Q::UBYTES + (pts ? 2 * Q::PBYTES : 0));
+        tile3(ring + (g % RU) * Q::US, &tmu, xb, yb, min(z0 + g, zqmax) + K, b);
+        if (pts) {
+            const int zp = min(z0 + g - K, z1 - 1) + K, sl = (g - K) % RP;
+            tile3(lr + sl * Q::PT, &tml, xb + G::PX, yb + K, zp, b);
+            tile3(gr + sl * Q::PT, &tmg, xb + G::PX, yb + K, zp, b);
+        }
+    };
+    auto wait_group = [&](int g) { return bar_wait(bar + g % RU, (unsigned)((g / RU) & 1), rounds); };
+
+    if (tid == 0) {
+        abort_s = 0;
+        for (int sl = 0; sl < RU; ++sl) bar_init(bar + sl);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        for (int g = 0; g < K + D; ++g) issue(g);
+    }
+    __syncthreads();
+    int issued = K + D;
+    float q[2 * K + 1][V];
+#pragma unroll
+    for (int i = 0; i < K; ++i) {
+        if (cload) gld<V>(q[i], u + (z0 - K + i) * pxy + col);
+        else vzero<V>(q[i]);
+    }
+    int g0 = 0;
+    while (g0 < K && wait_group(g0)) ++g0;
+    if (g0 < K) abort_s = 1;
+    int confirmed = g0;
+#pragma unroll
+    for (int i = 0; i < K; ++i) sld<V>(q[K + i], ring + i * Q::US + cs);
+
+    for (int step = 0; step < nstep; ++step) {
+        const int z = z0 + step;
+        if (!wait_group(step + K)) abort_s = 1;
+        __syncthreads();
+        if (abort_s) break;
+        confirmed = step + K + 1;
+        if (tid == 0) issue(step + K + D);
+        issued = step + K + D + 1;
+        sld<V>(q[2 * K], ring + ((step + K) % RU) * Q::US + cs);
+        const float* sm = ring + (step % RU) * Q::US;
+        if (cload) {
+            float lv[V], gv[V];
+            sld<V>(lv, lr + (step % RP) * Q::PT + ps);
+            sld<V>(gv, gr + (step % RP) * Q::PT + ps);
+            float su[V];
+            lap3<K, V, TX, TY>(su, q, sm, tx, ty, a.c);
+            is.add(su, a.src, z);
+            float gn[V];
+#pragma unroll
+            for (int p = 0; p < V / 2; ++p) {
+                const int i = 2 * p;
+                const float2 gg = __ffma2_rn(f2(lv[i], lv[i + 1]), f2(su[i], su[i + 1]), f2(gv[i], gv[i + 1]));
+                gn[i] = gg.x;
+                gn[i + 1] = gg.y;
+            }
+            const long long o = (long long)z * pxy + col;
+            if (full) {
+                vst<V>(a.gacc + o, gn);
+            } else {
+#pragma unroll
+                for (int i = 0; i < V; ++i)
+                    if (x0 + i < nx) a.gacc[o + i] = gn[i];
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < 2 * K; ++i) {
+#pragma unroll
+            for (int k = 0; k < V; ++k) q[i][k] = q[i + 1][k];
+        }
+    }
+    if (tid == 0) {
+        bool drained = true;
+        for (int g = confirmed; g < issued; ++g) drained = wait_group(g) && drained;
+        if (abort_s || !drained) atomicOr(a.err, 8);
+    }
+}
+
+template <int K, int PF>
+cudaError_t gradq_go(const AdjArgs& a, const CUtensorMap& tu, const CUtensorMap& tl, const CUtensorMap& tg,
+                     cudaStream_t s)
+{
+    using Q = TQ<K, PF>;
+    using G = typename Q::G;
+    const dim3 blk(Q::TX, Q::TY, 1);
+    const dim3 grd((a.g.nx + G::BXP - 1) / G::BXP, (a.g.ny + Q::TY - 1) / Q::TY, (a.g.nz + a.zlen - 1) / a.zlen);
+    cudaError_t e = cudaFuncSetAttribute(gradq_kernel<K, PF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Q::SMEM);
+    if (e != cudaSuccess) return e;
+    gradq_kernel<K, PF><<<grd, blk, Q::SMEM, s>>>(a, tu, tl, tg);
+    return cudaGetLastError();
+}
+
+template <int K>
+cudaError_t gradq_p(const AdjArgs& a, const CUtensorMap& tu, const CUtensorMap& tl, const CUtensorMap& tg, int pf,
+                    cudaStream_t s)
+{
+    return pf == 2 ? gradq_go<K, 2>(a, tu, tl, tg, s) : gradq_go<K, 1>(a, tu, tl, tg, s);
+}
+
 }  // namespace
 
 bool tq_supported(int dims, int K, const Tile& t)
@@ -319,6 +467,39 @@ cudaError_t launch_fwdq(const FwdArgs& a, const CUtensorMap& tu, const CUtensorM
     case 2: return fwdq_p<2>(b, tu, tp, tw, t.pf, ck, s);
     case 4: return fwdq_p<4>(b, tu, tp, tw, t.pf, ck, s);
     case 8: return fwdq_p<8>(b, tu, tp, tw, t.pf, ck, s);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_adjq(const AdjArgs& a, const CUtensorMap* maps, const Tile& t, int K, cudaStream_t s)
+{
+    if (!v3_fits(a.g, K) || !tq_supported(a.g.dims, K, t)) return cudaErrorInvalidValue;
+    if (a.g.X0 != (K <= 4 ? 4 : 8) || a.g.H != K) return cudaErrorInvalidValue;
+    // the lam half: a forward step of the adjoint field with the adjoint injection
+    FwdArgs f{};
+    f.g = a.g;
+    f.u = a.l1;
+    f.up = a.l2;
+    f.w = a.w;
+    f.out = a.l0;
+    f.eta = a.eta;
+    f.hdt = a.hdt;
+    for (int j = 0; j <= MAXK; ++j) f.c[j] = a.c[j];
+    f.src = a.adj;
+    f.smp.n = 0;
+    f.ck_u = nullptr;
+    f.ck_up = nullptr;
+    f.err = a.err;
+    f.wait_limit = a.wait_limit;
+    cudaError_t e = launch_fwdq(f, maps[0], maps[1], maps[2], t, K, CK_NONE, s);
+    if (e != cudaSuccess) return e;
+    AdjArgs b = a;
+    b.zlen = t.zlen;
+    switch (K) {
+    case 1: return gradq_p<1>(b, maps[3], maps[4], maps[5], t.pf, s);
+    case 2: return gradq_p<2>(b, maps[3], maps[4], maps[5], t.pf, s);
+    case 4: return gradq_p<4>(b, maps[3], maps[4], maps[5], t.pf, s);
+    case 8: return gradq_p<8>(b, maps[3], maps[4], maps[5], t.pf, s);
     default: return cudaErrorInvalidValue;
     }
 }

@@ -130,10 +130,13 @@ def test_async_copy_forward_bitwise_equal_register_queue(so, shape, vec, mode):
                                       (16, (36, 41, 77)), (4, (21, 19, 13))])
 @pytest.mark.parametrize("mode", ["fp32", "fp16"])
 def test_tensor_copy_forward_bitwise_equal_register_queue(so, shape, mode):
-    """The forward step fed by tensor copies (generation 8), one or two
-    planes of prefetch, with z runs of one plane, several planes and the
-    whole column, paired with reverse steps of other generations; the
-    forced tile must be the one that ran."""
+    """Generation 8: the forward step fed by tensor copies and the reverse
+    step split into its lam half (the same kernel with the adjoint
+    injection) and its gradient half, one or two planes of prefetch, z runs
+    of one plane, several planes and the whole column, alone and paired
+    with other generations (with FP16 checkpoints the reverse step reads
+    16-bit u^{j-1} through the lean kernel); the forced tiles must be the
+    ones that ran."""
     case = make_case(3, so, shape, nbl=6, nt=70, seed=so + 11)
     rng = np.random.default_rng(so + 2)
     dobs = torch.from_numpy((rng.standard_normal((71, case.rec.shape[0])) * 1e-3).astype(np.float32)).cuda()
@@ -143,9 +146,12 @@ def test_tensor_copy_forward_bitwise_equal_register_queue(so, shape, mode):
     tiles = [("8,32,16,%d,4" % z, "3,32,16,9,4") for z in (1, 7, 64)]
     tiles.append(("8,32,16,9,4", "7,32,16,9,4,1"))
     tiles += [("8,32,16,%d,4,2" % z, "3,32,16,9,4") for z in (1, 2, 9)]   # two planes of prefetch
+    # the reverse step split in two launches (lam half by the forward kernel, gradient half)
+    tiles += [("3,32,16,9,4", "8,32,16,%d,4,%d" % (z, pf)) for z, pf in ((1, 1), (7, 1), (64, 1), (9, 2))]
+    tiles.append(("8,32,16,7,4", "8,32,16,9,4"))
     for tf, ta in tiles:
         got = _run(case, tf, ta, dobs, 5, mode)
-        assert got[3]["fwd_ver"] == 8, (tf, ta)
+        assert got[3]["fwd_ver"] == int(tf[0]) and got[3]["adj_ver"] == int(ta[0]), (tf, ta)
         assert np.array_equal(got[0], ref[0]), (tf, ta)
         assert got[1] == ref[1], (tf, ta)
         assert np.array_equal(got[2], ref[2]), (tf, ta)

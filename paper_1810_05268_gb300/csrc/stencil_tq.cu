@@ -56,6 +56,9 @@ __device__ __forceinline__ bool bar_try(uint64_t* bar, unsigned parity)
 }
 
 // bounded wait with a short back-off; rounds < 0 gives up without looking
+// (how a test makes a plane's wait run out); the drain before a CTA leaves
+// always waits with the full bound, so no copy lands after it has gone
+constexpr long long DRAIN_ROUNDS = 1LL << 22;
 __device__ __forceinline__ bool bar_wait(uint64_t* bar, unsigned parity, long long rounds)
 {
     if (rounds < 0) return false;
@@ -256,7 +259,8 @@ __global__ void __launch_bounds__(128, tq_min_blocks<K, PF>())
     // confirmed (bounded); a wait that ran out is reported
     if (tid == 0) {
         bool drained = true;
-        for (int g = confirmed; g < issued; ++g) drained = wait_group(g) && drained;
+        for (int g = confirmed; g < issued; ++g)
+            drained = bar_wait(bar + g % RU, (unsigned)((g / RU) & 1), DRAIN_ROUNDS) && drained;
         if (abort_s || !drained) atomicOr(a.err, 8);
     }
 }
@@ -417,7 +421,8 @@ __global__ void __launch_bounds__(128, tq_min_blocks<K, PF>())
     }
     if (tid == 0) {
         bool drained = true;
-        for (int g = confirmed; g < issued; ++g) drained = wait_group(g) && drained;
+        for (int g = confirmed; g < issued; ++g)
+            drained = bar_wait(bar + g % RU, (unsigned)((g / RU) & 1), DRAIN_ROUNDS) && drained;
         if (abort_s || !drained) atomicOr(a.err, 8);
     }
 }

@@ -182,24 +182,34 @@ def test_lean_kernels_bitwise_equal_register_queue(so, shape, np_, mode):
         assert np.array_equal(got[2], ref[2]), (tf, ta)
 
 
-def test_tma_wait_that_runs_out_reports_timeout():
+@pytest.mark.parametrize("tf,ta,call", [("2,64,16,2", "2,64,16,2", "forward"),
+                                        ("8,32,16,7,4,1", "3,32,16,9,4", "forward"),
+                                        ("3,32,16,9,4", "8,32,16,7,4,1", "gradient")])
+def test_tma_wait_that_runs_out_reports_timeout(tf, ta, call):
     """A TMA kernel whose plane waits run out (CKFWI_TMA_WAIT_LIMIT < 0: the
-    waits give up at once, the copies in flight are still drained) reports
-    CKFWI_TIMEOUT; the device stays usable and the next model is exact."""
+    waits give up at once, the copies in flight are still drained with the
+    full bound) reports CKFWI_TIMEOUT, in the TMA-fed generation, the
+    tensor-copy forward step and the split reverse step; the device stays
+    usable and the next model is exact."""
     case = make_case(3, 8, (35, 43, 70), nbl=6, nt=40, seed=9)
+    zeros = torch.zeros((41, case.rec.shape[0]), device="cuda")
     os.environ["CKFWI_TMA_WAIT_LIMIT"] = "-1"
-    os.environ["CKFWI_TILE_FWD"] = "2,64,16,2"
-    os.environ["CKFWI_TILE_ADJ"] = "2,64,16,2"
+    os.environ["CKFWI_TILE_FWD"] = tf
+    os.environ["CKFWI_TILE_ADJ"] = ta
     try:
         m = C.Model(case.pg)
         m.set_model(torch.from_numpy(case.vel).cuda())
         with pytest.raises(C.CkfwiError) as e:
-            m.forward_shot(case.shot())
+            if call == "forward":
+                m.forward_shot(case.shot())
+            else:
+                m.adjoint_gradient(case.shot(), zeros, ckpt_slots=5)
         assert e.value.status == C.TIMEOUT
         m.close()
     finally:
         for k in ("CKFWI_TMA_WAIT_LIMIT", "CKFWI_TILE_FWD", "CKFWI_TILE_ADJ"):
             del os.environ[k]
-    ref = _run(case, "1,32,8,9", "1,32,8,9", torch.zeros((41, case.rec.shape[0]), device="cuda"), 5)
-    got = _run(case, "2,64,16,2", "2,64,16,2", torch.zeros((41, case.rec.shape[0]), device="cuda"), 5)
+    ref = _run(case, "1,32,8,9", "1,32,8,9", zeros, 5)
+    got = _run(case, tf, ta, zeros, 5)
     assert np.array_equal(got[0], ref[0])
+    assert np.array_equal(got[2], ref[2])

@@ -1,18 +1,21 @@
-// Forward step with TMA-fed rings and a register z queue (3D, Tile.ver 8).
+// Stencil steps fed by tensor copies, with a register z queue (3D,
+// Tile.ver 8): the forward step, and the reverse step split into its
+// lambda half (the same forward kernel on the adjoint field with the
+// adjoint injection) and its gradient half (gradq_kernel).
 //
 // The async-copy generation (stencil_v4.cu) has every thread issue its own
 // copies of a plane: its vector of the u tile, at most one halo vector, its
 // vectors of u^{n-1} and w, each with an address, a predicate and a
 // zero-fill size, and keeps those copy descriptors in registers.  Here one
 // thread issues three tensor copies a plane instead (cp.async.bulk.tensor):
-// the halo'd u tile of plane z + K + D and the point tiles of u^{n-1} and w
-// of plane z + D (D = 1 or 2 planes of prefetch, Tile.pf; 0 reads as 1),
-// all completing on the mbarrier of their ring slot.  The
-// other threads only wait on that barrier.  Everything else is the
-// async-copy generation's: a 32 x 16 tile, four x points a thread, the
-// queue of 2K + 1 planes in registers fed from the ring, and the same
-// arithmetic in the same order (lap3, leap2v), so
-// the results are bitwise those of every other generation.
+// the halo'd tile of plane z + K + D of the staged field and the point
+// tiles of plane z + D (D = 1 or 2 planes of prefetch, Tile.pf; 0 reads as
+// 1), all completing on the mbarrier of their ring slot.  The other
+// threads only wait on that barrier.  Everything else is the async-copy
+// generation's: a 32 x 16 tile, four x points a thread, the queue of 2K + 1
+// planes in registers fed from the ring, and the same arithmetic in the
+// same order (lap3, leap2v, the reverse kernels' packed FMA for g), so the
+// results are bitwise those of every other generation.
 //
 // The tensor maps cover the padded allocations (x from 0 to px, y and z
 // with their H = K halo cells), so a tile's box starts at the field's
@@ -24,7 +27,8 @@
 //
 // Waits on the mbarriers are bounded; a wait that runs out raises error
 // bit 8, the CTA stops at the next plane boundary, and thread 0 waits
-// (bounded again) for every copy still in flight before the CTA leaves.
+// (with the full bound) for every copy still in flight before the CTA
+// leaves.
 #include <cuda.h>
 
 #include "stencil_v3.cuh"

@@ -105,6 +105,21 @@ def test_roofline_block_of_a_stencil_dominated_mode():
     json.dumps(r)
 
 
+def test_every_step_kernel_generation_has_a_name_and_the_chosen_ones_a_traffic_entry():
+    """The roofline names the kernel of every Tile generation the library
+    reports, and the generations the autotuner picks on the bench grid (the
+    tensor-copy forward step, the lean reverse step) carry committed DRAM
+    traffic for their tile."""
+    assert set(bench.KERNEL_NAMES) == set(range(1, 9))
+    npts = 208 ** 3
+    H = _headline()
+    H["fwd_kernel"] = [8, 32, 16, 4, 21, 1]
+    r = bench.roofline_block(H, 1000, npts, 6686.1, "measured")
+    assert r["kernel"] == "fwdq_kernel" and r["traffic"] is not None
+    assert 15.0 < r["traffic"] / npts < 18.0
+    assert bench.traffic_per_point("adj5_kernel", [7, 32, 16, 4, 21, 1]) is not None
+
+
 def test_roofline_block_of_a_codec_dominated_mode():
     npts, nt = 208 ** 3, 1000
     H = _headline(store_mode="codec", ckpt_slots=232, ratio_mean=25.0, comp_ms=500.0, comp_calls=1692)

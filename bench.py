@@ -85,15 +85,16 @@ def traffic_per_point(kernel, tile):
     try:
         with open(p) as f:
             d = json.load(f)
-        e = d[kernel]
+        entries = d[kernel] if isinstance(d[kernel], list) else [d[kernel]]
         # the same kernel, tile shape (version, x, y, points per thread) and
         # prefetch depth; the z-run length moves the halo re-reads by a few
         # percent only
         t = list(tile) + [0] * (6 - len(tile))
-        want = list(e["tile"]) + [0] * (6 - len(e["tile"]))
-        if e.get("tile") is not None and (want[:4] != t[:4] or want[5] != t[5]):
-            return None
-        return float(e["dram_bytes_per_point"])
+        for e in entries:
+            want = list(e["tile"]) + [0] * (6 - len(e["tile"]))
+            if want[:4] == t[:4] and want[5] == t[5]:
+                return float(e["dram_bytes_per_point"])
+        return None
     except (OSError, ValueError, KeyError, TypeError, IndexError):
         return None
 

@@ -9,6 +9,10 @@ checkpoint).  Its time is
 
     T(M, mode) = (p + 1) C_F + N C_R + n_c t_c + n_d t_d,
 
+where C_R is the reverse step of the FP32 run, or of the 16-bit run for the
+modes whose restores land in a working field (a 16-bit up-cast or a codec
+decode: the reverse step then reads u^s from that field),
+
 and at a memory budget of B bytes each storage mode gets the slots that fit:
 FP32 checkpoints B / S, 16-bit ones 2 (B / S - 1) + 1 (slot 0 is the initial
 state), codec ones B F / (S 1.1) with F the worst compression ratio seen.
@@ -39,7 +43,8 @@ from . import ckfwi as C
 class Costs:
     c_f: float                     # forward step [ms]
     c_r: float                     # reverse step reading FP32 checkpoints [ms]
-    c_r16: Optional[float] = None  # reverse step in a 16-bit run (reported, not used: u^s is up-cast) [ms]
+    c_r16: Optional[float] = None  # reverse step after a restore into a working field (a 16-bit
+                                   # up-cast or a codec decode), measured in the 16-bit run [ms]
     t_d16: Optional[float] = None  # up-cast of one 16-bit checkpoint field [ms]
     t_ck32: float = 0.0            # extra cost of a forward step that writes an FP32 checkpoint [ms]
     t_ck16: float = 0.0            # extra cost of a forward step that writes a 16-bit checkpoint [ms]
@@ -88,7 +93,10 @@ def predict(costs: Costs, nt, slots, mode):
     (Sec. 3-4: recomputation, storage writes and reads, compression)."""
     ev = events(nt, slots, mode)
     nf, nc, nd = ev["fwd"], ev["comp"], ev["decomp"]
-    t = nf * costs.c_f + nt * costs.c_r
+    # a reverse step whose u^s was just up-cast or decoded into a working
+    # field costs what the 16-bit run measured, where known
+    c_rev = costs.c_r16 if (mode != "fp32" and costs.c_r16 is not None) else costs.c_r
+    t = nf * costs.c_f + nt * c_rev
     if mode == "fp32":
         return t + ev["takeshots"] * costs.t_ck32
     if mode in ("fp16", "bf16"):

@@ -126,8 +126,11 @@ def test_async_copy_forward_bitwise_equal_register_queue(so, shape, vec, mode):
         assert np.array_equal(got[2], ref[2])
 
 
+# nx % 32 of the shapes: 6, 3, 6, 8, 13, 13 (a grid narrower than one tile),
+# 16, 26 and 0 (no partial tile)
 @pytest.mark.parametrize("so,shape", [(2, (30, 37, 70)), (4, (33, 41, 131)), (8, (35, 43, 70)), (8, (26, 29, 200)),
-                                      (16, (36, 41, 77)), (4, (21, 19, 13))])
+                                      (16, (36, 41, 77)), (4, (21, 19, 13)), (4, (27, 33, 80)), (8, (30, 35, 90)),
+                                      (8, (25, 40, 64))])
 @pytest.mark.parametrize("mode", ["fp32", "fp16"])
 def test_tensor_copy_forward_bitwise_equal_register_queue(so, shape, mode):
     """Generation 8: the forward step fed by tensor copies and the reverse
@@ -135,8 +138,8 @@ def test_tensor_copy_forward_bitwise_equal_register_queue(so, shape, mode):
     injection) and its gradient half, one or two planes of prefetch, z runs
     of one plane, several planes and the whole column, alone and paired
     with other generations (with FP16 checkpoints the reverse step reads
-    16-bit u^{j-1} through the lean kernel); the forced tiles must be the
-    ones that ran."""
+    16-bit u^{j-1} through the lean kernel), on grids with and without a
+    partial last x tile; the forced tiles must be the ones that ran."""
     case = make_case(3, so, shape, nbl=6, nt=70, seed=so + 11)
     rng = np.random.default_rng(so + 2)
     dobs = torch.from_numpy((rng.standard_normal((71, case.rec.shape[0])) * 1e-3).astype(np.float32)).cuda()

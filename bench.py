@@ -314,15 +314,17 @@ def time_modes(C, torch, model, shot, d_obs, modes, nt, npts, args, ws, lr, full
         # timed region: K gradients replayed from the recorded graph, CUDA
         # events on torch's stream (the library launches on that stream), max
         # over ranks
-        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         k_steps = args.steps if full is None or name in full else max(1, min(args.steps, 5))
-        ev0.record()
-        for _ in range(k_steps):
+        evs = [torch.cuda.Event(enable_timing=True) for _ in range(k_steps + 1)]
+        evs[0].record()
+        for i in range(k_steps):
             _, phi, st_plain = one(kw, False)
-        ev1.record()
+            evs[i + 1].record()
         torch.cuda.synchronize()
         clocks[name] = clk.stop()
-        ms = max_over_ranks(ev0.elapsed_time(ev1) / k_steps, "cuda")
+        ms = max_over_ranks(evs[0].elapsed_time(evs[-1]) / k_steps, "cuda")
+        # each replay's own time (this rank): the spread behind the mean
+        replay = [evs[i].elapsed_time(evs[i + 1]) for i in range(k_steps)]
         # per-kernel-class device time from profiled gradients (same work)
         sts = []
         for _ in range(max(1, min(args.steps, 3))):
@@ -332,6 +334,7 @@ def time_modes(C, torch, model, shot, d_obs, modes, nt, npts, args, ws, lr, full
         avg = lambda k: float(np.mean([s[k] for s in sts]))
         results[name] = {
             "ms": ms, "gpts": 2.0 * nt * npts / (ms / 1e3) / 1e9 * ws, "timed_steps": k_steps,
+            "replay_ms": [round(r, 2) for r in replay], "replay_ms_median": float(np.median(replay)),
             "u_absmax": st["u_absmax"],
             "ckpt_slots": kw["ckpt_slots"], "store_mode": kw["store_mode"],
             "pool_bytes": kw.get("pool_bytes", st["pool_bytes_peak"]), "host_slots": kw.get("host_slots", 0),

@@ -134,6 +134,10 @@ def roofline_block(H, nt, npts, peak, peak_kind, delta=0.0):
             "algorithmic_bytes_per_launch": b_d, "launches": n_d, "launch_us": 1e3 * per[dom],
             "event_overhead_us_per_call": 1e3 * delta,
             "traffic": (tpp * npts) if tpp is not None else None,
+            # the ncu figure is of a launch without a fused checkpoint write:
+            # compare it with that launch's algorithmic bytes
+            "traffic_basis": ("one launch without a checkpoint write (ncu), against %.0f algorithmic bytes"
+                              % ((FWD_BYTES if dom == "fwd" else ADJ_BYTES) * npts)) if tpp is not None else None,
             "class_gbs": gbs}
 
 

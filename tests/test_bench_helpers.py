@@ -101,6 +101,9 @@ def test_roofline_block_of_a_stencil_dominated_mode():
     assert r["algorithmic_bytes_per_launch"] * r["launches"] == pytest.approx(total)
     tpp = bench.traffic_per_point("fwd4_kernel", H["fwd_kernel"])
     assert tpp is not None and r["traffic"] == pytest.approx(tpp * npts)
+    # the captured traffic is of a launch without a checkpoint write: the
+    # basis names that launch's algorithmic bytes (16 B/pt)
+    assert r["traffic_basis"] and ("%.0f" % (16.0 * npts)) in r["traffic_basis"]
     assert set(r["class_gbs"]) == {"fwd", "adj", "comp", "decomp"}
     json.dumps(r)
 
@@ -108,8 +111,9 @@ def test_roofline_block_of_a_stencil_dominated_mode():
 def test_every_step_kernel_generation_has_a_name_and_the_chosen_ones_a_traffic_entry():
     """The roofline names the kernel of every Tile generation the library
     reports, and the generations the autotuner picks on the bench grid (the
-    tensor-copy forward step, the lean reverse step) carry committed DRAM
-    traffic for their tile."""
+    tensor-copy forward step with one or two planes of prefetch, the lean
+    reverse step and the split one) carry committed DRAM traffic for their
+    tile."""
     assert set(bench.KERNEL_NAMES) == set(range(1, 9))
     npts = 208 ** 3
     H = _headline()
@@ -118,6 +122,8 @@ def test_every_step_kernel_generation_has_a_name_and_the_chosen_ones_a_traffic_e
     assert r["kernel"] == "fwdq_kernel" and r["traffic"] is not None
     assert 15.0 < r["traffic"] / npts < 18.0
     assert bench.traffic_per_point("adj5_kernel", [7, 32, 16, 4, 21, 1]) is not None
+    assert bench.traffic_per_point("fwdq_kernel", [8, 32, 16, 4, 25, 2]) is not None
+    assert bench.traffic_per_point("fwdq_kernel+gradq_kernel", [8, 32, 16, 4, 25, 2]) is not None
 
 
 def test_roofline_block_of_a_codec_dominated_mode():

@@ -138,6 +138,7 @@ def roofline_block(H, nt, npts, peak, peak_kind, delta=0.0):
             # compare it with that launch's algorithmic bytes
             "traffic_basis": ("one launch without a checkpoint write (ncu), against %.0f algorithmic bytes"
                               % ((FWD_BYTES if dom == "fwd" else ADJ_BYTES) * npts)) if tpp is not None else None,
+            "traffic_basis_bytes": (FWD_BYTES if dom == "fwd" else ADJ_BYTES) * npts if tpp is not None else None,
             "class_gbs": gbs}
 
 
@@ -1143,7 +1144,8 @@ def main():
                          "achieved": round(roof["achieved"], 1), "peak": roof["peak"], "unit": "GB/s",
                          "frac": round(roof["frac"], 4), "peak_kind": roof["peak_kind"],
                          "algorithmic_bytes_per_launch": roof["algorithmic_bytes_per_launch"],
-                         "launch_us": round(roof["launch_us"], 2), "traffic": roof["traffic"]},
+                         "launch_us": round(roof["launch_us"], 2), "traffic": roof["traffic"],
+                         "traffic_basis_bytes": roof["traffic_basis_bytes"]},
             "cpu_baseline": cpu,
             "e2e": {"value": 2.0 * nt * npts / e2e_s / 1e9, "unit": "Gpt/s",
                     "h2d_bytes_per_step": int(dh.numel() * 4), "d2h_bytes_per_step": int(gh.numel() * 4 + 8)},

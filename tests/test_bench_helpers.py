@@ -104,6 +104,7 @@ def test_roofline_block_of_a_stencil_dominated_mode():
     # the captured traffic is of a launch without a checkpoint write: the
     # basis names that launch's algorithmic bytes (16 B/pt)
     assert r["traffic_basis"] and ("%.0f" % (16.0 * npts)) in r["traffic_basis"]
+    assert r["traffic_basis_bytes"] == pytest.approx(16.0 * npts)
     assert set(r["class_gbs"]) == {"fwd", "adj", "comp", "decomp"}
     json.dumps(r)
 

@@ -339,6 +339,8 @@ def time_modes(C, torch, model, shot, d_obs, modes, nt, npts, args, ws, lr, full
         avg = lambda k: float(np.mean([s[k] for s in sts]))
         results[name] = {
             "ms": ms, "gpts": 2.0 * nt * npts / (ms / 1e3) / 1e9 * ws, "timed_steps": k_steps,
+            # executed rate: every forward (recomputations included) and reverse step
+            "executed_gpts": (st["fwd_steps"] + nt) * npts / (ms / 1e3) / 1e9 * ws,
             "replay_ms": [round(r, 2) for r in replay], "replay_ms_median": float(np.median(replay)),
             "u_absmax": st["u_absmax"],
             "ckpt_slots": kw["ckpt_slots"], "store_mode": kw["store_mode"],
@@ -960,7 +962,7 @@ def one_core(name, steps):
 def compact_line(line, limit=1400):
     """The bench line as JSON of at most `limit` bytes: optional keys are
     dropped, in order, if it is longer."""
-    optional = ["oracle", "gradients_per_hour", "recompute_ratio", "clocks"]
+    optional = ["executed_gpts", "oracle", "gradients_per_hour", "recompute_ratio", "clocks"]
     out = json.dumps(line)
     for k in optional:
         if len(out) <= limit:
@@ -1153,6 +1155,7 @@ def main():
             "clocks": {"sm_mhz": clk.get("sm_mhz"), "sm_max_mhz": clk.get("sm_max_mhz"),
                        "reasons": clk.get("reasons")} if clk else None,
             "recompute_ratio": round(H["recompute_ratio"], 4),
+            "executed_gpts": round(H["executed_gpts"], 2),
             "gradients_per_hour": round(3.6e6 / H["ms"] * ws, 1),
             "oracle": {"grad_rel_err": H.get("grad_rel_err_vs_oracle"), "tol": GRAD_TOL} if oracle else None,
         }

@@ -427,7 +427,7 @@ template <int K, int TY, int CK>
 __global__ void __launch_bounds__(NTX * TY) fwd_tma_kernel(const FwdArgs a, const __grid_constant__ CUtensorMap tmu)
 {
     using RU = Ring<K, TY, float, PF_FWD>;
-    __shared__ int abort_s;
+    __shared__ int abort_s[2];   // a wait gave up at a plane step of this parity
     unsigned char* smem = align128(smem_raw);
     const unsigned base_u = (unsigned)(smem - smem_raw);
     RU R{reinterpret_cast<float*>(smem), reinterpret_cast<uint64_t*>(smem + RU::NS * RU::STRIDE)};
@@ -447,12 +447,14 @@ __global__ void __launch_bounds__(NTX * TY) fwd_tma_kernel(const FwdArgs a, cons
     const int ncx = (nx + TX - 1) / TX, ncy = (ny + TY - 1) / TY;
     Work wk;
     wk.init(ncx * ncy, ncx, nz);
-    if (tid == 0) abort_s = 0;
+    if (tid == 0) abort_s[0] = abort_s[1] = 0;
     ring_init(R, tid);
     __syncthreads();
     int kb = 0;
     int col, za, zc;
     bool ok = true;
+    bool aborted = false;        // the same in every thread: read after one barrier
+    int ph = 0;                  // parity of the plane steps so far
     while (wk.next(&col, &za, &zc)) {
         int x0, y0;
         column_of(col, ncx, TY, &x0, &y0);
@@ -528,13 +530,19 @@ __global__ void __launch_bounds__(NTX * TY) fwd_tma_kernel(const FwdArgs a, cons
                     if (__hisinf(__float2half_rn(mx))) atomicOr(a.err, 1);
                 }
             }
-            if (!ok) abort_s = 1;
+            // a thread one step ahead flags the other slot, so all threads
+            // leave at the same plane
+            if (!ok) abort_s[ph] = 1;
             __syncthreads();
-            if (abort_s) break;
+            if (abort_s[ph]) {
+                aborted = true;
+                break;
+            }
+            ph ^= 1;
             if (tid == 0) ring_refill(R, &tmu, x0, y0, z, zb, zlast, kb, H);
             W.advance();
         }
-        if (abort_s) {
+        if (aborted) {
             if (tid == 0) {
                 atomicOr(a.err, 8);
                 ring_drain(R, z, zb, zlast, kb);
@@ -551,7 +559,7 @@ __global__ void __launch_bounds__(NTX * TY) adj_tma_kernel(const AdjArgs a, cons
 {
     using RL = Ring<K, TY, float, PF_ADJ>;
     using RUu = Ring<K, TY, UT, PF_ADJ>;
-    __shared__ int abort_s;
+    __shared__ int abort_s[2];
     unsigned char* smem = align128(smem_raw);
     const unsigned base_l = (unsigned)(smem - smem_raw);
     const unsigned base_uu = base_l + RL::NS * RL::STRIDE;
@@ -563,13 +571,15 @@ __global__ void __launch_bounds__(NTX * TY) adj_tma_kernel(const AdjArgs a, cons
     const int ncx = (nx + TX - 1) / TX, ncy = (ny + TY - 1) / TY;
     Work wk;
     wk.init(ncx * ncy, ncx, nz);
-    if (tid == 0) abort_s = 0;
+    if (tid == 0) abort_s[0] = abort_s[1] = 0;
     ring_init(L, tid);
     ring_init(U, tid);
     __syncthreads();
     int kb = 0;
     int col, za, zc;
     bool ok = true;
+    bool aborted = false;        // the same in every thread: read after one barrier
+    int ph = 0;                  // parity of the plane steps so far
     while (wk.next(&col, &za, &zc)) {
         int x0, y0;
         column_of(col, ncx, TY, &x0, &y0);
@@ -649,9 +659,15 @@ __global__ void __launch_bounds__(NTX * TY) adj_tma_kernel(const AdjArgs a, cons
                 st4(a.l0 + o, make_float4(v0.x, v0.y, v1.x, v1.y), nvalid);
                 st4(a.gacc + o, make_float4(g0.x, g0.y, g1.x, g1.y), nvalid);
             }
-            if (!ok) abort_s = 1;
+            // a thread one step ahead flags the other slot, so all threads
+            // leave at the same plane
+            if (!ok) abort_s[ph] = 1;
             __syncthreads();
-            if (abort_s) break;
+            if (abort_s[ph]) {
+                aborted = true;
+                break;
+            }
+            ph ^= 1;
             if (tid == 0) {
                 ring_refill(L, &tml, x0, y0, z, zb, zlast, kb, H);
                 ring_refill(U, &tmu, x0, y0, z, zb, zlast, kb, H);
@@ -659,7 +675,7 @@ __global__ void __launch_bounds__(NTX * TY) adj_tma_kernel(const AdjArgs a, cons
             WL.advance();
             WU.advance();
         }
-        if (abort_s) {
+        if (aborted) {
             if (tid == 0) {
                 atomicOr(a.err, 8);
                 ring_drain(L, z, zb, zlast, kb);

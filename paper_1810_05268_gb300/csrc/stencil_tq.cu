@@ -117,7 +117,7 @@ __global__ void __launch_bounds__(128, tq_min_blocks<K, PF>())
     using G = typename Q::G;
     constexpr int V = Q::V, TX = Q::TX, TY = Q::TY, D = Q::D, RU = Q::RU, RP = Q::RP;
     extern __shared__ unsigned char smq_raw[];
-    __shared__ int abort_s;
+    __shared__ int abort_s[2];                  // a wait gave up at a step of this parity
     unsigned char* sm0 = align128(smq_raw);
     float* ring = reinterpret_cast<float*>(sm0);
     float* upr = ring + RU * Q::US;
@@ -178,7 +178,7 @@ __global__ void __launch_bounds__(128, tq_min_blocks<K, PF>())
     auto wait_group = [&](int g) { return bar_wait(bar + g % RU, (unsigned)((g / RU) & 1), rounds); };
 
     if (tid == 0) {
-        abort_s = 0;
+        abort_s[0] = abort_s[1] = 0;
         for (int s = 0; s < RU; ++s) bar_init(bar + s);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         for (int g = 0; g < K + D; ++g) issue(g);
@@ -196,7 +196,8 @@ __global__ void __launch_bounds__(128, tq_min_blocks<K, PF>())
     }
     int g0 = 0;
     while (g0 < K && wait_group(g0)) ++g0;
-    if (g0 < K) abort_s = 1;
+    if (g0 < K) abort_s[0] = 1;
+    bool aborted = false;                        // the same in every thread: read after one barrier
     int confirmed = g0;                          // groups 0 .. confirmed - 1 are known complete
 #pragma unroll
     for (int i = 0; i < K; ++i) sld<V>(q[K + i], ring + i * Q::US + cs);
@@ -205,9 +206,14 @@ __global__ void __launch_bounds__(128, tq_min_blocks<K, PF>())
     for (; step < nstep; ++step) {
         const int z = z0 + step;
         // the group of u plane z + K and point plane z
-        if (!wait_group(step + K)) abort_s = 1;
+        // a wait that gave up flags this step's slot (step & 1): a thread one
+        // step ahead writes the other slot, so all leave at the same step
+        if (!wait_group(step + K)) abort_s[step & 1] = 1;
         __syncthreads();                        // every thread is past step - 1: its slots are free
-        if (abort_s) break;
+        if (abort_s[step & 1]) {
+            aborted = true;
+            break;
+        }
         confirmed = step + K + 1;
         if (tid == 0) issue(step + K + D);      // into the slots step - 1 read
         issued = step + K + D + 1;
@@ -265,7 +271,7 @@ __global__ void __launch_bounds__(128, tq_min_blocks<K, PF>())
         bool drained = true;
         for (int g = confirmed; g < issued; ++g)
             drained = bar_wait(bar + g % RU, (unsigned)((g / RU) & 1), DRAIN_ROUNDS) && drained;
-        if (abort_s || !drained) atomicOr(a.err, 8);
+        if (aborted || !drained) atomicOr(a.err, 8);
     }
 }
 
@@ -319,7 +325,7 @@ __global__ void __launch_bounds__(128, tq_min_blocks<K, PF>())
     using G = typename Q::G;
     constexpr int V = Q::V, TX = Q::TX, TY = Q::TY, D = Q::D, RU = Q::RU, RP = Q::RP;
     extern __shared__ unsigned char smq_raw[];
-    __shared__ int abort_s;
+    __shared__ int abort_s[2];                  // a wait gave up at a step of this parity
     unsigned char* sm0 = align128(smq_raw);
     float* ring = reinterpret_cast<float*>(sm0);
     float* lr = ring + RU * Q::US;
@@ -363,7 +369,7 @@ __global__ void __launch_bounds__(128, tq_min_blocks<K, PF>())
     auto wait_group = [&](int g) { return bar_wait(bar + g % RU, (unsigned)((g / RU) & 1), rounds); };
 
     if (tid == 0) {
-        abort_s = 0;
+        abort_s[0] = abort_s[1] = 0;
         for (int sl = 0; sl < RU; ++sl) bar_init(bar + sl);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         for (int g = 0; g < K + D; ++g) issue(g);
@@ -378,16 +384,20 @@ __global__ void __launch_bounds__(128, tq_min_blocks<K, PF>())
     }
     int g0 = 0;
     while (g0 < K && wait_group(g0)) ++g0;
-    if (g0 < K) abort_s = 1;
+    if (g0 < K) abort_s[0] = 1;
+    bool aborted = false;                        // the same in every thread: read after one barrier
     int confirmed = g0;
 #pragma unroll
     for (int i = 0; i < K; ++i) sld<V>(q[K + i], ring + i * Q::US + cs);
 
     for (int step = 0; step < nstep; ++step) {
         const int z = z0 + step;
-        if (!wait_group(step + K)) abort_s = 1;
+        if (!wait_group(step + K)) abort_s[step & 1] = 1;
         __syncthreads();
-        if (abort_s) break;
+        if (abort_s[step & 1]) {
+            aborted = true;
+            break;
+        }
         confirmed = step + K + 1;
         if (tid == 0) issue(step + K + D);
         issued = step + K + D + 1;
@@ -427,7 +437,7 @@ __global__ void __launch_bounds__(128, tq_min_blocks<K, PF>())
         bool drained = true;
         for (int g = confirmed; g < issued; ++g)
             drained = bar_wait(bar + g % RU, (unsigned)((g / RU) & 1), DRAIN_ROUNDS) && drained;
-        if (abort_s || !drained) atomicOr(a.err, 8);
+        if (aborted || !drained) atomicOr(a.err, 8);
     }
 }
 

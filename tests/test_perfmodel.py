@@ -68,6 +68,21 @@ def test_gradient_tolerance_excludes_modes():
     assert P.choose(c, 1000, 20, modes=("fp32", "bf16"))[0] == "bf16"
 
 
+def test_working_field_restores_take_the_16_bit_reverse_cost():
+    """Modes whose restores fill a working field (16-bit up-cast, codec
+    decode) take the reverse cost measured in the 16-bit run; FP32 modes
+    keep the FP32 run's; without a 16-bit measurement every mode uses C_R."""
+    base = dict(c_f=0.05, c_r=0.09, t_c=0.03, t_d=0.01, f_min=10.0, t_d16=0.01)
+    c0 = P.Costs(**base)
+    c1 = P.Costs(c_r16=0.1, **base)
+    nt = 300
+    for mode, slots in (("fp16", 9), ("bf16", 9), ("codec", 20)):
+        d = P.predict(c1, nt, slots, mode) - P.predict(c0, nt, slots, mode)
+        assert d == pytest.approx(nt * (0.1 - 0.09), rel=1e-12), mode
+    for slots in (5, nt):
+        assert P.predict(c1, nt, slots, "fp32") == P.predict(c0, nt, slots, "fp32")
+
+
 def _oracle_peak(nt, slots, size_of):
     # independent replay on the oracle's Revolve: the slots held at each takeshot
     acts, _ = R.schedule(nt, slots)

@@ -21,7 +21,7 @@ storage mode at the memory of 20 and of 5 checkpoints, store-all, host
 slots, the time model's predictions, the OT4 kernel's modes, a batch of 16
 2D shots, and the tolerance -> gradient-error table against the FP64
 oracle (the analogue of the paper's Table 2) -- goes to a side file whose
-path is printed on stderr (default bench_out/bench_detail.json).
+path is printed on stderr (`--detail` sets it).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
                   [--detail PATH] [--modes M,...] [--sweep c3|c4|c5]
@@ -980,7 +980,7 @@ def main():
     ap.add_argument("--impl", default="ckfwi")
     ap.add_argument("--nt", type=int, default=None, help="override the number of time steps (smaller runs)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle (baseline, errors, table)")
-    ap.add_argument("--detail", default=os.path.join(ROOT, "bench_out", "bench_detail.json"),
+    ap.add_argument("--detail", default=os.path.join(ROOT, "gpurun_out", "bench_detail.json"),
                     help="side file for everything but the headline")
     ap.add_argument("--modes",
                     default="storeall,codec,codec_sched,rate,fp32,fp16,bf16,codec_low,rate_low,"

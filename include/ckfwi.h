@@ -181,12 +181,15 @@ typedef struct ckfwi_stats {
     /* stencil kernel generation the autotuner chose for the forward and the
      * reverse step: 1 register-queue, 2 TMA-fed, 3 vector-blocked, 4 fed by
      * asynchronous copies, 5 / 6 the OT4 kernels (register-queue / vector-
-     * blocked); and the
-     * tile (x points, y rows, x points per thread, z planes per CTA or, for
-     * generation 2, CTAs per SM) */
+     * blocked), 7 lean asynchronous copies, 8 fed by tensor copies (its
+     * reverse step split in two launches); and the tile (x points, y rows,
+     * x points per thread, z planes per CTA or, for generation 2, CTAs per
+     * SM) */
     int fwd_ver, fwd_bx, fwd_by, fwd_vec, fwd_zlen;
     int adj_ver, adj_bx, adj_by, adj_vec, adj_zlen;
-    int fwd_pf, adj_pf;      /* generation 4: planes of prefetch (0: the default, 2) */
+    int fwd_pf, adj_pf;      /* generations 4 and 8: planes of prefetch (4: 0 = the
+                                default, 2; 8: 0 reads as 1); generation 7: planes
+                                a step (1 or 2) */
 } ckfwi_stats;
 
 typedef struct ckfwi_model ckfwi_model;

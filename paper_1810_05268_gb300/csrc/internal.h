@@ -138,9 +138,11 @@ struct Tile {
                           // by asynchronous copies (3D), 5: the two-pass OT4 kernels,
                           // 6: the same vector-blocked (3D), 7: the lean async-copy
                           // OT2 kernels (3D, one or two planes per step), 8: the
-                          // forward step fed by tensor copies (3D)
+                          // forward step fed by tensor copies and the reverse step split
+                          // in two launches (3D)
     int vec = 1;          // ver 3, 4: x points per thread (2 or 4)
-    int pf = 0;           // ver 4: planes of prefetch (0 = the default, 2); ver 7: planes per step (1, 2)
+    int pf = 0;           // ver 4: planes of prefetch (0 = the default, 2); ver 7: planes per step (1, 2);
+                          // ver 8: planes of prefetch (1, 2; 0 reads as 1)
 };
 
 // One batched step over several lanes (shots): lane l's arguments are
